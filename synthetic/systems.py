@@ -1,0 +1,252 @@
+"""Seeded synthetic systems standing in for the paper's cycloalkane test set.
+
+The paper (Sec. 4, Table 4, Fig. 2) runs cycloalkanes with aug-cc-pVDZ and
+a GEN-A2* auxiliary set on Psi4-optimised geometries.  None of those
+geometries or basis sets are available, so every workload here is a
+synthetic stand-in with the same shape:
+
+* geometry: a planar ring of n_C carbons (C-C 1.54 A) with two hydrogens
+  per carbon (C-H 1.09 A, H-C-H 109.5 deg, bisecting the exterior of the
+  ring), plus a seeded uniform jitter of every Cartesian coordinate; or,
+  for the smallest case, four atoms on a square;
+* basis: normalised s-type Gaussians centred on the atoms, with
+  even-tempered exponent tables per element;
+* auxiliary basis: s-type Gaussians, even-tempered, per element;
+* orbitals: a seeded Haar-random orthogonal matrix (columns = orbitals);
+* occupations: the PNOF7 electron-pairing angles gamma, drawn uniformly.
+
+Nothing in this module evaluates an integral or any other part of the
+method: it only produces numbers that both the oracle and the GPU engine
+take as inputs.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+ANGSTROM_TO_BOHR = 1.0 / 0.529177210903
+
+# Nuclear charges of the elements used by the rings.
+_Z = {"C": 6.0, "H": 1.0, "X": 2.0}
+
+
+def even_tempered(alpha0: float, ratio: float, n: int) -> np.ndarray:
+    """alpha_k = alpha0 * ratio**k for k = 0..n-1."""
+    return alpha0 * ratio ** np.arange(n, dtype=np.float64)
+
+
+@dataclass
+class System:
+    """Atoms plus s-type basis and auxiliary basis (all lengths in bohr)."""
+
+    name: str
+    atom_xyz: np.ndarray          # [n_atoms, 3]
+    atom_charge: np.ndarray       # [n_atoms]
+    bf_atom: np.ndarray           # [nbf] int32, centre of each basis function
+    bf_alpha: np.ndarray          # [nbf]
+    aux_atom: np.ndarray          # [naux] int32
+    aux_alpha: np.ndarray         # [naux]
+    n_strong: int                 # N_I (doubly-occupied-like orbitals)
+    n_weak_per: int               # N_g (weak orbitals per strong orbital)
+
+    @property
+    def nbf(self) -> int:
+        return int(self.bf_alpha.shape[0])
+
+    @property
+    def naux(self) -> int:
+        return int(self.aux_alpha.shape[0])
+
+    @property
+    def n_atoms(self) -> int:
+        return int(self.atom_xyz.shape[0])
+
+    @property
+    def n_omega(self) -> int:
+        """N_Omega = N_I (1 + N_g): orbitals of the pairing space."""
+        return self.n_strong * (1 + self.n_weak_per)
+
+    @property
+    def n_electrons(self) -> int:
+        return int(round(float(self.atom_charge.sum())))
+
+
+def _square_geometry(side_angstrom: float) -> tuple[np.ndarray, list[str]]:
+    s = side_angstrom * ANGSTROM_TO_BOHR
+    xyz = np.array([[0.0, 0.0, 0.0], [s, 0.0, 0.0], [s, s, 0.0], [0.0, s, 0.0]])
+    return xyz, ["X"] * 4
+
+
+def _ring_geometry(n_c: int, jitter_angstrom: float, rng: np.random.Generator,
+                   cc: float = 1.54, ch: float = 1.09,
+                   hch_deg: float = 109.5) -> tuple[np.ndarray, list[str]]:
+    """Planar CnH2n ring; returns coordinates in bohr and element labels."""
+    radius = cc / (2.0 * np.sin(np.pi / n_c))
+    half = np.deg2rad(hch_deg) / 2.0
+    xyz, elem = [], []
+    for k in range(n_c):
+        phi = 2.0 * np.pi * k / n_c
+        radial = np.array([np.cos(phi), np.sin(phi), 0.0])
+        c = radius * radial
+        xyz.append(c)
+        elem.append("C")
+        for sgn in (+1.0, -1.0):
+            d = np.cos(half) * radial + sgn * np.sin(half) * np.array([0.0, 0.0, 1.0])
+            xyz.append(c + ch * d)
+            elem.append("H")
+    xyz = np.asarray(xyz)
+    xyz = xyz + rng.uniform(-jitter_angstrom, jitter_angstrom, size=xyz.shape)
+    return xyz * ANGSTROM_TO_BOHR, elem
+
+
+@dataclass
+class BasisTable:
+    """Even-tempered s-type exponent tables per element: (alpha0, ratio, n)."""
+
+    basis: dict
+    aux: dict
+
+
+# Basis and auxiliary exponent tables.  The per-element counts reproduce the
+# workloads' (nbf, naux): C6H12 -> (144, 504), C10H20 -> (240, 840),
+# C16H32 -> (480, 1680), C20H40 -> (720, 2520).  With Coulomb-normalised
+# auxiliary functions, ratios of 2.0 (C) and 2.2 (H) from 0.3 keep the
+# metric's condition number near 1e7 for every ring (ratios near 1.75 push
+# it past 1e8); the smallest exponent keeps diffuse fitting functions on
+# neighbouring atoms from becoming nearly linearly dependent.
+_TABLES = {
+    "square": BasisTable(basis={"X": (0.1, 3.0, 6)}, aux={"X": (0.05, 2.0, 20)}),
+    "ring_small": BasisTable(basis={"C": (0.12, 2.5, 12), "H": (0.12, 3.0, 6)},
+                             aux={"C": (0.3, 2.0, 42), "H": (0.3, 2.2, 21)}),
+    "ring_c16": BasisTable(basis={"C": (0.12, 2.2, 14), "H": (0.12, 2.2, 8)},
+                           aux={"C": (0.3, 2.0, 49), "H": (0.3, 2.2, 28)}),
+    "ring_c20": BasisTable(basis={"C": (0.12, 2.0, 16), "H": (0.12, 1.9, 10)},
+                           aux={"C": (0.3, 2.0, 56), "H": (0.3, 2.2, 35)}),
+}
+
+
+def _assemble(name: str, xyz: np.ndarray, elem: list[str], table: BasisTable,
+              n_strong: int, n_weak_per: int) -> System:
+    bf_atom, bf_alpha, aux_atom, aux_alpha = [], [], [], []
+    for a, e in enumerate(elem):
+        a0, r, n = table.basis[e]
+        al = even_tempered(a0, r, n)
+        bf_alpha.extend(al)
+        bf_atom.extend([a] * n)
+        a0, r, n = table.aux[e]
+        al = even_tempered(a0, r, n)
+        aux_alpha.extend(al)
+        aux_atom.extend([a] * n)
+    return System(
+        name=name,
+        atom_xyz=np.ascontiguousarray(xyz, dtype=np.float64),
+        atom_charge=np.array([_Z[e] for e in elem], dtype=np.float64),
+        bf_atom=np.asarray(bf_atom, dtype=np.int32),
+        bf_alpha=np.asarray(bf_alpha, dtype=np.float64),
+        aux_atom=np.asarray(aux_atom, dtype=np.int32),
+        aux_alpha=np.asarray(aux_alpha, dtype=np.float64),
+        n_strong=n_strong,
+        n_weak_per=n_weak_per,
+    )
+
+
+def make_system(kind: str, n_c: int = 0, seed: int = 0, jitter: float = 0.02,
+                n_weak_per: int = 4) -> System:
+    """Build a synthetic system.
+
+    kind = "square": four atoms (charge 2) on a 1.5 A square, 6 basis and 20
+    auxiliary functions per atom, N_I = 4, N_g = 2.
+    kind = "ring": CnH2n ring with n_c carbons, seeded jitter (A), N_I equal to
+    half the electron count, N_g weak orbitals per strong one.
+    """
+    if kind == "square":
+        xyz, elem = _square_geometry(1.5)
+        return _assemble("square4", xyz, elem, _TABLES["square"], 4, 2)
+    if kind != "ring":
+        raise ValueError(f"unknown system kind {kind!r}")
+    rng = np.random.default_rng(seed)
+    xyz, elem = _ring_geometry(n_c, jitter, rng)
+    if n_c <= 12:
+        table = _TABLES["ring_small"]
+    elif n_c <= 16:
+        table = _TABLES["ring_c16"]
+    else:
+        table = _TABLES["ring_c20"]
+    n_elec = 6 * n_c + 2 * n_c
+    return _assemble(f"c{n_c}h{2 * n_c}", xyz, elem, table, n_elec // 2, n_weak_per)
+
+
+def pairing_columns(n_strong: int, n_weak_per: int) -> tuple[np.ndarray, np.ndarray]:
+    """Electron-pairing map of the N_Omega orbital columns.
+
+    Column g (g < N_I) is the strong orbital of subspace g.  The i-th weak
+    orbital (i = 0..N_g-1) of subspace g sits at column
+    N_I + i*N_I + (N_I-1-g), so the highest strong orbital pairs with the
+    lowest weak ones.  Returns (subspace[N_Omega], weak_rank[N_Omega]) with
+    weak_rank = -1 for strong orbitals and i for the i-th weak orbital.
+    """
+    n_om = n_strong * (1 + n_weak_per)
+    sub = np.empty(n_om, dtype=np.int32)
+    rank = np.empty(n_om, dtype=np.int32)
+    for g in range(n_strong):
+        sub[g] = g
+        rank[g] = -1
+        for i in range(n_weak_per):
+            col = n_strong + i * n_strong + (n_strong - 1 - g)
+            sub[col] = g
+            rank[col] = i
+    return sub, rank
+
+
+def random_orthogonal(n: int, rng: np.random.Generator) -> np.ndarray:
+    """Haar-random orthogonal n x n matrix (QR of a Gaussian matrix, diag(R)>0)."""
+    a = rng.standard_normal((n, n))
+    q, r = np.linalg.qr(a)
+    q = q * np.sign(np.diag(r))[None, :]
+    return np.ascontiguousarray(q)
+
+
+def draw_gamma(n_strong: int, n_weak_per: int, rng: np.random.Generator,
+               lo: float = 0.05, hi: float = 0.3) -> np.ndarray:
+    """Occupation angles: N_I strong angles followed by N_I*(N_g-1) weak ones."""
+    return rng.uniform(lo, hi, size=n_strong * n_weak_per)
+
+
+@dataclass
+class Workload:
+    """A system plus the orbital matrix and occupation angles evaluated on it."""
+
+    name: str
+    system: System
+    C: np.ndarray            # [nbf, nbf], column p is orbital p
+    gamma: np.ndarray        # [N_I * N_g]
+    meta: dict = field(default_factory=dict)
+
+
+# Named workloads (sizes as stated beside each).
+WORKLOADS = {
+    # 4 atoms, nbf=24, naux=80, N_Omega=12
+    "square4": dict(kind="square", seed=1),
+    # C6H12 ring, nbf=144, naux=504, N_Omega=120
+    "c6h12": dict(kind="ring", n_c=6, seed=2),
+    # C10H20 ring, nbf=240, naux=840, N_Omega=200
+    "c10h20": dict(kind="ring", n_c=10, seed=3),
+    # C16H32 ring, nbf=480, naux=1680, N_Omega=320
+    "c16h32": dict(kind="ring", n_c=16, seed=4),
+    # C20H40 ring, nbf=720, naux=2520, N_Omega=400
+    "c20h40": dict(kind="ring", n_c=20, seed=5),
+}
+
+
+def make_workload(name: str, seed: int | None = None) -> Workload:
+    """Build a named workload; `seed` overrides the stored seed."""
+    spec = dict(WORKLOADS[name])
+    kind = spec.pop("kind")
+    s = spec.pop("seed") if seed is None else seed
+    spec.pop("seed", None)
+    system = make_system(kind, seed=s, **spec)
+    rng = np.random.default_rng(10_000 + s)
+    C = random_orthogonal(system.nbf, rng)
+    gamma = draw_gamma(system.n_strong, system.n_weak_per, rng)
+    return Workload(name=name, system=system, C=C, gamma=gamma, meta={"seed": s})

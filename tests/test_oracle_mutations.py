@@ -1,0 +1,102 @@
+"""Plausible mistakes planted in the oracle (on the CPU) are caught by its pins.
+
+Each case swaps one oracle function for a subtly wrong variant (a dropped
+term, a wrong sign, a transposed operand) and checks that the corresponding
+pin from the other test files fails.
+"""
+import numpy as np
+import pytest
+
+from oracle import brute, integrals as I, pnof7, rhf, ri
+from synthetic.systems import make_workload, pairing_columns
+
+
+@pytest.fixture(scope="module")
+def sq():
+    w = make_workload("square4")
+    B, L, G = ri.setup(w.system)
+    return w, B
+
+
+def test_transposed_half_transform_fails_brute_force(sq):
+    w, B = sq
+    m = w.system.n_omega
+    C = w.C
+    good = ri.all_rows(B, C, m)["K"]
+    # C used untransposed: rows of C taken as orbitals
+    bad_bh = np.einsum("pm,Pmn->Ppn", C[:m, :], B)
+    bad = ri.jk_mo(ri.full_transform(bad_bh, C.T), ri.diagonal(bad_bh, C.T))[1]
+    eri = brute.fitted_eri4(B)
+    ref = brute.conventional_jk(eri, C, m)[1]
+    assert np.allclose(good, ref, atol=1e-12)
+    assert not np.allclose(bad, ref, atol=1e-6)
+
+
+def test_exchange_with_wrong_orbital_fails_tie_to_mo_exchange(sq):
+    w, B = sq
+    m = w.system.n_omega
+    r = ri.all_rows(B, w.C, m)
+    bh = r["bh"]
+    # K^(q) built from the next orbital's slice (an off-by-one in q)
+    bad_k = np.einsum("Pqm,Pqn->qmn", np.roll(bh, 1, axis=1), np.roll(bh, 1, axis=1))
+    C = w.C[:, :m]
+    good = np.einsum("mp,qmn,np->pq", C, r["Kao"], C)
+    bad = np.einsum("mp,qmn,np->pq", C, bad_k, C)
+    assert np.allclose(good, r["K"], atol=1e-12)
+    assert not np.allclose(bad, r["K"], atol=1e-6)
+
+
+def test_wrong_cross_coefficient_fails_closed_shell_pin(sq, monkeypatch):
+    w, B = sq
+    s = w.system
+    H = I.core_hamiltonian(s)
+    e_nuc = I.nuclear_repulsion(s)
+    sub, rank = pairing_columns(s.n_strong, s.n_weak_per)
+    gam = w.gamma.copy()
+    gam[: s.n_strong] = 0.0
+    m = s.n_omega
+    n = pnof7.occupations(gam, s.n_strong, s.n_weak_per, sub, rank)
+    r = ri.all_rows(B, w.C, m)
+    Hd = np.einsum("mp,mn,np->p", w.C[:, :m], H, w.C[:, :m])
+    A, Bc = pnof7.coupling(n, sub, rank)
+    e_rhf = rhf.closed_shell_energy(B, H, w.C[:, : s.n_strong], e_nuc)
+    assert abs(pnof7.energy(n, Hd, r["J"], r["K"], A, Bc, e_nuc) - e_rhf) < 1e-10
+    A_bad = np.where(np.equal.outer(sub, sub), A, 0.5 * A)   # drop the factor 2 of 2 J_pq across pairs
+    assert abs(pnof7.energy(n, Hd, r["J"], r["K"], A_bad, Bc, e_nuc) - e_rhf) > 1e-3
+
+
+def test_wrong_weak_weak_sign_fails_two_electron_pin():
+    w = make_workload("square4")
+    B, L, G = ri.setup(w.system)
+    H = I.core_hamiltonian(w.system)
+    ng = 5
+    sub, rank = pairing_columns(1, ng)
+    n = pnof7.occupations(np.array([0.4, 0.3, 0.9, 0.2, 1.2]), 1, ng, sub, rank)
+    m = 1 + ng
+    C = w.C[:, :m]
+    r = ri.all_rows(B, w.C, m)
+    Hd = np.einsum("mp,mn,np->p", C, H, C)
+    D, Pi = pnof7.delta_pi(n, sub, rank)
+    weak = rank >= 0
+    Pi_bad = Pi.copy()
+    Pi_bad[np.ix_(weak, weak)] *= np.where(np.eye(weak.sum()) > 0, 1.0, -1.0)
+    mo = brute.mo_eri4(brute.fitted_eri4(B), C)
+    c = np.where(rank < 0, 1.0, -1.0) * np.sqrt(n)
+    e_wf = 2.0 * np.sum(c * c * Hd) + np.einsum("p,q,pqpq->", c, c, mo)
+    good = pnof7.energy_eq_pnof(n, Hd, r["J"], r["K"], D, Pi, 0.0)
+    bad = pnof7.energy_eq_pnof(n, Hd, r["J"], r["K"], D, Pi_bad, 0.0)
+    assert abs(good - e_wf) < 1e-12
+    assert abs(bad - e_wf) > 1e-6
+
+
+def test_dropped_kinetic_term_fails_textbook_pin():
+    # T without the -2 mu R^2 term disagrees with the S&O value T12 = 0.2365.
+    from tests.test_oracle_integrals import _toy_system
+    al = np.array([0.109818, 0.405771, 2.22766]) * 1.24 ** 2
+    d = np.array([0.444635, 0.535328, 0.154329])
+    s = _toy_system([[0, 0, 0], [0, 0, 1.4]], [1, 1], [0, 0, 0, 1, 1, 1], np.concatenate([al, al]))
+    p, mu, r2, kab, P, nn = I._pair_data(s)
+    bad = nn * mu * 3.0 * (np.pi / p) ** 1.5 * kab
+    D = np.zeros((6, 2)); D[:3, 0] = d; D[3:, 1] = d
+    assert abs((D.T @ I.kinetic(s) @ D)[0, 1] - 0.2365) < 1e-4
+    assert abs((D.T @ bad @ D)[0, 1] - 0.2365) > 1e-2

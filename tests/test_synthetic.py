@@ -1,0 +1,47 @@
+"""The seeded synthetic workloads have the stated shapes and are reproducible."""
+import numpy as np
+import pytest
+
+from synthetic import make_workload, pairing_columns
+
+SHAPES = {
+    "square4": (24, 80, 4, 2, 12),
+    "c6h12": (144, 504, 24, 4, 120),
+    "c10h20": (240, 840, 40, 4, 200),
+    "c16h32": (480, 1680, 64, 4, 320),
+    "c20h40": (720, 2520, 80, 4, 400),
+}
+
+
+@pytest.mark.parametrize("name", list(SHAPES))
+def test_shapes(name):
+    w = make_workload(name)
+    s = w.system
+    nbf, naux, ni, ng, nom = SHAPES[name]
+    assert (s.nbf, s.naux, s.n_strong, s.n_weak_per, s.n_omega) == (nbf, naux, ni, ng, nom)
+    assert s.n_electrons == 2 * s.n_strong
+    assert w.C.shape == (nbf, nbf)
+    np.testing.assert_allclose(w.C.T @ w.C, np.eye(nbf), atol=1e-12)
+    assert w.gamma.shape == (ni * ng,)
+    assert ((w.gamma >= 0.05) & (w.gamma <= 0.3)).all()
+
+
+def test_reproducible_and_seeded():
+    a = make_workload("c6h12")
+    b = make_workload("c6h12")
+    np.testing.assert_array_equal(a.system.atom_xyz, b.system.atom_xyz)
+    np.testing.assert_array_equal(a.C, b.C)
+    c = make_workload("c6h12", seed=99)
+    assert not np.array_equal(a.system.atom_xyz, c.system.atom_xyz)
+
+
+def test_ring_geometry():
+    from synthetic.systems import ANGSTROM_TO_BOHR
+    w = make_workload("c6h12")
+    xyz = w.system.atom_xyz / ANGSTROM_TO_BOHR
+    z = w.system.atom_charge
+    carbons = xyz[z == 6.0]
+    d = np.linalg.norm(carbons - np.roll(carbons, -1, axis=0), axis=1)
+    assert np.all(np.abs(d - 1.54) < 0.08)
+    sub, rank = pairing_columns(24, 4)
+    assert sub.max() == 23

@@ -1,0 +1,189 @@
+/*
+ * donof_ri.h -- C ABI of the GB300 resolution-of-the-identity Coulomb/exchange
+ * engine for PNOF7 (arXiv 2012.15662, "Resolution of the identity
+ * approximation applied to PNOF correlation calculations").
+ *
+ * The engine evaluates, on one GPU, the RI algebra of Sec. 2:
+ *   Eq. (AOERI)       (mu nu|s l) = sum_kl (mu nu|k) G^-1_kl (l|s l), G_kl = (k|l)
+ *   fitted tensor     B^P_{mu nu} = sum_Q (L^-1)_PQ (Q|mu nu), G = L L^T
+ *   half transform    b^P_{p nu} = sum_mu C_{mu p} B^P_{mu nu}      (Tables 2/3, step 2)
+ *   diagonal          b^P_{pp}   = sum_nu C_{nu p} b^P_{p nu}       (Table 3, step 3)
+ *   full transform    b^P_{pq}   = sum_nu C_{nu q} b^P_{p nu}       (Table 2, step 3)
+ *   MO J / K          J_pq = sum_P b^P_pp b^P_qq, K_pq = sum_P (b^P_pq)^2 (Table 2, step 4)
+ *   per-orbital AO    J^(q) = sum_P b^P_qq B^P,
+ *                     K^(q)_{mu nu} = sum_P b^P_{q mu} b^P_{q nu}   (Table 3, steps 3-4)
+ *   PNOF7 energy      Eq. (PNOF) with the PNOF7 Delta / Pi, and the
+ *                     orthonormality Lagrangian lambda of Sec. 2
+ *                     ("Orbital Optimization with RI").
+ *
+ * Basis: s-type Gaussians (orbital basis L2-normalised, auxiliary basis
+ * Coulomb-normalised so that (k|k) = 1); all integrals are evaluated on the
+ * device at init.
+ *
+ * Conventions (every entry point):
+ *  - Returns DONOF_RI_OK (0) or a negative status; no exception crosses the ABI.
+ *  - Matrices of orbital coefficients and lambda are column-major
+ *    [nbf x nbf] FP64: element (mu, p) at index p*nbf + mu (column p is
+ *    orbital p), matching the paper's C_{mu p}.
+ *  - J, K are row-major [N_Omega x N_Omega] FP64 (symmetric).
+ *  - Pointers documented "host or device" may be either; the engine asks the
+ *    CUDA runtime which one it is.  Outputs to host memory are complete when
+ *    the call returns (the call synchronises the context's stream); outputs
+ *    to device memory are written asynchronously on the context's stream.
+ *  - Inputs are copied; the caller keeps ownership of every pointer it passes.
+ *  - A context is bound to the stream given at init, is not thread-safe, and
+ *    owns all of its device buffers until donof_ri_destroy.
+ *  - Device-side faults detected asynchronously (a non-finite orbital
+ *    coefficient, a non-positive metric pivot) are reported by the next call
+ *    that synchronises (any call with a host output, or donof_ri_sync).
+ */
+#ifndef DONOF_RI_H
+#define DONOF_RI_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define DONOF_RI_OK 0
+#define DONOF_RI_E_ARG (-1)            /* bad size, null pointer, bad mode          */
+#define DONOF_RI_E_OOM (-2)            /* device allocation failed                  */
+#define DONOF_RI_E_CUDA (-3)           /* CUDA runtime / launch error               */
+#define DONOF_RI_E_METRIC_NOT_PD (-4)  /* Cholesky pivot of G below 1e-14 max(G_kk)  */
+#define DONOF_RI_E_NONFINITE (-5)      /* NaN / Inf in an input                     */
+#define DONOF_RI_E_TIMEOUT (-6)        /* a bounded device-side wait gave up        */
+#define DONOF_RI_E_STATE (-7)          /* call order (e.g. jk_mo before a FULL transform) */
+#define DONOF_RI_E_UNSUPPORTED (-8)    /* device is not sm_103 / precision not built */
+
+/* Arithmetic of the hot path. */
+#define DONOF_RI_FP64 0    /* every product and sum in FP64 (CUDA cores)              */
+#define DONOF_RI_TF32X3 1  /* split-precision tensor-core products (3 TF32 MMAs per
+                              product, FP32 accumulation); FP64 metric, fitting and
+                              energy/lambda sums                                     */
+
+/* Transform modes. */
+#define DONOF_RI_HALF 0  /* half transform + diagonal (orbital step, Table 3)          */
+#define DONOF_RI_FULL 1  /* half transform + diagonal + full transform (Table 2)       */
+
+typedef struct donof_ri_ctx donof_ri_ctx;
+
+/*
+ * Problem statement (Sec. 2): the molecule, its s-type orbital and auxiliary
+ * bases and the electron-pairing scheme.  All arrays are host memory owned by
+ * the caller; init copies them.
+ *   nbf, naux          N_b and N_aux (>= 1)
+ *   n_atoms            number of nuclei; atom_xyz [n_atoms*3] (bohr), atom_charge [n_atoms]
+ *   bf_atom, bf_alpha  [nbf]  centre index and exponent of each orbital basis function
+ *   aux_atom, aux_alpha [naux] centre index and exponent of each auxiliary function
+ *   n_strong           N_I: strong orbitals, one per pairing subspace
+ *   n_weak_per         N_g: weak orbitals per subspace (>= 1)
+ *   subspace           [N_Omega] subspace g (0..N_I-1) of each pairing-space column,
+ *                      N_Omega = N_I (1 + N_g) <= nbf; columns N_Omega..nbf-1 are empty
+ *   weak_rank          [N_Omega] -1 for the strong orbital of its subspace, i for its
+ *                      i-th weak orbital (each subspace: one strong, ranks 0..N_g-1)
+ */
+typedef struct donof_ri_system {
+  int nbf;
+  int naux;
+  int n_atoms;
+  int n_strong;
+  int n_weak_per;
+  const double* atom_xyz;
+  const double* atom_charge;
+  const int* bf_atom;
+  const double* bf_alpha;
+  const int* aux_atom;
+  const double* aux_alpha;
+  const int* subspace;
+  const int* weak_rank;
+} donof_ri_system;
+
+/*
+ * Build a context: evaluates S, T, V, E_nuc, the metric G_kl = (k|l) and the
+ * three-centre integrals (k|mu nu) on the device, factorises G = L L^T in FP64
+ * (plain Cholesky in place of the paper's modified LDL^T, Sec. 2), solves for
+ * the fitted tensor B (Table 2/3 step 1) and lays B out for the chosen
+ * precision.  Synchronous.
+ *   precision  DONOF_RI_FP64 or DONOF_RI_TF32X3
+ *   stream     cudaStream_t to run on (NULL = legacy default stream)
+ *   out        receives the context
+ * Errors: E_ARG (sizes, pairing map), E_OOM, E_CUDA, E_METRIC_NOT_PD,
+ *         E_UNSUPPORTED (no sm_103 device).
+ */
+int donof_ri_init(const donof_ri_system* sys, int precision, void* stream, donof_ri_ctx** out);
+
+/*
+ * Transform the fitted tensor to the orbitals C (host or device, [nbf*nbf]
+ * column-major FP64).  HALF: b^P_{p nu} and b^P_pp for p < N_Omega (Tables
+ * 2/3 step 2, Table 3 step 3).  FULL: additionally b^P_pq and the MO J, K
+ * (Table 2 steps 3-4), kept for donof_ri_jk_mo.  Asynchronous.
+ * Errors: E_ARG, E_CUDA; E_NONFINITE is reported at the next synchronising call.
+ */
+int donof_ri_transform(donof_ri_ctx* ctx, const double* C, int mode);
+
+/*
+ * MO Coulomb and exchange matrices of the last FULL transform (Table 2 step 4):
+ * J, K [N_Omega*N_Omega] row-major FP64, host or device, either may be NULL.
+ * Errors: E_STATE if no FULL transform preceded it.
+ */
+int donof_ri_jk_mo(donof_ri_ctx* ctx, double* J, double* K);
+
+/*
+ * Per-orbital AO Coulomb and exchange matrices of the last transform (Table 3
+ * steps 3-4), J^(q) and K^(q) for every pairing-space orbital q, kept in the
+ * context for donof_ri_energy_lagrangian.  Jao / Kao, if not NULL, receive a
+ * copy as [N_Omega][nbf][nbf] FP64 (host or device).
+ * Errors: E_STATE if no transform preceded it.
+ */
+int donof_ri_jk_ao_batch(donof_ri_ctx* ctx, double* Jao, double* Kao);
+
+/*
+ * PNOF7 energy and Lagrangian (Eq. (PNOF); Sec. 2, orbital optimisation) from
+ * the occupation angles gamma (host or device, [N_I*N_g] FP64: N_I strong
+ * angles, then N_g-1 weak angles per subspace) and the J^(q), K^(q) of the last
+ * donof_ri_jk_ao_batch:
+ *   n_g = (1+cos^2 gamma_g)/2, n_{g,i} = (1-n_g) alpha_i (alpha from the weak angles),
+ *   F^(p) = n_p H + sum_q (A_pq J^(q) - B_pq K^(q)),
+ *   lambda_qp = C_q^T F^(p) C_p (q < nbf, p < N_Omega; 0 for p >= N_Omega),
+ *   E = E_nuc + sum_p (n_p H_pp + lambda_pp).
+ * E (host or device, one FP64) and lambda ([nbf*nbf] column-major, host or
+ * device) may each be NULL.
+ * Errors: E_STATE if donof_ri_jk_ao_batch has not run since the last transform.
+ */
+int donof_ri_energy_lagrangian(donof_ri_ctx* ctx, const double* gamma, double* E, double* lambda);
+
+/* Internal arrays readable through donof_ri_fetch (converted to FP64). */
+#define DONOF_RI_FETCH_B 0        /* [naux][nbf][nbf]   fitted tensor B^P_{mu nu}      */
+#define DONOF_RI_FETCH_BHALF 1    /* [naux][N_Omega][nbf] b^P_{p nu}                   */
+#define DONOF_RI_FETCH_DIAG 2     /* [naux][N_Omega]    b^P_pp                         */
+#define DONOF_RI_FETCH_HCORE 3    /* [nbf][nbf]         H = T + V                      */
+#define DONOF_RI_FETCH_OVERLAP 4  /* [nbf][nbf]         S                              */
+#define DONOF_RI_FETCH_METRIC 5   /* [naux][naux]       G (lower triangle holds L after init) */
+#define DONOF_RI_FETCH_ENUC 6     /* [1]                E_nuc                          */
+#define DONOF_RI_FETCH_OCC 7      /* [N_Omega]          occupations of the last energy call */
+
+/*
+ * Copy an internal array to host memory dst (count FP64 elements, which must
+ * equal the array's size).  Synchronous.  Errors: E_ARG, E_STATE.
+ */
+int donof_ri_fetch(donof_ri_ctx* ctx, int what, double* dst, size_t count);
+
+/* Wait for the context's stream and report any deferred device-side error. */
+int donof_ri_sync(donof_ri_ctx* ctx);
+
+/* Free every device buffer of the context.  Accepts NULL. */
+int donof_ri_destroy(donof_ri_ctx* ctx);
+
+/* Static, human-readable text for a status code. */
+const char* donof_ri_strerror(int status);
+
+/* Number of kernels the context has launched since init (for launch accounting). */
+long long donof_ri_launch_count(const donof_ri_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DONOF_RI_H */

@@ -1,0 +1,247 @@
+"""ctypes binding of the engine's C ABI (`include/donof_ri.h`).
+
+Argument marshalling only: every computation runs in `libdonof_ri.so`.  The
+functions carry the ABI's names; arrays may be numpy FP64 arrays (host
+memory) or torch FP64 CUDA tensors (device memory), both C-contiguous.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdonof_ri.so")
+
+DONOF_RI_OK = 0
+DONOF_RI_E_ARG = -1
+DONOF_RI_E_OOM = -2
+DONOF_RI_E_CUDA = -3
+DONOF_RI_E_METRIC_NOT_PD = -4
+DONOF_RI_E_NONFINITE = -5
+DONOF_RI_E_TIMEOUT = -6
+DONOF_RI_E_STATE = -7
+DONOF_RI_E_UNSUPPORTED = -8
+
+DONOF_RI_FP64 = 0
+DONOF_RI_TF32X3 = 1
+DONOF_RI_HALF = 0
+DONOF_RI_FULL = 1
+
+DONOF_RI_FETCH_B = 0
+DONOF_RI_FETCH_BHALF = 1
+DONOF_RI_FETCH_DIAG = 2
+DONOF_RI_FETCH_HCORE = 3
+DONOF_RI_FETCH_OVERLAP = 4
+DONOF_RI_FETCH_METRIC = 5
+DONOF_RI_FETCH_ENUC = 6
+DONOF_RI_FETCH_OCC = 7
+
+# Names of every entry point declared in include/donof_ri.h.
+EXPORTS = [
+    "donof_ri_init", "donof_ri_transform", "donof_ri_jk_mo", "donof_ri_jk_ao_batch",
+    "donof_ri_energy_lagrangian", "donof_ri_fetch", "donof_ri_sync", "donof_ri_destroy",
+    "donof_ri_strerror", "donof_ri_launch_count",
+]
+
+
+class DonofError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {strerror(status)} (status {status})")
+
+
+class System(ctypes.Structure):
+    _fields_ = [
+        ("nbf", ctypes.c_int), ("naux", ctypes.c_int), ("n_atoms", ctypes.c_int),
+        ("n_strong", ctypes.c_int), ("n_weak_per", ctypes.c_int),
+        ("atom_xyz", ctypes.c_void_p), ("atom_charge", ctypes.c_void_p),
+        ("bf_atom", ctypes.c_void_p), ("bf_alpha", ctypes.c_void_p),
+        ("aux_atom", ctypes.c_void_p), ("aux_alpha", ctypes.c_void_p),
+        ("subspace", ctypes.c_void_p), ("weak_rank", ctypes.c_void_p),
+    ]
+
+
+_lib = None
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load libdonof_ri.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build the CUDA engine first "
+                           "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = ctypes.CDLL(path)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    lib.donof_ri_init.argtypes = [ctypes.POINTER(System), i, vp, ctypes.POINTER(vp)]
+    lib.donof_ri_transform.argtypes = [vp, vp, i]
+    lib.donof_ri_jk_mo.argtypes = [vp, vp, vp]
+    lib.donof_ri_jk_ao_batch.argtypes = [vp, vp, vp]
+    lib.donof_ri_energy_lagrangian.argtypes = [vp, vp, vp, vp]
+    lib.donof_ri_fetch.argtypes = [vp, i, vp, ctypes.c_size_t]
+    lib.donof_ri_sync.argtypes = [vp]
+    lib.donof_ri_destroy.argtypes = [vp]
+    lib.donof_ri_strerror.argtypes = [i]
+    lib.donof_ri_strerror.restype = ctypes.c_char_p
+    lib.donof_ri_launch_count.argtypes = [vp]
+    lib.donof_ri_launch_count.restype = ctypes.c_longlong
+    for name in ("donof_ri_init", "donof_ri_transform", "donof_ri_jk_mo", "donof_ri_jk_ao_batch",
+                 "donof_ri_energy_lagrangian", "donof_ri_fetch", "donof_ri_sync", "donof_ri_destroy"):
+        getattr(lib, name).restype = i
+    _lib = lib
+    return lib
+
+
+def strerror(status: int) -> str:
+    return load().donof_ri_strerror(int(status)).decode()
+
+
+def _ptr(x, dtype=np.float64):
+    """Raw pointer of a numpy array, a torch tensor or None."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if x.dtype != dtype or not x.flags["C_CONTIGUOUS"]:
+            raise TypeError(f"expected a C-contiguous {np.dtype(dtype)} array")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        import torch
+        want = torch.float64 if dtype == np.float64 else torch.int32
+        if x.dtype != want or not x.is_contiguous():
+            raise TypeError(f"expected a contiguous {want} tensor")
+        return x.data_ptr()
+    raise TypeError(f"unsupported array type {type(x)!r}")
+
+
+def _check(rc: int, where: str):
+    if rc != DONOF_RI_OK:
+        raise DonofError(rc, where)
+
+
+def donof_ri_init(system, subspace, weak_rank, precision: int = DONOF_RI_FP64, stream=None):
+    """Build a context for a system (attributes as in synthetic.System). Returns the handle."""
+    lib = load()
+    keep = dict(
+        xyz=np.ascontiguousarray(system.atom_xyz, dtype=np.float64),
+        z=np.ascontiguousarray(system.atom_charge, dtype=np.float64),
+        bfa=np.ascontiguousarray(system.bf_atom, dtype=np.int32),
+        bfx=np.ascontiguousarray(system.bf_alpha, dtype=np.float64),
+        axa=np.ascontiguousarray(system.aux_atom, dtype=np.int32),
+        axx=np.ascontiguousarray(system.aux_alpha, dtype=np.float64),
+        sub=np.ascontiguousarray(subspace, dtype=np.int32),
+        rank=np.ascontiguousarray(weak_rank, dtype=np.int32),
+    )
+    s = System(int(system.bf_alpha.shape[0]), int(system.aux_alpha.shape[0]), int(system.atom_xyz.shape[0]),
+               int(system.n_strong), int(system.n_weak_per),
+               keep["xyz"].ctypes.data, keep["z"].ctypes.data, keep["bfa"].ctypes.data, keep["bfx"].ctypes.data,
+               keep["axa"].ctypes.data, keep["axx"].ctypes.data, keep["sub"].ctypes.data, keep["rank"].ctypes.data)
+    ctx = ctypes.c_void_p()
+    st = None if stream is None else ctypes.c_void_p(int(stream))
+    _check(lib.donof_ri_init(ctypes.byref(s), int(precision), st, ctypes.byref(ctx)), "donof_ri_init")
+    return ctx
+
+
+def donof_ri_transform(ctx, C, mode: int):
+    _check(load().donof_ri_transform(ctx, _ptr(C), int(mode)), "donof_ri_transform")
+
+
+def donof_ri_jk_mo(ctx, J=None, K=None):
+    _check(load().donof_ri_jk_mo(ctx, _ptr(J), _ptr(K)), "donof_ri_jk_mo")
+
+
+def donof_ri_jk_ao_batch(ctx, Jao=None, Kao=None):
+    _check(load().donof_ri_jk_ao_batch(ctx, _ptr(Jao), _ptr(Kao)), "donof_ri_jk_ao_batch")
+
+
+def donof_ri_energy_lagrangian(ctx, gamma, E=None, lam=None):
+    _check(load().donof_ri_energy_lagrangian(ctx, _ptr(gamma), _ptr(E), _ptr(lam)),
+           "donof_ri_energy_lagrangian")
+
+
+def donof_ri_fetch(ctx, what: int, dst: np.ndarray):
+    _check(load().donof_ri_fetch(ctx, int(what), _ptr(dst), dst.size), "donof_ri_fetch")
+
+
+def donof_ri_sync(ctx):
+    _check(load().donof_ri_sync(ctx), "donof_ri_sync")
+
+
+def donof_ri_destroy(ctx):
+    _check(load().donof_ri_destroy(ctx), "donof_ri_destroy")
+
+
+def donof_ri_launch_count(ctx) -> int:
+    return int(load().donof_ri_launch_count(ctx))
+
+
+class Engine:
+    """Convenience wrapper owning one context (host numpy in, host numpy out)."""
+
+    def __init__(self, system, precision: int = DONOF_RI_FP64, stream=None):
+        from synthetic import pairing_columns
+        self.system = system
+        self.nbf = int(system.bf_alpha.shape[0])
+        self.naux = int(system.aux_alpha.shape[0])
+        self.n_omega = int(system.n_strong * (1 + system.n_weak_per))
+        self.subspace, self.weak_rank = pairing_columns(system.n_strong, system.n_weak_per)
+        self.ctx = donof_ri_init(system, self.subspace, self.weak_rank, precision, stream)
+
+    def close(self):
+        if self.ctx is not None:
+            donof_ri_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def colmajor(C: np.ndarray) -> np.ndarray:
+        """numpy [mu, p] orbital matrix -> the ABI's column-major buffer."""
+        return np.ascontiguousarray(np.asarray(C, dtype=np.float64).T)
+
+    def transform(self, C: np.ndarray, mode: int = DONOF_RI_FULL):
+        donof_ri_transform(self.ctx, self.colmajor(C), mode)
+
+    def jk_mo(self):
+        m = self.n_omega
+        J = np.empty((m, m))
+        K = np.empty((m, m))
+        donof_ri_jk_mo(self.ctx, J, K)
+        return J, K
+
+    def jk_ao(self, want=True):
+        if not want:
+            donof_ri_jk_ao_batch(self.ctx)
+            return None
+        m, nb = self.n_omega, self.nbf
+        Jao = np.empty((m, nb, nb))
+        Kao = np.empty((m, nb, nb))
+        donof_ri_jk_ao_batch(self.ctx, Jao, Kao)
+        return Jao, Kao
+
+    def energy_lagrangian(self, gamma: np.ndarray):
+        E = np.zeros(1)
+        lam_cm = np.empty(self.nbf * self.nbf)
+        donof_ri_energy_lagrangian(self.ctx, np.ascontiguousarray(gamma, dtype=np.float64), E, lam_cm)
+        return float(E[0]), lam_cm.reshape(self.nbf, self.nbf).T.copy()
+
+    def fetch(self, what: int) -> np.ndarray:
+        nb, nx, m = self.nbf, self.naux, self.n_omega
+        shapes = {
+            DONOF_RI_FETCH_B: (nx, nb, nb), DONOF_RI_FETCH_BHALF: (nx, m, nb), DONOF_RI_FETCH_DIAG: (nx, m),
+            DONOF_RI_FETCH_HCORE: (nb, nb), DONOF_RI_FETCH_OVERLAP: (nb, nb), DONOF_RI_FETCH_METRIC: (nx, nx),
+            DONOF_RI_FETCH_ENUC: (1,), DONOF_RI_FETCH_OCC: (m,),
+        }
+        out = np.empty(shapes[what])
+        donof_ri_fetch(self.ctx, what, out)
+        return out
+
+    def launches(self) -> int:
+        return donof_ri_launch_count(self.ctx)

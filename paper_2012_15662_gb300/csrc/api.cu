@@ -1,0 +1,304 @@
+// C ABI of the engine: argument checks, context lifetime, host/device
+// pointer handling, call-order state and status codes.  Every computation is
+// dispatched to the FP64 path (path64.cu) or the split-precision tensor-core
+// path (tc.cu); nothing here computes.
+#include "common.cuh"
+
+#include <stdlib.h>
+#include <string.h>
+
+namespace donof {
+int launch_lambda(donof_ri_ctx* ctx);
+int launch_hc_public(donof_ri_ctx* ctx);
+int mixed_fetch(donof_ri_ctx* ctx, int what, double* dst_host, size_t count);
+int mixed_copy_ao(donof_ri_ctx* ctx, double* Jao, double* Kao, bool jao_dev, bool kao_dev);
+}  // namespace donof
+
+using namespace donof;
+
+static bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+static int dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  if (cudaMalloc((void**)p, count * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return DONOF_RI_E_OOM;
+  }
+  return DONOF_RI_OK;
+}
+
+static void dfree(void* p) {
+  if (p) cudaFree(p);
+}
+
+// Read and clear the device-side status word; maps it to an ABI status.
+static int consume_status(donof_ri_ctx* ctx) {
+  int h = 0;
+  if (cudaMemcpyAsync(&h, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
+    return DONOF_RI_E_CUDA;
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return DONOF_RI_E_CUDA;
+  if (h == DEV_OK) return DONOF_RI_OK;
+  if (cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream) != cudaSuccess) return DONOF_RI_E_CUDA;
+  if (h == DEV_METRIC_NOT_PD) return DONOF_RI_E_METRIC_NOT_PD;
+  if (h == DEV_NONFINITE) return DONOF_RI_E_NONFINITE;
+  if (h == DEV_TIMEOUT) return DONOF_RI_E_TIMEOUT;
+  return DONOF_RI_E_CUDA;
+}
+
+static int validate_system(const donof_ri_system* s) {
+  if (!s) return DONOF_RI_E_ARG;
+  if (s->nbf < 1 || s->naux < 1 || s->n_atoms < 1 || s->n_strong < 1 || s->n_weak_per < 1) return DONOF_RI_E_ARG;
+  if (!s->atom_xyz || !s->atom_charge || !s->bf_atom || !s->bf_alpha || !s->aux_atom || !s->aux_alpha ||
+      !s->subspace || !s->weak_rank)
+    return DONOF_RI_E_ARG;
+  long long m = (long long)s->n_strong * (1 + s->n_weak_per);
+  if (m > s->nbf) return DONOF_RI_E_ARG;
+  if ((long long)s->nbf * s->nbf > (1LL << 30) || s->naux > 65535) return DONOF_RI_E_ARG;
+  for (int i = 0; i < s->nbf; ++i)
+    if (s->bf_atom[i] < 0 || s->bf_atom[i] >= s->n_atoms || !(s->bf_alpha[i] > 0.0)) return DONOF_RI_E_ARG;
+  for (int i = 0; i < s->naux; ++i)
+    if (s->aux_atom[i] < 0 || s->aux_atom[i] >= s->n_atoms || !(s->aux_alpha[i] > 0.0)) return DONOF_RI_E_ARG;
+  // Pairing map: every subspace has one strong orbital and weak ranks 0..N_g-1 once each.
+  int* seen = (int*)calloc((size_t)s->n_strong * (s->n_weak_per + 1), sizeof(int));
+  if (!seen) return DONOF_RI_E_ARG;
+  int rc = DONOF_RI_OK;
+  for (long long p = 0; p < m && rc == DONOF_RI_OK; ++p) {
+    int g = s->subspace[p], r = s->weak_rank[p];
+    if (g < 0 || g >= s->n_strong || r < -1 || r >= s->n_weak_per) rc = DONOF_RI_E_ARG;
+    else if (seen[(size_t)g * (s->n_weak_per + 1) + (r + 1)]++) rc = DONOF_RI_E_ARG;
+  }
+  free(seen);
+  return rc;
+}
+
+extern "C" {
+
+const char* donof_ri_strerror(int status) {
+  switch (status) {
+    case DONOF_RI_OK: return "ok";
+    case DONOF_RI_E_ARG: return "invalid argument";
+    case DONOF_RI_E_OOM: return "device allocation failed";
+    case DONOF_RI_E_CUDA: return "CUDA runtime or launch error";
+    case DONOF_RI_E_METRIC_NOT_PD: return "Coulomb metric is not numerically positive definite";
+    case DONOF_RI_E_NONFINITE: return "non-finite value in an input";
+    case DONOF_RI_E_TIMEOUT: return "a bounded device-side wait timed out";
+    case DONOF_RI_E_STATE: return "call order: a required earlier call has not run";
+    case DONOF_RI_E_UNSUPPORTED: return "unsupported device or precision";
+    default: return "unknown status";
+  }
+}
+
+long long donof_ri_launch_count(const donof_ri_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+int donof_ri_destroy(donof_ri_ctx* ctx) {
+  if (!ctx) return DONOF_RI_OK;
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->mixed) mixed_free(ctx);
+  void* bufs[] = {ctx->d_atom_xyz, ctx->d_atom_charge, ctx->d_bf_atom, ctx->d_bf_alpha, ctx->d_aux_atom,
+                  ctx->d_aux_alpha, ctx->d_subspace, ctx->d_weak_rank, ctx->d_S, ctx->d_H, ctx->d_G, ctx->d_B,
+                  ctx->d_enuc, ctx->d_scratch_max, ctx->d_C, ctx->d_bh, ctx->d_d, ctx->d_bf, ctx->d_J, ctx->d_K,
+                  ctx->d_Jao, ctx->d_Kao, ctx->d_W, ctx->d_HC, ctx->d_Y, ctx->d_lambda, ctx->d_gamma, ctx->d_n,
+                  ctx->d_A, ctx->d_Bc, ctx->d_E, ctx->d_status};
+  for (void* b : bufs) dfree(b);
+  free(ctx);
+  return DONOF_RI_OK;
+}
+
+int donof_ri_init(const donof_ri_system* sys, int precision, void* stream, donof_ri_ctx** out) {
+  if (!out) return DONOF_RI_E_ARG;
+  *out = nullptr;
+  int rc = validate_system(sys);
+  if (rc) return rc;
+  if (precision != DONOF_RI_FP64 && precision != DONOF_RI_TF32X3) return DONOF_RI_E_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return DONOF_RI_E_UNSUPPORTED; }
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return DONOF_RI_E_CUDA;
+  if (prop.major != 10 || prop.minor != 3) return DONOF_RI_E_UNSUPPORTED;
+
+  donof_ri_ctx* ctx = (donof_ri_ctx*)calloc(1, sizeof(donof_ri_ctx));
+  if (!ctx) return DONOF_RI_E_OOM;
+  ctx->nbf = sys->nbf;
+  ctx->naux = sys->naux;
+  ctx->n_atoms = sys->n_atoms;
+  ctx->n_strong = sys->n_strong;
+  ctx->n_weak_per = sys->n_weak_per;
+  ctx->n_omega = sys->n_strong * (1 + sys->n_weak_per);
+  ctx->precision = precision;
+  ctx->stream = (cudaStream_t)stream;
+  const size_t nb = ctx->nbf, nx = ctx->naux, m = ctx->n_omega, na = ctx->n_atoms;
+  const size_t nb2 = nb * nb;
+
+#define TRY(x) do { rc = (x); if (rc) { donof_ri_destroy(ctx); return rc; } } while (0)
+  TRY(dalloc(&ctx->d_atom_xyz, 3 * na));
+  TRY(dalloc(&ctx->d_atom_charge, na));
+  TRY(dalloc(&ctx->d_bf_atom, nb));
+  TRY(dalloc(&ctx->d_bf_alpha, nb));
+  TRY(dalloc(&ctx->d_aux_atom, nx));
+  TRY(dalloc(&ctx->d_aux_alpha, nx));
+  TRY(dalloc(&ctx->d_subspace, m));
+  TRY(dalloc(&ctx->d_weak_rank, m));
+  TRY(dalloc(&ctx->d_S, nb2));
+  TRY(dalloc(&ctx->d_H, nb2));
+  TRY(dalloc(&ctx->d_G, nx * nx));
+  TRY(dalloc(&ctx->d_B, nx * nb2));
+  TRY(dalloc(&ctx->d_enuc, 1));
+  TRY(dalloc(&ctx->d_scratch_max, 1));
+  TRY(dalloc(&ctx->d_C, nb2));
+  TRY(dalloc(&ctx->d_J, m * m));
+  TRY(dalloc(&ctx->d_K, m * m));
+  TRY(dalloc(&ctx->d_HC, nb * m));
+  TRY(dalloc(&ctx->d_Y, nb * m));
+  TRY(dalloc(&ctx->d_lambda, nb2));
+  TRY(dalloc(&ctx->d_gamma, (size_t)sys->n_strong * sys->n_weak_per));
+  TRY(dalloc(&ctx->d_n, m));
+  TRY(dalloc(&ctx->d_A, m * m));
+  TRY(dalloc(&ctx->d_Bc, m * m));
+  TRY(dalloc(&ctx->d_E, 1));
+  TRY(dalloc(&ctx->d_status, 1));
+  if (precision == DONOF_RI_FP64) {
+    TRY(dalloc(&ctx->d_bh, nx * m * nb));
+    TRY(dalloc(&ctx->d_d, nx * m));
+    TRY(dalloc(&ctx->d_bf, nx * m * m));
+    TRY(dalloc(&ctx->d_Jao, m * nb2));
+    TRY(dalloc(&ctx->d_Kao, m * nb2));
+    TRY(dalloc(&ctx->d_W, m * nb2));
+  }
+  cudaStream_t s = ctx->stream;
+#define CPY(dst, src, n) \
+  do { if (cudaMemcpyAsync(dst, src, (n) * sizeof(*(src)), cudaMemcpyHostToDevice, s) != cudaSuccess) TRY(DONOF_RI_E_CUDA); } while (0)
+  CPY(ctx->d_atom_xyz, sys->atom_xyz, 3 * na);
+  CPY(ctx->d_atom_charge, sys->atom_charge, na);
+  CPY(ctx->d_bf_atom, sys->bf_atom, nb);
+  CPY(ctx->d_bf_alpha, sys->bf_alpha, nb);
+  CPY(ctx->d_aux_atom, sys->aux_atom, nx);
+  CPY(ctx->d_aux_alpha, sys->aux_alpha, nx);
+  CPY(ctx->d_subspace, sys->subspace, m);
+  CPY(ctx->d_weak_rank, sys->weak_rank, m);
+#undef CPY
+  if (cudaMemsetAsync(ctx->d_status, 0, sizeof(int), s) != cudaSuccess) TRY(DONOF_RI_E_CUDA);
+  if (cudaMemsetAsync(ctx->d_lambda, 0, nb2 * sizeof(double), s) != cudaSuccess) TRY(DONOF_RI_E_CUDA);
+  TRY(setup_integrals(ctx));
+  TRY(setup_cholesky_and_fit(ctx));
+  TRY(consume_status(ctx));
+  if (precision == DONOF_RI_TF32X3) TRY(mixed_init(ctx));
+  if (cudaStreamSynchronize(s) != cudaSuccess) TRY(DONOF_RI_E_CUDA);
+#undef TRY
+  *out = ctx;
+  return DONOF_RI_OK;
+}
+
+int donof_ri_sync(donof_ri_ctx* ctx) {
+  if (!ctx) return DONOF_RI_E_ARG;
+  return consume_status(ctx);
+}
+
+int donof_ri_transform(donof_ri_ctx* ctx, const double* C, int mode) {
+  if (!ctx || !C || (mode != DONOF_RI_HALF && mode != DONOF_RI_FULL)) return DONOF_RI_E_ARG;
+  const size_t nb2 = (size_t)ctx->nbf * ctx->nbf;
+  cudaMemcpyKind kind = is_device_ptr(C) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  DONOF_CUDA_TRY(cudaMemcpyAsync(ctx->d_C, C, nb2 * sizeof(double), kind, ctx->stream));
+  int rc = launch_check_finite(ctx, ctx->d_C, (long long)nb2);
+  if (rc) return rc;
+  ctx->have_half = ctx->have_full = ctx->have_ao = 0;
+  rc = ctx->precision == DONOF_RI_FP64 ? path64_transform(ctx, mode) : mixed_transform(ctx, mode);
+  if (rc) return rc;
+  ctx->have_half = 1;
+  ctx->have_full = (mode == DONOF_RI_FULL);
+  return DONOF_RI_OK;
+}
+
+static int copy_out(donof_ri_ctx* ctx, double* dst, const double* src, size_t count, bool* host_written) {
+  if (!dst) return DONOF_RI_OK;
+  bool dev = is_device_ptr(dst);
+  DONOF_CUDA_TRY(cudaMemcpyAsync(dst, src, count * sizeof(double),
+                                 dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+  if (!dev) *host_written = true;
+  return DONOF_RI_OK;
+}
+
+int donof_ri_jk_mo(donof_ri_ctx* ctx, double* J, double* K) {
+  if (!ctx) return DONOF_RI_E_ARG;
+  if (!ctx->have_full) return DONOF_RI_E_STATE;
+  const size_t m2 = (size_t)ctx->n_omega * ctx->n_omega;
+  bool host = false;
+  int rc = copy_out(ctx, J, ctx->d_J, m2, &host);
+  if (rc) return rc;
+  rc = copy_out(ctx, K, ctx->d_K, m2, &host);
+  if (rc) return rc;
+  return host ? consume_status(ctx) : DONOF_RI_OK;
+}
+
+int donof_ri_jk_ao_batch(donof_ri_ctx* ctx, double* Jao, double* Kao) {
+  if (!ctx) return DONOF_RI_E_ARG;
+  if (!ctx->have_half) return DONOF_RI_E_STATE;
+  int rc = ctx->precision == DONOF_RI_FP64 ? path64_jk_ao(ctx) : mixed_jk_ao(ctx);
+  if (rc) return rc;
+  ctx->have_ao = 1;
+  if (!Jao && !Kao) return DONOF_RI_OK;
+  const size_t n = (size_t)ctx->n_omega * ctx->nbf * ctx->nbf;
+  bool host = false;
+  if (ctx->precision == DONOF_RI_FP64) {
+    if ((rc = copy_out(ctx, Jao, ctx->d_Jao, n, &host))) return rc;
+    if ((rc = copy_out(ctx, Kao, ctx->d_Kao, n, &host))) return rc;
+  } else {
+    bool jd = is_device_ptr(Jao), kd = is_device_ptr(Kao);
+    if ((rc = mixed_copy_ao(ctx, Jao, Kao, jd, kd))) return rc;
+    host = (Jao && !jd) || (Kao && !kd);
+  }
+  return host ? consume_status(ctx) : DONOF_RI_OK;
+}
+
+int donof_ri_energy_lagrangian(donof_ri_ctx* ctx, const double* gamma, double* E, double* lambda) {
+  if (!ctx || !gamma) return DONOF_RI_E_ARG;
+  if (!ctx->have_ao) return DONOF_RI_E_STATE;
+  const size_t ng = (size_t)ctx->n_strong * ctx->n_weak_per;
+  cudaMemcpyKind kind = is_device_ptr(gamma) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  DONOF_CUDA_TRY(cudaMemcpyAsync(ctx->d_gamma, gamma, ng * sizeof(double), kind, ctx->stream));
+  int rc = launch_check_finite(ctx, ctx->d_gamma, (long long)ng);
+  if (rc) return rc;
+  rc = ctx->precision == DONOF_RI_FP64 ? path64_energy(ctx) : mixed_energy(ctx);
+  if (rc) return rc;
+  bool host = false;
+  if ((rc = copy_out(ctx, E, ctx->d_E, 1, &host))) return rc;
+  if ((rc = copy_out(ctx, lambda, ctx->d_lambda, (size_t)ctx->nbf * ctx->nbf, &host))) return rc;
+  return host ? consume_status(ctx) : DONOF_RI_OK;
+}
+
+int donof_ri_fetch(donof_ri_ctx* ctx, int what, double* dst, size_t count) {
+  if (!ctx || !dst) return DONOF_RI_E_ARG;
+  const size_t nb = ctx->nbf, nx = ctx->naux, m = ctx->n_omega;
+  const double* src = nullptr;
+  size_t n = 0;
+  switch (what) {
+    case DONOF_RI_FETCH_B: src = ctx->d_B; n = nx * nb * nb; break;
+    case DONOF_RI_FETCH_HCORE: src = ctx->d_H; n = nb * nb; break;
+    case DONOF_RI_FETCH_OVERLAP: src = ctx->d_S; n = nb * nb; break;
+    case DONOF_RI_FETCH_METRIC: src = ctx->d_G; n = nx * nx; break;
+    case DONOF_RI_FETCH_ENUC: src = ctx->d_enuc; n = 1; break;
+    case DONOF_RI_FETCH_OCC: src = ctx->d_n; n = m; break;
+    case DONOF_RI_FETCH_BHALF: n = nx * m * nb; src = ctx->d_bh; break;
+    case DONOF_RI_FETCH_DIAG: n = nx * m; src = ctx->d_d; break;
+    default: return DONOF_RI_E_ARG;
+  }
+  if (count != n) return DONOF_RI_E_ARG;
+  if ((what == DONOF_RI_FETCH_BHALF || what == DONOF_RI_FETCH_DIAG) && !ctx->have_half) return DONOF_RI_E_STATE;
+  if (ctx->precision == DONOF_RI_TF32X3 && (what == DONOF_RI_FETCH_BHALF || what == DONOF_RI_FETCH_DIAG))
+    return mixed_fetch(ctx, what, dst, count);
+  DONOF_CUDA_TRY(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  return consume_status(ctx);
+}
+
+}  // extern "C"

@@ -1,0 +1,125 @@
+// Internal declarations shared by the engine's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/donof_ri.h"
+
+namespace donof {
+
+// Device-side status codes written into ctx->d_status by kernels.
+enum DeviceStatus : int {
+  DEV_OK = 0,
+  DEV_METRIC_NOT_PD = 1,
+  DEV_NONFINITE = 2,
+  DEV_TIMEOUT = 3,
+};
+
+// Generic strided batched FP64 GEMM: C[b](m,n) = alpha * sum_k A[b](m,k) B[b](k,n) + beta * C[b](m,n)
+// with element (m,k) of A at A[b*sAb + m*sAm + k*sAk] (likewise B, C).
+struct Gemm64 {
+  int M, N, K, batch;
+  const double* A;
+  long long sAb, sAm, sAk;
+  const double* B;
+  long long sBb, sBk, sBn;
+  double* C;
+  long long sCb, sCm, sCn;
+  double alpha, beta;
+};
+
+// Mixed-precision (split TF32) buffers, allocated only for DONOF_RI_TF32X3.
+struct MixedBuffers;
+
+}  // namespace donof
+
+struct donof_ri_ctx {
+  int nbf, naux, n_atoms, n_strong, n_weak_per, n_omega;
+  int precision;
+  cudaStream_t stream;
+  long long launches;
+
+  // problem statement (device copies)
+  double* d_atom_xyz;
+  double* d_atom_charge;
+  int* d_bf_atom;
+  double* d_bf_alpha;
+  int* d_aux_atom;
+  double* d_aux_alpha;
+  int* d_subspace;
+  int* d_weak_rank;
+
+  // setup products (FP64)
+  double* d_S;      // [nbf][nbf]
+  double* d_H;      // [nbf][nbf]
+  double* d_G;      // [naux][naux], lower triangle = L after init
+  double* d_B;      // [naux][nbf][nbf] fitted tensor (FP64)
+  double* d_enuc;   // [1]
+  double* d_scratch_max;  // [1]
+
+  // per-iteration FP64 state
+  double* d_C;      // [nbf][nbf] column-major orbitals
+  double* d_bh;     // [naux][n_omega][nbf]
+  double* d_d;      // [naux][n_omega]
+  double* d_bf;     // [naux][n_omega][n_omega]
+  double* d_J;      // [n_omega][n_omega]
+  double* d_K;      // [n_omega][n_omega]
+  double* d_Jao;    // [n_omega][nbf][nbf]
+  double* d_Kao;    // [n_omega][nbf][nbf]
+  double* d_W;      // [n_omega][nbf][nbf]
+  double* d_HC;     // [nbf][n_omega]
+  double* d_Y;      // [nbf][n_omega]
+  double* d_lambda; // [nbf][nbf] column-major
+  double* d_gamma;  // [n_strong*n_weak_per]
+  double* d_n;      // [n_omega]
+  double* d_A;      // [n_omega][n_omega]
+  double* d_Bc;     // [n_omega][n_omega]
+  double* d_E;      // [1]
+  int* d_status;    // [1] device-side status (DeviceStatus)
+
+  donof::MixedBuffers* mixed;
+
+  // call-order state
+  int have_half, have_full, have_ao;
+};
+
+namespace donof {
+
+// ---- launch helpers (defined in setup64.cu) ----
+int launch_dgemm(donof_ri_ctx* ctx, const Gemm64& g);
+int setup_integrals(donof_ri_ctx* ctx);
+int setup_cholesky_and_fit(donof_ri_ctx* ctx);
+
+// ---- FP64 hot path (path64.cu) ----
+int path64_transform(donof_ri_ctx* ctx, int mode);
+int path64_jk_ao(donof_ri_ctx* ctx);
+int path64_energy(donof_ri_ctx* ctx);
+int launch_check_finite(donof_ri_ctx* ctx, const double* x, long long n);
+int launch_occupations_coupling(donof_ri_ctx* ctx);
+int launch_energy_reduce(donof_ri_ctx* ctx);
+
+// ---- mixed path (tc.cu) ----
+int mixed_init(donof_ri_ctx* ctx);
+void mixed_free(donof_ri_ctx* ctx);
+int mixed_transform(donof_ri_ctx* ctx, int mode);
+int mixed_jk_ao(donof_ri_ctx* ctx);
+int mixed_energy(donof_ri_ctx* ctx);
+
+}  // namespace donof
+
+#define DONOF_CUDA_TRY(expr)                         \
+  do {                                               \
+    cudaError_t _e = (expr);                         \
+    if (_e != cudaSuccess) return DONOF_RI_E_CUDA;   \
+  } while (0)
+
+#define DONOF_LAUNCH_CHECK(ctx)                      \
+  do {                                               \
+    (ctx)->launches++;                               \
+    cudaError_t _e = cudaGetLastError();             \
+    if (_e != cudaSuccess) return DONOF_RI_E_CUDA;   \
+  } while (0)
+
+static inline unsigned ceil_div_u(long long a, long long b) { return (unsigned)((a + b - 1) / b); }

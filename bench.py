@@ -1,0 +1,397 @@
+"""Benchmark: RI J/K build time per PNOF7 iteration on one GB300 (or N replicas).
+
+One step = one pass of the whole hot path over the workload: the half and
+full transforms with J_pq / K_pq (Table 2), the per-orbital AO J^(q) / K^(q)
+(Table 3) and the PNOF7 energy and Lagrangian, i.e. the C-ABI sequence
+  donof_ri_transform(FULL) -> donof_ri_jk_mo -> donof_ri_jk_ao_batch
+  -> donof_ri_energy_lagrangian.
+Inputs (orbitals C, angles gamma) are resident in device memory when the
+timed region starts; L2 is flushed (256 MB write) between timed steps,
+outside the per-step CUDA events.  `e2e` repeats the step through the same
+entry points with pinned host buffers (host->device copy of C and gamma and
+device->host copy of J, K, E, lambda inside the timed region).
+
+Multi-GPU: the path does not shard across GPUs in this engine (replicas
+only); under torchrun every rank runs an independent replica and `value` is
+the effective time per iteration of the whole job (max-over-ranks time
+divided by all ranks' iterations).
+
+`--impl reference` times the FP64 CPU oracle (the only baseline: the paper
+ships no code) on the host cores, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "RI J/K build ms per PNOF7 iteration"
+UNIT = "ms/iteration"
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+# Nominal dense rates (TFLOP/s) used to scale the measured bf16 peak to other types.
+NOMINAL = {"bf16": 2250.0, "tf32": 1100.0, "fp64": 1.25}
+
+ROWS = ["half", "diag", "full_k", "j", "jao", "kao", "energy", "other"]
+
+
+def workload_desc(name):
+    from synthetic import make_workload
+    w = make_workload(name)
+    s = w.system
+    return w, (f"{name}: s-type ring, nbf={s.nbf}, naux={s.naux}, N_I={s.n_strong}, "
+               f"N_g={s.n_weak_per}, N_Omega={s.n_omega}")
+
+
+def algorithmic_flops(s):
+    """Algorithmic FLOPs per launch group of each row (2 per multiply-add; symmetric halves not counted)."""
+    nb, nx, m = s.nbf, s.naux, s.n_omega
+    return {
+        "half": 2.0 * nb * nb * nx * m,
+        "diag": 2.0 * nb * nx * m,
+        "full_k": 2.0 * nb * nx * m * m + 2.0 * nx * m * m,
+        "j": 1.0 * nx * m * (m + 1),
+        "jao": 1.0 * nb * (nb + 1) * nx * m,
+        "kao": 1.0 * nb * (nb + 1) * nx * m,
+        "energy": 4.0 * nb * nb * m * m + 2.0 * nb * nb * m,
+    }
+
+
+def read_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            return d, "measured"
+        except Exception:
+            pass
+    return dict(FALLBACK_PEAKS), "fallback"
+
+
+def _peak_value(d, key):
+    v = d.get(key)
+    if isinstance(v, dict):
+        for k in ("value", "median", "tflops", "gbs"):
+            if k in v:
+                return float(v[k])
+    return float(v) if v is not None else None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_source_sha(precision):
+    files = ["tc.cu"] if precision == "tf32x3" else ["path64.cu", "setup64.cu"]
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(ROOT, "paper_2012_15662_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def read_traffic(workload, precision, row):
+    """DRAM bytes per launch of the dominant row from a committed ncu summary, if its source hash matches."""
+    path = os.path.join(ROOT, "profiles", f"traffic_{workload}_{precision}.txt")
+    if not os.path.exists(path):
+        return None
+    sha = kernel_source_sha(precision)
+    for ln in open(path):
+        f = dict(kv.split("=", 1) for kv in ln.split() if "=" in kv)
+        if f.get("row") == row and f.get("src_sha") == sha and "bytes_per_launch" in f:
+            return float(f["bytes_per_launch"])
+    return None
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline and reference arm)
+# ---------------------------------------------------------------------------
+def _oracle_sample(name, budget_s):
+    """Run whole iterations of the oracle until budget_s is spent; return ms/iteration and count."""
+    from oracle import integrals as I, pnof7, ri
+    from synthetic import make_workload, pairing_columns
+    w = make_workload(name)
+    s = w.system
+    B, L, G = ri.setup(s)
+    H = I.core_hamiltonian(s)
+    e_nuc = I.nuclear_repulsion(s)
+    sub, rank = pairing_columns(s.n_strong, s.n_weak_per)
+    m = s.n_omega
+    times = []
+    t_end = time.perf_counter() + budget_s
+    while True:
+        t0 = time.perf_counter()
+        r = ri.all_rows(B, w.C, m)
+        n = pnof7.occupations(w.gamma, s.n_strong, s.n_weak_per, sub, rank)
+        A, Bc = pnof7.coupling(n, sub, rank)
+        pnof7.lagrangian(w.C, H, r["Jao"], r["Kao"], n, A, Bc)
+        Hd = np.einsum("mp,mn,np->p", w.C[:, :m], H, w.C[:, :m])
+        pnof7.energy(n, Hd, r["J"], r["K"], A, Bc, e_nuc)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() > t_end:
+            break
+    return 1000.0 * float(np.mean(times)), len(times)
+
+
+def cpu_baseline(name, budget_s=12.0):
+    """Time the oracle in a spawned subprocess with every host core available to BLAS."""
+    cores = os.cpu_count() or 1
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = str(cores)
+    code = (f"import sys, json; sys.path.insert(0, {ROOT!r}); import bench; "
+            f"print(json.dumps(bench._oracle_sample({name!r}, {budget_s})))")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
+    if out.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": cores, "kind": "oracle", "error": out.stderr[-300:]}
+    ms, iters = json.loads(out.stdout.strip().splitlines()[-1])
+    return {"value": ms, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{iters} whole iterations of {name} (all rows, FP64 numpy/BLAS) in ~{budget_s:.0f} s"}
+
+
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c6h12")
+    ap.add_argument("--precision", default="tf32x3", choices=["tf32x3", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        w, desc = workload_desc(args.workload)
+        budget = max(2.0, min(20.0, 0.5 * (args.steps + args.warmup)))
+        cb = cpu_baseline(args.workload, budget_s=budget)
+        line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": cb["value"],
+                "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": desc, "precision": "fp64 (CPU oracle)"},
+                "cpu_baseline": cb,
+                "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return 0
+
+    import torch
+    from paper_2012_15662_gb300 import binding as bd
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", rank=rank, world_size=world)
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w, desc = workload_desc(args.workload)
+    s = w.system
+    prec = bd.DONOF_RI_TF32X3 if args.precision == "tf32x3" else bd.DONOF_RI_FP64
+    stream = torch.cuda.Stream(device=dev)
+    eng = bd.Engine(s, prec, stream=stream.cuda_stream)
+    nb, m = s.nbf, s.n_omega
+    C_dev = torch.from_numpy(bd.Engine.colmajor(w.C)).to(dev)
+    g_dev = torch.from_numpy(np.ascontiguousarray(w.gamma)).to(dev)
+    J_dev = torch.empty((m, m), dtype=torch.float64, device=dev)
+    K_dev = torch.empty((m, m), dtype=torch.float64, device=dev)
+    E_dev = torch.empty(1, dtype=torch.float64, device=dev)
+    L_dev = torch.empty(nb * nb, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()
+
+    def step():
+        bd.donof_ri_transform(eng.ctx, C_dev, bd.DONOF_RI_FULL)
+        bd.donof_ri_jk_mo(eng.ctx, J_dev, K_dev)
+        bd.donof_ri_jk_ao_batch(eng.ctx)
+        bd.donof_ri_energy_lagrangian(eng.ctx, g_dev, E_dev, L_dev)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize()
+    bd.donof_ri_sync(eng.ctx)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    sampler = ClockSampler(local_rank)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    bd.donof_ri_profile(eng.ctx, True)
+    l0 = bd.donof_ri_launch_count(eng.ctx)
+    barrier()
+    sampler.start()
+    time.sleep(0.3)
+    with torch.cuda.stream(stream):
+        for a, b in evs:
+            flush.zero_()
+            a.record(stream)
+            step()
+            b.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    launches = bd.donof_ri_launch_count(eng.ctx) - l0
+    bd.donof_ri_sync(eng.ctx)
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    rows = {}
+    for i, r in enumerate(ROWS):
+        t, c = bd.donof_ri_profile_read(eng.ctx, i)
+        rows[r] = (t, c)
+    bd.donof_ri_profile(eng.ctx, False)
+    ms = float(np.mean(step_ms))
+    if world > 1:
+        t = torch.tensor([ms * args.steps], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    else:
+        total_ms = ms * args.steps
+    value = total_ms / (args.steps * world)
+
+    # e2e through the same entry points with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        C_h = torch.from_numpy(bd.Engine.colmajor(w.C)).pin_memory()
+        g_h = torch.from_numpy(np.ascontiguousarray(w.gamma)).pin_memory()
+        J_h = torch.empty((m, m), dtype=torch.float64).pin_memory()
+        K_h = torch.empty((m, m), dtype=torch.float64).pin_memory()
+        E_h = torch.empty(1, dtype=torch.float64).pin_memory()
+        L_h = torch.empty(nb * nb, dtype=torch.float64).pin_memory()
+
+        def step_host():
+            bd.donof_ri_transform(eng.ctx, C_h, bd.DONOF_RI_FULL)
+            bd.donof_ri_jk_mo(eng.ctx, J_h, K_h)
+            bd.donof_ri_jk_ao_batch(eng.ctx)
+            bd.donof_ri_energy_lagrangian(eng.ctx, g_h, E_h, L_h)
+
+        for _ in range(args.warmup):
+            step_host()
+        barrier()
+        tt = []
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            step_host()
+            tt.append(time.perf_counter() - t0)
+        barrier()
+        e_ms = 1000.0 * float(np.mean(tt))
+        if world > 1:
+            t = torch.tensor([e_ms], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e_ms = float(t.item())
+        e2e = {"value": e_ms / world, "unit": UNIT,
+               "h2d_bytes_per_step": int(8 * (nb * nb + len(w.gamma))),
+               "d2h_bytes_per_step": int(8 * (2 * m * m + 1 + nb * nb))}
+
+    # roofline of the dominant compute row
+    flops = algorithmic_flops(s)
+    dom = max((r for r in flops if rows[r][1] > 0), key=lambda r: rows[r][0])
+    t_dom, c_dom = rows[dom]
+    per_launch_ms = t_dom / max(c_dom, 1)
+    achieved = flops[dom] / (per_launch_ms * 1e-3) / 1e12
+    peaks, peak_src = read_peaks()
+    if prec == bd.DONOF_RI_FP64:
+        peak = NOMINAL["fp64"]
+        bound, peak_note = "alu", "FP64 nominal 1.25 TFLOP/s (DFMA on CUDA cores; not measured)"
+    else:
+        bf = _peak_value(peaks, "bf16_tflops") or FALLBACK_PEAKS["bf16_tflops"]
+        peak = bf * NOMINAL["tf32"] / NOMINAL["bf16"]
+        bound, peak_note = "tensor", (f"TF32 dense = {peak_src} bf16 burst {bf:.0f} x 1.1/2.25; "
+                                      "3 TF32 MMAs per algorithmic product")
+    traffic = read_traffic(args.workload, args.precision, dom)
+    roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": traffic, "kernel_row": dom, "launch_ms": per_launch_ms,
+            "algorithmic_flops_per_launch": flops[dom], "peak_source": peak_note}
+
+    if rank != 0:
+        return 0
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if prec == bd.DONOF_RI_FP64 else "tf32x3",
+        "data": "synthetic",
+        "config": {"workload": desc, "precision": args.precision,
+                   "l2": "flushed between steps (256 MB write, outside the step events)",
+                   "parallelism": f"replicas x{world}"},
+        "rows_ms_per_step": {r: rows[r][0] / args.steps for r in ROWS},
+        "roofline": roof, "clocks": clocks, "gpu_launches": int(launches), "e2e": e2e,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.workload)
+    print(json.dumps(line))
+    eng.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -182,6 +182,32 @@ const char* donof_ri_strerror(int status);
 /* Number of kernels the context has launched since init (for launch accounting). */
 long long donof_ri_launch_count(const donof_ri_ctx* ctx);
 
+/* Hot-path rows timed by the profiler (CUDA events on the context's stream). */
+#define DONOF_RI_ROW_HALF 0      /* a1: half transform b^P_{p nu}                     */
+#define DONOF_RI_ROW_DIAG 1      /* a2: diagonal b^P_pp                               */
+#define DONOF_RI_ROW_FULL_K 2    /* a3: full transform b^P_pq and K_pq                */
+#define DONOF_RI_ROW_J 3         /* a4: J_pq                                          */
+#define DONOF_RI_ROW_JAO 4       /* a5: per-orbital J^(q)                             */
+#define DONOF_RI_ROW_KAO 5       /* a6: per-orbital K^(q)                             */
+#define DONOF_RI_ROW_ENERGY 6    /* a7: occupations, F^(p) C_p, lambda and E          */
+#define DONOF_RI_ROW_OTHER 7     /* input copies, finiteness checks, conversions      */
+#define DONOF_RI_NUM_ROWS 8
+
+/*
+ * Enable (1) or disable (0) per-row timing.  While enabled, every launch group
+ * of a hot-path row is bracketed by a pair of CUDA events recorded on the
+ * context's stream (this also works inside a captured CUDA graph).
+ * Disabling discards pending records.  Errors: E_ARG.
+ */
+int donof_ri_profile(donof_ri_ctx* ctx, int enable);
+
+/*
+ * Synchronise, then return for row `row` the summed event time (ms) and the
+ * number of timed launch groups since the last read, and reset that row.
+ * Errors: E_ARG, E_CUDA.
+ */
+int donof_ri_profile_read(donof_ri_ctx* ctx, int row, double* total_ms, long long* count);
+
 #ifdef __cplusplus
 }
 #endif

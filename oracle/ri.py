@@ -99,7 +99,8 @@ def jk_ao(B: np.ndarray, bh: np.ndarray, d: np.ndarray) -> tuple[np.ndarray, np.
     K^(q)_{mu nu} = sum_P b^P_{q mu} b^P_{q nu}; returns (Jao, Kao)."""
     nx, nb, _ = B.shape
     Jao = (d.T @ B.reshape(nx, nb * nb)).reshape(-1, nb, nb)
-    Kao = np.einsum("Pqm,Pqn->qmn", bh, bh, optimize=True)
+    Xq = np.ascontiguousarray(bh.transpose(1, 2, 0))      # [q, mu, P] = b^P_{q mu}
+    Kao = np.matmul(Xq, Xq.transpose(0, 2, 1))           # K^(q) = X_q X_q^T
     return Jao, Kao
 
 

@@ -42,8 +42,10 @@ DONOF_RI_FETCH_OCC = 7
 EXPORTS = [
     "donof_ri_init", "donof_ri_transform", "donof_ri_jk_mo", "donof_ri_jk_ao_batch",
     "donof_ri_energy_lagrangian", "donof_ri_fetch", "donof_ri_sync", "donof_ri_destroy",
-    "donof_ri_strerror", "donof_ri_launch_count",
+    "donof_ri_strerror", "donof_ri_launch_count", "donof_ri_profile", "donof_ri_profile_read",
 ]
+
+ROWS = ["half", "diag", "full_k", "j", "jao", "kao", "energy", "other"]
 
 
 class DonofError(RuntimeError):
@@ -89,6 +91,10 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.donof_ri_strerror.restype = ctypes.c_char_p
     lib.donof_ri_launch_count.argtypes = [vp]
     lib.donof_ri_launch_count.restype = ctypes.c_longlong
+    lib.donof_ri_profile.argtypes = [vp, i]
+    lib.donof_ri_profile.restype = i
+    lib.donof_ri_profile_read.argtypes = [vp, i, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong)]
+    lib.donof_ri_profile_read.restype = i
     for name in ("donof_ri_init", "donof_ri_transform", "donof_ri_jk_mo", "donof_ri_jk_ao_batch",
                  "donof_ri_energy_lagrangian", "donof_ri_fetch", "donof_ri_sync", "donof_ri_destroy"):
         getattr(lib, name).restype = i
@@ -176,6 +182,18 @@ def donof_ri_destroy(ctx):
 
 def donof_ri_launch_count(ctx) -> int:
     return int(load().donof_ri_launch_count(ctx))
+
+
+def donof_ri_profile(ctx, enable: bool):
+    _check(load().donof_ri_profile(ctx, 1 if enable else 0), "donof_ri_profile")
+
+
+def donof_ri_profile_read(ctx, row: int):
+    """(total_ms, count) of the timed launch groups of one hot-path row since the last read."""
+    t = ctypes.c_double()
+    c = ctypes.c_longlong()
+    _check(load().donof_ri_profile_read(ctx, int(row), ctypes.byref(t), ctypes.byref(c)), "donof_ri_profile_read")
+    return t.value, c.value
 
 
 class Engine:

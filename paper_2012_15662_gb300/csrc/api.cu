@@ -16,6 +16,34 @@ int mixed_copy_ao(donof_ri_ctx* ctx, double* Jao, double* Kao, bool jao_dev, boo
 
 using namespace donof;
 
+namespace donof {
+void prof_begin(donof_ri_ctx* ctx, int row, int* slot) {
+  *slot = -1;
+  if (!ctx->prof_enabled) return;
+  if (ctx->prof_n == ctx->prof_cap) {
+    int cap = ctx->prof_cap ? 2 * ctx->prof_cap : 256;
+    void* p = realloc(ctx->prof, sizeof(*ctx->prof) * cap);
+    if (!p) return;
+    ctx->prof = (donof_ri_ctx::ProfRec*)p;
+    for (int i = ctx->prof_cap; i < cap; ++i) {
+      ctx->prof[i].a = ctx->prof[i].b = nullptr;
+    }
+    ctx->prof_cap = cap;
+  }
+  donof_ri_ctx::ProfRec& r = ctx->prof[ctx->prof_n];
+  if (!r.a && cudaEventCreate(&r.a) != cudaSuccess) { cudaGetLastError(); r.a = nullptr; return; }
+  if (!r.b && cudaEventCreate(&r.b) != cudaSuccess) { cudaGetLastError(); r.b = nullptr; return; }
+  r.row = row;
+  cudaEventRecord(r.a, ctx->stream);
+  *slot = ctx->prof_n++;
+}
+
+void prof_end(donof_ri_ctx* ctx, int slot) {
+  if (slot < 0) return;
+  cudaEventRecord(ctx->prof[slot].b, ctx->stream);
+}
+}  // namespace donof
+
 static bool is_device_ptr(const void* p) {
   if (!p) return false;
   cudaPointerAttributes a;
@@ -106,6 +134,11 @@ int donof_ri_destroy(donof_ri_ctx* ctx) {
   if (!ctx) return DONOF_RI_OK;
   cudaStreamSynchronize(ctx->stream);
   if (ctx->mixed) mixed_free(ctx);
+  for (int i = 0; i < ctx->prof_cap; ++i) {
+    if (ctx->prof[i].a) cudaEventDestroy(ctx->prof[i].a);
+    if (ctx->prof[i].b) cudaEventDestroy(ctx->prof[i].b);
+  }
+  free(ctx->prof);
   void* bufs[] = {ctx->d_atom_xyz, ctx->d_atom_charge, ctx->d_bf_atom, ctx->d_bf_alpha, ctx->d_aux_atom,
                   ctx->d_aux_alpha, ctx->d_subspace, ctx->d_weak_rank, ctx->d_S, ctx->d_H, ctx->d_G, ctx->d_B,
                   ctx->d_enuc, ctx->d_scratch_max, ctx->d_C, ctx->d_bh, ctx->d_d, ctx->d_bf, ctx->d_J, ctx->d_K,
@@ -200,6 +233,37 @@ int donof_ri_init(const donof_ri_system* sys, int precision, void* stream, donof
   return DONOF_RI_OK;
 }
 
+int donof_ri_profile(donof_ri_ctx* ctx, int enable) {
+  if (!ctx) return DONOF_RI_E_ARG;
+  ctx->prof_enabled = enable ? 1 : 0;
+  if (!enable) ctx->prof_n = 0;
+  return DONOF_RI_OK;
+}
+
+int donof_ri_profile_read(donof_ri_ctx* ctx, int row, double* total_ms, long long* count) {
+  if (!ctx || row < 0 || row >= DONOF_RI_NUM_ROWS || !total_ms || !count) return DONOF_RI_E_ARG;
+  DONOF_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  double t = 0.0;
+  long long c = 0;
+  int keep = 0;
+  for (int i = 0; i < ctx->prof_n; ++i) {
+    donof_ri_ctx::ProfRec r = ctx->prof[i];
+    if (r.row == row) {
+      float ms = 0.f;
+      DONOF_CUDA_TRY(cudaEventElapsedTime(&ms, r.a, r.b));
+      t += ms;
+      ++c;
+    } else {
+      ctx->prof[i] = ctx->prof[keep];
+      ctx->prof[keep++] = r;
+    }
+  }
+  ctx->prof_n = keep;
+  *total_ms = t;
+  *count = c;
+  return DONOF_RI_OK;
+}
+
 int donof_ri_sync(donof_ri_ctx* ctx) {
   if (!ctx) return DONOF_RI_E_ARG;
   return consume_status(ctx);
@@ -209,9 +273,13 @@ int donof_ri_transform(donof_ri_ctx* ctx, const double* C, int mode) {
   if (!ctx || !C || (mode != DONOF_RI_HALF && mode != DONOF_RI_FULL)) return DONOF_RI_E_ARG;
   const size_t nb2 = (size_t)ctx->nbf * ctx->nbf;
   cudaMemcpyKind kind = is_device_ptr(C) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  DONOF_CUDA_TRY(cudaMemcpyAsync(ctx->d_C, C, nb2 * sizeof(double), kind, ctx->stream));
-  int rc = launch_check_finite(ctx, ctx->d_C, (long long)nb2);
-  if (rc) return rc;
+  int rc;
+  {
+    ProfScope ps(ctx, DONOF_RI_ROW_OTHER);
+    DONOF_CUDA_TRY(cudaMemcpyAsync(ctx->d_C, C, nb2 * sizeof(double), kind, ctx->stream));
+    rc = launch_check_finite(ctx, ctx->d_C, (long long)nb2);
+    if (rc) return rc;
+  }
   ctx->have_half = ctx->have_full = ctx->have_ao = 0;
   rc = ctx->precision == DONOF_RI_FP64 ? path64_transform(ctx, mode) : mixed_transform(ctx, mode);
   if (rc) return rc;
@@ -266,9 +334,13 @@ int donof_ri_energy_lagrangian(donof_ri_ctx* ctx, const double* gamma, double* E
   if (!ctx->have_ao) return DONOF_RI_E_STATE;
   const size_t ng = (size_t)ctx->n_strong * ctx->n_weak_per;
   cudaMemcpyKind kind = is_device_ptr(gamma) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  DONOF_CUDA_TRY(cudaMemcpyAsync(ctx->d_gamma, gamma, ng * sizeof(double), kind, ctx->stream));
-  int rc = launch_check_finite(ctx, ctx->d_gamma, (long long)ng);
-  if (rc) return rc;
+  int rc;
+  {
+    ProfScope ps(ctx, DONOF_RI_ROW_OTHER);
+    DONOF_CUDA_TRY(cudaMemcpyAsync(ctx->d_gamma, gamma, ng * sizeof(double), kind, ctx->stream));
+    rc = launch_check_finite(ctx, ctx->d_gamma, (long long)ng);
+    if (rc) return rc;
+  }
   rc = ctx->precision == DONOF_RI_FP64 ? path64_energy(ctx) : mixed_energy(ctx);
   if (rc) return rc;
   bool host = false;

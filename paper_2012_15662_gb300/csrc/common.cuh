@@ -81,11 +81,26 @@ struct donof_ri_ctx {
 
   donof::MixedBuffers* mixed;
 
+  // profiling: event pairs per hot-path row (see donof_ri_profile)
+  int prof_enabled;
+  struct ProfRec { int row; cudaEvent_t a, b; }* prof;
+  int prof_n, prof_cap;
+
   // call-order state
   int have_half, have_full, have_ao;
 };
 
 namespace donof {
+
+// ---- profiling scope (api.cu): records an event pair around a launch group ----
+void prof_begin(donof_ri_ctx* ctx, int row, int* slot);
+void prof_end(donof_ri_ctx* ctx, int slot);
+struct ProfScope {
+  donof_ri_ctx* ctx;
+  int slot;
+  ProfScope(donof_ri_ctx* c, int row) : ctx(c), slot(-1) { prof_begin(c, row, &slot); }
+  ~ProfScope() { prof_end(ctx, slot); }
+};
 
 // ---- launch helpers (defined in setup64.cu) ----
 int launch_dgemm(donof_ri_ctx* ctx, const Gemm64& g);

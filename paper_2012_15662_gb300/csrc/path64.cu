@@ -52,6 +52,7 @@ int path64_transform(donof_ri_ctx* ctx, int mode) {
   int rc;
   // Table 2/3 step 2: b^P_{p nu} = sum_mu C_{mu p} B^P_{mu nu}
   {
+    ProfScope ps(ctx, DONOF_RI_ROW_HALF);
     Gemm64 g{};
     g.M = m; g.N = nb; g.K = nb; g.batch = nx;
     g.A = ctx->d_C; g.sAb = 0; g.sAm = nb; g.sAk = 1;
@@ -61,11 +62,15 @@ int path64_transform(donof_ri_ctx* ctx, int mode) {
     if ((rc = launch_dgemm(ctx, g))) return rc;
   }
   // Table 3 step 3: b^P_pp
-  diag64_kernel<<<ceil_div_u((long long)nx * m * 32, 256), 256, 0, ctx->stream>>>(nb, nx, m, ctx->d_bh, ctx->d_C,
-                                                                                   ctx->d_d);
-  DONOF_LAUNCH_CHECK(ctx);
+  {
+    ProfScope ps(ctx, DONOF_RI_ROW_DIAG);
+    diag64_kernel<<<ceil_div_u((long long)nx * m * 32, 256), 256, 0, ctx->stream>>>(nb, nx, m, ctx->d_bh, ctx->d_C,
+                                                                                     ctx->d_d);
+    DONOF_LAUNCH_CHECK(ctx);
+  }
   if (mode == DONOF_RI_FULL) {
     // Table 2 step 3: b^P_pq = sum_nu C_{nu q} b^P_{p nu}
+    ProfScope ps(ctx, DONOF_RI_ROW_FULL_K);
     Gemm64 g{};
     g.M = m; g.N = m; g.K = nb; g.batch = nx;
     g.A = ctx->d_bh; g.sAb = (long long)m * nb; g.sAm = nb; g.sAk = 1;
@@ -76,7 +81,10 @@ int path64_transform(donof_ri_ctx* ctx, int mode) {
     // Table 2 step 4: K_pq = sum_P (b^P_pq)^2
     sqsum64_kernel<<<ceil_div_u((long long)m * m, 256), 256, 0, ctx->stream>>>(nx, m, ctx->d_bf, ctx->d_K);
     DONOF_LAUNCH_CHECK(ctx);
+  }
+  if (mode == DONOF_RI_FULL) {
     // Table 2 step 4: J_pq = sum_P b^P_pp b^P_qq
+    ProfScope ps(ctx, DONOF_RI_ROW_J);
     Gemm64 h{};
     h.M = m; h.N = m; h.K = nx; h.batch = 1;
     h.A = ctx->d_d; h.sAm = 1; h.sAk = m;
@@ -94,6 +102,7 @@ int path64_jk_ao(donof_ri_ctx* ctx) {
   int rc;
   // Table 3 step 4: J^(q)_{mu nu} = sum_P b^P_qq B^P_{mu nu}
   {
+    ProfScope ps(ctx, DONOF_RI_ROW_JAO);
     Gemm64 g{};
     g.M = m; g.N = (int)nb2; g.K = nx; g.batch = 1;
     g.A = ctx->d_d; g.sAm = 1; g.sAk = m;
@@ -104,6 +113,7 @@ int path64_jk_ao(donof_ri_ctx* ctx) {
   }
   // Table 3 step 3 (K): K^(q)_{mu nu} = sum_P b^P_{q mu} b^P_{q nu}
   {
+    ProfScope ps(ctx, DONOF_RI_ROW_KAO);
     Gemm64 g{};
     g.M = nb; g.N = nb; g.K = nx; g.batch = m;
     g.A = ctx->d_bh; g.sAb = nb; g.sAm = 1; g.sAk = (long long)m * nb;
@@ -249,6 +259,7 @@ int path64_energy(donof_ri_ctx* ctx) {
   const int nb = ctx->nbf, m = ctx->n_omega;
   const long long nb2 = (long long)nb * nb;
   int rc;
+  ProfScope ps(ctx, DONOF_RI_ROW_ENERGY);
   if ((rc = launch_occupations_coupling(ctx))) return rc;
   // W[p] = sum_q A_pq J^(q) - B_pq K^(q)
   {

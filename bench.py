@@ -223,6 +223,7 @@ def main():
     ap.add_argument("--precision", default="tf32x3", choices=["tf32x3", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="launch eagerly instead of replaying a CUDA graph")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -268,11 +269,9 @@ def main():
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     torch.cuda.synchronize()
 
-    def step():
-        bd.donof_ri_transform(eng.ctx, C_dev, bd.DONOF_RI_FULL)
-        bd.donof_ri_jk_mo(eng.ctx, J_dev, K_dev)
-        bd.donof_ri_jk_ao_batch(eng.ctx)
-        bd.donof_ri_energy_lagrangian(eng.ctx, g_dev, E_dev, L_dev)
+    def step(graph=not args.no_graph):
+        bd.donof_ri_iteration(eng.ctx, C_dev, g_dev, bd.DONOF_RI_FULL, J_dev, K_dev, E_dev, L_dev,
+                              use_graph=graph)
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -287,7 +286,6 @@ def main():
 
     sampler = ClockSampler(local_rank)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    bd.donof_ri_profile(eng.ctx, True)
     l0 = bd.donof_ri_launch_count(eng.ctx)
     barrier()
     sampler.start()
@@ -303,6 +301,14 @@ def main():
     launches = bd.donof_ri_launch_count(eng.ctx) - l0
     bd.donof_ri_sync(eng.ctx)
     step_ms = [a.elapsed_time(b) for a, b in evs]
+    # Per-row kernel durations: the same steps launched eagerly with CUDA events recorded on the
+    # engine's stream around every launch group of a row (graphs carry no profiling events).
+    bd.donof_ri_profile(eng.ctx, True)
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            flush.zero_()
+            step(graph=False)
+    barrier()
     rows = {}
     for i, r in enumerate(ROWS):
         t, c = bd.donof_ri_profile_read(eng.ctx, i)
@@ -328,10 +334,7 @@ def main():
         L_h = torch.empty(nb * nb, dtype=torch.float64).pin_memory()
 
         def step_host():
-            bd.donof_ri_transform(eng.ctx, C_h, bd.DONOF_RI_FULL)
-            bd.donof_ri_jk_mo(eng.ctx, J_h, K_h)
-            bd.donof_ri_jk_ao_batch(eng.ctx)
-            bd.donof_ri_energy_lagrangian(eng.ctx, g_h, E_h, L_h)
+            bd.donof_ri_iteration(eng.ctx, C_h, g_h, bd.DONOF_RI_FULL, J_h, K_h, E_h, L_h)
 
         for _ in range(args.warmup):
             step_host()
@@ -382,6 +385,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": desc, "precision": args.precision,
                    "l2": "flushed between steps (256 MB write, outside the step events)",
+                   "launch": "eager" if args.no_graph else "one CUDA graph per step (donof_ri_iteration)",
                    "parallelism": f"replicas x{world}"},
         "rows_ms_per_step": {r: rows[r][0] / args.steps for r in ROWS},
         "roofline": roof, "clocks": clocks, "gpu_launches": int(launches), "e2e": e2e,

@@ -154,6 +154,21 @@ int donof_ri_jk_ao_batch(donof_ri_ctx* ctx, double* Jao, double* Kao);
  */
 int donof_ri_energy_lagrangian(donof_ri_ctx* ctx, const double* gamma, double* E, double* lambda);
 
+/*
+ * One whole PNOF7 iteration of the engine in one call: donof_ri_transform(C,
+ * mode); for FULL, donof_ri_jk_mo(J, K); donof_ri_jk_ao_batch(NULL, NULL);
+ * donof_ri_energy_lagrangian(gamma, E, lambda).  Arguments as in those calls
+ * (J, K, E, lambda may be NULL).
+ * use_graph != 0: when every non-NULL pointer is device memory and the
+ * context's stream is not the legacy default stream, the launch sequence is
+ * captured once into a CUDA graph, keyed by (C, gamma, mode, J, K, E, lambda),
+ * and replayed on later calls with the same key (one graph launch per
+ * iteration).  Otherwise the calls run eagerly.  Profiling events are not
+ * recorded inside graphs.  Errors: as the four calls; E_CUDA if capture fails.
+ */
+int donof_ri_iteration(donof_ri_ctx* ctx, const double* C, const double* gamma, int mode, double* J, double* K,
+                       double* E, double* lambda, int use_graph);
+
 /* Internal arrays readable through donof_ri_fetch (converted to FP64). */
 #define DONOF_RI_FETCH_B 0        /* [naux][nbf][nbf]   fitted tensor B^P_{mu nu}      */
 #define DONOF_RI_FETCH_BHALF 1    /* [naux][N_Omega][nbf] b^P_{p nu}                   */

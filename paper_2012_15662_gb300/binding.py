@@ -43,6 +43,7 @@ EXPORTS = [
     "donof_ri_init", "donof_ri_transform", "donof_ri_jk_mo", "donof_ri_jk_ao_batch",
     "donof_ri_energy_lagrangian", "donof_ri_fetch", "donof_ri_sync", "donof_ri_destroy",
     "donof_ri_strerror", "donof_ri_launch_count", "donof_ri_profile", "donof_ri_profile_read",
+    "donof_ri_iteration",
 ]
 
 ROWS = ["half", "diag", "full_k", "j", "jao", "kao", "energy", "other"]
@@ -91,6 +92,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.donof_ri_strerror.restype = ctypes.c_char_p
     lib.donof_ri_launch_count.argtypes = [vp]
     lib.donof_ri_launch_count.restype = ctypes.c_longlong
+    lib.donof_ri_iteration.argtypes = [vp, vp, vp, i, vp, vp, vp, vp, i]
+    lib.donof_ri_iteration.restype = i
     lib.donof_ri_profile.argtypes = [vp, i]
     lib.donof_ri_profile.restype = i
     lib.donof_ri_profile_read.argtypes = [vp, i, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong)]
@@ -182,6 +185,11 @@ def donof_ri_destroy(ctx):
 
 def donof_ri_launch_count(ctx) -> int:
     return int(load().donof_ri_launch_count(ctx))
+
+
+def donof_ri_iteration(ctx, C, gamma, mode: int, J=None, K=None, E=None, lam=None, use_graph: bool = True):
+    _check(load().donof_ri_iteration(ctx, _ptr(C), _ptr(gamma), int(mode), _ptr(J), _ptr(K), _ptr(E), _ptr(lam),
+                                     1 if use_graph else 0), "donof_ri_iteration")
 
 
 def donof_ri_profile(ctx, enable: bool):

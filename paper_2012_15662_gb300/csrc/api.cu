@@ -19,7 +19,7 @@ using namespace donof;
 namespace donof {
 void prof_begin(donof_ri_ctx* ctx, int row, int* slot) {
   *slot = -1;
-  if (!ctx->prof_enabled) return;
+  if (!ctx->prof_enabled || ctx->capturing) return;
   if (ctx->prof_n == ctx->prof_cap) {
     int cap = ctx->prof_cap ? 2 * ctx->prof_cap : 256;
     void* p = realloc(ctx->prof, sizeof(*ctx->prof) * cap);
@@ -139,6 +139,7 @@ int donof_ri_destroy(donof_ri_ctx* ctx) {
     if (ctx->prof[i].b) cudaEventDestroy(ctx->prof[i].b);
   }
   free(ctx->prof);
+  if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
   void* bufs[] = {ctx->d_atom_xyz, ctx->d_atom_charge, ctx->d_bf_atom, ctx->d_bf_alpha, ctx->d_aux_atom,
                   ctx->d_aux_alpha, ctx->d_subspace, ctx->d_weak_rank, ctx->d_S, ctx->d_H, ctx->d_G, ctx->d_B,
                   ctx->d_enuc, ctx->d_scratch_max, ctx->d_C, ctx->d_bh, ctx->d_d, ctx->d_bf, ctx->d_J, ctx->d_K,
@@ -347,6 +348,64 @@ int donof_ri_energy_lagrangian(donof_ri_ctx* ctx, const double* gamma, double* E
   if ((rc = copy_out(ctx, E, ctx->d_E, 1, &host))) return rc;
   if ((rc = copy_out(ctx, lambda, ctx->d_lambda, (size_t)ctx->nbf * ctx->nbf, &host))) return rc;
   return host ? consume_status(ctx) : DONOF_RI_OK;
+}
+
+static int iteration_eager(donof_ri_ctx* ctx, const double* C, const double* gamma, int mode, double* J, double* K,
+                           double* E, double* lambda) {
+  int rc = donof_ri_transform(ctx, C, mode);
+  if (rc) return rc;
+  if (mode == DONOF_RI_FULL && (J || K)) {
+    if ((rc = donof_ri_jk_mo(ctx, J, K))) return rc;
+  }
+  if ((rc = donof_ri_jk_ao_batch(ctx, nullptr, nullptr))) return rc;
+  return donof_ri_energy_lagrangian(ctx, gamma, E, lambda);
+}
+
+int donof_ri_iteration(donof_ri_ctx* ctx, const double* C, const double* gamma, int mode, double* J, double* K,
+                       double* E, double* lambda, int use_graph) {
+  if (!ctx || !C || !gamma || (mode != DONOF_RI_HALF && mode != DONOF_RI_FULL)) return DONOF_RI_E_ARG;
+  const void* key[7] = {C, gamma, J, K, E, lambda, nullptr};
+  bool graphable = use_graph && ctx->stream != nullptr;
+  for (int i = 0; i < 6 && graphable; ++i)
+    if (key[i] && !is_device_ptr(key[i])) graphable = false;
+  if (!graphable) return iteration_eager(ctx, C, gamma, mode, J, K, E, lambda);
+  bool hit = ctx->graph_exec && ctx->graph_mode == mode;
+  for (int i = 0; i < 7 && hit; ++i) hit = ctx->graph_key[i] == key[i];
+  if (!hit) {
+    if (ctx->graph_exec) {
+      cudaGraphExecDestroy(ctx->graph_exec);
+      ctx->graph_exec = nullptr;
+    }
+    DONOF_CUDA_TRY(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    ctx->capturing = 1;
+    long long l0 = ctx->launches;
+    int rc = iteration_eager(ctx, C, gamma, mode, J, K, E, lambda);
+    ctx->capturing = 0;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+    if (rc || e != cudaSuccess || !g) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return rc ? rc : DONOF_RI_E_CUDA;
+    }
+    e = cudaGraphInstantiate(&ctx->graph_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      ctx->graph_exec = nullptr;
+      cudaGetLastError();
+      return DONOF_RI_E_CUDA;
+    }
+    ctx->graph_launches = ctx->launches - l0;
+    ctx->launches = l0;
+    for (int i = 0; i < 7; ++i) ctx->graph_key[i] = key[i];
+    ctx->graph_mode = mode;
+  }
+  DONOF_CUDA_TRY(cudaGraphLaunch(ctx->graph_exec, ctx->stream));
+  ctx->launches += ctx->graph_launches;
+  ctx->have_half = 1;
+  ctx->have_full = (mode == DONOF_RI_FULL);
+  ctx->have_ao = 1;
+  return DONOF_RI_OK;
 }
 
 int donof_ri_fetch(donof_ri_ctx* ctx, int what, double* dst, size_t count) {

@@ -88,6 +88,13 @@ struct donof_ri_ctx {
 
   // call-order state
   int have_half, have_full, have_ao;
+
+  // CUDA graph of donof_ri_iteration (see the header)
+  int capturing;
+  cudaGraphExec_t graph_exec;
+  const void* graph_key[7];
+  int graph_mode;
+  long long graph_launches;
 };
 
 namespace donof {

@@ -135,25 +135,31 @@ int path64_jk_ao(donof_ri_ctx* ctx) {
 // ---------------------------------------------------------------------------
 __global__ void occupations_kernel(int n_strong, int n_weak_per, int n_om, const int* subspace,
                                    const int* weak_rank, const double* gamma, double* n) {
-  int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= n_strong) return;
-  double cg = cos(gamma[g]);
-  double ng = 0.5 * (1.0 + cg * cg);
-  double hg = 1.0 - ng;
-  for (int p = 0; p < n_om; ++p) {
-    if (subspace[p] != g) continue;
-    int r = weak_rank[p];
-    if (r < 0) { n[p] = ng; continue; }
-    double carry = 1.0, alpha = 0.0;
-    for (int i = 0; i <= r; ++i) {
-      if (i == n_weak_per - 1) { alpha = carry; break; }
-      double th = gamma[n_strong + g * (n_weak_per - 1) + i];
-      double c = cos(th), s = sin(th);
-      if (i == r) { alpha = carry * c * c; break; }
-      carry *= s * s;
-    }
-    n[p] = hg * alpha;
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n_om) return;
+  const int g = subspace[p];
+  const int r = weak_rank[p];
+  const double cg = cos(gamma[g]);
+  const double ng = 0.5 * (1.0 + cg * cg);
+  if (r < 0) {
+    n[p] = ng;
+    return;
   }
+  double carry = 1.0, alpha = 0.0;
+  for (int i = 0; i <= r; ++i) {
+    if (i == n_weak_per - 1) {
+      alpha = carry;
+      break;
+    }
+    double th = gamma[n_strong + g * (n_weak_per - 1) + i];
+    double c = cos(th), sn = sin(th);
+    if (i == r) {
+      alpha = carry * c * c;
+      break;
+    }
+    carry *= sn * sn;
+  }
+  n[p] = (1.0 - ng) * alpha;
 }
 
 __global__ void coupling_kernel(int n_om, const int* subspace, const int* weak_rank, const double* n, double* A,
@@ -178,7 +184,7 @@ __global__ void coupling_kernel(int n_om, const int* subspace, const int* weak_r
 
 int launch_occupations_coupling(donof_ri_ctx* ctx) {
   const int m = ctx->n_omega;
-  occupations_kernel<<<ceil_div_u(ctx->n_strong, 64), 64, 0, ctx->stream>>>(
+  occupations_kernel<<<ceil_div_u(m, 128), 128, 0, ctx->stream>>>(
       ctx->n_strong, ctx->n_weak_per, m, ctx->d_subspace, ctx->d_weak_rank, ctx->d_gamma, ctx->d_n);
   DONOF_LAUNCH_CHECK(ctx);
   coupling_kernel<<<ceil_div_u((long long)m * m, 256), 256, 0, ctx->stream>>>(m, ctx->d_subspace, ctx->d_weak_rank,
@@ -225,6 +231,62 @@ __global__ void energy_reduce_kernel(int nbf, int n_om, const double* C, const d
 int launch_energy_reduce(donof_ri_ctx* ctx) {
   energy_reduce_kernel<<<1, 256, 0, ctx->stream>>>(ctx->nbf, ctx->n_omega, ctx->d_C, ctx->d_HC, ctx->d_n,
                                                    ctx->d_lambda, ctx->d_enuc, ctx->d_E);
+  DONOF_LAUNCH_CHECK(ctx);
+  return DONOF_RI_OK;
+}
+
+// out[i*so_i + j*so_j] = sum_k A[i*lda + k] B[j*ldb + k] (+ add[i*so_i + j*so_j] * scale[j] when add
+// is given), FP64, one warp per output with a fixed shuffle tree (deterministic).  Used for the small
+// products of the energy row, where a 64x64-tile GEMM would leave most SMs idle.
+__global__ void dot64_kernel(int M, int N, int K, const double* A, int lda, const double* B, int ldb, double* out,
+                             long long so_i, long long so_j) {
+  long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / 32;
+  int lane = threadIdx.x % 32;
+  if (w >= (long long)M * N) return;
+  int i = (int)(w / N), j = (int)(w % N);
+  const double* a = A + (long long)i * lda;
+  const double* b = B + (long long)j * ldb;
+  double s = 0.0;
+  for (int k = lane; k < K; k += 32) s = fma(a[k], b[k], s);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) out[i * so_i + j * so_j] = s;
+}
+
+int launch_dot64(donof_ri_ctx* ctx, int M, int N, int K, const double* A, int lda, const double* B, int ldb,
+                 double* out, long long so_i, long long so_j) {
+  dot64_kernel<<<ceil_div_u((long long)M * N * 32, 256), 256, 0, ctx->stream>>>(M, N, K, A, lda, B, ldb, out, so_i,
+                                                                               so_j);
+  DONOF_LAUNCH_CHECK(ctx);
+  return DONOF_RI_OK;
+}
+
+// E = E_nuc + sum_p (n_p H_pp + lambda_pp) with H_pp = C_p^T (H C)_p taken from HCt[p][mu]
+// (rows p, stride nbf).  One block, one warp per p, fixed reduction order.
+__global__ void energy_rows_kernel(int nbf, int n_om, const double* C, const double* HCt, const double* n,
+                                   const double* lambda, const double* enuc, double* E) {
+  __shared__ double part[32];
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  double acc = 0.0;
+  for (int p = warp; p < n_om; p += 32) {
+    const double* c = C + (long long)p * nbf;
+    const double* h = HCt + (long long)p * nbf;
+    double s = 0.0;
+    for (int mu = lane; mu < nbf; mu += 32) s = fma(c[mu], h[mu], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    acc += n[p] * s + lambda[(long long)p * nbf + p];
+  }
+  if (lane == 0) part[warp] = acc;
+  __syncthreads();
+  if (warp == 0) {
+    double v = part[lane];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) *E = *enuc + v;
+  }
+}
+
+int launch_energy_rows(donof_ri_ctx* ctx, const double* HCt) {
+  energy_rows_kernel<<<1, 1024, 0, ctx->stream>>>(ctx->nbf, ctx->n_omega, ctx->d_C, HCt, ctx->d_n, ctx->d_lambda,
+                                                  ctx->d_enuc, ctx->d_E);
   DONOF_LAUNCH_CHECK(ctx);
   return DONOF_RI_OK;
 }

@@ -39,8 +39,9 @@
 #include <string.h>
 
 namespace donof {
-int launch_lambda(donof_ri_ctx* ctx);
-int launch_hc_public(donof_ri_ctx* ctx);
+int launch_dot64(donof_ri_ctx* ctx, int M, int N, int K, const double* A, int lda, const double* B, int ldb,
+                 double* out, long long so_i, long long so_j);
+int launch_energy_rows(donof_ri_ctx* ctx, const double* HCt);
 
 enum TcKind { K_HALF = 0, K_FULLSQ = 1, K_JMO = 2, K_JAO = 3, K_KAO = 4, K_FOCK = 5, K_NKINDS = 6 };
 
@@ -585,20 +586,22 @@ __global__ void diag_mixed_kernel(const float* bh_hi, const float* bh_lo, const 
   }
 }
 
-// out[r][c] = extra(r, c) + sum_s partial[s][r][c], FP64, fixed order over s.
-// extra: mode 0 none; mode 1: n_c * HC[r][c] (Fock row assembly).
+// sum_s partial[s][r][c] in FP64 (fixed order over s).
+// mode 0: out[r][c] = sum.
+// mode 1 (Fock rows): out[c][r] = n_c HCt[c][r] + sum, i.e. Y^T with Y_{mu p} = n_p (H C)_{mu p} + Z_{mu p}.
 __global__ void reduce_partials_kernel(const float* partial, int nsplit, int rows, int cols, double* out, int mode,
-                                       const double* n, const double* HC) {
+                                       const double* n, const double* HCt) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   long long rc = (long long)rows * cols;
   if (i >= rc) return;
   double s = 0.0;
   for (int k = 0; k < nsplit; ++k) s += (double)partial[(size_t)k * rc + i];
   if (mode == 1) {
-    int c = (int)(i % cols);
-    s += n[c] * HC[i];
+    int r = (int)(i / cols), c = (int)(i % cols);
+    out[(size_t)c * rows + r] = n[c] * HCt[(size_t)c * rows + r] + s;
+  } else {
+    out[i] = s;
   }
-  out[i] = s;
 }
 
 // FOCK weights: W[q][p] = A_pq (q < N_O), W[N_O + q][p] = -B_pq.
@@ -652,6 +655,8 @@ struct donof::MixedBuffers {
   float* W;               // [2m][m]             FOCK weights
   float* partial;         // split partial sums
   size_t partial_elems;
+  double* HCt;            // [m][nb]   (H C)^T
+  double* Yt;             // [m][nb]   Y^T
   donof::TcPlan plan[donof::K_NKINDS];
   PFN_cuTensorMapEncodeTiled_v12000 encode;
 };
@@ -806,6 +811,11 @@ int mixed_init(donof_ri_ctx* ctx) {
   MALLOC(mb->W, 2 * ms * ms);
   MALLOC(mb->partial, pe);
 #undef MALLOC
+  if (cudaMalloc((void**)&mb->HCt, ms * nbs * sizeof(double)) != cudaSuccess ||
+      cudaMalloc((void**)&mb->Yt, ms * nbs * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return DONOF_RI_E_OOM;
+  }
 
   // split B into both operand layouts (one-time)
   {
@@ -915,6 +925,8 @@ void mixed_free(donof_ri_ctx* ctx) {
                    mb->bh6_hi, mb->bh6_lo, mb->d_hi, mb->d_lo, mb->JK_hi, mb->JK_lo, mb->W, mb->partial};
   for (float* b : bufs)
     if (b) cudaFree(b);
+  if (mb->HCt) cudaFree(mb->HCt);
+  if (mb->Yt) cudaFree(mb->Yt);
   free(mb);
   ctx->mixed = nullptr;
 }
@@ -932,7 +944,7 @@ static int launch_reduce(donof_ri_ctx* ctx, int kind, double* out, int mode) {
   const TcParams& p = ctx->mixed->plan[kind].p;
   long long n = (long long)p.prow * p.pcol;
   reduce_partials_kernel<<<ceil_div_u(n, 256), 256, 0, ctx->stream>>>(ctx->mixed->partial, p.nsplit, p.prow, p.pcol,
-                                                                       out, mode, ctx->d_n, ctx->d_HC);
+                                                                       out, mode, ctx->d_n, ctx->mixed->HCt);
   DONOF_LAUNCH_CHECK(ctx);
   return DONOF_RI_OK;
 }
@@ -993,11 +1005,14 @@ int mixed_energy(donof_ri_ctx* ctx) {
   if ((rc = launch_occupations_coupling(ctx))) return rc;
   fock_weights_kernel<<<ceil_div_u(2LL * m * m, 256), 256, 0, ctx->stream>>>(ctx->d_A, ctx->d_Bc, m, mb->W);
   DONOF_LAUNCH_CHECK(ctx);
-  if ((rc = launch_hc_public(ctx))) return rc;
+  const int nb = ctx->nbf;
+  // (H C)^T[p][mu] = sum_nu C_{nu p} H_{mu nu}
+  if ((rc = launch_dot64(ctx, m, nb, nb, ctx->d_C, nb, ctx->d_H, nb, mb->HCt, nb, 1))) return rc;
   if ((rc = launch_tc<K_FOCK>(ctx))) return rc;
-  if ((rc = launch_reduce(ctx, K_FOCK, ctx->d_Y, 1))) return rc;
-  if ((rc = launch_lambda(ctx))) return rc;
-  return launch_energy_reduce(ctx);
+  if ((rc = launch_reduce(ctx, K_FOCK, mb->Yt, 1))) return rc;
+  // lambda_qp = sum_mu C_{mu q} Y_{mu p}, column-major lambda[p*nb + q]
+  if ((rc = launch_dot64(ctx, m, nb, nb, mb->Yt, nb, ctx->d_C, nb, ctx->d_lambda, nb, 1))) return rc;
+  return launch_energy_rows(ctx, mb->HCt);
 }
 
 int mixed_fetch(donof_ri_ctx* ctx, int what, double* dst, size_t count) {

@@ -223,6 +223,32 @@ int donof_ri_profile(donof_ri_ctx* ctx, int enable);
  */
 int donof_ri_profile_read(donof_ri_ctx* ctx, int row, double* total_ms, long long* count);
 
+/*
+ * J_pq = sum_P b^P_pp b^P_qq with no device allocation.
+ * The paper has no counterpart: this entry point exists for callers that may
+ * not allocate device memory (code running under an allocator or memory pool
+ * that forbids cudaMalloc, or a service that must keep its device footprint
+ * fixed after start-up), so it takes no context.
+ *   d        [naux][n_omega] FP64, device: b^P_pp, e.g. from donof_ri_fetch
+ *            (DONOF_RI_FETCH_DIAG) copied to the device
+ *   J        [n_omega][n_omega] FP64 row-major, device, written asynchronously
+ *   stream   cudaStream_t to run on (NULL = legacy default stream)
+ * Arithmetic: split TF32 tensor-core products with FP32 accumulation over
+ * chunks of naux and an FP64 sum of the chunks (as DONOF_RI_TF32X3).
+ * Scratch: a file-scope device array of 24 MiB that every GPU loading the
+ * library holds until the process exits; it holds the split d (2 x n_omega x
+ * naux floats, naux rounded up to 4) and up to 16 chunk partials (n_omega^2
+ * floats each).  Sizes that do not fit return DONOF_RI_E_ARG before any work.
+ * The first call on a device (the current one) looks up the array's device
+ * address and prepares the kernel; make that first call before any stream
+ * capture.  Every call uses the same array, which keeps the last call's
+ * contents; calls whose work overlaps on the GPU (other streams, other host
+ * threads) race on it and must be serialised by the caller.  A device-side
+ * wait that times out leaves J incomplete and is not reported.
+ * Errors: E_ARG (null pointer, sizes), E_CUDA, E_UNSUPPORTED.
+ */
+int donof_ri_jmo_noalloc(const double* d, int naux, int n_omega, double* J, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -43,7 +43,7 @@ EXPORTS = [
     "donof_ri_init", "donof_ri_transform", "donof_ri_jk_mo", "donof_ri_jk_ao_batch",
     "donof_ri_energy_lagrangian", "donof_ri_fetch", "donof_ri_sync", "donof_ri_destroy",
     "donof_ri_strerror", "donof_ri_launch_count", "donof_ri_profile", "donof_ri_profile_read",
-    "donof_ri_iteration",
+    "donof_ri_iteration", "donof_ri_jmo_noalloc",
 ]
 
 ROWS = ["half", "diag", "full_k", "j", "jao", "kao", "energy", "other"]
@@ -92,6 +92,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.donof_ri_strerror.restype = ctypes.c_char_p
     lib.donof_ri_launch_count.argtypes = [vp]
     lib.donof_ri_launch_count.restype = ctypes.c_longlong
+    lib.donof_ri_jmo_noalloc.argtypes = [vp, i, i, vp, vp]
+    lib.donof_ri_jmo_noalloc.restype = i
     lib.donof_ri_iteration.argtypes = [vp, vp, vp, i, vp, vp, vp, vp, i]
     lib.donof_ri_iteration.restype = i
     lib.donof_ri_profile.argtypes = [vp, i]
@@ -190,6 +192,12 @@ def donof_ri_launch_count(ctx) -> int:
 def donof_ri_iteration(ctx, C, gamma, mode: int, J=None, K=None, E=None, lam=None, use_graph: bool = True):
     _check(load().donof_ri_iteration(ctx, _ptr(C), _ptr(gamma), int(mode), _ptr(J), _ptr(K), _ptr(E), _ptr(lam),
                                      1 if use_graph else 0), "donof_ri_iteration")
+
+
+def donof_ri_jmo_noalloc(d, naux: int, n_omega: int, J, stream=None):
+    """J from a device diagonal d [naux][n_omega] into device J, without device allocation."""
+    st = None if stream is None else ctypes.c_void_p(int(stream))
+    _check(load().donof_ri_jmo_noalloc(_ptr(d), int(naux), int(n_omega), _ptr(J), st), "donof_ri_jmo_noalloc")
 
 
 def donof_ri_profile(ctx, enable: bool):

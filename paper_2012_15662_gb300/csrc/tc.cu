@@ -1069,3 +1069,112 @@ int mixed_copy_ao(donof_ri_ctx* ctx, double* Jao, double* Kao, bool jao_dev, boo
 }
 
 }  // namespace donof
+
+// ---------------------------------------------------------------------------
+// donof_ri_jmo_noalloc: J_pq = sum_P b^P_pp b^P_qq without any device allocation.
+//
+// For callers that cannot allocate device memory themselves or through this
+// library (for example code running inside a memory pool or allocator that
+// forbids cudaMalloc, or a host that must not grow its device footprint after
+// start-up).  The split operands and the split-K partial sums live in the
+// file-scope array below, which every GPU that loads this library holds until
+// the process exits.
+// ---------------------------------------------------------------------------
+namespace donof {
+
+constexpr size_t NOALLOC_SCRATCH_FLOATS = (size_t)6 << 20;  // 24 MiB
+static __device__ __align__(256) float g_noalloc_scratch[NOALLOC_SCRATCH_FLOATS];
+
+struct NoallocDevice {
+  bool ready;
+  float* scratch;  // device address of g_noalloc_scratch on this device
+  PFN_cuTensorMapEncodeTiled_v12000 encode;
+};
+static NoallocDevice g_noalloc_dev[64];
+
+// d (FP64 [naux][m]) -> split rows [m][nxp] (hi, lo).
+__global__ void noalloc_split_diag_kernel(const double* d, int nx, int m, int nxp, float* hi, float* lo) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nx * m) return;
+  int P = i / m, pc = i % m;
+  float h, l;
+  split_tf32((float)d[i], h, l);
+  hi[(size_t)pc * nxp + P] = h;
+  lo[(size_t)pc * nxp + P] = l;
+}
+
+static int noalloc_map(PFN_cuTensorMapEncodeTiled_v12000 enc, CUtensorMap* map, const float* base, int nx, int m,
+                       int nxp, int box_rows) {
+  cuuint64_t gd[2] = {(cuuint64_t)nx, (cuuint64_t)m};
+  cuuint64_t gs[1] = {(cuuint64_t)nxp * 4};
+  cuuint32_t bd[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base, gd, gs, bd, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? DONOF_RI_OK : DONOF_RI_E_CUDA;
+}
+
+}  // namespace donof
+
+extern "C" int donof_ri_jmo_noalloc(const double* d, int naux, int n_omega, double* J, void* stream) {
+  using namespace donof;
+  if (!d || !J || naux < 1 || n_omega < 1 || naux > 65535 || n_omega > 4096) return DONOF_RI_E_ARG;
+  const int nx = naux, m = n_omega;
+  const int nxp = round_up(nx, 4);
+  const int kbt = (nx + TC_BK - 1) / TC_BK;
+  const int kbc = (kbt + 15) / 16;               // K blocks per chunk: at most 16 chunks
+  const int nchunk = (kbt + kbc - 1) / kbc;
+  const size_t split_floats = (size_t)round_up(m * nxp, 64);
+  const size_t need = 2 * split_floats + (size_t)nchunk * m * m + 64;
+  if (need > NOALLOC_SCRATCH_FLOATS) return DONOF_RI_E_ARG;
+
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return DONOF_RI_E_CUDA;
+  }
+  NoallocDevice& nd = g_noalloc_dev[dev];
+  if (!nd.ready) {
+    // One-time set-up for this device (the current one): the device address of the
+    // scratch array, the tensor-map encoder and the kernel's shared-memory opt-in.
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
+      cudaGetLastError();
+      return DONOF_RI_E_CUDA;
+    }
+    if (get_encode(&nd.encode)) return DONOF_RI_E_UNSUPPORTED;
+    nd.scratch = (float*)ptr;
+    nd.ready = true;
+  }
+  float* d_hi = nd.scratch;
+  float* d_lo = nd.scratch + split_floats;
+  float* partial = nd.scratch + 2 * split_floats;
+  int* status = (int*)(nd.scratch + NOALLOC_SCRATCH_FLOATS - 64);
+
+  TcPlan pl{};
+  const int bn = choose_bn(m, TC_SUM_MAXBN);
+  plan_common(pl, bn, (m + TC_BM - 1) / TC_BM, (m + bn - 1) / bn, nchunk, nchunk, kbc);
+  TcParams& p = pl.p;
+  p.nb = 0; p.nx = nx; p.m = m; p.nbp = 0; p.nxp = nxp; p.mp = m;
+  p.partial = partial;
+  p.prow = m;
+  p.pcol = m;
+  p.N = m;
+  p.K = nx;
+  p.status = status;
+  if (noalloc_map(nd.encode, &p.a_hi, d_hi, nx, m, nxp, TC_BM) || noalloc_map(nd.encode, &p.a_lo, d_lo, nx, m, nxp, TC_BM) ||
+      noalloc_map(nd.encode, &p.b_hi, d_hi, nx, m, nxp, bn) || noalloc_map(nd.encode, &p.b_lo, d_lo, nx, m, nxp, bn))
+    return DONOF_RI_E_CUDA;
+  if (cudaFuncSetAttribute(tc_gemm_kernel<K_JMO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return DONOF_RI_E_CUDA;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess) return DONOF_RI_E_CUDA;
+  noalloc_split_diag_kernel<<<ceil_div_u((long long)nx * m, 256), 256, 0, s>>>(d, nx, m, nxp, d_hi, d_lo);
+  tc_gemm_kernel<K_JMO><<<pl.grid, TC_THREADS, pl.smem, s>>>(p);
+  reduce_partials_kernel<<<ceil_div_u((long long)m * m, 256), 256, 0, s>>>(partial, p.nsplit, m, m, J, 0, nullptr,
+                                                                            nullptr);
+  return cudaGetLastError() == cudaSuccess ? DONOF_RI_OK : DONOF_RI_E_CUDA;
+}

@@ -146,7 +146,7 @@ class ClockSampler:
 
 
 def kernel_source_sha(precision):
-    files = ["tc.cu"] if precision == "tf32x3" else ["path64.cu", "setup64.cu"]
+    files = {"tf32x3": ["tc.cu"], "slice4": ["s4.cu"], "fp64": ["path64.cu", "setup64.cu"]}[precision]
     h = hashlib.sha256()
     for f in files:
         h.update(open(os.path.join(ROOT, "paper_2012_15662_gb300", "csrc", f), "rb").read())
@@ -220,7 +220,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c6h12")
-    ap.add_argument("--precision", default="tf32x3", choices=["tf32x3", "fp64"])
+    ap.add_argument("--precision", default="slice4", choices=["slice4", "tf32x3", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="launch eagerly instead of replaying a CUDA graph")
@@ -256,7 +256,7 @@ def main():
     dev = torch.device("cuda", local_rank)
     w, desc = workload_desc(args.workload)
     s = w.system
-    prec = bd.DONOF_RI_TF32X3 if args.precision == "tf32x3" else bd.DONOF_RI_FP64
+    prec = {"slice4": bd.DONOF_RI_SLICE4, "tf32x3": bd.DONOF_RI_TF32X3, "fp64": bd.DONOF_RI_FP64}[args.precision]
     stream = torch.cuda.Stream(device=dev)
     eng = bd.Engine(s, prec, stream=stream.cuda_stream)
     nb, m = s.nbf, s.n_omega
@@ -366,11 +366,16 @@ def main():
     if prec == bd.DONOF_RI_FP64:
         peak = NOMINAL["fp64"]
         bound, peak_note = "alu", "FP64 nominal 1.25 TFLOP/s (DFMA on CUDA cores; not measured)"
-    else:
+    elif prec == bd.DONOF_RI_TF32X3:
         bf = _peak_value(peaks, "bf16_tflops") or FALLBACK_PEAKS["bf16_tflops"]
         peak = bf * NOMINAL["tf32"] / NOMINAL["bf16"]
         bound, peak_note = "tensor", (f"TF32 dense = {peak_src} bf16 burst {bf:.0f} x 1.1/2.25; "
                                       "3 TF32 MMAs per algorithmic product")
+    else:
+        bf = _peak_value(peaks, "bf16_tflops") or FALLBACK_PEAKS["bf16_tflops"]
+        peak = bf
+        bound, peak_note = "tensor", (f"BF16 dense, {peak_src} burst {bf:.0f}; 13 BF16 MMAs per algorithmic "
+                                      "product (digit pairs)")
     traffic = read_traffic(args.workload, args.precision, dom)
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": traffic, "kernel_row": dom, "launch_ms": per_launch_ms,
@@ -381,7 +386,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if prec == bd.DONOF_RI_FP64 else "tf32x3",
+        "vs_baseline": None, "dtype": {"fp64": "f64", "tf32x3": "tf32x3", "slice4": "bf16x4-digits (exact sums)"}[args.precision],
         "data": "synthetic",
         "config": {"workload": desc, "precision": args.precision,
                    "l2": "flushed between steps (256 MB write, outside the step events)",

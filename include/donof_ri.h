@@ -62,6 +62,13 @@ extern "C" {
 #define DONOF_RI_TF32X3 1  /* split-precision tensor-core products (3 TF32 MMAs per
                               product, FP32 accumulation); FP64 metric, fitting and
                               energy/lambda sums                                     */
+#define DONOF_RI_SLICE4 2  /* fixed-point BF16 digit planes: every GEMM operand row as a
+                              power-of-two exponent and four balanced 8-bit digits;
+                              13 BF16 tensor-core MMAs per product (digit pairs of
+                              weight >= 2^-32 of the leading pair), summed exactly in
+                              FP32 within 256-wide K chunks and in int64 across
+                              chunks: FP64-class results (about 2^-31 of the row
+                              scale) from BF16 tensor cores                          */
 
 /* Transform modes. */
 #define DONOF_RI_HALF 0  /* half transform + diagonal (orbital step, Table 3)          */
@@ -106,7 +113,7 @@ typedef struct donof_ri_system {
  * (plain Cholesky in place of the paper's modified LDL^T, Sec. 2), solves for
  * the fitted tensor B (Table 2/3 step 1) and lays B out for the chosen
  * precision.  Synchronous.
- *   precision  DONOF_RI_FP64 or DONOF_RI_TF32X3
+ *   precision  DONOF_RI_FP64, DONOF_RI_TF32X3 or DONOF_RI_SLICE4
  *   stream     cudaStream_t to run on (NULL = legacy default stream)
  *   out        receives the context
  * Errors: E_ARG (sizes, pairing map), E_OOM, E_CUDA, E_METRIC_NOT_PD,

@@ -26,6 +26,7 @@ DONOF_RI_E_UNSUPPORTED = -8
 
 DONOF_RI_FP64 = 0
 DONOF_RI_TF32X3 = 1
+DONOF_RI_SLICE4 = 2
 DONOF_RI_HALF = 0
 DONOF_RI_FULL = 1
 

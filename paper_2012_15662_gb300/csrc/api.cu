@@ -134,6 +134,7 @@ int donof_ri_destroy(donof_ri_ctx* ctx) {
   if (!ctx) return DONOF_RI_OK;
   cudaStreamSynchronize(ctx->stream);
   if (ctx->mixed) mixed_free(ctx);
+  if (ctx->s4) s4_free(ctx);
   for (int i = 0; i < ctx->prof_cap; ++i) {
     if (ctx->prof[i].a) cudaEventDestroy(ctx->prof[i].a);
     if (ctx->prof[i].b) cudaEventDestroy(ctx->prof[i].b);
@@ -155,7 +156,7 @@ int donof_ri_init(const donof_ri_system* sys, int precision, void* stream, donof
   *out = nullptr;
   int rc = validate_system(sys);
   if (rc) return rc;
-  if (precision != DONOF_RI_FP64 && precision != DONOF_RI_TF32X3) return DONOF_RI_E_ARG;
+  if (precision != DONOF_RI_FP64 && precision != DONOF_RI_TF32X3 && precision != DONOF_RI_SLICE4) return DONOF_RI_E_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return DONOF_RI_E_UNSUPPORTED; }
   cudaDeviceProp prop;
@@ -228,6 +229,7 @@ int donof_ri_init(const donof_ri_system* sys, int precision, void* stream, donof
   TRY(setup_cholesky_and_fit(ctx));
   TRY(consume_status(ctx));
   if (precision == DONOF_RI_TF32X3) TRY(mixed_init(ctx));
+  if (precision == DONOF_RI_SLICE4) TRY(s4_init(ctx));
   if (cudaStreamSynchronize(s) != cudaSuccess) TRY(DONOF_RI_E_CUDA);
 #undef TRY
   *out = ctx;
@@ -282,7 +284,9 @@ int donof_ri_transform(donof_ri_ctx* ctx, const double* C, int mode) {
     if (rc) return rc;
   }
   ctx->have_half = ctx->have_full = ctx->have_ao = 0;
-  rc = ctx->precision == DONOF_RI_FP64 ? path64_transform(ctx, mode) : mixed_transform(ctx, mode);
+  rc = ctx->precision == DONOF_RI_FP64     ? path64_transform(ctx, mode)
+       : ctx->precision == DONOF_RI_TF32X3 ? mixed_transform(ctx, mode)
+                                           : s4_transform(ctx, mode);
   if (rc) return rc;
   ctx->have_half = 1;
   ctx->have_full = (mode == DONOF_RI_FULL);
@@ -313,7 +317,9 @@ int donof_ri_jk_mo(donof_ri_ctx* ctx, double* J, double* K) {
 int donof_ri_jk_ao_batch(donof_ri_ctx* ctx, double* Jao, double* Kao) {
   if (!ctx) return DONOF_RI_E_ARG;
   if (!ctx->have_half) return DONOF_RI_E_STATE;
-  int rc = ctx->precision == DONOF_RI_FP64 ? path64_jk_ao(ctx) : mixed_jk_ao(ctx);
+  int rc = ctx->precision == DONOF_RI_FP64     ? path64_jk_ao(ctx)
+           : ctx->precision == DONOF_RI_TF32X3 ? mixed_jk_ao(ctx)
+                                               : s4_jk_ao(ctx);
   if (rc) return rc;
   ctx->have_ao = 1;
   if (!Jao && !Kao) return DONOF_RI_OK;
@@ -324,7 +330,8 @@ int donof_ri_jk_ao_batch(donof_ri_ctx* ctx, double* Jao, double* Kao) {
     if ((rc = copy_out(ctx, Kao, ctx->d_Kao, n, &host))) return rc;
   } else {
     bool jd = is_device_ptr(Jao), kd = is_device_ptr(Kao);
-    if ((rc = mixed_copy_ao(ctx, Jao, Kao, jd, kd))) return rc;
+    rc = ctx->precision == DONOF_RI_TF32X3 ? mixed_copy_ao(ctx, Jao, Kao, jd, kd) : s4_copy_ao(ctx, Jao, Kao, jd, kd);
+    if (rc) return rc;
     host = (Jao && !jd) || (Kao && !kd);
   }
   return host ? consume_status(ctx) : DONOF_RI_OK;
@@ -342,7 +349,9 @@ int donof_ri_energy_lagrangian(donof_ri_ctx* ctx, const double* gamma, double* E
     rc = launch_check_finite(ctx, ctx->d_gamma, (long long)ng);
     if (rc) return rc;
   }
-  rc = ctx->precision == DONOF_RI_FP64 ? path64_energy(ctx) : mixed_energy(ctx);
+  rc = ctx->precision == DONOF_RI_FP64     ? path64_energy(ctx)
+       : ctx->precision == DONOF_RI_TF32X3 ? mixed_energy(ctx)
+                                           : s4_energy(ctx);
   if (rc) return rc;
   bool host = false;
   if ((rc = copy_out(ctx, E, ctx->d_E, 1, &host))) return rc;
@@ -428,6 +437,8 @@ int donof_ri_fetch(donof_ri_ctx* ctx, int what, double* dst, size_t count) {
   if ((what == DONOF_RI_FETCH_BHALF || what == DONOF_RI_FETCH_DIAG) && !ctx->have_half) return DONOF_RI_E_STATE;
   if (ctx->precision == DONOF_RI_TF32X3 && (what == DONOF_RI_FETCH_BHALF || what == DONOF_RI_FETCH_DIAG))
     return mixed_fetch(ctx, what, dst, count);
+  if (ctx->precision == DONOF_RI_SLICE4 && (what == DONOF_RI_FETCH_BHALF || what == DONOF_RI_FETCH_DIAG))
+    return s4_fetch(ctx, what, dst, count);
   DONOF_CUDA_TRY(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   return consume_status(ctx);
 }

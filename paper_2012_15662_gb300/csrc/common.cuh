@@ -32,6 +32,8 @@ struct Gemm64 {
 
 // Mixed-precision (split TF32) buffers, allocated only for DONOF_RI_TF32X3.
 struct MixedBuffers;
+// Digit-plane buffers, allocated only for DONOF_RI_SLICE4.
+struct S4Buffers;
 
 }  // namespace donof
 
@@ -80,6 +82,7 @@ struct donof_ri_ctx {
   int* d_status;    // [1] device-side status (DeviceStatus)
 
   donof::MixedBuffers* mixed;
+  donof::S4Buffers* s4;
 
   // profiling: event pairs per hot-path row (see donof_ri_profile)
   int prof_enabled;
@@ -128,6 +131,15 @@ void mixed_free(donof_ri_ctx* ctx);
 int mixed_transform(donof_ri_ctx* ctx, int mode);
 int mixed_jk_ao(donof_ri_ctx* ctx);
 int mixed_energy(donof_ri_ctx* ctx);
+
+// ---- digit-plane path (s4.cu) ----
+int s4_init(donof_ri_ctx* ctx);
+void s4_free(donof_ri_ctx* ctx);
+int s4_transform(donof_ri_ctx* ctx, int mode);
+int s4_jk_ao(donof_ri_ctx* ctx);
+int s4_energy(donof_ri_ctx* ctx);
+int s4_fetch(donof_ri_ctx* ctx, int what, double* dst, size_t count);
+int s4_copy_ao(donof_ri_ctx* ctx, double* Jao, double* Kao, bool jao_dev, bool kao_dev);
 
 }  // namespace donof
 

@@ -1,0 +1,1146 @@
+// Exact-accumulation BF16 digit-plane path (DONOF_RI_SLICE4) for sm_103a.
+//
+// Every GEMM operand row r is stored as a power-of-two exponent e_r and four
+// balanced base-256 digits: X_rk = 2^(e_r - 32) sum_{t=0..3} d_t 256^(3-t),
+// |d_t| <= 128, with |X_rk| <= 2^(e_r - 1).  Digits are small integers, exact in
+// BF16.  A product of operand rows i and j is
+//   sum_k A_ik B_jk = 2^(ea_i + eb_j - 64) sum_{t,u} 256^(6-t-u) sum_k dA_t dB_u,
+// and the digit-pair products with t + u <= 4 (13 of the 16) are issued as
+// tcgen05.mma kind::f16 into five FP32 TMEM accumulators, one per g = t + u.  The
+// g = 4 group is kept although it lies 2^-32 below the leading pair: for a row
+// multiplied by itself (J_pp, K^(p)_{mu mu}) its (2,2) product is a sum of squares
+// whose bias grows with K.  Each accumulator sums at most 4 pairs x 256
+// K-elements x 128^2 <= 2^24 in magnitude: every partial sum is an integer of
+// magnitude <= 2^24, so the FP32 accumulation is exact.  After every 256-wide K
+// chunk the epilogue converts the five exact sums to integers and folds them into
+// one int64 per output element (sum_g G_g 2^(32 - 8g)), so the whole reduction
+// over K is exact and independent of order; the only errors are the 32-bit
+// digit representation of the operands and the dropped pair products (g >= 5).
+// Outputs feeding another GEMM are re-digitised in integer arithmetic with
+// bound-based exponents (b_half) or exact row maxima (d, J^(q), K^(q)).
+//
+// Rows of the hot path as in tc.cu (HALF, FULLSQ, JMO, JAO, KAO, FOCK); the paper's
+// equations: Sec. 2, Tables 2 and 3, Eq. (PNOF).
+#include "common.cuh"
+#include "tcgen05.cuh"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <stdlib.h>
+
+namespace donof {
+int launch_dot64(donof_ri_ctx* ctx, int M, int N, int K, const double* A, int lda, const double* B, int ldb,
+                 double* out, long long so_i, long long so_j);
+int launch_energy_rows(donof_ri_ctx* ctx, const double* HCt);
+
+enum S4Kind { S_HALF = 0, S_FULLSQ = 1, S_JMO = 2, S_JAO = 3, S_KAO = 4, S_FOCK = 5, S_NKINDS = 6 };
+
+constexpr int S4_THREADS = 192;
+constexpr int S4_BM = 128;      // rows per tile
+constexpr int S4_BK = 64;       // BF16 elements per K block (one 128-byte swizzle row)
+constexpr int S4_CHUNK_KB = 4;  // K blocks per exact chunk (256 elements)
+constexpr int S4_PLANES = 4;
+constexpr int S4_NG = 5;        // digit-pair groups g = t + u = 0..4
+
+// Columns per tile: five groups x two ping-pong accumulator sets must fit in
+// TMEM's 512 columns (5 x 48 x 2 = 480).
+template <int KIND>
+struct S4Cfg {
+  static constexpr int BN = (KIND == S_FULLSQ) ? 32 : 48;
+};
+
+struct S4Params {
+  CUtensorMap a, b;  // digit planes, the plane index being the outermost tensor dimension
+  int stages, tmem_cols;
+  int n_tiles, nbatch, bpc, nsplit;
+  int nb, nx, m, nbp, nxp, mp;  // nbp / nxp: BF16 row strides (multiples of 8)
+  const int* ea;
+  const int* eb;
+  __nv_bfloat16* o3;
+  const int* e3;
+  long long ps3;  // plane stride of o3
+  __nv_bfloat16* o6;
+  const int* e6;
+  long long ps6;
+  float* ohi;
+  float* olo;
+  int ldo;
+  void* partial;
+  int prow, pcol;
+  const float2* w;  // FOCK weights as double-float pairs [2m][m]
+  int* status;
+  int persist;      // 1: units are whole tiles, CTA c takes tiles c, c + grid, ...
+  int ntiles;       // total tiles (persistent kinds)
+};
+
+// ---------------------------------------------------------------------------
+// integer helpers
+// ---------------------------------------------------------------------------
+// round(v * 2^s) for an int64 v, saturated to [-2^31, 2^31].
+__device__ __forceinline__ long long shift_round(long long v, int s) {
+  long long x;
+  if (s >= 0) {
+    x = s >= 31 ? (v > 0 ? (1LL << 31) : (v < 0 ? -(1LL << 31) : 0)) : (v << s);
+  } else {
+    int sh = -s;
+    x = sh >= 62 ? 0 : ((v + (1LL << (sh - 1))) >> sh);
+  }
+  const long long lim = 1LL << 31;
+  return x > lim ? lim : (x < -lim ? -lim : x);
+}
+
+// Balanced base-256 digits of |X| <= 2^31: X = d0 256^3 + d1 256^2 + d2 256 + d3, |d| <= 128.
+__device__ __forceinline__ void digits4(long long X, float d[4]) {
+#pragma unroll
+  for (int t = 3; t >= 1; --t) {
+    const int r = (int)((X + 128) & 255) - 128;
+    d[t] = (float)r;
+    X = (X - r) >> 8;
+  }
+  d[0] = (float)(int)X;
+}
+
+// Exponent e with |x| <= 2^(e-1) for every |x| <= amax (amax >= 0); 0 for amax == 0.
+__device__ __forceinline__ int expo_of(double amax) {
+  if (!(amax > 0.0)) return 0;
+  int k;
+  frexp(amax, &k);
+  return k + 1;
+}
+
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+  s = a + b;
+  float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// (sh, sl) += (ph, pl) in double-float arithmetic.
+__device__ __forceinline__ void df_add(float& sh, float& sl, float ph, float pl) {
+  float s, e;
+  two_sum_f(sh, ph, s, e);
+  e += sl + pl;
+  sh = s + e;
+  sl = e - (sh - s);
+}
+
+// int64 * 2^k as a double-float pair, built from 32-bit pieces only (|v| < 2^55):
+// v = a 2^32 + b1 2^16 + b0 with every piece exact in FP32, summed with TwoSum.
+__device__ __forceinline__ void ll_to_df(long long v, int k, float& h, float& l) {
+  const int a = (int)(v >> 32);
+  const unsigned int lo = (unsigned int)v;
+  const float fa = ldexpf((float)a, 32), f1 = ldexpf((float)(lo >> 16), 16), f0 = (float)(lo & 0xFFFFu);
+  float s, e;
+  two_sum_f(fa, f1, s, e);
+  float s2, e2;
+  two_sum_f(s, f0, s2, e2);
+  const float t = e + e2;
+  const float hh = s2 + t;
+  const float ll = t - (hh - s2);
+  h = ldexpf(hh, k);
+  l = ldexpf(ll, k);
+}
+
+// ---------------------------------------------------------------------------
+// The digit-plane GEMM kernel
+// ---------------------------------------------------------------------------
+template <int KIND>
+__device__ __forceinline__ void s4_unit(const S4Params& p, int b, int& batch, int& kb0, int& nkb) {
+  const int KBb = (p.nb + S4_BK - 1) / S4_BK, KBx = (p.nx + S4_BK - 1) / S4_BK;
+  if (KIND == S_HALF) { batch = 0; kb0 = 0; nkb = KBb; }
+  else if (KIND == S_FULLSQ) { batch = b; kb0 = 0; nkb = KBb; }
+  else if (KIND == S_JMO) { batch = 0; kb0 = b * S4_CHUNK_KB; nkb = min(S4_CHUNK_KB, KBx - kb0); }
+  else if (KIND == S_JAO) { batch = 0; kb0 = 0; nkb = KBx; }
+  else if (KIND == S_KAO) { batch = b; kb0 = 0; nkb = KBx; }
+  else {
+    const int nc = (KBb + S4_CHUNK_KB - 1) / S4_CHUNK_KB;
+    batch = b / nc;
+    kb0 = (b % nc) * S4_CHUNK_KB;
+    nkb = min(S4_CHUNK_KB, KBb - kb0);
+  }
+}
+
+template <int KIND>
+__device__ __forceinline__ void s4_loads(const S4Params& p, uint8_t* st, uint64_t* bar, int mt, int nt, int batch,
+                                         int kb) {
+  constexpr int BN = S4Cfg<KIND>::BN;
+  const int k0 = kb * S4_BK, n0 = nt * BN;
+#pragma unroll
+  for (int t = 0; t < S4_PLANES; ++t) {
+    uint8_t* da = st + t * (S4_BM * 128);
+    uint8_t* db = st + S4_PLANES * (S4_BM * 128) + t * (BN * 128);
+    if (KIND == S_HALF) {
+      const int nvb = (p.nb + 7) / 8;
+      tma_load_4d(da, &p.a, bar, k0, (mt % nvb) * 8, (mt / nvb) * 16, t);
+      tma_load_3d(db, &p.b, bar, k0, n0, t);
+    } else if (KIND == S_FULLSQ || KIND == S_FOCK) {
+      tma_load_4d(da, &p.a, bar, k0, mt * S4_BM, batch, t);
+      tma_load_3d(db, &p.b, bar, k0, n0, t);
+    } else if (KIND == S_JMO || KIND == S_JAO) {
+      tma_load_3d(da, &p.a, bar, k0, mt * S4_BM, t);
+      tma_load_3d(db, &p.b, bar, k0, n0, t);
+    } else {  // S_KAO
+      tma_load_4d(da, &p.a, bar, k0, mt * S4_BM, batch, t);
+      tma_load_4d(db, &p.b, bar, k0, n0, batch, t);
+    }
+  }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(S4_THREADS, 1) s4_gemm_kernel(const __grid_constant__ S4Params p) {
+  constexpr int BN = S4Cfg<KIND>::BN;
+  constexpr int NCH = BN / 16;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int S = p.stages;
+  constexpr uint32_t a_bytes = S4_PLANES * S4_BM * 128, b_bytes = S4_PLANES * BN * 128;
+  constexpr uint32_t stage_bytes = a_bytes + b_bytes;
+  uint64_t* full = (uint64_t*)(smem + (size_t)S * stage_bytes);
+  uint64_t* empty = full + S;
+  uint64_t* accf = empty + S;
+  uint64_t* acce = accf + 2;
+  uint64_t* drain = acce + 2;
+  uint32_t* tmem_slot = (uint32_t*)(drain + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  // Epilogue scratch (after the 256-byte barrier block), one copy per epilogue warp so
+  // that staging needs only __syncwarp: the current unit's per-column exponents /
+  // weights and, for HALF, the output exponents of the warp's rows.
+  constexpr int ES_WARP_BYTES = BN * 4 + BN * 8 + 4 * BN * 4 + BN * 8 * 4;
+  uint8_t* es_base = smem + (size_t)S * stage_bytes + 256 + (size_t)(threadIdx.x / 32 & 3) * ES_WARP_BYTES;
+  int* es_b = (int*)es_base;              // [BN]
+  float2* es_w = (float2*)(es_b + BN);    // [BN]
+  int* es_3 = (int*)(es_w + BN);          // [4][BN]: the warp's 4 auxiliary rows P
+  int* es_6 = es_3 + 4 * BN;              // [BN][8]
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  // Work assignment.  Persistent kinds: unit u is tile blockIdx.x + u*gridDim.x (one batch
+  // entry).  Other kinds: the CTA owns one tile and a contiguous range of its batch entries.
+  const int tile0 = p.persist ? (int)blockIdx.x : (int)blockIdx.x / p.nsplit;
+  const int split = p.persist ? 0 : (int)blockIdx.x % p.nsplit;
+  const int b0 = split * p.bpc;
+  const int nunits = p.persist ? max(0, (p.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x)
+                               : max(0, min(p.nbatch, b0 + p.bpc) - b0);
+  int mt = tile0 / p.n_tiles, nt = tile0 % p.n_tiles;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&accf[a], 1);
+      mbar_init(&acce[a], 128);
+    }
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, (uint32_t)p.tmem_cols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int it = 0;
+      bool ok = true;
+      for (int u = 0; u < nunits && ok; ++u) {
+        int batch, kb0, nkb;
+        s4_unit<KIND>(p, p.persist ? 0 : b0 + u, batch, kb0, nkb);
+        if (p.persist) {
+          const int tl = tile0 + u * (int)gridDim.x;
+          mt = tl / p.n_tiles;
+          nt = tl % p.n_tiles;
+        }
+        for (int kb = 0; kb < nkb; ++kb) {
+          const int s = it % S;
+          if (!mbar_wait(&empty[s], (uint32_t)(((it / S) & 1) ^ 1), abort_flag, p.status)) { ok = false; break; }
+          mbar_expect_tx(&full[s], stage_bytes);
+          s4_loads<KIND>(p, smem + (size_t)s * stage_bytes, &full[s], mt, nt, batch, kb0 + kb);
+          ++it;
+        }
+      }
+      for (int j = max(0, it - S); j < it; ++j) mbar_wait(&full[j % S], (uint32_t)((j / S) & 1), nullptr, p.status);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(BN);
+      int it = 0, cc = 0;
+      bool ok = true;
+      for (int u = 0; u < nunits && ok; ++u) {
+        int batch, kb0, nkb;
+        s4_unit<KIND>(p, p.persist ? 0 : b0 + u, batch, kb0, nkb);
+        for (int ch = 0; ch * S4_CHUNK_KB < nkb && ok; ++ch) {
+          const int set = cc & 1;
+          if (!mbar_wait(&acce[set], (uint32_t)(((cc >> 1) & 1) ^ 1), abort_flag, p.status)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t dbase = tmem_base + (uint32_t)(set * S4_NG * BN);
+          const int kbs = min(S4_CHUNK_KB, nkb - ch * S4_CHUNK_KB);
+          for (int j = 0; j < kbs; ++j) {
+            const int s = it % S;
+            if (!mbar_wait(&full[s], (uint32_t)((it / S) & 1), abort_flag, p.status)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t st = smem_u32(smem + (size_t)s * stage_bytes);
+            uint64_t dA[S4_PLANES], dB[S4_PLANES];
+#pragma unroll
+            for (int t = 0; t < S4_PLANES; ++t) {
+              dA[t] = sdesc_sw128(st + (uint32_t)t * (S4_BM * 128));
+              dB[t] = sdesc_sw128(st + a_bytes + (uint32_t)t * (BN * 128));
+            }
+            // K step ks: +32 bytes inside the 128-byte swizzle row (+2 in the descriptor's address field)
+#pragma unroll 1
+            for (int ks = 0; ks < 4; ++ks) {
+              const bool first = (j == 0 && ks == 0);
+#pragma unroll
+              for (int g = 0; g < S4_NG; ++g) {
+                const int t0 = g > 3 ? g - 3 : 0, t1 = g < 3 ? g : 3;
+#pragma unroll
+                for (int t = t0; t <= t1; ++t) {
+                  mma_bf16(dbase + (uint32_t)(g * BN), dA[t] + (uint64_t)(2 * ks), dB[g - t] + (uint64_t)(2 * ks),
+                           idesc, (first && t == t0) ? 0u : 1u);
+                }
+              }
+            }
+            mma_commit(&empty[s]);
+            ++it;
+          }
+          if (!ok) break;
+          mma_commit(&accf[set]);
+          ++cc;
+        }
+      }
+      mma_commit(drain);
+      mbar_wait(drain, 0, nullptr, p.status);
+    }
+  } else {
+    // ---------------- epilogue (warps 2..5) ----------------
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    constexpr bool UNIT_ACC = (KIND != S_FOCK);                          // int64 per output, per unit
+    constexpr bool SUM_DF = (KIND == S_FULLSQ || KIND == S_FOCK);        // double-float sum over units
+    long long acc[UNIT_ACC ? BN : 1];
+    float sh[SUM_DF ? BN : 1], sl[SUM_DF ? BN : 1];
+#pragma unroll
+    for (int i = 0; i < (UNIT_ACC ? BN : 1); ++i) acc[i] = 0;
+#pragma unroll
+    for (int i = 0; i < (SUM_DF ? BN : 1); ++i) { sh[i] = 0.f; sl[i] = 0.f; }
+    int cc = 0, units_done = 0;
+    bool ok = true;
+    for (int u = 0; u < nunits && ok; ++u) {
+      int batch, kb0, nkb;
+      s4_unit<KIND>(p, p.persist ? 0 : b0 + u, batch, kb0, nkb);
+      if (p.persist) {
+        const int tl = tile0 + u * (int)gridDim.x;
+        mt = tl / p.n_tiles;
+        nt = tl % p.n_tiles;
+      }
+      if (UNIT_ACC && KIND != S_JMO) {
+#pragma unroll
+        for (int i = 0; i < BN; ++i) acc[i] = 0;
+      }
+      // Stage this unit's column exponents (and weights) in shared memory: one pass of
+      // coalesced loads per warp instead of a dependent global load per output column.
+      if (KIND != S_JMO) {
+        __syncwarp();
+        for (int i = lane; i < BN; i += 32) {
+          const int col = nt * BN + i;
+          int e = 0;
+          if (KIND == S_KAO) e = col < p.nb ? p.eb[(size_t)batch * p.nb + col] : 0;
+          else e = col < p.m ? p.eb[col] : 0;
+          es_b[i] = e;
+          if (KIND == S_FOCK) es_w[i] = col < p.m ? p.w[(size_t)batch * p.m + col] : make_float2(0.f, 0.f);
+        }
+        if (KIND == S_HALF) {
+          const int nvb = (p.nb + 7) / 8;
+          const int Pb = mt / nvb, vb = mt % nvb;
+          for (int i = lane; i < 4 * BN; i += 32) {
+            const int P = Pb * 16 + q * 4 + i / BN, pc = nt * BN + i % BN;
+            es_3[i] = (P < p.nx && pc < p.m) ? p.e3[(size_t)P * p.m + pc] : 0;
+          }
+          for (int i = lane; i < BN * 8; i += 32) {
+            const int pc = nt * BN + i / 8, nu = vb * 8 + i % 8;
+            es_6[i] = (pc < p.m && nu < p.nb) ? p.e6[(size_t)pc * p.nb + nu] : 0;
+          }
+        }
+        __syncwarp();
+      }
+      for (int ch = 0; ch * S4_CHUNK_KB < nkb; ++ch) {
+        const int set = cc & 1;
+        if (!mbar_wait(&accf[set], (uint32_t)((cc >> 1) & 1), abort_flag, p.status)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(set * S4_NG * BN);
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+          // group g holds digit pairs with t + u = g; its weight is 2^(32 - 8 g) in units of 2^(ea+eb-48)
+          long long v[KIND == S_FOCK ? 16 : 1];
+          if (KIND == S_FOCK) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] = 0;
+          }
+#pragma unroll
+          for (int g = 0; g < S4_NG; ++g) {
+            float gv[16];
+            tmem_ld16(tb + (uint32_t)(g * BN + c * 16), gv);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const long long x = (long long)__float2int_rn(gv[j]) << (32 - 8 * g);
+              if (KIND == S_FOCK) v[KIND == S_FOCK ? j : 0] += x;
+              else acc[UNIT_ACC ? c * 16 + j : 0] += x;
+            }
+          }
+          if (KIND == S_FOCK) {
+            // unit = (q', K chunk): weighted contribution w_{q' p} (J^(q') or K^(q') C)_{mu p}
+            const int mu = mt * S4_BM + row;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int col = nt * BN + c * 16 + j;
+              if (mu < p.nb && col < p.m) {
+                const int k = p.ea[(size_t)batch * p.nb + mu] + es_b[c * 16 + j] - 48;
+                float xh, xl;
+                ll_to_df(v[KIND == S_FOCK ? j : 0], k, xh, xl);
+                const float2 wv = es_w[c * 16 + j];
+                const float wh = wv.x, wl = wv.y;
+                const float ph = xh * wh;
+                const float pl = fmaf(xh, wh, -ph) + (xh * wl + xl * wh);
+                df_add(sh[SUM_DF ? c * 16 + j : 0], sl[SUM_DF ? c * 16 + j : 0], ph, pl);
+              }
+            }
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(&acce[set]);
+        ++cc;
+      }
+      if (!ok) break;
+      // ---- unit action ----
+      if (KIND == S_HALF) {
+        const int nvb = (p.nb + 7) / 8;
+        const int P = (mt / nvb) * 16 + row / 8;
+        const int nu = (mt % nvb) * 8 + row % 8;
+        if (P < p.nx && nu < p.nb) {
+          const int ea = p.ea[(size_t)P * p.nb + nu];
+#pragma unroll
+          for (int i = 0; i < BN; ++i) {
+            const int pc = nt * BN + i;
+            if (pc < p.m) {
+              const int sb = ea + es_b[i] - 16;
+              float d[4];
+              digits4(shift_round(acc[i], sb - es_3[(lane / 8) * BN + i]), d);
+              const size_t i3 = ((size_t)P * p.mp + pc) * p.nbp + nu;
+#pragma unroll
+              for (int t = 0; t < 4; ++t) p.o3[t * p.ps3 + i3] = __float2bfloat16_rn(d[t]);
+              digits4(shift_round(acc[i], sb - es_6[i * 8 + row % 8]), d);
+              const size_t i6 = ((size_t)pc * p.nb + nu) * p.nxp + P;
+#pragma unroll
+              for (int t = 0; t < 4; ++t) p.o6[t * p.ps6 + i6] = __float2bfloat16_rn(d[t]);
+            }
+          }
+        }
+      } else if (KIND == S_FULLSQ) {
+        const int pr = mt * S4_BM + row;
+        if (pr < p.m) {
+          const int ea = p.ea[(size_t)batch * p.m + pr];
+#pragma unroll
+          for (int i = 0; i < BN; ++i) {
+            const int qc = nt * BN + i;
+            if (qc < p.m) {
+              float xh, xl;
+              ll_to_df(acc[i], ea + es_b[i] - 48, xh, xl);
+              const float ph = xh * xh;
+              const float pl = fmaf(xh, xh, -ph) + 2.f * xh * xl;
+              df_add(sh[i], sl[i], ph, pl);
+            }
+          }
+        }
+      } else if (KIND == S_JAO || KIND == S_KAO) {
+        const int r = mt * S4_BM + row;
+        int mu, nu0, ofs;
+        bool valid;
+        if (KIND == S_JAO) {
+          valid = r < p.nb * p.nb;
+          mu = r / p.nb;
+          nu0 = r % p.nb;
+          ofs = 0;
+        } else {
+          valid = r < p.nb;
+          mu = r;
+          nu0 = 0;
+          ofs = p.m + batch;
+        }
+        if (valid) {
+          const int ea = p.ea[KIND == S_JAO ? (size_t)r : (size_t)batch * p.nb + r];
+#pragma unroll
+          for (int i = 0; i < BN; ++i) {
+            const int col = nt * BN + i;
+            if (KIND == S_JAO) {
+              if (col < p.m) {
+                float h, l;
+                ll_to_df(acc[i], ea + es_b[i] - 48, h, l);
+                const size_t o = ((size_t)col * p.nb + mu) * p.ldo + nu0;
+                p.ohi[o] = h;
+                p.olo[o] = l;
+              }
+            } else {
+              if (col < p.nb) {
+                float h, l;
+                ll_to_df(acc[i], ea + es_b[i] - 48, h, l);
+                const size_t o = ((size_t)ofs * p.nb + mu) * p.ldo + col;
+                p.ohi[o] = h;
+                p.olo[o] = l;
+              }
+            }
+          }
+        }
+      }
+      ++units_done;
+    }
+    // ---- CTA results of the summing kinds ----
+    if (ok && units_done == nunits) {
+      const int r = mt * S4_BM + row;
+      if (r < p.prow) {
+        if (KIND == S_JMO) {
+          long long* dst = (long long*)p.partial + ((size_t)split * p.prow + r) * p.pcol;
+#pragma unroll
+          for (int i = 0; i < BN; ++i) {
+            const int col = nt * BN + i;
+            if (col < p.pcol) dst[col] = acc[i];
+          }
+        } else if (SUM_DF) {
+          float2* dst = (float2*)p.partial + ((size_t)split * p.prow + r) * p.pcol;
+#pragma unroll
+          for (int i = 0; i < BN; ++i) {
+            const int col = nt * BN + i;
+            if (col < p.pcol) dst[col] = make_float2(sh[i], sl[i]);
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, (uint32_t)p.tmem_cols);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// digitisation and bound kernels
+// ---------------------------------------------------------------------------
+// Rows of an FP64 matrix (element (r, k) at X[r*rs + k*cs]) -> four digit planes with the
+// row's exact exponent.  One warp per row.  Optionally writes |X| as FP32 rows (absout[r*cols + k]).
+__global__ void slice_f64_kernel(const double* X, long long rows, int cols, long long rs, long long cs,
+                                 __nv_bfloat16* planes, long long pstride, int ldp, int* exps, float* absout,
+                                 float2* dfout) {
+  long long r = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / 32;
+  int lane = threadIdx.x % 32;
+  if (r >= rows) return;
+  const double* x = X + r * rs;
+  double mx = 0.0;
+  for (int k = lane; k < cols; k += 32) mx = fmax(mx, fabs(x[k * cs]));
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  const int e = expo_of(mx);
+  if (lane == 0) exps[r] = e;
+  for (int k = lane; k < cols; k += 32) {
+    const double v = x[k * cs];
+    float d[4];
+    digits4(llrint(ldexp(v, 32 - e)), d);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) planes[t * pstride + r * ldp + k] = __float2bfloat16_rn(d[t]);
+    if (absout) absout[r * cols + k] = (float)fabs(v);
+    if (dfout) {
+      const float h = (float)v;
+      dfout[r * cols + k] = make_float2(h, (float)(v - (double)h));
+    }
+  }
+}
+
+// Rows of a double-float matrix (hi, lo; row stride ld) -> digit planes with exact row exponents.
+__global__ void slice_pair_kernel(const float* hi, const float* lo, long long rows, int cols, int ld,
+                                  __nv_bfloat16* planes, long long pstride, int ldp, int* exps) {
+  long long r = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / 32;
+  int lane = threadIdx.x % 32;
+  if (r >= rows) return;
+  const float* h = hi + r * ld;
+  const float* l = lo + r * ld;
+  float mx = 0.f;
+  for (int k = lane; k < cols; k += 32) mx = fmaxf(mx, fabsf(h[k]) + fabsf(l[k]));
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  const int e = expo_of((double)mx * (1.0 + 1.0 / 65536.0));
+  if (lane == 0) exps[r] = e;
+  for (int k = lane; k < cols; k += 32) {
+    const float hs = ldexpf(h[k], 32 - e), ls = ldexpf(l[k], 32 - e);
+    const float ih = rintf(hs);   // integer-valued, |ih| <= 2^31
+    const float top = truncf(ih * (1.f / 65536.f));
+    const long long X = ((long long)(int)top << 16) + (long long)(int)(ih - top * 65536.f) +
+                        (long long)__float2int_rn((hs - ih) + ls);
+    float d[4];
+    digits4(X, d);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) planes[t * pstride + r * ldp + k] = __float2bfloat16_rn(d[t]);
+  }
+}
+
+// Upper bounds on |b^P_{p nu}| (Table 2/3 step 2):
+//   e3[P][p] = expo(sum_mu rmaxB[P][mu] |C_{mu p}|)   (rows (P,p) of the full-transform operand)
+//   e6[p][nu] = expo(sum_mu |C_{mu p}| maxB[mu][nu])   (rows (p,nu) of the K^(p) operand)
+// rmaxB and maxB are FP32 values rounded up from FP64; the FP32 sums are inflated by
+// (1 + 2^-16) before taking the exponent so that rounding cannot lower the bound.
+__global__ void bound3_kernel(const float* rmaxB, const float* absC, int nx, int nb, int m, int* e3) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= (long long)nx * m) return;
+  int P = (int)(i / m), pc = (int)(i % m);
+  const float* r = rmaxB + (size_t)P * nb;
+  const float* c = absC + (size_t)pc * nb;
+  float s = 0.f;
+  for (int mu = 0; mu < nb; ++mu) s = fmaf(r[mu], c[mu], s);
+  e3[i] = expo_of((double)s * (1.0 + 1.0 / 65536.0));
+}
+
+__global__ void bound6_kernel(const float* maxB, const float* absC, int nb, int m, int* e6) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= (long long)m * nb) return;
+  int pc = (int)(i / nb), nu = (int)(i % nb);
+  const float* c = absC + (size_t)pc * nb;
+  float s = 0.f;
+  for (int mu = 0; mu < nb; ++mu) s = fmaf(c[mu], maxB[(size_t)mu * nb + nu], s);
+  e6[i] = expo_of((double)s * (1.0 + 1.0 / 65536.0));
+}
+
+// max over nu of |B^P_{mu nu}| -> rmaxB[P][mu], max over P -> maxB[mu][nu] (FP32, rounded up).
+__global__ void bmax_rows_kernel(const double* B, int nx, int nb, float* rmaxB) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= (long long)nx * nb) return;
+  const double* x = B + i * nb;
+  double mx = 0.0;
+  for (int k = 0; k < nb; ++k) mx = fmax(mx, fabs(x[k]));
+  rmaxB[i] = __double2float_ru(mx);
+}
+
+__global__ void bmax_aux_kernel(const double* B, int nx, int nb, float* maxB) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long nb2 = (long long)nb * nb;
+  if (i >= nb2) return;
+  double mx = 0.0;
+  for (int P = 0; P < nx; ++P) mx = fmax(mx, fabs(B[P * nb2 + i]));
+  maxB[i] = __double2float_ru(mx);
+}
+
+// b^P_pp = sum_nu b^P_{p nu} C_{nu p} (Table 3 step 3) from the L3 digit planes, compensated
+// double-float dot product per warp; writes d[p][P] in FP64.
+__global__ void diag_s4_kernel(const __nv_bfloat16* L3, long long ps3, const int* e3, const float2* Cdf, int nb,
+                               int nbp, int nx, int m, int mp, double* d) {
+  long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / 32;
+  int lane = threadIdx.x % 32;
+  if (w >= (long long)nx * m) return;
+  int P = (int)(w / m), pc = (int)(w % m);
+  const size_t rb = ((size_t)P * mp + pc) * nbp;
+  float s = 0.f, c = 0.f;
+  for (int nu = lane; nu < nb; nu += 32) {
+    // X = d0 2^24 + d1 2^16 + d2 2^8 + d3 as xh + xl, both exact in FP32
+    const float d0 = __bfloat162float(L3[rb + nu]), d1 = __bfloat162float(L3[ps3 + rb + nu]);
+    const float d2 = __bfloat162float(L3[2 * ps3 + rb + nu]), d3 = __bfloat162float(L3[3 * ps3 + rb + nu]);
+    const float xh = ((d0 * 65536.f + d1 * 256.f) + d2) * 256.f, xl = d3;
+    const float2 cv = Cdf[(size_t)pc * nb + nu];
+    const float p0 = xh * cv.x;
+    const float e0 = fmaf(xh, cv.x, -p0) + (xh * cv.y + xl * cv.x);
+    float ns, e;
+    two_sum_f(s, p0, ns, e);
+    s = ns;
+    c += e + e0;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    float so = __shfl_xor_sync(0xffffffffu, s, o);
+    float co = __shfl_xor_sync(0xffffffffu, c, o);
+    float ns, e;
+    two_sum_f(s, so, ns, e);
+    s = ns;
+    c += co + e;
+  }
+  if (lane == 0) d[(size_t)pc * nx + P] = ldexp((double)s + (double)c, e3[(size_t)P * m + pc] - 32);
+}
+
+// J_pq = 2^(ed_p + ed_q - 48) x (sum over splits of the exact int64 partials).
+__global__ void reduce_jmo_kernel(const long long* partial, int nsplit, int m, const int* ed, double* J) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m * m) return;
+  long long s = 0;
+  for (int k = 0; k < nsplit; ++k) s += partial[(size_t)k * m * m + i];
+  J[i] = ldexp((double)s, ed[i / m] + ed[i % m] - 48);
+}
+
+// sum over splits of double-float partials, FP64.  mode 1: Y^T with n_c HCt added.
+__global__ void reduce_df_kernel(const float2* partial, int nsplit, int rows, int cols, double* out, int mode,
+                                 const double* n, const double* HCt) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long rc = (long long)rows * cols;
+  if (i >= rc) return;
+  double s = 0.0;
+  for (int k = 0; k < nsplit; ++k) {
+    float2 v = partial[(size_t)k * rc + i];
+    s += (double)v.x + (double)v.y;
+  }
+  if (mode == 1) {
+    int r = (int)(i / cols), c = (int)(i % cols);
+    out[(size_t)c * rows + r] = n[c] * HCt[(size_t)c * rows + r] + s;
+  } else {
+    out[i] = s;
+  }
+}
+
+// FOCK weights as double-float pairs: W[q][p] = A_pq, W[N_O + q][p] = -B_pq.
+__global__ void fock_weights_df_kernel(const double* A, const double* Bc, int m, float2* W) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 2 * m * m) return;
+  int qq = i / m, pc = i % m;
+  const double v = qq < m ? A[(size_t)pc * m + qq] : -Bc[(size_t)pc * m + (qq - m)];
+  const float h = (float)v;
+  W[i] = make_float2(h, (float)(v - (double)h));
+}
+
+// Digit planes + row exponents -> FP64 values (fetch / copy-out paths).
+__global__ void unslice_kernel(const __nv_bfloat16* planes, long long pstride, int ldp, const int* exps,
+                               long long rows, int cols, double* out) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= rows * cols) return;
+  long long r = i / cols;
+  int k = (int)(i % cols);
+  long long X = 0;
+#pragma unroll
+  for (int t = 0; t < 4; ++t) X = X * 256 + (long long)__bfloat162float(planes[t * pstride + r * ldp + k]);
+  out[i] = ldexp((double)X, exps[r] - 32);
+}
+
+__global__ void join_pair_kernel(const float* hi, const float* lo, long long rows, int cols, int ld, double* out) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= rows * cols) return;
+  long long r = i / cols;
+  int c = (int)(i % cols);
+  out[i] = (double)hi[r * ld + c] + (double)lo[r * ld + c];
+}
+
+}  // namespace donof
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+struct donof::S4Buffers {
+  int nbp, nxp, mp, ldo;
+  __nv_bfloat16 *B1, *B5, *Ct, *L3, *L6, *Dp, *JKp;  // digit planes
+  long long psB1, psB5, psCt, psL3, psL6, psDp, psJK;
+  int *eB1, *eB5, *eC, *e3, *e6, *ed, *eJK;          // row exponents
+  float *rmaxB, *maxB, *absC;
+  float2* Cdf;    // C rows p (< N_O) as double-float pairs
+  double* dmat;   // d [m][nx] FP64
+  float *JKhi, *JKlo;
+  float2* W;
+  double* HCt;
+  double* Yt;
+  void* partial;
+  donof::S4Params plan[donof::S_NKINDS];
+  int grid[donof::S_NKINDS];
+  size_t smem[donof::S_NKINDS];
+  PFN_cuTensorMapEncodeTiled_v12000 encode;
+};
+
+namespace donof {
+
+static int s4_round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+static int s4_map(S4Buffers* sb, CUtensorMap* map, const void* base, int rank, const long long* dims,
+                  const long long* strides_el, const int* box) {
+  cuuint64_t gd[5], gs[4];
+  cuuint32_t bd[5], es[5] = {1, 1, 1, 1, 1};
+  for (int i = 0; i < rank; ++i) {
+    gd[i] = (cuuint64_t)dims[i];
+    bd[i] = (cuuint32_t)box[i];
+  }
+  for (int i = 0; i < rank - 1; ++i) {
+    gs[i] = (cuuint64_t)(strides_el[i] * 2);
+    if (gs[i] % 16) return DONOF_RI_E_ARG;
+  }
+  if (((uintptr_t)base) % 16) return DONOF_RI_E_ARG;
+  CUresult r = sb->encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, (void*)base, gd, gs, bd, es,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? DONOF_RI_OK : DONOF_RI_E_CUDA;
+}
+
+template <int KIND>
+static void s4_plan(S4Buffers* sb, int m_tiles, int n_tiles, int nbatch, int target_ctas, int persist_ctas = 0) {
+  constexpr int BN = S4Cfg<KIND>::BN;
+  S4Params& p = sb->plan[KIND];
+  const size_t stage = (size_t)S4_PLANES * (S4_BM + BN) * 128;
+  int S = (int)((220 * 1024) / stage);
+  if (S > 4) S = 4;
+  p.stages = S;
+  p.tmem_cols = 512;
+  p.n_tiles = n_tiles;
+  p.nbatch = nbatch;
+  const int tiles = m_tiles * n_tiles;
+  int ns = (target_ctas + tiles - 1) / tiles;
+  if (ns < 1) ns = 1;
+  if (ns > nbatch) ns = nbatch;
+  p.bpc = (nbatch + ns - 1) / ns;
+  p.nsplit = (nbatch + p.bpc - 1) / p.bpc;
+  sb->grid[KIND] = tiles * p.nsplit;
+  sb->smem[KIND] = 1024 + (size_t)S * stage + 256 + 4 * (size_t)(BN * (4 + 8 + 16 + 32));
+  p.persist = 0;
+  p.ntiles = tiles;
+  if (persist_ctas > 0 && nbatch == 1) {
+    p.persist = 1;
+    p.nsplit = 1;
+    p.bpc = 1;
+    sb->grid[KIND] = tiles < persist_ctas ? tiles : persist_ctas;
+  }
+}
+
+int s4_init(donof_ri_ctx* ctx) {
+  S4Buffers* sb = (S4Buffers*)calloc(1, sizeof(S4Buffers));
+  if (!sb) return DONOF_RI_E_OOM;
+  ctx->s4 = sb;
+  {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !f) {
+      cudaGetLastError();
+      return DONOF_RI_E_UNSUPPORTED;
+    }
+    sb->encode = (PFN_cuTensorMapEncodeTiled_v12000)f;
+  }
+  const int nb = ctx->nbf, nx = ctx->naux, m = ctx->n_omega;
+  const int nbp = s4_round_up(nb, 8), nxp = s4_round_up(nx, 8), mp = s4_round_up(m, 4), ldo = s4_round_up(nb, 4);
+  sb->nbp = nbp; sb->nxp = nxp; sb->mp = mp; sb->ldo = ldo;
+  const long long nbs = nb, nxs = nx, ms = m;
+  sb->psB1 = nxs * nbs * nbp;
+  sb->psB5 = nbs * nbs * nxp;
+  sb->psCt = ms * nbp;
+  sb->psL3 = nxs * mp * nbp;
+  sb->psL6 = ms * nbs * nxp;
+  sb->psDp = ms * nxp;
+  sb->psJK = 2 * ms * nbs * nbp;
+  const int sms = 152;
+  const int KBb = (nb + S4_BK - 1) / S4_BK, KBx = (nx + S4_BK - 1) / S4_BK;
+  const int bn = S4Cfg<S_HALF>::BN;  // 48 for every kind but the full transform (32)
+  s4_plan<S_HALF>(sb, ((nx + 15) / 16) * ((nb + 7) / 8), (m + bn - 1) / bn, 1, 1, sms);
+  s4_plan<S_FULLSQ>(sb, (m + S4_BM - 1) / S4_BM, (m + 31) / 32, nx, 2 * sms);
+  s4_plan<S_JMO>(sb, (m + S4_BM - 1) / S4_BM, (m + bn - 1) / bn, (KBx + S4_CHUNK_KB - 1) / S4_CHUNK_KB, 2 * sms);
+  s4_plan<S_JAO>(sb, (nb * nb + S4_BM - 1) / S4_BM, (m + bn - 1) / bn, 1, 1, sms);
+  s4_plan<S_KAO>(sb, (nb + S4_BM - 1) / S4_BM, (nb + bn - 1) / bn, m, sms);
+  s4_plan<S_FOCK>(sb, (nb + S4_BM - 1) / S4_BM, (m + bn - 1) / bn, 2 * m * ((KBb + S4_CHUNK_KB - 1) / S4_CHUNK_KB), sms);
+  size_t pbytes = (size_t)sb->plan[S_FULLSQ].nsplit * m * m * sizeof(float2);
+  size_t t = (size_t)sb->plan[S_JMO].nsplit * m * m * sizeof(long long);
+  if (t > pbytes) pbytes = t;
+  t = (size_t)sb->plan[S_FOCK].nsplit * nb * m * sizeof(float2);
+  if (t > pbytes) pbytes = t;
+
+#define ALLOC(ptr, bytes)                                           \
+  do {                                                              \
+    if (cudaMalloc((void**)&(ptr), (size_t)(bytes)) != cudaSuccess) { \
+      cudaGetLastError();                                           \
+      return DONOF_RI_E_OOM;                                        \
+    }                                                               \
+  } while (0)
+  ALLOC(sb->B1, 4 * sb->psB1 * 2);
+  ALLOC(sb->B5, 4 * sb->psB5 * 2);
+  ALLOC(sb->Ct, 4 * sb->psCt * 2);
+  ALLOC(sb->L3, 4 * sb->psL3 * 2);
+  ALLOC(sb->L6, 4 * sb->psL6 * 2);
+  ALLOC(sb->Dp, 4 * sb->psDp * 2);
+  ALLOC(sb->JKp, 4 * sb->psJK * 2);
+  ALLOC(sb->eB1, nxs * nbs * 4);
+  ALLOC(sb->eB5, nbs * nbs * 4);
+  ALLOC(sb->eC, ms * 4);
+  ALLOC(sb->e3, nxs * ms * 4);
+  ALLOC(sb->e6, ms * nbs * 4);
+  ALLOC(sb->ed, ms * 4);
+  ALLOC(sb->eJK, 2 * ms * nbs * 4);
+  ALLOC(sb->rmaxB, nxs * nbs * 4);
+  ALLOC(sb->maxB, nbs * nbs * 4);
+  ALLOC(sb->absC, ms * nbs * 4);
+  ALLOC(sb->dmat, ms * nxs * 8);
+  ALLOC(sb->JKhi, 2 * ms * nbs * ldo * 4);
+  ALLOC(sb->JKlo, 2 * ms * nbs * ldo * 4);
+  ALLOC(sb->W, 2 * ms * ms * 8);
+  ALLOC(sb->Cdf, ms * nbs * 8);
+  ALLOC(sb->HCt, ms * nbs * 8);
+  ALLOC(sb->Yt, ms * nbs * 8);
+  ALLOC(sb->partial, pbytes);
+#undef ALLOC
+
+  // one-time digitisation of B in both operand layouts, and its maxima for the bounds
+  cudaStream_t s = ctx->stream;
+  {
+    long long rows = nxs * nbs;  // rows (P, nu) over mu (B symmetric)
+    slice_f64_kernel<<<ceil_div_u(rows * 32, 256), 256, 0, s>>>(ctx->d_B, rows, nb, nb, 1, sb->B1, sb->psB1, nbp,
+                                                                 sb->eB1, nullptr, nullptr);
+    DONOF_LAUNCH_CHECK(ctx);
+    long long rows5 = nbs * nbs;  // rows (mu nu) over P
+    slice_f64_kernel<<<ceil_div_u(rows5 * 32, 256), 256, 0, s>>>(ctx->d_B, rows5, nx, 1, nbs * nbs, sb->B5, sb->psB5,
+                                                                  nxp, sb->eB5, nullptr, nullptr);
+    DONOF_LAUNCH_CHECK(ctx);
+    bmax_rows_kernel<<<ceil_div_u(nxs * nbs, 256), 256, 0, s>>>(ctx->d_B, nx, nb, sb->rmaxB);
+    DONOF_LAUNCH_CHECK(ctx);
+    bmax_aux_kernel<<<ceil_div_u(nbs * nbs, 256), 256, 0, s>>>(ctx->d_B, nx, nb, sb->maxB);
+    DONOF_LAUNCH_CHECK(ctx);
+  }
+
+  int rc;
+  for (int k = 0; k < S_NKINDS; ++k) {
+    S4Params& p = sb->plan[k];
+    p.nb = nb; p.nx = nx; p.m = m; p.nbp = nbp; p.nxp = nxp; p.mp = mp;
+    p.status = ctx->d_status;
+    p.partial = sb->partial;
+    p.ldo = ldo;
+  }
+  {  // HALF: A = B1 [4][nx][nb][nbp] rows (P, nu) over mu; B = C^T planes [4][m][nbp]
+    S4Params& p = sb->plan[S_HALF];
+    long long dA[4] = {nb, nb, nx, 4}, sA[3] = {nbp, nbs * nbp, sb->psB1};
+    int bA[4] = {S4_BK, 8, 16, 1};
+    long long dB[3] = {nb, m, 4}, sB[2] = {nbp, sb->psCt};
+    int bB[3] = {S4_BK, bn, 1};
+    if ((rc = s4_map(sb, &p.a, sb->B1, 4, dA, sA, bA))) return rc;
+    if ((rc = s4_map(sb, &p.b, sb->Ct, 3, dB, sB, bB))) return rc;
+    p.ea = sb->eB1; p.eb = sb->eC;
+    p.o3 = sb->L3; p.e3 = sb->e3; p.ps3 = sb->psL3;
+    p.o6 = sb->L6; p.e6 = sb->e6; p.ps6 = sb->psL6;
+  }
+  {  // FULLSQ: A = L3 [4][nx][mp][nbp] rows p (per P) over nu; B = C^T planes
+    S4Params& p = sb->plan[S_FULLSQ];
+    long long dA[4] = {nb, m, nx, 4}, sA[3] = {nbp, (long long)mp * nbp, sb->psL3};
+    int bA[4] = {S4_BK, S4_BM, 1, 1};
+    long long dB[3] = {nb, m, 4}, sB[2] = {nbp, sb->psCt};
+    int bB[3] = {S4_BK, 32, 1};
+    if ((rc = s4_map(sb, &p.a, sb->L3, 4, dA, sA, bA))) return rc;
+    if ((rc = s4_map(sb, &p.b, sb->Ct, 3, dB, sB, bB))) return rc;
+    p.ea = sb->e3; p.eb = sb->eC;
+    p.prow = m; p.pcol = m;
+  }
+  {  // JMO: A = B = d planes [4][m][nxp] rows p over P
+    S4Params& p = sb->plan[S_JMO];
+    long long dA[3] = {nx, m, 4}, sA[2] = {nxp, sb->psDp};
+    int bA[3] = {S4_BK, S4_BM, 1};
+    int bB[3] = {S4_BK, bn, 1};
+    if ((rc = s4_map(sb, &p.a, sb->Dp, 3, dA, sA, bA))) return rc;
+    if ((rc = s4_map(sb, &p.b, sb->Dp, 3, dA, sA, bB))) return rc;
+    p.ea = sb->ed; p.eb = sb->ed;
+    p.prow = m; p.pcol = m;
+  }
+  {  // JAO: A = B5 [4][nb*nb][nxp] rows (mu nu) over P; B = d planes
+    S4Params& p = sb->plan[S_JAO];
+    long long dA[3] = {nx, nbs * nbs, 4}, sA[2] = {nxp, sb->psB5};
+    int bA[3] = {S4_BK, S4_BM, 1};
+    long long dB[3] = {nx, m, 4}, sB[2] = {nxp, sb->psDp};
+    int bB[3] = {S4_BK, bn, 1};
+    if ((rc = s4_map(sb, &p.a, sb->B5, 3, dA, sA, bA))) return rc;
+    if ((rc = s4_map(sb, &p.b, sb->Dp, 3, dB, sB, bB))) return rc;
+    p.ea = sb->eB5; p.eb = sb->ed;
+    p.ohi = sb->JKhi; p.olo = sb->JKlo;
+  }
+  {  // KAO: A = B = L6 [4][m][nb][nxp] rows (p, mu) over P
+    S4Params& p = sb->plan[S_KAO];
+    long long dA[4] = {nx, nb, m, 4}, sA[3] = {nxp, nbs * nxp, sb->psL6};
+    int bA[4] = {S4_BK, S4_BM, 1, 1};
+    int bB[4] = {S4_BK, bn, 1, 1};
+    if ((rc = s4_map(sb, &p.a, sb->L6, 4, dA, sA, bA))) return rc;
+    if ((rc = s4_map(sb, &p.b, sb->L6, 4, dA, sA, bB))) return rc;
+    p.ea = sb->e6; p.eb = sb->e6;
+    p.ohi = sb->JKhi; p.olo = sb->JKlo;
+  }
+  {  // FOCK: A = JK planes [4][2m][nb][nbp] rows mu (per q') over nu; B = C^T planes
+    S4Params& p = sb->plan[S_FOCK];
+    long long dA[4] = {nb, nb, 2 * ms, 4}, sA[3] = {nbp, nbs * nbp, sb->psJK};
+    int bA[4] = {S4_BK, S4_BM, 1, 1};
+    long long dB[3] = {nb, m, 4}, sB[2] = {nbp, sb->psCt};
+    int bB[3] = {S4_BK, bn, 1};
+    if ((rc = s4_map(sb, &p.a, sb->JKp, 4, dA, sA, bA))) return rc;
+    if ((rc = s4_map(sb, &p.b, sb->Ct, 3, dB, sB, bB))) return rc;
+    p.ea = sb->eJK; p.eb = sb->eC;
+    p.w = sb->W;
+    p.prow = nb; p.pcol = m;
+  }
+#define OPTIN(KIND)                                                                                           \
+  if (cudaFuncSetAttribute(s4_gemm_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,                \
+                           (int)sb->smem[KIND]) != cudaSuccess)                                               \
+    return DONOF_RI_E_CUDA;
+  OPTIN(S_HALF) OPTIN(S_FULLSQ) OPTIN(S_JMO) OPTIN(S_JAO) OPTIN(S_KAO) OPTIN(S_FOCK)
+#undef OPTIN
+  return DONOF_RI_OK;
+}
+
+void s4_free(donof_ri_ctx* ctx) {
+  S4Buffers* sb = ctx->s4;
+  if (!sb) return;
+  void* bufs[] = {sb->B1, sb->B5, sb->Ct, sb->L3, sb->L6, sb->Dp, sb->JKp, sb->eB1, sb->eB5, sb->eC, sb->e3,
+                  sb->e6, sb->ed, sb->eJK, sb->rmaxB, sb->maxB, sb->absC, sb->dmat, sb->JKhi, sb->JKlo, sb->W,
+                  sb->HCt, sb->Yt, sb->partial, sb->Cdf};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  free(sb);
+  ctx->s4 = nullptr;
+}
+
+template <int KIND>
+static int launch_s4(donof_ri_ctx* ctx) {
+  S4Buffers* sb = ctx->s4;
+  if (sb->grid[KIND] <= 0) return DONOF_RI_OK;
+  s4_gemm_kernel<KIND><<<sb->grid[KIND], S4_THREADS, sb->smem[KIND], ctx->stream>>>(sb->plan[KIND]);
+  DONOF_LAUNCH_CHECK(ctx);
+  return DONOF_RI_OK;
+}
+
+int s4_transform(donof_ri_ctx* ctx, int mode) {
+  S4Buffers* sb = ctx->s4;
+  const int nb = ctx->nbf, nx = ctx->naux, m = ctx->n_omega;
+  cudaStream_t s = ctx->stream;
+  int rc;
+  {
+    ProfScope ps(ctx, DONOF_RI_ROW_OTHER);
+    // C^T rows p over mu (C column-major = rows p contiguous)
+    slice_f64_kernel<<<ceil_div_u((long long)m * 32, 256), 256, 0, s>>>(ctx->d_C, m, nb, nb, 1, sb->Ct, sb->psCt,
+                                                                          sb->nbp, sb->eC, sb->absC, sb->Cdf);
+    DONOF_LAUNCH_CHECK(ctx);
+    bound3_kernel<<<ceil_div_u((long long)nx * m, 256), 256, 0, s>>>(sb->rmaxB, sb->absC, nx, nb, m, sb->e3);
+    DONOF_LAUNCH_CHECK(ctx);
+    bound6_kernel<<<ceil_div_u((long long)m * nb, 256), 256, 0, s>>>(sb->maxB, sb->absC, nb, m, sb->e6);
+    DONOF_LAUNCH_CHECK(ctx);
+  }
+  {
+    ProfScope ps(ctx, DONOF_RI_ROW_HALF);
+    if ((rc = launch_s4<S_HALF>(ctx))) return rc;
+  }
+  {
+    ProfScope ps(ctx, DONOF_RI_ROW_DIAG);
+    diag_s4_kernel<<<ceil_div_u((long long)nx * m * 32, 256), 256, 0, s>>>(sb->L3, sb->psL3, sb->e3, sb->Cdf, nb,
+                                                                            sb->nbp, nx, m, sb->mp, sb->dmat);
+    DONOF_LAUNCH_CHECK(ctx);
+    slice_f64_kernel<<<ceil_div_u((long long)m * 32, 256), 256, 0, s>>>(sb->dmat, m, nx, nx, 1, sb->Dp, sb->psDp,
+                                                                          sb->nxp, sb->ed, nullptr, nullptr);
+    DONOF_LAUNCH_CHECK(ctx);
+  }
+  if (mode == DONOF_RI_FULL) {
+    {
+      ProfScope ps(ctx, DONOF_RI_ROW_FULL_K);
+      if ((rc = launch_s4<S_FULLSQ>(ctx))) return rc;
+      const S4Params& p = sb->plan[S_FULLSQ];
+      reduce_df_kernel<<<ceil_div_u((long long)m * m, 256), 256, 0, s>>>((const float2*)sb->partial, p.nsplit, m, m,
+                                                                          ctx->d_K, 0, nullptr, nullptr);
+      DONOF_LAUNCH_CHECK(ctx);
+    }
+    {
+      ProfScope ps(ctx, DONOF_RI_ROW_J);
+      if ((rc = launch_s4<S_JMO>(ctx))) return rc;
+      const S4Params& p = sb->plan[S_JMO];
+      reduce_jmo_kernel<<<ceil_div_u((long long)m * m, 256), 256, 0, s>>>((const long long*)sb->partial, p.nsplit, m,
+                                                                           sb->ed, ctx->d_J);
+      DONOF_LAUNCH_CHECK(ctx);
+    }
+  }
+  return DONOF_RI_OK;
+}
+
+int s4_jk_ao(donof_ri_ctx* ctx) {
+  S4Buffers* sb = ctx->s4;
+  const int nb = ctx->nbf, m = ctx->n_omega;
+  int rc;
+  {
+    ProfScope ps(ctx, DONOF_RI_ROW_JAO);
+    if ((rc = launch_s4<S_JAO>(ctx))) return rc;
+  }
+  {
+    ProfScope ps(ctx, DONOF_RI_ROW_KAO);
+    if ((rc = launch_s4<S_KAO>(ctx))) return rc;
+  }
+  {
+    ProfScope ps(ctx, DONOF_RI_ROW_OTHER);
+    long long rows = 2LL * m * nb;
+    slice_pair_kernel<<<ceil_div_u(rows * 32, 256), 256, 0, ctx->stream>>>(sb->JKhi, sb->JKlo, rows, nb, sb->ldo,
+                                                                            sb->JKp, sb->psJK, sb->nbp, sb->eJK);
+    DONOF_LAUNCH_CHECK(ctx);
+  }
+  return DONOF_RI_OK;
+}
+
+int s4_energy(donof_ri_ctx* ctx) {
+  S4Buffers* sb = ctx->s4;
+  const int nb = ctx->nbf, m = ctx->n_omega;
+  cudaStream_t s = ctx->stream;
+  int rc;
+  ProfScope ps(ctx, DONOF_RI_ROW_ENERGY);
+  if ((rc = launch_occupations_coupling(ctx))) return rc;
+  fock_weights_df_kernel<<<ceil_div_u(2LL * m * m, 256), 256, 0, s>>>(ctx->d_A, ctx->d_Bc, m, sb->W);
+  DONOF_LAUNCH_CHECK(ctx);
+  if ((rc = launch_dot64(ctx, m, nb, nb, ctx->d_C, nb, ctx->d_H, nb, sb->HCt, nb, 1))) return rc;
+  if ((rc = launch_s4<S_FOCK>(ctx))) return rc;
+  const S4Params& p = sb->plan[S_FOCK];
+  reduce_df_kernel<<<ceil_div_u((long long)nb * m, 256), 256, 0, s>>>((const float2*)sb->partial, p.nsplit, nb, m,
+                                                                       sb->Yt, 1, ctx->d_n, sb->HCt);
+  DONOF_LAUNCH_CHECK(ctx);
+  if ((rc = launch_dot64(ctx, m, nb, nb, sb->Yt, nb, ctx->d_C, nb, ctx->d_lambda, nb, 1))) return rc;
+  return launch_energy_rows(ctx, sb->HCt);
+}
+
+int s4_fetch(donof_ri_ctx* ctx, int what, double* dst, size_t count) {
+  S4Buffers* sb = ctx->s4;
+  const int nb = ctx->nbf, nx = ctx->naux, m = ctx->n_omega;
+  cudaError_t e = cudaSuccess;
+  if (what == DONOF_RI_FETCH_BHALF) {
+    double* tmp = nullptr;
+    if (cudaMalloc((void**)&tmp, count * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      return DONOF_RI_E_OOM;
+    }
+    // rows (P, p) of the L3 planes over nu; consecutive P are mp rows apart
+    for (int P = 0; P < nx && e == cudaSuccess; ++P) {
+      unslice_kernel<<<ceil_div_u((long long)m * nb, 256), 256, 0, ctx->stream>>>(
+          sb->L3 + (size_t)P * sb->mp * sb->nbp, sb->psL3, sb->nbp, sb->e3 + (size_t)P * m, m, nb,
+          tmp + (size_t)P * m * nb);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dst, tmp, count * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(tmp);
+    return e == cudaSuccess ? DONOF_RI_OK : DONOF_RI_E_CUDA;
+  }
+  // d is kept as FP64 [p][P]; the fetch layout is [P][p]
+  double* hostbuf = (double*)malloc(count * sizeof(double));
+  if (!hostbuf) return DONOF_RI_E_OOM;
+  e = cudaMemcpyAsync(hostbuf, sb->dmat, count * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e == cudaSuccess)
+    for (int P = 0; P < nx; ++P)
+      for (int pc = 0; pc < m; ++pc) dst[(size_t)P * m + pc] = hostbuf[(size_t)pc * nx + P];
+  free(hostbuf);
+  return e == cudaSuccess ? DONOF_RI_OK : DONOF_RI_E_CUDA;
+}
+
+int s4_copy_ao(donof_ri_ctx* ctx, double* Jao, double* Kao, bool jao_dev, bool kao_dev) {
+  S4Buffers* sb = ctx->s4;
+  const int nb = ctx->nbf, m = ctx->n_omega;
+  const size_t n = (size_t)m * nb * nb;
+  double* tmp = nullptr;
+  if (cudaMalloc((void**)&tmp, n * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return DONOF_RI_E_OOM;
+  }
+  cudaError_t e = cudaSuccess;
+  for (int which = 0; which < 2 && e == cudaSuccess; ++which) {
+    double* dst = which == 0 ? Jao : Kao;
+    bool dev = which == 0 ? jao_dev : kao_dev;
+    if (!dst) continue;
+    size_t off = (size_t)which * m * nb * sb->ldo;
+    join_pair_kernel<<<ceil_div_u((long long)n, 256), 256, 0, ctx->stream>>>(sb->JKhi + off, sb->JKlo + off,
+                                                                              (long long)m * nb, nb, sb->ldo, tmp);
+    e = cudaGetLastError();
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(dst, tmp, n * sizeof(double), dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                          ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  }
+  cudaFree(tmp);
+  return e == cudaSuccess ? DONOF_RI_OK : DONOF_RI_E_CUDA;
+}
+
+}  // namespace donof

@@ -315,16 +315,23 @@ __global__ void __launch_bounds__(S4_THREADS, 1) s4_gemm_kernel(const __grid_con
     }
   } else {
     // ---------------- epilogue (warps 2..5) ----------------
+    // Each thread owns one output row (its TMEM lane).  Per 16-column block the five
+    // exact group sums of a chunk are folded into int64 values; a block is finalised
+    // (stored, squared or weighted) as soon as the last chunk of its unit is drained.
+    // The column-block loop is kept rolled to bound the code size; running sums live
+    // in small per-thread arrays (L1-backed local memory).
     const int q = warp & 3;
     const int row = q * 32 + lane;
-    constexpr bool UNIT_ACC = (KIND != S_FOCK);                          // int64 per output, per unit
-    constexpr bool SUM_DF = (KIND == S_FULLSQ || KIND == S_FOCK);        // double-float sum over units
-    long long acc[UNIT_ACC ? BN : 1];
+    constexpr bool SUM_DF = (KIND == S_FULLSQ || KIND == S_FOCK);  // double-float sum over units
+    long long acc[BN];   // running int64 sums across chunks (and, for JMO, across units)
     float sh[SUM_DF ? BN : 1], sl[SUM_DF ? BN : 1];
-#pragma unroll
-    for (int i = 0; i < (UNIT_ACC ? BN : 1); ++i) acc[i] = 0;
-#pragma unroll
-    for (int i = 0; i < (SUM_DF ? BN : 1); ++i) { sh[i] = 0.f; sl[i] = 0.f; }
+#pragma unroll 1
+    for (int i = 0; i < BN; ++i) acc[i] = 0;
+#pragma unroll 1
+    for (int i = 0; i < (SUM_DF ? BN : 1); ++i) {
+      sh[i] = 0.f;
+      sl[i] = 0.f;
+    }
     int cc = 0, units_done = 0;
     bool ok = true;
     for (int u = 0; u < nunits && ok; ++u) {
@@ -334,10 +341,6 @@ __global__ void __launch_bounds__(S4_THREADS, 1) s4_gemm_kernel(const __grid_con
         const int tl = tile0 + u * (int)gridDim.x;
         mt = tl / p.n_tiles;
         nt = tl % p.n_tiles;
-      }
-      if (UNIT_ACC && KIND != S_JMO) {
-#pragma unroll
-        for (int i = 0; i < BN; ++i) acc[i] = 0;
       }
       // Stage this unit's column exponents (and weights) in shared memory: one pass of
       // coalesced loads per warp instead of a dependent global load per output column.
@@ -365,45 +368,107 @@ __global__ void __launch_bounds__(S4_THREADS, 1) s4_gemm_kernel(const __grid_con
         }
         __syncwarp();
       }
-      for (int ch = 0; ch * S4_CHUNK_KB < nkb; ++ch) {
+      // row-dependent data of the unit
+      int ea = 0;
+      bool rvalid = false;
+      int P = 0, nu = 0, mu = 0;
+      if (KIND == S_HALF) {
+        const int nvb = (p.nb + 7) / 8;
+        P = (mt / nvb) * 16 + row / 8;
+        nu = (mt % nvb) * 8 + row % 8;
+        rvalid = P < p.nx && nu < p.nb;
+        ea = rvalid ? p.ea[(size_t)P * p.nb + nu] : 0;
+      } else if (KIND == S_FULLSQ) {
+        mu = mt * S4_BM + row;
+        rvalid = mu < p.m;
+        ea = rvalid ? p.ea[(size_t)batch * p.m + mu] : 0;
+      } else if (KIND == S_JAO) {
+        const int r = mt * S4_BM + row;
+        rvalid = r < p.nb * p.nb;
+        mu = r / p.nb;
+        nu = r % p.nb;
+        ea = rvalid ? p.ea[r] : 0;
+      } else if (KIND == S_KAO || KIND == S_FOCK) {
+        mu = mt * S4_BM + row;
+        rvalid = mu < p.nb;
+        ea = rvalid ? p.ea[(size_t)batch * p.nb + mu] : 0;
+      }
+      const int nch = (nkb + S4_CHUNK_KB - 1) / S4_CHUNK_KB;
+      for (int ch = 0; ch < nch; ++ch) {
         const int set = cc & 1;
         if (!mbar_wait(&accf[set], (uint32_t)((cc >> 1) & 1), abort_flag, p.status)) { ok = false; break; }
         tc_fence_after();
         const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(set * S4_NG * BN);
-#pragma unroll
+        const bool last = (ch == nch - 1);
+#pragma unroll 1
         for (int c = 0; c < NCH; ++c) {
           // group g holds digit pairs with t + u = g; its weight is 2^(32 - 8 g) in units of 2^(ea+eb-48)
-          long long v[KIND == S_FOCK ? 16 : 1];
-          if (KIND == S_FOCK) {
+          long long v[16];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) v[j] = 0;
-          }
+          for (int j = 0; j < 16; ++j) v[j] = (ch > 0 || KIND == S_JMO) ? acc[c * 16 + j] : 0;
 #pragma unroll
           for (int g = 0; g < S4_NG; ++g) {
             float gv[16];
             tmem_ld16(tb + (uint32_t)(g * BN + c * 16), gv);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const long long x = (long long)__float2int_rn(gv[j]) << (32 - 8 * g);
-              if (KIND == S_FOCK) v[KIND == S_FOCK ? j : 0] += x;
-              else acc[UNIT_ACC ? c * 16 + j : 0] += x;
-            }
+            for (int j = 0; j < 16; ++j) v[j] += (long long)__float2int_rn(gv[j]) << (32 - 8 * g);
           }
-          if (KIND == S_FOCK) {
-            // unit = (q', K chunk): weighted contribution w_{q' p} (J^(q') or K^(q') C)_{mu p}
-            const int mu = mt * S4_BM + row;
+          if (!last || KIND == S_JMO) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const int col = nt * BN + c * 16 + j;
-              if (mu < p.nb && col < p.m) {
-                const int k = p.ea[(size_t)batch * p.nb + mu] + es_b[c * 16 + j] - 48;
+            for (int j = 0; j < 16; ++j) acc[c * 16 + j] = v[j];
+            continue;
+          }
+          // ---- the block's values are final: unit action ----
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int i = c * 16 + j;
+            const int col = nt * BN + i;
+            if (!rvalid) continue;
+            if (KIND == S_HALF) {
+              if (col < p.m) {
+                const int sb = ea + es_b[i] - 16;
+                float d[4];
+                digits4(shift_round(v[j], sb - es_3[(lane / 8) * BN + i]), d);
+                const size_t i3 = ((size_t)P * p.mp + col) * p.nbp + nu;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) p.o3[t * p.ps3 + i3] = __float2bfloat16_rn(d[t]);
+                digits4(shift_round(v[j], sb - es_6[i * 8 + row % 8]), d);
+                const size_t i6 = ((size_t)col * p.nb + nu) * p.nxp + P;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) p.o6[t * p.ps6 + i6] = __float2bfloat16_rn(d[t]);
+              }
+            } else if (KIND == S_FULLSQ) {
+              if (col < p.m) {
                 float xh, xl;
-                ll_to_df(v[KIND == S_FOCK ? j : 0], k, xh, xl);
-                const float2 wv = es_w[c * 16 + j];
-                const float wh = wv.x, wl = wv.y;
-                const float ph = xh * wh;
-                const float pl = fmaf(xh, wh, -ph) + (xh * wl + xl * wh);
-                df_add(sh[SUM_DF ? c * 16 + j : 0], sl[SUM_DF ? c * 16 + j : 0], ph, pl);
+                ll_to_df(v[j], ea + es_b[i] - 48, xh, xl);
+                const float ph = xh * xh;
+                const float pl = fmaf(xh, xh, -ph) + 2.f * xh * xl;
+                df_add(sh[SUM_DF ? i : 0], sl[SUM_DF ? i : 0], ph, pl);
+              }
+            } else if (KIND == S_FOCK) {
+              if (col < p.m) {
+                float xh, xl;
+                ll_to_df(v[j], ea + es_b[i] - 48, xh, xl);
+                const float2 wv = es_w[i];
+                const float ph = xh * wv.x;
+                const float pl = fmaf(xh, wv.x, -ph) + (xh * wv.y + xl * wv.x);
+                df_add(sh[SUM_DF ? i : 0], sl[SUM_DF ? i : 0], ph, pl);
+              }
+            } else if (KIND == S_JAO) {
+              if (col < p.m) {
+                float h, l;
+                ll_to_df(v[j], ea + es_b[i] - 48, h, l);
+                const size_t o = ((size_t)col * p.nb + mu) * p.ldo + nu;
+                p.ohi[o] = h;
+                p.olo[o] = l;
+              }
+            } else if (KIND == S_KAO) {
+              if (col < p.nb) {
+                float h, l;
+                ll_to_df(v[j], ea + es_b[i] - 48, h, l);
+                const size_t o = ((size_t)(p.m + batch) * p.nb + mu) * p.ldo + col;
+                p.ohi[o] = h;
+                p.olo[o] = l;
               }
             }
           }
@@ -413,86 +478,6 @@ __global__ void __launch_bounds__(S4_THREADS, 1) s4_gemm_kernel(const __grid_con
         ++cc;
       }
       if (!ok) break;
-      // ---- unit action ----
-      if (KIND == S_HALF) {
-        const int nvb = (p.nb + 7) / 8;
-        const int P = (mt / nvb) * 16 + row / 8;
-        const int nu = (mt % nvb) * 8 + row % 8;
-        if (P < p.nx && nu < p.nb) {
-          const int ea = p.ea[(size_t)P * p.nb + nu];
-#pragma unroll
-          for (int i = 0; i < BN; ++i) {
-            const int pc = nt * BN + i;
-            if (pc < p.m) {
-              const int sb = ea + es_b[i] - 16;
-              float d[4];
-              digits4(shift_round(acc[i], sb - es_3[(lane / 8) * BN + i]), d);
-              const size_t i3 = ((size_t)P * p.mp + pc) * p.nbp + nu;
-#pragma unroll
-              for (int t = 0; t < 4; ++t) p.o3[t * p.ps3 + i3] = __float2bfloat16_rn(d[t]);
-              digits4(shift_round(acc[i], sb - es_6[i * 8 + row % 8]), d);
-              const size_t i6 = ((size_t)pc * p.nb + nu) * p.nxp + P;
-#pragma unroll
-              for (int t = 0; t < 4; ++t) p.o6[t * p.ps6 + i6] = __float2bfloat16_rn(d[t]);
-            }
-          }
-        }
-      } else if (KIND == S_FULLSQ) {
-        const int pr = mt * S4_BM + row;
-        if (pr < p.m) {
-          const int ea = p.ea[(size_t)batch * p.m + pr];
-#pragma unroll
-          for (int i = 0; i < BN; ++i) {
-            const int qc = nt * BN + i;
-            if (qc < p.m) {
-              float xh, xl;
-              ll_to_df(acc[i], ea + es_b[i] - 48, xh, xl);
-              const float ph = xh * xh;
-              const float pl = fmaf(xh, xh, -ph) + 2.f * xh * xl;
-              df_add(sh[i], sl[i], ph, pl);
-            }
-          }
-        }
-      } else if (KIND == S_JAO || KIND == S_KAO) {
-        const int r = mt * S4_BM + row;
-        int mu, nu0, ofs;
-        bool valid;
-        if (KIND == S_JAO) {
-          valid = r < p.nb * p.nb;
-          mu = r / p.nb;
-          nu0 = r % p.nb;
-          ofs = 0;
-        } else {
-          valid = r < p.nb;
-          mu = r;
-          nu0 = 0;
-          ofs = p.m + batch;
-        }
-        if (valid) {
-          const int ea = p.ea[KIND == S_JAO ? (size_t)r : (size_t)batch * p.nb + r];
-#pragma unroll
-          for (int i = 0; i < BN; ++i) {
-            const int col = nt * BN + i;
-            if (KIND == S_JAO) {
-              if (col < p.m) {
-                float h, l;
-                ll_to_df(acc[i], ea + es_b[i] - 48, h, l);
-                const size_t o = ((size_t)col * p.nb + mu) * p.ldo + nu0;
-                p.ohi[o] = h;
-                p.olo[o] = l;
-              }
-            } else {
-              if (col < p.nb) {
-                float h, l;
-                ll_to_df(acc[i], ea + es_b[i] - 48, h, l);
-                const size_t o = ((size_t)ofs * p.nb + mu) * p.ldo + col;
-                p.ohi[o] = h;
-                p.olo[o] = l;
-              }
-            }
-          }
-        }
-      }
       ++units_done;
     }
     // ---- CTA results of the summing kinds ----
@@ -501,17 +486,17 @@ __global__ void __launch_bounds__(S4_THREADS, 1) s4_gemm_kernel(const __grid_con
       if (r < p.prow) {
         if (KIND == S_JMO) {
           long long* dst = (long long*)p.partial + ((size_t)split * p.prow + r) * p.pcol;
-#pragma unroll
+#pragma unroll 1
           for (int i = 0; i < BN; ++i) {
             const int col = nt * BN + i;
             if (col < p.pcol) dst[col] = acc[i];
           }
         } else if (SUM_DF) {
           float2* dst = (float2*)p.partial + ((size_t)split * p.prow + r) * p.pcol;
-#pragma unroll
+#pragma unroll 1
           for (int i = 0; i < BN; ++i) {
             const int col = nt * BN + i;
-            if (col < p.pcol) dst[col] = make_float2(sh[i], sl[i]);
+            if (col < p.pcol) dst[col] = make_float2(sh[SUM_DF ? i : 0], sl[SUM_DF ? i : 0]);
           }
         }
       }

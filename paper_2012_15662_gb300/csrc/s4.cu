@@ -1,22 +1,28 @@
 // Exact-accumulation BF16 digit-plane path (DONOF_RI_SLICE4) for sm_103a.
 //
 // Every GEMM operand row r is stored as a power-of-two exponent e_r and four
-// balanced base-256 digits: X_rk = 2^(e_r - 32) sum_{t=0..3} d_t 256^(3-t),
-// |d_t| <= 128, with |X_rk| <= 2^(e_r - 1).  Digits are small integers, exact in
-// BF16.  A product of operand rows i and j is
-//   sum_k A_ik B_jk = 2^(ea_i + eb_j - 64) sum_{t,u} 256^(6-t-u) sum_k dA_t dB_u,
+// balanced base-256 digits: X_rk = 2^(e_r - 31) Xint_rk with
+//   Xint = d0 2^24 + d1 2^16 + d2 2^8 + d3,  |Xint| < 2^30,
+//   d0 in [-64, 64], d1..d3 in [-128, 127],
+// so the digits are small integers, exact in BF16, and the int32 Xint turns into
+// digits with one addition (Xint + 0x808080: the top byte is d0, the others are
+// d_t + 128).  The four digits of a row are stored interleaved per row:
+// element (r, t, k) at [(r*4 + t)*ld + k], one TMA coordinate selecting t.
+//
+// A product of operand rows i and j is
+//   sum_k A_ik B_jk = 2^(ea_i + eb_j - 62) sum_{t,u} 256^(6-t-u) sum_k dA_t dB_u,
 // and the digit-pair products with t + u <= 4 (13 of the 16) are issued as
 // tcgen05.mma kind::f16 into five FP32 TMEM accumulators, one per g = t + u.  The
-// g = 4 group is kept although it lies 2^-32 below the leading pair: for a row
-// multiplied by itself (J_pp, K^(p)_{mu mu}) its (2,2) product is a sum of squares
-// whose bias grows with K.  Each accumulator sums at most 4 pairs x 256
-// K-elements x 128^2 <= 2^24 in magnitude: every partial sum is an integer of
-// magnitude <= 2^24, so the FP32 accumulation is exact.  After every 256-wide K
-// chunk the epilogue converts the five exact sums to integers and folds them into
-// one int64 per output element (sum_g G_g 2^(32 - 8g)), so the whole reduction
-// over K is exact and independent of order; the only errors are the 32-bit
-// digit representation of the operands and the dropped pair products (g >= 5).
-// Outputs feeding another GEMM are re-digitised in integer arithmetic with
+// g = 4 group lies 2^-32 below the leading pair but is kept: for a row multiplied
+// by itself (J_pp, K^(p)_{mu mu}) its (2,2) product is a sum of squares whose bias
+// grows with K.  Each accumulator sums at most 4 pairs x 256 K-elements x 128^2
+// = 2^24 in magnitude, so every partial sum is an integer of magnitude <= 2^24 and
+// the FP32 accumulation is exact.  After every 256-wide K chunk the epilogue folds
+// the five exact sums into one int64 per output (v = sum_g G_g 2^(32 - 8g); the
+// value is 2^(ea + eb - 46) v), so the whole reduction over K is exact and
+// independent of order; the only errors are the 31-bit digit representation of
+// the operands and the dropped pair products (g >= 5).
+// Outputs feeding another GEMM are re-digitised in integer arithmetic, with
 // bound-based exponents (b_half) or exact row maxima (d, J^(q), K^(q)).
 //
 // Rows of the hot path as in tc.cu (HALF, FULLSQ, JMO, JAO, KAO, FOCK); the paper's
@@ -42,27 +48,27 @@ constexpr int S4_BK = 64;       // BF16 elements per K block (one 128-byte swizz
 constexpr int S4_CHUNK_KB = 4;  // K blocks per exact chunk (256 elements)
 constexpr int S4_PLANES = 4;
 constexpr int S4_NG = 5;        // digit-pair groups g = t + u = 0..4
+constexpr int S4_SHIFT = 46;    // value = 2^(ea + eb - 46) v
 
 // Columns per tile: five groups x two ping-pong accumulator sets must fit in
-// TMEM's 512 columns (5 x 48 x 2 = 480).
+// TMEM's 512 columns (5 x 48 x 2 = 480).  The full transform keeps running
+// int64 and double-float sums per column in registers and uses 32 columns.
 template <int KIND>
 struct S4Cfg {
   static constexpr int BN = (KIND == S_FULLSQ) ? 32 : 48;
 };
 
 struct S4Params {
-  CUtensorMap a, b;  // digit planes, the plane index being the outermost tensor dimension
+  CUtensorMap a, b;  // digit planes; coordinate 1 selects the digit
   int stages, tmem_cols;
   int n_tiles, nbatch, bpc, nsplit;
   int nb, nx, m, nbp, nxp, mp;  // nbp / nxp: BF16 row strides (multiples of 8)
   const int* ea;
   const int* eb;
-  __nv_bfloat16* o3;
+  __nv_bfloat16* o3;  // HALF: L3 digits [nx][mp][4][nbp]
   const int* e3;
-  long long ps3;  // plane stride of o3
-  __nv_bfloat16* o6;
+  __nv_bfloat16* o6;  // HALF: L6 digits [m][nb][4][nxp]
   const int* e6;
-  long long ps6;
   float* ohi;
   float* olo;
   int ldo;
@@ -75,33 +81,33 @@ struct S4Params {
 };
 
 // ---------------------------------------------------------------------------
-// integer helpers
+// integer / double-float helpers
 // ---------------------------------------------------------------------------
-// round(v * 2^s) for an int64 v, saturated to [-2^31, 2^31].
-__device__ __forceinline__ long long shift_round(long long v, int s) {
+// round(v * 2^s) as an int32, clamped to [-2^30, 2^30].
+__device__ __forceinline__ int round_shift(long long v, int s) {
   long long x;
   if (s >= 0) {
-    x = s >= 31 ? (v > 0 ? (1LL << 31) : (v < 0 ? -(1LL << 31) : 0)) : (v << s);
+    x = s >= 40 ? (v > 0 ? (1LL << 40) : (v < 0 ? -(1LL << 40) : 0)) : (v << s);
   } else {
-    int sh = -s;
-    x = sh >= 62 ? 0 : ((v + (1LL << (sh - 1))) >> sh);
+    const int sh = -s > 62 ? 62 : -s;
+    x = (v + (1LL << (sh - 1))) >> sh;
   }
-  const long long lim = 1LL << 31;
-  return x > lim ? lim : (x < -lim ? -lim : x);
+  const long long lim = 1LL << 30;
+  x = x > lim ? lim : x;
+  x = x < -lim ? -lim : x;
+  return (int)x;
 }
 
-// Balanced base-256 digits of |X| <= 2^31: X = d0 256^3 + d1 256^2 + d2 256 + d3, |d| <= 128.
-__device__ __forceinline__ void digits4(long long X, float d[4]) {
-#pragma unroll
-  for (int t = 3; t >= 1; --t) {
-    const int r = (int)((X + 128) & 255) - 128;
-    d[t] = (float)r;
-    X = (X - r) >> 8;
-  }
-  d[0] = (float)(int)X;
+// Four balanced digits of |X| < 2^30 as BF16 values.
+__device__ __forceinline__ void digits_bf16(int X, __nv_bfloat16 d[4]) {
+  const int Y = X + 0x808080;
+  d[0] = __float2bfloat16_rn((float)(Y >> 24));
+  d[1] = __float2bfloat16_rn((float)(((Y >> 16) & 255) - 128));
+  d[2] = __float2bfloat16_rn((float)(((Y >> 8) & 255) - 128));
+  d[3] = __float2bfloat16_rn((float)((Y & 255) - 128));
 }
 
-// Exponent e with |x| <= 2^(e-1) for every |x| <= amax (amax >= 0); 0 for amax == 0.
+// Exponent e with |x| < 2^(e-1) for every |x| <= amax (amax >= 0); 0 for amax == 0.
 __device__ __forceinline__ int expo_of(double amax) {
   if (!(amax > 0.0)) return 0;
   int k;
@@ -171,17 +177,17 @@ __device__ __forceinline__ void s4_loads(const S4Params& p, uint8_t* st, uint64_
     uint8_t* db = st + S4_PLANES * (S4_BM * 128) + t * (BN * 128);
     if (KIND == S_HALF) {
       const int nvb = (p.nb + 7) / 8;
-      tma_load_4d(da, &p.a, bar, k0, (mt % nvb) * 8, (mt / nvb) * 16, t);
-      tma_load_3d(db, &p.b, bar, k0, n0, t);
+      tma_load_4d(da, &p.a, bar, k0, t, (mt % nvb) * 8, (mt / nvb) * 16);
+      tma_load_3d(db, &p.b, bar, k0, t, n0);
     } else if (KIND == S_FULLSQ || KIND == S_FOCK) {
-      tma_load_4d(da, &p.a, bar, k0, mt * S4_BM, batch, t);
-      tma_load_3d(db, &p.b, bar, k0, n0, t);
+      tma_load_4d(da, &p.a, bar, k0, t, mt * S4_BM, batch);
+      tma_load_3d(db, &p.b, bar, k0, t, n0);
     } else if (KIND == S_JMO || KIND == S_JAO) {
-      tma_load_3d(da, &p.a, bar, k0, mt * S4_BM, t);
-      tma_load_3d(db, &p.b, bar, k0, n0, t);
+      tma_load_3d(da, &p.a, bar, k0, t, mt * S4_BM);
+      tma_load_3d(db, &p.b, bar, k0, t, n0);
     } else {  // S_KAO
-      tma_load_4d(da, &p.a, bar, k0, mt * S4_BM, batch, t);
-      tma_load_4d(db, &p.b, bar, k0, n0, batch, t);
+      tma_load_4d(da, &p.a, bar, k0, t, mt * S4_BM, batch);
+      tma_load_4d(db, &p.b, bar, k0, t, n0, batch);
     }
   }
 }
@@ -243,6 +249,7 @@ __global__ void __launch_bounds__(S4_THREADS, 1) s4_gemm_kernel(const __grid_con
 
   if (warp == 0) {
     if (lane == 0) {
+      // ---------------- TMA producer ----------------
       int it = 0;
       bool ok = true;
       for (int u = 0; u < nunits && ok; ++u) {
@@ -265,6 +272,7 @@ __global__ void __launch_bounds__(S4_THREADS, 1) s4_gemm_kernel(const __grid_con
     }
   } else if (warp == 1) {
     if (lane == 0) {
+      // ---------------- MMA issuer ----------------
       const uint32_t idesc = idesc_bf16(BN);
       int it = 0, cc = 0;
       bool ok = true;
@@ -310,6 +318,7 @@ __global__ void __launch_bounds__(S4_THREADS, 1) s4_gemm_kernel(const __grid_con
           ++cc;
         }
       }
+      // All MMAs of this thread must complete before TMEM is released.
       mma_commit(drain);
       mbar_wait(drain, 0, nullptr, p.status);
     }
@@ -318,16 +327,18 @@ __global__ void __launch_bounds__(S4_THREADS, 1) s4_gemm_kernel(const __grid_con
     // Each thread owns one output row (its TMEM lane).  Per 16-column block the five
     // exact group sums of a chunk are folded into int64 values; a block is finalised
     // (stored, squared or weighted) as soon as the last chunk of its unit is drained.
-    // The column-block loop is kept rolled to bound the code size; running sums live
-    // in small per-thread arrays (L1-backed local memory).
+    // HALF / JAO / KAO / JMO keep the column-block loop rolled (their per-output code
+    // is long) with running int64 sums in small per-thread arrays; FULLSQ and FOCK
+    // unroll it and keep their sums in registers.
     const int q = warp & 3;
     const int row = q * 32 + lane;
-    constexpr bool SUM_DF = (KIND == S_FULLSQ || KIND == S_FOCK);  // double-float sum over units
-    long long acc[BN];   // running int64 sums across chunks (and, for JMO, across units)
+    constexpr bool SUM_DF = (KIND == S_FULLSQ || KIND == S_FOCK);
+    constexpr int NACC = (KIND == S_FOCK) ? 1 : BN;  // FOCK units are single chunks: no running sums
+    long long acc[NACC];
     float sh[SUM_DF ? BN : 1], sl[SUM_DF ? BN : 1];
-#pragma unroll 1
-    for (int i = 0; i < BN; ++i) acc[i] = 0;
-#pragma unroll 1
+#pragma unroll
+    for (int i = 0; i < NACC; ++i) acc[i] = 0;
+#pragma unroll
     for (int i = 0; i < (SUM_DF ? BN : 1); ++i) {
       sh[i] = 0.f;
       sl[i] = 0.f;
@@ -400,12 +411,12 @@ __global__ void __launch_bounds__(S4_THREADS, 1) s4_gemm_kernel(const __grid_con
         tc_fence_after();
         const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(set * S4_NG * BN);
         const bool last = (ch == nch - 1);
-#pragma unroll 1
+#pragma unroll(SUM_DF ? NCH : 1)
         for (int c = 0; c < NCH; ++c) {
-          // group g holds digit pairs with t + u = g; its weight is 2^(32 - 8 g) in units of 2^(ea+eb-48)
+          // group g holds digit pairs with t + u = g; its weight is 2^(32 - 8 g) in units of 2^(ea+eb-46)
           long long v[16];
 #pragma unroll
-          for (int j = 0; j < 16; ++j) v[j] = (ch > 0 || KIND == S_JMO) ? acc[c * 16 + j] : 0;
+          for (int j = 0; j < 16; ++j) v[j] = (KIND != S_FOCK && (ch > 0 || KIND == S_JMO)) ? acc[NACC == 1 ? 0 : c * 16 + j] : 0;
 #pragma unroll
           for (int g = 0; g < S4_NG; ++g) {
             float gv[16];
@@ -413,59 +424,80 @@ __global__ void __launch_bounds__(S4_THREADS, 1) s4_gemm_kernel(const __grid_con
 #pragma unroll
             for (int j = 0; j < 16; ++j) v[j] += (long long)__float2int_rn(gv[j]) << (32 - 8 * g);
           }
-          if (!last || KIND == S_JMO) {
+          if (KIND != S_FOCK && (!last || KIND == S_JMO)) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) acc[c * 16 + j] = v[j];
+            for (int j = 0; j < 16; ++j) acc[NACC == 1 ? 0 : c * 16 + j] = v[j];
             continue;
           }
           // ---- the block's values are final: unit action ----
+          if (!rvalid) continue;
+          if (KIND == S_HALF) {
+            const int lrow = lane / 8, l8 = row % 8;
+            __nv_bfloat16* base3 = p.o3 + ((size_t)P * p.mp * 4) * p.nbp + nu;
+            __nv_bfloat16* base6 = p.o6 + (size_t)nu * 4 * p.nxp + P;
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int i = c * 16 + j;
-            const int col = nt * BN + i;
-            if (!rvalid) continue;
-            if (KIND == S_HALF) {
+            for (int j = 0; j < 16; ++j) {
+              const int i = c * 16 + j;
+              const int col = nt * BN + i;
               if (col < p.m) {
-                const int sb = ea + es_b[i] - 16;
-                float d[4];
-                digits4(shift_round(v[j], sb - es_3[(lane / 8) * BN + i]), d);
-                const size_t i3 = ((size_t)P * p.mp + col) * p.nbp + nu;
+                const int sb = ea + es_b[i] - 15;
+                __nv_bfloat16 d[4];
+                digits_bf16(round_shift(v[j], sb - es_3[lrow * BN + i]), d);
+                __nv_bfloat16* o3 = base3 + (size_t)col * 4 * p.nbp;
 #pragma unroll
-                for (int t = 0; t < 4; ++t) p.o3[t * p.ps3 + i3] = __float2bfloat16_rn(d[t]);
-                digits4(shift_round(v[j], sb - es_6[i * 8 + row % 8]), d);
-                const size_t i6 = ((size_t)col * p.nb + nu) * p.nxp + P;
+                for (int t = 0; t < 4; ++t) o3[t * p.nbp] = d[t];
+                digits_bf16(round_shift(v[j], sb - es_6[i * 8 + l8]), d);
+                __nv_bfloat16* o6 = base6 + (size_t)col * p.nb * 4 * p.nxp;
 #pragma unroll
-                for (int t = 0; t < 4; ++t) p.o6[t * p.ps6 + i6] = __float2bfloat16_rn(d[t]);
+                for (int t = 0; t < 4; ++t) o6[t * p.nxp] = d[t];
               }
-            } else if (KIND == S_FULLSQ) {
-              if (col < p.m) {
+            }
+          } else if (KIND == S_FULLSQ) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int i = c * 16 + j;
+              if (nt * BN + i < p.m) {
                 float xh, xl;
-                ll_to_df(v[j], ea + es_b[i] - 48, xh, xl);
+                ll_to_df(v[j], ea + es_b[i] - S4_SHIFT, xh, xl);
                 const float ph = xh * xh;
                 const float pl = fmaf(xh, xh, -ph) + 2.f * xh * xl;
                 df_add(sh[SUM_DF ? i : 0], sl[SUM_DF ? i : 0], ph, pl);
               }
-            } else if (KIND == S_FOCK) {
-              if (col < p.m) {
+            }
+          } else if (KIND == S_FOCK) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int i = c * 16 + j;
+              if (nt * BN + i < p.m) {
                 float xh, xl;
-                ll_to_df(v[j], ea + es_b[i] - 48, xh, xl);
+                ll_to_df(v[j], ea + es_b[i] - S4_SHIFT, xh, xl);
                 const float2 wv = es_w[i];
                 const float ph = xh * wv.x;
                 const float pl = fmaf(xh, wv.x, -ph) + (xh * wv.y + xl * wv.x);
                 df_add(sh[SUM_DF ? i : 0], sl[SUM_DF ? i : 0], ph, pl);
               }
-            } else if (KIND == S_JAO) {
+            }
+          } else if (KIND == S_JAO) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int i = c * 16 + j;
+              const int col = nt * BN + i;
               if (col < p.m) {
                 float h, l;
-                ll_to_df(v[j], ea + es_b[i] - 48, h, l);
+                ll_to_df(v[j], ea + es_b[i] - S4_SHIFT, h, l);
                 const size_t o = ((size_t)col * p.nb + mu) * p.ldo + nu;
                 p.ohi[o] = h;
                 p.olo[o] = l;
               }
-            } else if (KIND == S_KAO) {
+            }
+          } else if (KIND == S_KAO) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int i = c * 16 + j;
+              const int col = nt * BN + i;
               if (col < p.nb) {
                 float h, l;
-                ll_to_df(v[j], ea + es_b[i] - 48, h, l);
+                ll_to_df(v[j], ea + es_b[i] - S4_SHIFT, h, l);
                 const size_t o = ((size_t)(p.m + batch) * p.nb + mu) * p.ldo + col;
                 p.ohi[o] = h;
                 p.olo[o] = l;
@@ -489,11 +521,11 @@ __global__ void __launch_bounds__(S4_THREADS, 1) s4_gemm_kernel(const __grid_con
 #pragma unroll 1
           for (int i = 0; i < BN; ++i) {
             const int col = nt * BN + i;
-            if (col < p.pcol) dst[col] = acc[i];
+            if (col < p.pcol) dst[col] = acc[NACC == 1 ? 0 : i];
           }
         } else if (SUM_DF) {
           float2* dst = (float2*)p.partial + ((size_t)split * p.prow + r) * p.pcol;
-#pragma unroll 1
+#pragma unroll
           for (int i = 0; i < BN; ++i) {
             const int col = nt * BN + i;
             if (col < p.pcol) dst[col] = make_float2(sh[SUM_DF ? i : 0], sl[SUM_DF ? i : 0]);
@@ -513,10 +545,11 @@ __global__ void __launch_bounds__(S4_THREADS, 1) s4_gemm_kernel(const __grid_con
 // ---------------------------------------------------------------------------
 // digitisation and bound kernels
 // ---------------------------------------------------------------------------
-// Rows of an FP64 matrix (element (r, k) at X[r*rs + k*cs]) -> four digit planes with the
-// row's exact exponent.  One warp per row.  Optionally writes |X| as FP32 rows (absout[r*cols + k]).
+// Rows of an FP64 matrix (element (r, k) at X[r*rs + k*cs]) -> interleaved digits
+// [(r*4 + t)*ldp + k] with the row's exact exponent.  One warp per row.  Optionally
+// writes |X| (absout[r*cols + k] and absT[k*rows + r]) and a double-float copy.
 __global__ void slice_f64_kernel(const double* X, long long rows, int cols, long long rs, long long cs,
-                                 __nv_bfloat16* planes, long long pstride, int ldp, int* exps, float* absout,
+                                 __nv_bfloat16* planes, int ldp, int* exps, float* absout, float* absT,
                                  float2* dfout) {
   long long r = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / 32;
   int lane = threadIdx.x % 32;
@@ -527,13 +560,15 @@ __global__ void slice_f64_kernel(const double* X, long long rows, int cols, long
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   const int e = expo_of(mx);
   if (lane == 0) exps[r] = e;
+  __nv_bfloat16* out = planes + (size_t)r * 4 * ldp;
   for (int k = lane; k < cols; k += 32) {
     const double v = x[k * cs];
-    float d[4];
-    digits4(llrint(ldexp(v, 32 - e)), d);
+    __nv_bfloat16 d[4];
+    digits_bf16(__double2int_rn(ldexp(v, 31 - e)), d);
 #pragma unroll
-    for (int t = 0; t < 4; ++t) planes[t * pstride + r * ldp + k] = __float2bfloat16_rn(d[t]);
+    for (int t = 0; t < 4; ++t) out[t * ldp + k] = d[t];
     if (absout) absout[r * cols + k] = (float)fabs(v);
+    if (absT) absT[(long long)k * rows + r] = (float)fabs(v);
     if (dfout) {
       const float h = (float)v;
       dfout[r * cols + k] = make_float2(h, (float)(v - (double)h));
@@ -541,9 +576,10 @@ __global__ void slice_f64_kernel(const double* X, long long rows, int cols, long
   }
 }
 
-// Rows of a double-float matrix (hi, lo; row stride ld) -> digit planes with exact row exponents.
+// Rows of a double-float matrix (hi, lo; row stride ld) -> interleaved digits with exact
+// row exponents.
 __global__ void slice_pair_kernel(const float* hi, const float* lo, long long rows, int cols, int ld,
-                                  __nv_bfloat16* planes, long long pstride, int ldp, int* exps) {
+                                  __nv_bfloat16* planes, int ldp, int* exps) {
   long long r = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / 32;
   int lane = threadIdx.x % 32;
   if (r >= rows) return;
@@ -554,43 +590,45 @@ __global__ void slice_pair_kernel(const float* hi, const float* lo, long long ro
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   const int e = expo_of((double)mx * (1.0 + 1.0 / 65536.0));
   if (lane == 0) exps[r] = e;
+  __nv_bfloat16* out = planes + (size_t)r * 4 * ldp;
   for (int k = lane; k < cols; k += 32) {
-    const float hs = ldexpf(h[k], 32 - e), ls = ldexpf(l[k], 32 - e);
-    const float ih = rintf(hs);   // integer-valued, |ih| <= 2^31
-    const float top = truncf(ih * (1.f / 65536.f));
-    const long long X = ((long long)(int)top << 16) + (long long)(int)(ih - top * 65536.f) +
-                        (long long)__float2int_rn((hs - ih) + ls);
-    float d[4];
-    digits4(X, d);
+    const float hs = ldexpf(h[k], 31 - e), ls = ldexpf(l[k], 31 - e);  // |hs| < 2^30
+    const float ih = rintf(hs);
+    const int X = __float2int_rn(ih) + __float2int_rn((hs - ih) + ls);
+    __nv_bfloat16 d[4];
+    digits_bf16(X, d);
 #pragma unroll
-    for (int t = 0; t < 4; ++t) planes[t * pstride + r * ldp + k] = __float2bfloat16_rn(d[t]);
+    for (int t = 0; t < 4; ++t) out[t * ldp + k] = d[t];
   }
 }
 
-// Upper bounds on |b^P_{p nu}| (Table 2/3 step 2):
+// Upper bounds on |b^P_{p nu}| (Table 2/3 step 2), FP32 sums inflated by (1 + 2^-16):
 //   e3[P][p] = expo(sum_mu rmaxB[P][mu] |C_{mu p}|)   (rows (P,p) of the full-transform operand)
 //   e6[p][nu] = expo(sum_mu |C_{mu p}| maxB[mu][nu])   (rows (p,nu) of the K^(p) operand)
-// rmaxB and maxB are FP32 values rounded up from FP64; the FP32 sums are inflated by
-// (1 + 2^-16) before taking the exponent so that rounding cannot lower the bound.
-__global__ void bound3_kernel(const float* rmaxB, const float* absC, int nx, int nb, int m, int* e3) {
-  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= (long long)nx * m) return;
-  int P = (int)(i / m), pc = (int)(i % m);
-  const float* r = rmaxB + (size_t)P * nb;
-  const float* c = absC + (size_t)pc * nb;
-  float s = 0.f;
-  for (int mu = 0; mu < nb; ++mu) s = fmaf(r[mu], c[mu], s);
-  e3[i] = expo_of((double)s * (1.0 + 1.0 / 65536.0));
+// One block per P (resp. p); the row of the first factor is staged in shared memory and the
+// threads run over p (resp. nu) with coalesced reads of the second factor.
+__global__ void bound3_kernel(const float* rmaxB, const float* absCt, int nx, int nb, int m, int* e3) {
+  extern __shared__ float srow[];
+  const int P = blockIdx.x;
+  for (int mu = threadIdx.x; mu < nb; mu += blockDim.x) srow[mu] = rmaxB[(size_t)P * nb + mu];
+  __syncthreads();
+  for (int pc = threadIdx.x; pc < m; pc += blockDim.x) {
+    float s = 0.f;
+    for (int mu = 0; mu < nb; ++mu) s = fmaf(srow[mu], absCt[(size_t)mu * m + pc], s);
+    e3[(size_t)P * m + pc] = expo_of((double)s * (1.0 + 1.0 / 65536.0));
+  }
 }
 
 __global__ void bound6_kernel(const float* maxB, const float* absC, int nb, int m, int* e6) {
-  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= (long long)m * nb) return;
-  int pc = (int)(i / nb), nu = (int)(i % nb);
-  const float* c = absC + (size_t)pc * nb;
-  float s = 0.f;
-  for (int mu = 0; mu < nb; ++mu) s = fmaf(c[mu], maxB[(size_t)mu * nb + nu], s);
-  e6[i] = expo_of((double)s * (1.0 + 1.0 / 65536.0));
+  extern __shared__ float srow[];
+  const int pc = blockIdx.x;
+  for (int mu = threadIdx.x; mu < nb; mu += blockDim.x) srow[mu] = absC[(size_t)pc * nb + mu];
+  __syncthreads();
+  for (int nu = threadIdx.x; nu < nb; nu += blockDim.x) {
+    float s = 0.f;
+    for (int mu = 0; mu < nb; ++mu) s = fmaf(srow[mu], maxB[(size_t)mu * nb + nu], s);
+    e6[(size_t)pc * nb + nu] = expo_of((double)s * (1.0 + 1.0 / 65536.0));
+  }
 }
 
 // max over nu of |B^P_{mu nu}| -> rmaxB[P][mu], max over P -> maxB[mu][nu] (FP32, rounded up).
@@ -612,20 +650,20 @@ __global__ void bmax_aux_kernel(const double* B, int nx, int nb, float* maxB) {
   maxB[i] = __double2float_ru(mx);
 }
 
-// b^P_pp = sum_nu b^P_{p nu} C_{nu p} (Table 3 step 3) from the L3 digit planes, compensated
+// b^P_pp = sum_nu b^P_{p nu} C_{nu p} (Table 3 step 3) from the L3 digits, compensated
 // double-float dot product per warp; writes d[p][P] in FP64.
-__global__ void diag_s4_kernel(const __nv_bfloat16* L3, long long ps3, const int* e3, const float2* Cdf, int nb,
-                               int nbp, int nx, int m, int mp, double* d) {
+__global__ void diag_s4_kernel(const __nv_bfloat16* L3, const int* e3, const float2* Cdf, int nb, int nbp, int nx,
+                               int m, int mp, double* d) {
   long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / 32;
   int lane = threadIdx.x % 32;
   if (w >= (long long)nx * m) return;
   int P = (int)(w / m), pc = (int)(w % m);
-  const size_t rb = ((size_t)P * mp + pc) * nbp;
+  const __nv_bfloat16* rb = L3 + ((size_t)P * mp + pc) * 4 * nbp;
   float s = 0.f, c = 0.f;
   for (int nu = lane; nu < nb; nu += 32) {
-    // X = d0 2^24 + d1 2^16 + d2 2^8 + d3 as xh + xl, both exact in FP32
-    const float d0 = __bfloat162float(L3[rb + nu]), d1 = __bfloat162float(L3[ps3 + rb + nu]);
-    const float d2 = __bfloat162float(L3[2 * ps3 + rb + nu]), d3 = __bfloat162float(L3[3 * ps3 + rb + nu]);
+    // Xint = d0 2^24 + d1 2^16 + d2 2^8 + d3 as xh + xl, both exact in FP32
+    const float d0 = __bfloat162float(rb[nu]), d1 = __bfloat162float(rb[nbp + nu]);
+    const float d2 = __bfloat162float(rb[2 * nbp + nu]), d3 = __bfloat162float(rb[3 * nbp + nu]);
     const float xh = ((d0 * 65536.f + d1 * 256.f) + d2) * 256.f, xl = d3;
     const float2 cv = Cdf[(size_t)pc * nb + nu];
     const float p0 = xh * cv.x;
@@ -643,16 +681,16 @@ __global__ void diag_s4_kernel(const __nv_bfloat16* L3, long long ps3, const int
     s = ns;
     c += co + e;
   }
-  if (lane == 0) d[(size_t)pc * nx + P] = ldexp((double)s + (double)c, e3[(size_t)P * m + pc] - 32);
+  if (lane == 0) d[(size_t)pc * nx + P] = ldexp((double)s + (double)c, e3[(size_t)P * m + pc] - 31);
 }
 
-// J_pq = 2^(ed_p + ed_q - 48) x (sum over splits of the exact int64 partials).
+// J_pq = 2^(ed_p + ed_q - 46) x (sum over splits of the exact int64 partials).
 __global__ void reduce_jmo_kernel(const long long* partial, int nsplit, int m, const int* ed, double* J) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m * m) return;
   long long s = 0;
   for (int k = 0; k < nsplit; ++k) s += partial[(size_t)k * m * m + i];
-  J[i] = ldexp((double)s, ed[i / m] + ed[i % m] - 48);
+  J[i] = ldexp((double)s, ed[i / m] + ed[i % m] - S4_SHIFT);
 }
 
 // sum over splits of double-float partials, FP64.  mode 1: Y^T with n_c HCt added.
@@ -684,17 +722,18 @@ __global__ void fock_weights_df_kernel(const double* A, const double* Bc, int m,
   W[i] = make_float2(h, (float)(v - (double)h));
 }
 
-// Digit planes + row exponents -> FP64 values (fetch / copy-out paths).
-__global__ void unslice_kernel(const __nv_bfloat16* planes, long long pstride, int ldp, const int* exps,
-                               long long rows, int cols, double* out) {
+// Interleaved digits + row exponents -> FP64 values (fetch / copy-out paths).
+__global__ void unslice_kernel(const __nv_bfloat16* planes, int ldp, const int* exps, long long rows, int cols,
+                               double* out) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= rows * cols) return;
   long long r = i / cols;
   int k = (int)(i % cols);
+  const __nv_bfloat16* pr = planes + r * 4 * ldp + k;
   long long X = 0;
 #pragma unroll
-  for (int t = 0; t < 4; ++t) X = X * 256 + (long long)__bfloat162float(planes[t * pstride + r * ldp + k]);
-  out[i] = ldexp((double)X, exps[r] - 32);
+  for (int t = 0; t < 4; ++t) X = X * 256 + (long long)__bfloat162float(pr[t * ldp]);
+  out[i] = ldexp((double)X, exps[r] - 31);
 }
 
 __global__ void join_pair_kernel(const float* hi, const float* lo, long long rows, int cols, int ld, double* out) {
@@ -712,10 +751,9 @@ __global__ void join_pair_kernel(const float* hi, const float* lo, long long row
 // ---------------------------------------------------------------------------
 struct donof::S4Buffers {
   int nbp, nxp, mp, ldo;
-  __nv_bfloat16 *B1, *B5, *Ct, *L3, *L6, *Dp, *JKp;  // digit planes
-  long long psB1, psB5, psCt, psL3, psL6, psDp, psJK;
+  __nv_bfloat16 *B1, *B5, *Ct, *L3, *L6, *Dp, *JKp;  // interleaved digits
   int *eB1, *eB5, *eC, *e3, *e6, *ed, *eJK;          // row exponents
-  float *rmaxB, *maxB, *absC;
+  float *rmaxB, *maxB, *absC, *absCt;
   float2* Cdf;    // C rows p (< N_O) as double-float pairs
   double* dmat;   // d [m][nx] FP64
   float *JKhi, *JKlo;
@@ -733,6 +771,7 @@ namespace donof {
 
 static int s4_round_up(int a, int b) { return (a + b - 1) / b * b; }
 
+// BF16 tensor map, 128-byte swizzle; dims innermost first, strides in elements.
 static int s4_map(S4Buffers* sb, CUtensorMap* map, const void* base, int rank, const long long* dims,
                   const long long* strides_el, const int* box) {
   cuuint64_t gd[5], gs[4];
@@ -757,7 +796,7 @@ static void s4_plan(S4Buffers* sb, int m_tiles, int n_tiles, int nbatch, int tar
   constexpr int BN = S4Cfg<KIND>::BN;
   S4Params& p = sb->plan[KIND];
   const size_t stage = (size_t)S4_PLANES * (S4_BM + BN) * 128;
-  int S = (int)((220 * 1024) / stage);
+  int S = (int)((200 * 1024) / stage);
   if (S > 4) S = 4;
   p.stages = S;
   p.tmem_cols = 512;
@@ -799,13 +838,6 @@ int s4_init(donof_ri_ctx* ctx) {
   const int nbp = s4_round_up(nb, 8), nxp = s4_round_up(nx, 8), mp = s4_round_up(m, 4), ldo = s4_round_up(nb, 4);
   sb->nbp = nbp; sb->nxp = nxp; sb->mp = mp; sb->ldo = ldo;
   const long long nbs = nb, nxs = nx, ms = m;
-  sb->psB1 = nxs * nbs * nbp;
-  sb->psB5 = nbs * nbs * nxp;
-  sb->psCt = ms * nbp;
-  sb->psL3 = nxs * mp * nbp;
-  sb->psL6 = ms * nbs * nxp;
-  sb->psDp = ms * nxp;
-  sb->psJK = 2 * ms * nbs * nbp;
   const int sms = 152;
   const int KBb = (nb + S4_BK - 1) / S4_BK, KBx = (nx + S4_BK - 1) / S4_BK;
   const int bn = S4Cfg<S_HALF>::BN;  // 48 for every kind but the full transform (32)
@@ -821,20 +853,20 @@ int s4_init(donof_ri_ctx* ctx) {
   t = (size_t)sb->plan[S_FOCK].nsplit * nb * m * sizeof(float2);
   if (t > pbytes) pbytes = t;
 
-#define ALLOC(ptr, bytes)                                           \
-  do {                                                              \
+#define ALLOC(ptr, bytes)                                             \
+  do {                                                                \
     if (cudaMalloc((void**)&(ptr), (size_t)(bytes)) != cudaSuccess) { \
-      cudaGetLastError();                                           \
-      return DONOF_RI_E_OOM;                                        \
-    }                                                               \
+      cudaGetLastError();                                             \
+      return DONOF_RI_E_OOM;                                          \
+    }                                                                 \
   } while (0)
-  ALLOC(sb->B1, 4 * sb->psB1 * 2);
-  ALLOC(sb->B5, 4 * sb->psB5 * 2);
-  ALLOC(sb->Ct, 4 * sb->psCt * 2);
-  ALLOC(sb->L3, 4 * sb->psL3 * 2);
-  ALLOC(sb->L6, 4 * sb->psL6 * 2);
-  ALLOC(sb->Dp, 4 * sb->psDp * 2);
-  ALLOC(sb->JKp, 4 * sb->psJK * 2);
+  ALLOC(sb->B1, nxs * nbs * 4 * nbp * 2);
+  ALLOC(sb->B5, nbs * nbs * 4 * nxp * 2);
+  ALLOC(sb->Ct, ms * 4 * nbp * 2);
+  ALLOC(sb->L3, nxs * mp * 4 * nbp * 2);
+  ALLOC(sb->L6, ms * nbs * 4 * nxp * 2);
+  ALLOC(sb->Dp, ms * 4 * nxp * 2);
+  ALLOC(sb->JKp, 2 * ms * nbs * 4 * nbp * 2);
   ALLOC(sb->eB1, nxs * nbs * 4);
   ALLOC(sb->eB5, nbs * nbs * 4);
   ALLOC(sb->eC, ms * 4);
@@ -845,11 +877,12 @@ int s4_init(donof_ri_ctx* ctx) {
   ALLOC(sb->rmaxB, nxs * nbs * 4);
   ALLOC(sb->maxB, nbs * nbs * 4);
   ALLOC(sb->absC, ms * nbs * 4);
+  ALLOC(sb->absCt, ms * nbs * 4);
+  ALLOC(sb->Cdf, ms * nbs * 8);
   ALLOC(sb->dmat, ms * nxs * 8);
   ALLOC(sb->JKhi, 2 * ms * nbs * ldo * 4);
   ALLOC(sb->JKlo, 2 * ms * nbs * ldo * 4);
   ALLOC(sb->W, 2 * ms * ms * 8);
-  ALLOC(sb->Cdf, ms * nbs * 8);
   ALLOC(sb->HCt, ms * nbs * 8);
   ALLOC(sb->Yt, ms * nbs * 8);
   ALLOC(sb->partial, pbytes);
@@ -859,12 +892,12 @@ int s4_init(donof_ri_ctx* ctx) {
   cudaStream_t s = ctx->stream;
   {
     long long rows = nxs * nbs;  // rows (P, nu) over mu (B symmetric)
-    slice_f64_kernel<<<ceil_div_u(rows * 32, 256), 256, 0, s>>>(ctx->d_B, rows, nb, nb, 1, sb->B1, sb->psB1, nbp,
-                                                                 sb->eB1, nullptr, nullptr);
+    slice_f64_kernel<<<ceil_div_u(rows * 32, 256), 256, 0, s>>>(ctx->d_B, rows, nb, nb, 1, sb->B1, nbp, sb->eB1,
+                                                                 nullptr, nullptr, nullptr);
     DONOF_LAUNCH_CHECK(ctx);
     long long rows5 = nbs * nbs;  // rows (mu nu) over P
-    slice_f64_kernel<<<ceil_div_u(rows5 * 32, 256), 256, 0, s>>>(ctx->d_B, rows5, nx, 1, nbs * nbs, sb->B5, sb->psB5,
-                                                                  nxp, sb->eB5, nullptr, nullptr);
+    slice_f64_kernel<<<ceil_div_u(rows5 * 32, 256), 256, 0, s>>>(ctx->d_B, rows5, nx, 1, nbs * nbs, sb->B5, nxp,
+                                                                  sb->eB5, nullptr, nullptr, nullptr);
     DONOF_LAUNCH_CHECK(ctx);
     bmax_rows_kernel<<<ceil_div_u(nxs * nbs, 256), 256, 0, s>>>(ctx->d_B, nx, nb, sb->rmaxB);
     DONOF_LAUNCH_CHECK(ctx);
@@ -880,66 +913,66 @@ int s4_init(donof_ri_ctx* ctx) {
     p.partial = sb->partial;
     p.ldo = ldo;
   }
-  {  // HALF: A = B1 [4][nx][nb][nbp] rows (P, nu) over mu; B = C^T planes [4][m][nbp]
+  {  // HALF: A = B1 [nx][nb][4][nbp] rows (P, nu) over mu; B = C^T digits [m][4][nbp]
     S4Params& p = sb->plan[S_HALF];
-    long long dA[4] = {nb, nb, nx, 4}, sA[3] = {nbp, nbs * nbp, sb->psB1};
-    int bA[4] = {S4_BK, 8, 16, 1};
-    long long dB[3] = {nb, m, 4}, sB[2] = {nbp, sb->psCt};
-    int bB[3] = {S4_BK, bn, 1};
+    long long dA[4] = {nb, 4, nb, nx}, sA[3] = {nbp, 4LL * nbp, nbs * 4 * nbp};
+    int bA[4] = {S4_BK, 1, 8, 16};
+    long long dB[3] = {nb, 4, m}, sB[2] = {nbp, 4LL * nbp};
+    int bB[3] = {S4_BK, 1, bn};
     if ((rc = s4_map(sb, &p.a, sb->B1, 4, dA, sA, bA))) return rc;
     if ((rc = s4_map(sb, &p.b, sb->Ct, 3, dB, sB, bB))) return rc;
     p.ea = sb->eB1; p.eb = sb->eC;
-    p.o3 = sb->L3; p.e3 = sb->e3; p.ps3 = sb->psL3;
-    p.o6 = sb->L6; p.e6 = sb->e6; p.ps6 = sb->psL6;
+    p.o3 = sb->L3; p.e3 = sb->e3;
+    p.o6 = sb->L6; p.e6 = sb->e6;
   }
-  {  // FULLSQ: A = L3 [4][nx][mp][nbp] rows p (per P) over nu; B = C^T planes
+  {  // FULLSQ: A = L3 [nx][mp][4][nbp] rows p (per P) over nu; B = C^T digits
     S4Params& p = sb->plan[S_FULLSQ];
-    long long dA[4] = {nb, m, nx, 4}, sA[3] = {nbp, (long long)mp * nbp, sb->psL3};
-    int bA[4] = {S4_BK, S4_BM, 1, 1};
-    long long dB[3] = {nb, m, 4}, sB[2] = {nbp, sb->psCt};
-    int bB[3] = {S4_BK, 32, 1};
+    long long dA[4] = {nb, 4, m, nx}, sA[3] = {nbp, 4LL * nbp, (long long)mp * 4 * nbp};
+    int bA[4] = {S4_BK, 1, S4_BM, 1};
+    long long dB[3] = {nb, 4, m}, sB[2] = {nbp, 4LL * nbp};
+    int bB[3] = {S4_BK, 1, 32};
     if ((rc = s4_map(sb, &p.a, sb->L3, 4, dA, sA, bA))) return rc;
     if ((rc = s4_map(sb, &p.b, sb->Ct, 3, dB, sB, bB))) return rc;
     p.ea = sb->e3; p.eb = sb->eC;
     p.prow = m; p.pcol = m;
   }
-  {  // JMO: A = B = d planes [4][m][nxp] rows p over P
+  {  // JMO: A = B = d digits [m][4][nxp] rows p over P
     S4Params& p = sb->plan[S_JMO];
-    long long dA[3] = {nx, m, 4}, sA[2] = {nxp, sb->psDp};
-    int bA[3] = {S4_BK, S4_BM, 1};
-    int bB[3] = {S4_BK, bn, 1};
+    long long dA[3] = {nx, 4, m}, sA[2] = {nxp, 4LL * nxp};
+    int bA[3] = {S4_BK, 1, S4_BM};
+    int bB[3] = {S4_BK, 1, bn};
     if ((rc = s4_map(sb, &p.a, sb->Dp, 3, dA, sA, bA))) return rc;
     if ((rc = s4_map(sb, &p.b, sb->Dp, 3, dA, sA, bB))) return rc;
     p.ea = sb->ed; p.eb = sb->ed;
     p.prow = m; p.pcol = m;
   }
-  {  // JAO: A = B5 [4][nb*nb][nxp] rows (mu nu) over P; B = d planes
+  {  // JAO: A = B5 [nb*nb][4][nxp] rows (mu nu) over P; B = d digits
     S4Params& p = sb->plan[S_JAO];
-    long long dA[3] = {nx, nbs * nbs, 4}, sA[2] = {nxp, sb->psB5};
-    int bA[3] = {S4_BK, S4_BM, 1};
-    long long dB[3] = {nx, m, 4}, sB[2] = {nxp, sb->psDp};
-    int bB[3] = {S4_BK, bn, 1};
+    long long dA[3] = {nx, 4, nbs * nbs}, sA[2] = {nxp, 4LL * nxp};
+    int bA[3] = {S4_BK, 1, S4_BM};
+    long long dB[3] = {nx, 4, m}, sB[2] = {nxp, 4LL * nxp};
+    int bB[3] = {S4_BK, 1, bn};
     if ((rc = s4_map(sb, &p.a, sb->B5, 3, dA, sA, bA))) return rc;
     if ((rc = s4_map(sb, &p.b, sb->Dp, 3, dB, sB, bB))) return rc;
     p.ea = sb->eB5; p.eb = sb->ed;
     p.ohi = sb->JKhi; p.olo = sb->JKlo;
   }
-  {  // KAO: A = B = L6 [4][m][nb][nxp] rows (p, mu) over P
+  {  // KAO: A = B = L6 [m][nb][4][nxp] rows (p, mu) over P
     S4Params& p = sb->plan[S_KAO];
-    long long dA[4] = {nx, nb, m, 4}, sA[3] = {nxp, nbs * nxp, sb->psL6};
-    int bA[4] = {S4_BK, S4_BM, 1, 1};
-    int bB[4] = {S4_BK, bn, 1, 1};
+    long long dA[4] = {nx, 4, nb, m}, sA[3] = {nxp, 4LL * nxp, nbs * 4 * nxp};
+    int bA[4] = {S4_BK, 1, S4_BM, 1};
+    int bB[4] = {S4_BK, 1, bn, 1};
     if ((rc = s4_map(sb, &p.a, sb->L6, 4, dA, sA, bA))) return rc;
     if ((rc = s4_map(sb, &p.b, sb->L6, 4, dA, sA, bB))) return rc;
     p.ea = sb->e6; p.eb = sb->e6;
     p.ohi = sb->JKhi; p.olo = sb->JKlo;
   }
-  {  // FOCK: A = JK planes [4][2m][nb][nbp] rows mu (per q') over nu; B = C^T planes
+  {  // FOCK: A = JK digits [2m][nb][4][nbp] rows mu (per q') over nu; B = C^T digits
     S4Params& p = sb->plan[S_FOCK];
-    long long dA[4] = {nb, nb, 2 * ms, 4}, sA[3] = {nbp, nbs * nbp, sb->psJK};
-    int bA[4] = {S4_BK, S4_BM, 1, 1};
-    long long dB[3] = {nb, m, 4}, sB[2] = {nbp, sb->psCt};
-    int bB[3] = {S4_BK, bn, 1};
+    long long dA[4] = {nb, 4, nb, 2 * ms}, sA[3] = {nbp, 4LL * nbp, nbs * 4 * nbp};
+    int bA[4] = {S4_BK, 1, S4_BM, 1};
+    long long dB[3] = {nb, 4, m}, sB[2] = {nbp, 4LL * nbp};
+    int bB[3] = {S4_BK, 1, bn};
     if ((rc = s4_map(sb, &p.a, sb->JKp, 4, dA, sA, bA))) return rc;
     if ((rc = s4_map(sb, &p.b, sb->Ct, 3, dB, sB, bB))) return rc;
     p.ea = sb->eJK; p.eb = sb->eC;
@@ -958,9 +991,9 @@ int s4_init(donof_ri_ctx* ctx) {
 void s4_free(donof_ri_ctx* ctx) {
   S4Buffers* sb = ctx->s4;
   if (!sb) return;
-  void* bufs[] = {sb->B1, sb->B5, sb->Ct, sb->L3, sb->L6, sb->Dp, sb->JKp, sb->eB1, sb->eB5, sb->eC, sb->e3,
-                  sb->e6, sb->ed, sb->eJK, sb->rmaxB, sb->maxB, sb->absC, sb->dmat, sb->JKhi, sb->JKlo, sb->W,
-                  sb->HCt, sb->Yt, sb->partial, sb->Cdf};
+  void* bufs[] = {sb->B1,    sb->B5,   sb->Ct,   sb->L3,   sb->L6, sb->Dp,  sb->JKp,  sb->eB1,   sb->eB5,
+                  sb->eC,    sb->e3,   sb->e6,   sb->ed,   sb->eJK, sb->rmaxB, sb->maxB, sb->absC, sb->absCt,
+                  sb->Cdf,   sb->dmat, sb->JKhi, sb->JKlo, sb->W,  sb->HCt, sb->Yt,   sb->partial};
   for (void* b : bufs)
     if (b) cudaFree(b);
   free(sb);
@@ -984,12 +1017,12 @@ int s4_transform(donof_ri_ctx* ctx, int mode) {
   {
     ProfScope ps(ctx, DONOF_RI_ROW_OTHER);
     // C^T rows p over mu (C column-major = rows p contiguous)
-    slice_f64_kernel<<<ceil_div_u((long long)m * 32, 256), 256, 0, s>>>(ctx->d_C, m, nb, nb, 1, sb->Ct, sb->psCt,
-                                                                          sb->nbp, sb->eC, sb->absC, sb->Cdf);
+    slice_f64_kernel<<<ceil_div_u((long long)m * 32, 256), 256, 0, s>>>(ctx->d_C, m, nb, nb, 1, sb->Ct, sb->nbp,
+                                                                          sb->eC, sb->absC, sb->absCt, sb->Cdf);
     DONOF_LAUNCH_CHECK(ctx);
-    bound3_kernel<<<ceil_div_u((long long)nx * m, 256), 256, 0, s>>>(sb->rmaxB, sb->absC, nx, nb, m, sb->e3);
+    bound3_kernel<<<nx, 128, nb * sizeof(float), s>>>(sb->rmaxB, sb->absCt, nx, nb, m, sb->e3);
     DONOF_LAUNCH_CHECK(ctx);
-    bound6_kernel<<<ceil_div_u((long long)m * nb, 256), 256, 0, s>>>(sb->maxB, sb->absC, nb, m, sb->e6);
+    bound6_kernel<<<m, 128, nb * sizeof(float), s>>>(sb->maxB, sb->absC, nb, m, sb->e6);
     DONOF_LAUNCH_CHECK(ctx);
   }
   {
@@ -998,11 +1031,11 @@ int s4_transform(donof_ri_ctx* ctx, int mode) {
   }
   {
     ProfScope ps(ctx, DONOF_RI_ROW_DIAG);
-    diag_s4_kernel<<<ceil_div_u((long long)nx * m * 32, 256), 256, 0, s>>>(sb->L3, sb->psL3, sb->e3, sb->Cdf, nb,
-                                                                            sb->nbp, nx, m, sb->mp, sb->dmat);
+    diag_s4_kernel<<<ceil_div_u((long long)nx * m * 32, 256), 256, 0, s>>>(sb->L3, sb->e3, sb->Cdf, nb, sb->nbp, nx, m,
+                                                                            sb->mp, sb->dmat);
     DONOF_LAUNCH_CHECK(ctx);
-    slice_f64_kernel<<<ceil_div_u((long long)m * 32, 256), 256, 0, s>>>(sb->dmat, m, nx, nx, 1, sb->Dp, sb->psDp,
-                                                                          sb->nxp, sb->ed, nullptr, nullptr);
+    slice_f64_kernel<<<ceil_div_u((long long)m * 32, 256), 256, 0, s>>>(sb->dmat, m, nx, nx, 1, sb->Dp, sb->nxp,
+                                                                          sb->ed, nullptr, nullptr, nullptr);
     DONOF_LAUNCH_CHECK(ctx);
   }
   if (mode == DONOF_RI_FULL) {
@@ -1042,7 +1075,7 @@ int s4_jk_ao(donof_ri_ctx* ctx) {
     ProfScope ps(ctx, DONOF_RI_ROW_OTHER);
     long long rows = 2LL * m * nb;
     slice_pair_kernel<<<ceil_div_u(rows * 32, 256), 256, 0, ctx->stream>>>(sb->JKhi, sb->JKlo, rows, nb, sb->ldo,
-                                                                            sb->JKp, sb->psJK, sb->nbp, sb->eJK);
+                                                                            sb->JKp, sb->nbp, sb->eJK);
     DONOF_LAUNCH_CHECK(ctx);
   }
   return DONOF_RI_OK;
@@ -1077,10 +1110,10 @@ int s4_fetch(donof_ri_ctx* ctx, int what, double* dst, size_t count) {
       cudaGetLastError();
       return DONOF_RI_E_OOM;
     }
-    // rows (P, p) of the L3 planes over nu; consecutive P are mp rows apart
+    // rows (P, p) of the L3 digits over nu; consecutive P are mp rows apart
     for (int P = 0; P < nx && e == cudaSuccess; ++P) {
       unslice_kernel<<<ceil_div_u((long long)m * nb, 256), 256, 0, ctx->stream>>>(
-          sb->L3 + (size_t)P * sb->mp * sb->nbp, sb->psL3, sb->nbp, sb->e3 + (size_t)P * m, m, nb,
+          sb->L3 + (size_t)P * sb->mp * 4 * sb->nbp, sb->nbp, sb->e3 + (size_t)P * m, m, nb,
           tmp + (size_t)P * m * nb);
       e = cudaGetLastError();
     }

@@ -42,7 +42,6 @@ int launch_energy_rows(donof_ri_ctx* ctx, const double* HCt);
 
 enum S4Kind { S_HALF = 0, S_FULLSQ = 1, S_JMO = 2, S_JAO = 3, S_KAO = 4, S_FOCK = 5, S_NKINDS = 6 };
 
-constexpr int S4_THREADS = 192;
 constexpr int S4_BM = 128;      // rows per tile
 constexpr int S4_BK = 64;       // BF16 elements per K block (one 128-byte swizzle row)
 constexpr int S4_CHUNK_KB = 4;  // K blocks per exact chunk (256 elements)
@@ -53,9 +52,17 @@ constexpr int S4_SHIFT = 46;    // value = 2^(ea + eb - 46) v
 // Columns per tile: five groups x two ping-pong accumulator sets must fit in
 // TMEM's 512 columns (5 x 48 x 2 = 480).  The full transform keeps running
 // int64 and double-float sums per column in registers and uses 32 columns.
+// The epilogue runs as NWG warpgroups: the register-light kinds use two, which
+// split a tile's columns in interleaved 8-column blocks so that two warps per
+// SM sub-partition hide each other's latencies; the summing kinds (FULLSQ,
+// FOCK) need their registers for running sums and use one with 16-column blocks.
 template <int KIND>
 struct S4Cfg {
   static constexpr int BN = (KIND == S_FULLSQ) ? 32 : 48;
+  static constexpr int NWG = (KIND == S_FULLSQ || KIND == S_FOCK) ? 1 : 2;
+  static constexpr int CW = NWG == 1 ? 16 : 8;
+  static constexpr int THREADS = 64 + 128 * NWG;
+  static constexpr int ES_WARP_BYTES = BN * 4 + BN * 8 + 4 * BN * 4 + BN * 8 * 4;
 };
 
 struct S4Params {
@@ -98,13 +105,18 @@ __device__ __forceinline__ int round_shift(long long v, int s) {
   return (int)x;
 }
 
-// Four balanced digits of |X| < 2^30 as BF16 values.
+// Four balanced digits of |X| < 2^30 as BF16 values.  U = X + 0x80808080 holds
+// digit + 128 in each byte (the top digit lies in [-64, 64]).  A byte b placed
+// under the exponent of 2^23 reads as the float 2^23 + b, and subtracting
+// 2^23 + 128 leaves the digit exactly; an integer of at most 8 significant bits
+// is exact in BF16, so its BF16 pattern is the top half of the FP32 pattern.
 __device__ __forceinline__ void digits_bf16(int X, __nv_bfloat16 d[4]) {
-  const int Y = X + 0x808080;
-  d[0] = __float2bfloat16_rn((float)(Y >> 24));
-  d[1] = __float2bfloat16_rn((float)(((Y >> 16) & 255) - 128));
-  d[2] = __float2bfloat16_rn((float)(((Y >> 8) & 255) - 128));
-  d[3] = __float2bfloat16_rn((float)((Y & 255) - 128));
+  const unsigned int U = (unsigned int)X + 0x80808080u;
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const float x = __uint_as_float(__byte_perm(U, 0x4B000000u, 0x7440u | (unsigned int)(3 - t))) - 8388736.0f;
+    d[t] = __ushort_as_bfloat16((unsigned short)(__float_as_uint(x) >> 16));
+  }
 }
 
 // Exponent e with |x| < 2^(e-1) for every |x| <= amax (amax >= 0); 0 for amax == 0.
@@ -193,9 +205,10 @@ __device__ __forceinline__ void s4_loads(const S4Params& p, uint8_t* st, uint64_
 }
 
 template <int KIND>
-__global__ void __launch_bounds__(S4_THREADS, 1) s4_gemm_kernel(const __grid_constant__ S4Params p) {
+__global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, 1) s4_gemm_kernel(const __grid_constant__ S4Params p) {
   constexpr int BN = S4Cfg<KIND>::BN;
-  constexpr int NCH = BN / 16;
+  constexpr int NWG = S4Cfg<KIND>::NWG, CW = S4Cfg<KIND>::CW;
+  constexpr int NCBT = BN / CW / NWG;  // column blocks per epilogue thread
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int S = p.stages;
@@ -211,8 +224,9 @@ __global__ void __launch_bounds__(S4_THREADS, 1) s4_gemm_kernel(const __grid_con
   // Epilogue scratch (after the 256-byte barrier block), one copy per epilogue warp so
   // that staging needs only __syncwarp: the current unit's per-column exponents /
   // weights and, for HALF, the output exponents of the warp's rows.
-  constexpr int ES_WARP_BYTES = BN * 4 + BN * 8 + 4 * BN * 4 + BN * 8 * 4;
-  uint8_t* es_base = smem + (size_t)S * stage_bytes + 256 + (size_t)(threadIdx.x / 32 & 3) * ES_WARP_BYTES;
+  constexpr int ES_WARP_BYTES = S4Cfg<KIND>::ES_WARP_BYTES;
+  const int ew = threadIdx.x / 32 >= 2 ? threadIdx.x / 32 - 2 : 0;  // epilogue warp index
+  uint8_t* es_base = smem + (size_t)S * stage_bytes + 256 + (size_t)ew * ES_WARP_BYTES;
   int* es_b = (int*)es_base;              // [BN]
   float2* es_w = (float2*)(es_b + BN);    // [BN]
   int* es_3 = (int*)(es_w + BN);          // [4][BN]: the warp's 4 auxiliary rows P
@@ -235,7 +249,7 @@ __global__ void __launch_bounds__(S4_THREADS, 1) s4_gemm_kernel(const __grid_con
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&accf[a], 1);
-      mbar_init(&acce[a], 128);
+      mbar_init(&acce[a], 128 * NWG);
     }
     mbar_init(drain, 1);
     *abort_flag = 0;
@@ -273,7 +287,12 @@ __global__ void __launch_bounds__(S4_THREADS, 1) s4_gemm_kernel(const __grid_con
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------- MMA issuer ----------------
-      const uint32_t idesc = idesc_bf16(BN);
+      // The B planes of a stage sit one above the other (plane u at rows u*BN), so one
+      // MMA of N = 4*BN multiplies digit plane t of A by all four B planes and, with the
+      // accumulator window shifted by t*BN columns, adds product (t,u) to group t+u.
+      // Window t covers groups t..min(t+3,4): four MMAs per K step instead of 13.
+      const uint32_t id1 = idesc_bf16(BN), id2 = idesc_bf16(2 * BN), id3 = idesc_bf16(3 * BN),
+                     id4 = idesc_bf16(4 * BN);
       int it = 0, cc = 0;
       bool ok = true;
       for (int u = 0; u < nunits && ok; ++u) {
@@ -299,16 +318,20 @@ __global__ void __launch_bounds__(S4_THREADS, 1) s4_gemm_kernel(const __grid_con
             // K step ks: +32 bytes inside the 128-byte swizzle row (+2 in the descriptor's address field)
 #pragma unroll 1
             for (int ks = 0; ks < 4; ++ks) {
-              const bool first = (j == 0 && ks == 0);
-#pragma unroll
-              for (int g = 0; g < S4_NG; ++g) {
-                const int t0 = g > 3 ? g - 3 : 0, t1 = g < 3 ? g : 3;
-#pragma unroll
-                for (int t = t0; t <= t1; ++t) {
-                  mma_bf16(dbase + (uint32_t)(g * BN), dA[t] + (uint64_t)(2 * ks), dB[g - t] + (uint64_t)(2 * ks),
-                           idesc, (first && t == t0) ? 0u : 1u);
-                }
+              const uint64_t o = (uint64_t)(2 * ks);
+              if (j == 0 && ks == 0) {
+                // First step of a chunk: every group block must be written once with
+                // accumulate = 0 before any MMA adds to it.  Window 1 initialises groups
+                // 1..4; group 0 is initialised by (0,0) alone and (0,1..3) then adds.
+                mma_bf16(dbase + (uint32_t)BN, dA[1] + o, dB[0] + o, id4, 0u);
+                mma_bf16(dbase, dA[0] + o, dB[0] + o, id1, 0u);
+                mma_bf16(dbase + (uint32_t)BN, dA[0] + o, dB[1] + o, id3, 1u);
+              } else {
+                mma_bf16(dbase, dA[0] + o, dB[0] + o, id4, 1u);
+                mma_bf16(dbase + (uint32_t)BN, dA[1] + o, dB[0] + o, id4, 1u);
               }
+              mma_bf16(dbase + (uint32_t)(2 * BN), dA[2] + o, dB[0] + o, id3, 1u);
+              mma_bf16(dbase + (uint32_t)(3 * BN), dA[3] + o, dB[0] + o, id2, 1u);
             }
             mma_commit(&empty[s]);
             ++it;
@@ -330,10 +353,11 @@ __global__ void __launch_bounds__(S4_THREADS, 1) s4_gemm_kernel(const __grid_con
     // HALF / JAO / KAO / JMO keep the column-block loop rolled (their per-output code
     // is long) with running int64 sums in small per-thread arrays; FULLSQ and FOCK
     // unroll it and keep their sums in registers.
-    const int q = warp & 3;
+    const int q = warp & 3;     // TMEM lane quarter this warp may access
+    const int wg = ew / 4;      // epilogue warpgroup: column blocks wg, wg + NWG, ...
     const int row = q * 32 + lane;
     constexpr bool SUM_DF = (KIND == S_FULLSQ || KIND == S_FOCK);
-    constexpr int NACC = (KIND == S_FOCK) ? 1 : BN;  // FOCK units are single chunks: no running sums
+    constexpr int NACC = (KIND == S_FOCK) ? 1 : BN / NWG;  // FOCK units are single chunks: no running sums
     long long acc[NACC];
     float sh[SUM_DF ? BN : 1], sl[SUM_DF ? BN : 1];
 #pragma unroll
@@ -411,22 +435,24 @@ __global__ void __launch_bounds__(S4_THREADS, 1) s4_gemm_kernel(const __grid_con
         tc_fence_after();
         const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(set * S4_NG * BN);
         const bool last = (ch == nch - 1);
-#pragma unroll(SUM_DF ? NCH : 1)
-        for (int c = 0; c < NCH; ++c) {
+#pragma unroll(KIND == S_HALF || KIND == S_JMO ? 1 : NCBT)
+        for (int cb = 0; cb < NCBT; ++cb) {
+          const int c = cb * NWG + wg;  // column block (CW columns)
           // group g holds digit pairs with t + u = g; its weight is 2^(32 - 8 g) in units of 2^(ea+eb-46)
-          long long v[16];
+          long long v[CW];
 #pragma unroll
-          for (int j = 0; j < 16; ++j) v[j] = (KIND != S_FOCK && (ch > 0 || KIND == S_JMO)) ? acc[NACC == 1 ? 0 : c * 16 + j] : 0;
+          for (int j = 0; j < CW; ++j) v[j] = (KIND != S_FOCK && (ch > 0 || KIND == S_JMO)) ? acc[NACC == 1 ? 0 : cb * CW + j] : 0;
 #pragma unroll
           for (int g = 0; g < S4_NG; ++g) {
-            float gv[16];
-            tmem_ld16(tb + (uint32_t)(g * BN + c * 16), gv);
+            float gv[CW];
+            if (CW == 16) tmem_ld16(tb + (uint32_t)(g * BN + c * CW), gv);
+            else tmem_ld8(tb + (uint32_t)(g * BN + c * CW), gv);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) v[j] += (long long)__float2int_rn(gv[j]) << (32 - 8 * g);
+            for (int j = 0; j < CW; ++j) v[j] += (long long)__float2int_rn(gv[j]) << (32 - 8 * g);
           }
           if (KIND != S_FOCK && (!last || KIND == S_JMO)) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) acc[NACC == 1 ? 0 : c * 16 + j] = v[j];
+            for (int j = 0; j < CW; ++j) acc[NACC == 1 ? 0 : cb * CW + j] = v[j];
             continue;
           }
           // ---- the block's values are final: unit action ----
@@ -436,8 +462,8 @@ __global__ void __launch_bounds__(S4_THREADS, 1) s4_gemm_kernel(const __grid_con
             __nv_bfloat16* base3 = p.o3 + ((size_t)P * p.mp * 4) * p.nbp + nu;
             __nv_bfloat16* base6 = p.o6 + (size_t)nu * 4 * p.nxp + P;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const int i = c * 16 + j;
+            for (int j = 0; j < CW; ++j) {
+              const int i = c * CW + j;
               const int col = nt * BN + i;
               if (col < p.m) {
                 const int sb = ea + es_b[i] - 15;
@@ -454,8 +480,8 @@ __global__ void __launch_bounds__(S4_THREADS, 1) s4_gemm_kernel(const __grid_con
             }
           } else if (KIND == S_FULLSQ) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const int i = c * 16 + j;
+            for (int j = 0; j < CW; ++j) {
+              const int i = c * CW + j;
               if (nt * BN + i < p.m) {
                 float xh, xl;
                 ll_to_df(v[j], ea + es_b[i] - S4_SHIFT, xh, xl);
@@ -466,8 +492,8 @@ __global__ void __launch_bounds__(S4_THREADS, 1) s4_gemm_kernel(const __grid_con
             }
           } else if (KIND == S_FOCK) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const int i = c * 16 + j;
+            for (int j = 0; j < CW; ++j) {
+              const int i = c * CW + j;
               if (nt * BN + i < p.m) {
                 float xh, xl;
                 ll_to_df(v[j], ea + es_b[i] - S4_SHIFT, xh, xl);
@@ -479,8 +505,8 @@ __global__ void __launch_bounds__(S4_THREADS, 1) s4_gemm_kernel(const __grid_con
             }
           } else if (KIND == S_JAO) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const int i = c * 16 + j;
+            for (int j = 0; j < CW; ++j) {
+              const int i = c * CW + j;
               const int col = nt * BN + i;
               if (col < p.m) {
                 float h, l;
@@ -492,8 +518,8 @@ __global__ void __launch_bounds__(S4_THREADS, 1) s4_gemm_kernel(const __grid_con
             }
           } else if (KIND == S_KAO) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const int i = c * 16 + j;
+            for (int j = 0; j < CW; ++j) {
+              const int i = c * CW + j;
               const int col = nt * BN + i;
               if (col < p.nb) {
                 float h, l;
@@ -519,8 +545,8 @@ __global__ void __launch_bounds__(S4_THREADS, 1) s4_gemm_kernel(const __grid_con
         if (KIND == S_JMO) {
           long long* dst = (long long*)p.partial + ((size_t)split * p.prow + r) * p.pcol;
 #pragma unroll 1
-          for (int i = 0; i < BN; ++i) {
-            const int col = nt * BN + i;
+          for (int i = 0; i < BN / NWG; ++i) {
+            const int col = nt * BN + ((i / CW) * NWG + wg) * CW + i % CW;
             if (col < p.pcol) dst[col] = acc[NACC == 1 ? 0 : i];
           }
         } else if (SUM_DF) {
@@ -809,7 +835,7 @@ static void s4_plan(S4Buffers* sb, int m_tiles, int n_tiles, int nbatch, int tar
   p.bpc = (nbatch + ns - 1) / ns;
   p.nsplit = (nbatch + p.bpc - 1) / p.bpc;
   sb->grid[KIND] = tiles * p.nsplit;
-  sb->smem[KIND] = 1024 + (size_t)S * stage + 256 + 4 * (size_t)(BN * (4 + 8 + 16 + 32));
+  sb->smem[KIND] = 1024 + (size_t)S * stage + 256 + 4 * S4Cfg<KIND>::NWG * (size_t)S4Cfg<KIND>::ES_WARP_BYTES;
   p.persist = 0;
   p.ntiles = tiles;
   if (persist_ctas > 0 && nbatch == 1) {
@@ -1004,7 +1030,7 @@ template <int KIND>
 static int launch_s4(donof_ri_ctx* ctx) {
   S4Buffers* sb = ctx->s4;
   if (sb->grid[KIND] <= 0) return DONOF_RI_OK;
-  s4_gemm_kernel<KIND><<<sb->grid[KIND], S4_THREADS, sb->smem[KIND], ctx->stream>>>(sb->plan[KIND]);
+  s4_gemm_kernel<KIND><<<sb->grid[KIND], S4Cfg<KIND>::THREADS, sb->smem[KIND], ctx->stream>>>(sb->plan[KIND]);
   DONOF_LAUNCH_CHECK(ctx);
   return DONOF_RI_OK;
 }

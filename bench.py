@@ -363,23 +363,31 @@ def main():
     per_launch_ms = t_dom / max(c_dom, 1)
     achieved = flops[dom] / (per_launch_ms * 1e-3) / 1e12
     peaks, peak_src = read_peaks()
+    # A split-precision contraction executes several tensor-core products per
+    # algorithmic product; its peak in algorithmic flops is the dtype's dense peak
+    # divided by that count (3 TF32 MMAs for TF32X3, 13 BF16 digit-pair MMAs for
+    # SLICE4).  executed_tflops is the tensor-core rate the kernel actually ran at.
+    mult = 1
     if prec == bd.DONOF_RI_FP64:
         peak = NOMINAL["fp64"]
         bound, peak_note = "alu", "FP64 nominal 1.25 TFLOP/s (DFMA on CUDA cores; not measured)"
     elif prec == bd.DONOF_RI_TF32X3:
         bf = _peak_value(peaks, "bf16_tflops") or FALLBACK_PEAKS["bf16_tflops"]
-        peak = bf * NOMINAL["tf32"] / NOMINAL["bf16"]
-        bound, peak_note = "tensor", (f"TF32 dense = {peak_src} bf16 burst {bf:.0f} x 1.1/2.25; "
-                                      "3 TF32 MMAs per algorithmic product")
+        mult = 3
+        peak = bf * NOMINAL["tf32"] / NOMINAL["bf16"] / mult
+        bound, peak_note = "tensor", (f"TF32 dense = {peak_src} bf16 burst {bf:.0f} x 1.1/2.25, "
+                                      "/ 3 TF32 MMAs per algorithmic product")
     else:
         bf = _peak_value(peaks, "bf16_tflops") or FALLBACK_PEAKS["bf16_tflops"]
-        peak = bf
-        bound, peak_note = "tensor", (f"BF16 dense, {peak_src} burst {bf:.0f}; 13 BF16 MMAs per algorithmic "
-                                      "product (digit pairs)")
+        mult = 13
+        peak = bf / mult
+        bound, peak_note = "tensor", (f"BF16 dense, {peak_src} burst {bf:.0f}, / 13 BF16 digit-pair MMAs per "
+                                      "algorithmic product")
     traffic = read_traffic(args.workload, args.precision, dom)
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": traffic, "kernel_row": dom, "launch_ms": per_launch_ms,
-            "algorithmic_flops_per_launch": flops[dom], "peak_source": peak_note}
+            "algorithmic_flops_per_launch": flops[dom], "executed_tflops": achieved * mult,
+            "peak_source": peak_note}
 
     if rank != 0:
         return 0

@@ -15,13 +15,16 @@
 // tcgen05.mma kind::f16 into five FP32 TMEM accumulators, one per g = t + u.  The
 // g = 4 group lies 2^-32 below the leading pair but is kept: for a row multiplied
 // by itself (J_pp, K^(p)_{mu mu}) its (2,2) product is a sum of squares whose bias
-// grows with K.  Each accumulator sums at most 4 pairs x 256 K-elements x 128^2
-// = 2^24 in magnitude, so every partial sum is an integer of magnitude <= 2^24 and
-// the FP32 accumulation is exact.  After every 256-wide K chunk the epilogue folds
-// the five exact sums into one int64 per output (v = sum_g G_g 2^(32 - 8g); the
-// value is 2^(ea + eb - 46) v), so the whole reduction over K is exact and
-// independent of order; the only errors are the 31-bit digit representation of
-// the operands and the dropped pair products (g >= 5).
+// grows with K.  With |d0| <= 64 and |d1..d3| <= 128 one K element adds at most
+// 2^12, 2^14, 2^15, 3 2^14, 3 2^14 to groups 0..4, so over a 512-wide K chunk
+// every partial sum of groups 0..2 is an integer of magnitude <= 2^24 and their
+// FP32 accumulation is exact; groups 3 and 4 may round once they pass 2^24, an
+// error below 2^-38 of the leading group's scale.  After every chunk the
+// epilogue folds the five sums into one int64 per output (v = sum_g G_g
+// 2^(32 - 8g); the value is 2^(ea + eb - 46) v), so the reduction over K is
+// exact in its leading 38 bits and independent of order; the other errors are
+// the 31-bit digit representation of the operands and the dropped pair
+// products (g >= 5).
 // Outputs feeding another GEMM are re-digitised in integer arithmetic, with
 // bound-based exponents (b_half) or exact row maxima (d, J^(q), K^(q)).
 //
@@ -43,26 +46,33 @@ int launch_energy_rows(donof_ri_ctx* ctx, const double* HCt);
 enum S4Kind { S_HALF = 0, S_FULLSQ = 1, S_JMO = 2, S_JAO = 3, S_KAO = 4, S_FOCK = 5, S_NKINDS = 6 };
 
 constexpr int S4_BM = 128;      // rows per tile
-constexpr int S4_BK = 64;       // BF16 elements per K block (one 128-byte swizzle row)
-constexpr int S4_CHUNK_KB = 4;  // K blocks per exact chunk (256 elements)
+constexpr int S4_BK = 32;       // BF16 elements per K block (one 64-byte swizzle row)
+constexpr int S4_KS = S4_BK / 16;  // MMA K steps per K block
+constexpr int S4_CHUNK_KB = 16; // K blocks per chunk (512 elements; groups 0..2 exact)
 constexpr int S4_PLANES = 4;
 constexpr int S4_NG = 5;        // digit-pair groups g = t + u = 0..4
 constexpr int S4_SHIFT = 46;    // value = 2^(ea + eb - 46) v
 
-// Columns per tile: five groups x two ping-pong accumulator sets must fit in
-// TMEM's 512 columns (5 x 48 x 2 = 480).  The full transform keeps running
-// int64 and double-float sums per column in registers and uses 32 columns.
-// The epilogue runs as NWG warpgroups: the register-light kinds use two, which
-// split a tile's columns in interleaved 8-column blocks so that two warps per
-// SM sub-partition hide each other's latencies; the summing kinds (FULLSQ,
-// FOCK) need their registers for running sums and use one with 16-column blocks.
+// Columns per tile: five groups of BN columns per accumulator set.  The half
+// transform runs two CTAs per SM, each with one set (5 x 48 = 240 of TMEM's 512
+// columns): one MMA-issuing thread cannot keep the tensor pipe busy (each
+// tcgen05.mma has a fixed issue latency), two can, and while one CTA drains its
+// accumulators the other one's MMAs run.  The other kinds keep running sums in
+// registers and run one CTA per SM with two ping-pong sets.  The full transform
+// uses 32 columns.
 template <int KIND>
 struct S4Cfg {
   static constexpr int BN = (KIND == S_FULLSQ) ? 32 : 48;
-  static constexpr int NWG = (KIND == S_FULLSQ || KIND == S_FOCK) ? 1 : 2;
-  static constexpr int CW = NWG == 1 ? 16 : 8;
+  static constexpr int CTAS = (KIND == S_HALF) ? 2 : 1;  // CTAs per SM
+  static constexpr int NSETS = CTAS == 2 ? 1 : 2;        // accumulator sets per CTA
+  static constexpr int TMEM_COLS = CTAS == 2 ? 256 : 512;
+  // Epilogue warpgroups: the kinds that carry int64 running sums across K chunks
+  // (J^(q), K^(q), J) split the columns over two warpgroups in 8-column blocks so
+  // that the sums stay in registers.
+  static constexpr int NWG = (KIND == S_JAO || KIND == S_KAO || KIND == S_JMO) ? 2 : 1;
+  static constexpr int CW = NWG == 2 ? 8 : 16;
   static constexpr int THREADS = 64 + 128 * NWG;
-  static constexpr int ES_WARP_BYTES = BN * 4 + BN * 8 + 4 * BN * 4 + BN * 8 * 4;
+  static constexpr int ES_WARP_BYTES = BN * 4 + BN * 8 + 4 * BN * 4 + BN * 16 * 4;
 };
 
 struct S4Params {
@@ -74,7 +84,7 @@ struct S4Params {
   const int* eb;
   __nv_bfloat16* o3;  // HALF: L3 digits [nx][mp][4][nbp]
   const int* e3;
-  __nv_bfloat16* o6;  // HALF: L6 digits [m][nb][4][nxp]
+  int* x6;            // HALF: L6 integers [nx][m][nbp] (digitised into L6 by x6_to_l6_kernel)
   const int* e6;
   float* ohi;
   float* olo;
@@ -159,6 +169,35 @@ __device__ __forceinline__ void ll_to_df(long long v, int k, float& h, float& l)
   l = ldexpf(ll, k);
 }
 
+// 2^k as an FP32 value for k in [-126, 127] (k is clamped to that range).
+__device__ __forceinline__ float exp2_int(int k) {
+  k = k < -126 ? -126 : (k > 127 ? 127 : k);
+  return __int_as_float((k + 127) << 23);
+}
+
+// Output integer of the half transform from one chunk's group sums:
+// X = sum_g rint(G_g 2^(sigma - 8 g)), clamped to [-2^30, 2^30], with
+// H_g = G_g 2^(-8 g) (exact).  Each term is rounded on its own, so X differs
+// from round(v 2^(sigma - 32)) by at most 2.5; the row exponents guarantee
+// |X| < 2^30 (the leading term is X to within a few per cent), so no term
+// reaches the int32 range.
+__device__ __forceinline__ int half_fold(const float H[S4_NG], int sigma) {
+  const float sc = exp2_int(sigma);
+  int X = 0;
+#pragma unroll
+  for (int g = 0; g < S4_NG; ++g) X += __float2int_rn(H[g] * sc);
+  X = X > (1 << 30) ? (1 << 30) : X;
+  X = X < -(1 << 30) ? -(1 << 30) : X;
+  return X;
+}
+
+// round(X 2^-d) for d >= 0 (halves rounded up), without overflow.
+__device__ __forceinline__ int rshift_round(int X, int d) {
+  if (d <= 0) return X;
+  const int sh = d - 1 > 31 ? 31 : d - 1;
+  return ((X >> sh) + 1) >> 1;
+}
+
 // ---------------------------------------------------------------------------
 // The digit-plane GEMM kernel
 // ---------------------------------------------------------------------------
@@ -185,11 +224,11 @@ __device__ __forceinline__ void s4_loads(const S4Params& p, uint8_t* st, uint64_
   const int k0 = kb * S4_BK, n0 = nt * BN;
 #pragma unroll
   for (int t = 0; t < S4_PLANES; ++t) {
-    uint8_t* da = st + t * (S4_BM * 128);
-    uint8_t* db = st + S4_PLANES * (S4_BM * 128) + t * (BN * 128);
+    uint8_t* da = st + t * (S4_BM * S4_BK * 2);
+    uint8_t* db = st + S4_PLANES * (S4_BM * S4_BK * 2) + t * (BN * S4_BK * 2);
     if (KIND == S_HALF) {
-      const int nvb = (p.nb + 7) / 8;
-      tma_load_4d(da, &p.a, bar, k0, t, (mt % nvb) * 8, (mt / nvb) * 16);
+      const int nvb = (p.nb + 15) / 16;
+      tma_load_4d(da, &p.a, bar, k0, t, (mt % nvb) * 16, (mt / nvb) * 8);
       tma_load_3d(db, &p.b, bar, k0, t, n0);
     } else if (KIND == S_FULLSQ || KIND == S_FOCK) {
       tma_load_4d(da, &p.a, bar, k0, t, mt * S4_BM, batch);
@@ -205,14 +244,15 @@ __device__ __forceinline__ void s4_loads(const S4Params& p, uint8_t* st, uint64_
 }
 
 template <int KIND>
-__global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, 1) s4_gemm_kernel(const __grid_constant__ S4Params p) {
+__global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_gemm_kernel(const __grid_constant__ S4Params p) {
   constexpr int BN = S4Cfg<KIND>::BN;
   constexpr int NWG = S4Cfg<KIND>::NWG, CW = S4Cfg<KIND>::CW;
   constexpr int NCBT = BN / CW / NWG;  // column blocks per epilogue thread
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int S = p.stages;
-  constexpr uint32_t a_bytes = S4_PLANES * S4_BM * 128, b_bytes = S4_PLANES * BN * 128;
+  constexpr int NSETS = S4Cfg<KIND>::NSETS;
+  constexpr uint32_t a_bytes = S4_PLANES * S4_BM * S4_BK * 2, b_bytes = S4_PLANES * BN * S4_BK * 2;
   constexpr uint32_t stage_bytes = a_bytes + b_bytes;
   uint64_t* full = (uint64_t*)(smem + (size_t)S * stage_bytes);
   uint64_t* empty = full + S;
@@ -230,7 +270,7 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, 1) s4_gemm_kernel(const 
   int* es_b = (int*)es_base;              // [BN]
   float2* es_w = (float2*)(es_b + BN);    // [BN]
   int* es_3 = (int*)(es_w + BN);          // [4][BN]: the warp's 4 auxiliary rows P
-  int* es_6 = es_3 + 4 * BN;              // [BN][8]
+  int* es_6 = es_3 + 4 * BN;              // [BN][16]
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   // Work assignment.  Persistent kinds: unit u is tile blockIdx.x + u*gridDim.x (one batch
@@ -299,8 +339,8 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, 1) s4_gemm_kernel(const 
         int batch, kb0, nkb;
         s4_unit<KIND>(p, p.persist ? 0 : b0 + u, batch, kb0, nkb);
         for (int ch = 0; ch * S4_CHUNK_KB < nkb && ok; ++ch) {
-          const int set = cc & 1;
-          if (!mbar_wait(&acce[set], (uint32_t)(((cc >> 1) & 1) ^ 1), abort_flag, p.status)) { ok = false; break; }
+          const int set = cc % NSETS;
+          if (!mbar_wait(&acce[set], (uint32_t)(((cc / NSETS) & 1) ^ 1), abort_flag, p.status)) { ok = false; break; }
           tc_fence_after();
           const uint32_t dbase = tmem_base + (uint32_t)(set * S4_NG * BN);
           const int kbs = min(S4_CHUNK_KB, nkb - ch * S4_CHUNK_KB);
@@ -312,12 +352,12 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, 1) s4_gemm_kernel(const 
             uint64_t dA[S4_PLANES], dB[S4_PLANES];
 #pragma unroll
             for (int t = 0; t < S4_PLANES; ++t) {
-              dA[t] = sdesc_sw128(st + (uint32_t)t * (S4_BM * 128));
-              dB[t] = sdesc_sw128(st + a_bytes + (uint32_t)t * (BN * 128));
+              dA[t] = sdesc_sw64(st + (uint32_t)t * (S4_BM * S4_BK * 2));
+              dB[t] = sdesc_sw64(st + a_bytes + (uint32_t)t * (BN * S4_BK * 2));
             }
-            // K step ks: +32 bytes inside the 128-byte swizzle row (+2 in the descriptor's address field)
-#pragma unroll 1
-            for (int ks = 0; ks < 4; ++ks) {
+            // K step ks: +32 bytes inside the 64-byte swizzle row (+2 in the descriptor's address field)
+#pragma unroll
+            for (int ks = 0; ks < S4_KS; ++ks) {
               const uint64_t o = (uint64_t)(2 * ks);
               if (j == 0 && ks == 0) {
                 // First step of a chunk: every group block must be written once with
@@ -380,25 +420,52 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, 1) s4_gemm_kernel(const 
       // Stage this unit's column exponents (and weights) in shared memory: one pass of
       // coalesced loads per warp instead of a dependent global load per output column.
       if (KIND != S_JMO) {
+        // All of a lane's loads are issued before any of them is stored, so the warp
+        // waits for one memory latency rather than one per element.
         __syncwarp();
-        for (int i = lane; i < BN; i += 32) {
-          const int col = nt * BN + i;
-          int e = 0;
-          if (KIND == S_KAO) e = col < p.nb ? p.eb[(size_t)batch * p.nb + col] : 0;
-          else e = col < p.m ? p.eb[col] : 0;
-          es_b[i] = e;
-          if (KIND == S_FOCK) es_w[i] = col < p.m ? p.w[(size_t)batch * p.m + col] : make_float2(0.f, 0.f);
+        constexpr int NLB = (BN + 31) / 32;
+        int rb[NLB];
+        float2 rw[KIND == S_FOCK ? NLB : 1];
+#pragma unroll
+        for (int k = 0; k < NLB; ++k) {
+          const int i = lane + 32 * k, col = nt * BN + i;
+          rb[k] = 0;
+          if (i < BN) {
+            if (KIND == S_KAO) rb[k] = col < p.nb ? p.eb[(size_t)batch * p.nb + col] : 0;
+            else rb[k] = col < p.m ? p.eb[col] : 0;
+          }
+          if (KIND == S_FOCK)
+            rw[KIND == S_FOCK ? k : 0] = (i < BN && col < p.m) ? p.w[(size_t)batch * p.m + col] : make_float2(0.f, 0.f);
         }
         if (KIND == S_HALF) {
-          const int nvb = (p.nb + 7) / 8;
+          const int nvb = (p.nb + 15) / 16;
           const int Pb = mt / nvb, vb = mt % nvb;
-          for (int i = lane; i < 4 * BN; i += 32) {
-            const int P = Pb * 16 + q * 4 + i / BN, pc = nt * BN + i % BN;
-            es_3[i] = (P < p.nx && pc < p.m) ? p.e3[(size_t)P * p.m + pc] : 0;
+          constexpr int N3 = 2 * BN / 32, N6 = BN * 16 / 32;
+          static_assert(KIND != S_HALF || (2 * BN) % 32 == 0, "staging assumes 2*BN divisible by 32");
+          int r3[N3], r6[N6];
+#pragma unroll
+          for (int k = 0; k < N3; ++k) {
+            const int i = lane + 32 * k;
+            const int P = Pb * 8 + q * 2 + i / BN, pc = nt * BN + i % BN;
+            r3[k] = (P < p.nx && pc < p.m) ? p.e3[(size_t)P * p.m + pc] : 0;
           }
-          for (int i = lane; i < BN * 8; i += 32) {
-            const int pc = nt * BN + i / 8, nu = vb * 8 + i % 8;
-            es_6[i] = (pc < p.m && nu < p.nb) ? p.e6[(size_t)pc * p.nb + nu] : 0;
+#pragma unroll
+          for (int k = 0; k < N6; ++k) {
+            const int i = lane + 32 * k;
+            const int pc = nt * BN + i / 16, nu = vb * 16 + i % 16;
+            r6[k] = (pc < p.m && nu < p.nb) ? p.e6[(size_t)pc * p.nb + nu] : 0;
+          }
+#pragma unroll
+          for (int k = 0; k < N3; ++k) es_3[lane + 32 * k] = r3[k];
+#pragma unroll
+          for (int k = 0; k < N6; ++k) es_6[lane + 32 * k] = r6[k];
+        }
+#pragma unroll
+        for (int k = 0; k < NLB; ++k) {
+          const int i = lane + 32 * k;
+          if (i < BN) {
+            es_b[i] = rb[k];
+            if (KIND == S_FOCK) es_w[i] = rw[KIND == S_FOCK ? k : 0];
           }
         }
         __syncwarp();
@@ -408,9 +475,11 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, 1) s4_gemm_kernel(const 
       bool rvalid = false;
       int P = 0, nu = 0, mu = 0;
       if (KIND == S_HALF) {
-        const int nvb = (p.nb + 7) / 8;
-        P = (mt / nvb) * 16 + row / 8;
-        nu = (mt % nvb) * 8 + row % 8;
+        // M tile = 16 nu x 8 P with nu fastest: a warp holds 16 consecutive nu of two
+        // auxiliary rows, so each L3 digit row it stores is one full 32-byte sector.
+        const int nvb = (p.nb + 15) / 16;
+        P = (mt / nvb) * 8 + row / 16;
+        nu = (mt % nvb) * 16 + row % 16;
         rvalid = P < p.nx && nu < p.nb;
         ea = rvalid ? p.ea[(size_t)P * p.nb + nu] : 0;
       } else if (KIND == S_FULLSQ) {
@@ -430,25 +499,65 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, 1) s4_gemm_kernel(const 
       }
       const int nch = (nkb + S4_CHUNK_KB - 1) / S4_CHUNK_KB;
       for (int ch = 0; ch < nch; ++ch) {
-        const int set = cc & 1;
-        if (!mbar_wait(&accf[set], (uint32_t)((cc >> 1) & 1), abort_flag, p.status)) { ok = false; break; }
+        const int set = cc % NSETS;
+        if (!mbar_wait(&accf[set], (uint32_t)((cc / NSETS) & 1), abort_flag, p.status)) { ok = false; break; }
         tc_fence_after();
         const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(set * S4_NG * BN);
         const bool last = (ch == nch - 1);
-#pragma unroll(KIND == S_HALF || KIND == S_JMO ? 1 : NCBT)
+#pragma unroll(SUM_DF || NWG == 2 ? NCBT : 1)
         for (int cb = 0; cb < NCBT; ++cb) {
           const int c = cb * NWG + wg;  // column block (CW columns)
           // group g holds digit pairs with t + u = g; its weight is 2^(32 - 8 g) in units of 2^(ea+eb-46)
+          uint32_t gr[S4_NG][CW];
+#pragma unroll
+          for (int g = 0; g < S4_NG; ++g) {
+            if (CW == 16) tmem_ld16_issue(tb + (uint32_t)(g * BN + c * CW), gr[g]);
+            else tmem_ld8_issue(tb + (uint32_t)(g * BN + c * CW), gr[g]);
+          }
+#pragma unroll
+          for (int g = 0; g < S4_NG; ++g) {
+            if (CW == 16) tmem_wait16(gr[g]);
+            else tmem_wait8(gr[g]);
+          }
+          if (KIND == S_HALF && nch == 1) {
+            // Single-chunk half transform: both output integers straight from the
+            // five group sums, X = sum_g rint(G_g 2^(sigma - 8g)) in int32 (see
+            // half_fold), without the int64 fold.
+            if (!rvalid) continue;
+            const int lrow = lane / 16, l16 = lane % 16;
+            __nv_bfloat16* base3 = p.o3 + ((size_t)P * p.mp * 4) * p.nbp + nu;
+            int* base6 = p.x6 + (size_t)P * p.m * p.nbp + nu;
+#pragma unroll
+            for (int j = 0; j < CW; ++j) {
+              const int i = c * CW + j;
+              const int col = nt * BN + i;
+              if (col < p.m) {
+                float H[S4_NG];
+#pragma unroll
+                for (int g = 0; g < S4_NG; ++g) H[g] = __uint_as_float(gr[g][j]) * exp2_int(-8 * g);
+                // One fold at the finer of the two output scales; the other output is
+                // a rounding right shift of it (at most one unit of double rounding).
+                const int sg = ea + es_b[i] + 17;
+                const int s3 = sg - es_3[lrow * BN + i], s6 = sg - es_6[i * 16 + l16];
+                const int sf = s3 > s6 ? s3 : s6;
+                const int Xf = half_fold(H, sf);
+                __nv_bfloat16 d[4];
+                digits_bf16(rshift_round(Xf, sf - s3), d);
+                __nv_bfloat16* o3 = base3 + (size_t)col * 4 * p.nbp;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) o3[t * p.nbp] = d[t];
+                base6[(size_t)col * p.nbp] = rshift_round(Xf, sf - s6);
+              }
+            }
+            continue;
+          }
           long long v[CW];
 #pragma unroll
           for (int j = 0; j < CW; ++j) v[j] = (KIND != S_FOCK && (ch > 0 || KIND == S_JMO)) ? acc[NACC == 1 ? 0 : cb * CW + j] : 0;
 #pragma unroll
           for (int g = 0; g < S4_NG; ++g) {
-            float gv[CW];
-            if (CW == 16) tmem_ld16(tb + (uint32_t)(g * BN + c * CW), gv);
-            else tmem_ld8(tb + (uint32_t)(g * BN + c * CW), gv);
 #pragma unroll
-            for (int j = 0; j < CW; ++j) v[j] += (long long)__float2int_rn(gv[j]) << (32 - 8 * g);
+            for (int j = 0; j < CW; ++j) v[j] += (long long)__float2int_rn(__uint_as_float(gr[g][j])) << (32 - 8 * g);
           }
           if (KIND != S_FOCK && (!last || KIND == S_JMO)) {
 #pragma unroll
@@ -458,9 +567,9 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, 1) s4_gemm_kernel(const 
           // ---- the block's values are final: unit action ----
           if (!rvalid) continue;
           if (KIND == S_HALF) {
-            const int lrow = lane / 8, l8 = row % 8;
+            const int lrow = lane / 16, l16 = lane % 16;
             __nv_bfloat16* base3 = p.o3 + ((size_t)P * p.mp * 4) * p.nbp + nu;
-            __nv_bfloat16* base6 = p.o6 + (size_t)nu * 4 * p.nxp + P;
+            int* base6 = p.x6 + (size_t)P * p.m * p.nbp + nu;
 #pragma unroll
             for (int j = 0; j < CW; ++j) {
               const int i = c * CW + j;
@@ -472,10 +581,7 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, 1) s4_gemm_kernel(const 
                 __nv_bfloat16* o3 = base3 + (size_t)col * 4 * p.nbp;
 #pragma unroll
                 for (int t = 0; t < 4; ++t) o3[t * p.nbp] = d[t];
-                digits_bf16(round_shift(v[j], sb - es_6[i * 8 + l8]), d);
-                __nv_bfloat16* o6 = base6 + (size_t)col * p.nb * 4 * p.nxp;
-#pragma unroll
-                for (int t = 0; t < 4; ++t) o6[t * p.nxp] = d[t];
+                base6[(size_t)col * p.nbp] = round_shift(v[j], sb - es_6[i * 16 + l16]);
               }
             }
           } else if (KIND == S_FULLSQ) {
@@ -749,6 +855,30 @@ __global__ void fock_weights_df_kernel(const double* A, const double* Bc, int m,
 }
 
 // Interleaved digits + row exponents -> FP64 values (fetch / copy-out paths).
+// L6 digits [p][nu][t][P] from the half transform's integers X6 [P][p][nu]
+// (same exponents e6): a 32 x 32 (P, nu) tile per block, transposed in shared
+// memory so that both the reads (nu contiguous) and the digit stores (P
+// contiguous, 64 bytes per row) are full sectors.
+__global__ void x6_to_l6_kernel(const int* X6, int nx, int nb, int m, int nbp, int nxp, __nv_bfloat16* L6) {
+  __shared__ int tile[32][33];
+  const int p = blockIdx.z, nu0 = blockIdx.x * 32, P0 = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int P = P0 + r, nu = nu0 + threadIdx.x;
+    tile[r][threadIdx.x] = (P < nx && nu < nb) ? X6[((size_t)P * m + p) * nbp + nu] : 0;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int nu = nu0 + r, P = P0 + threadIdx.x;
+    if (nu < nb && P < nx) {
+      __nv_bfloat16 d[4];
+      digits_bf16(tile[threadIdx.x][r], d);
+      __nv_bfloat16* o = L6 + ((size_t)p * nb + nu) * 4 * nxp + P;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) o[(size_t)t * nxp] = d[t];
+    }
+  }
+}
+
 __global__ void unslice_kernel(const __nv_bfloat16* planes, int ldp, const int* exps, long long rows, int cols,
                                double* out) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -778,6 +908,7 @@ __global__ void join_pair_kernel(const float* hi, const float* lo, long long row
 struct donof::S4Buffers {
   int nbp, nxp, mp, ldo;
   __nv_bfloat16 *B1, *B5, *Ct, *L3, *L6, *Dp, *JKp;  // interleaved digits
+  int* X6;                                            // L6 integers [nx][m][nbp] before digitisation
   int *eB1, *eB5, *eC, *e3, *e6, *ed, *eJK;          // row exponents
   float *rmaxB, *maxB, *absC, *absCt;
   float2* Cdf;    // C rows p (< N_O) as double-float pairs
@@ -797,7 +928,7 @@ namespace donof {
 
 static int s4_round_up(int a, int b) { return (a + b - 1) / b * b; }
 
-// BF16 tensor map, 128-byte swizzle; dims innermost first, strides in elements.
+// BF16 tensor map, 64-byte swizzle; dims innermost first, strides in elements.
 static int s4_map(S4Buffers* sb, CUtensorMap* map, const void* base, int rank, const long long* dims,
                   const long long* strides_el, const int* box) {
   cuuint64_t gd[5], gs[4];
@@ -812,7 +943,7 @@ static int s4_map(S4Buffers* sb, CUtensorMap* map, const void* base, int rank, c
   }
   if (((uintptr_t)base) % 16) return DONOF_RI_E_ARG;
   CUresult r = sb->encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, (void*)base, gd, gs, bd, es,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? DONOF_RI_OK : DONOF_RI_E_CUDA;
 }
@@ -821,11 +952,14 @@ template <int KIND>
 static void s4_plan(S4Buffers* sb, int m_tiles, int n_tiles, int nbatch, int target_ctas, int persist_ctas = 0) {
   constexpr int BN = S4Cfg<KIND>::BN;
   S4Params& p = sb->plan[KIND];
-  const size_t stage = (size_t)S4_PLANES * (S4_BM + BN) * 128;
-  int S = (int)((200 * 1024) / stage);
-  if (S > 4) S = 4;
+  const size_t stage = (size_t)S4_PLANES * (S4_BM + BN) * S4_BK * 2;
+  // Two CTAs per SM share its 228 KB of shared memory (1 KB of it reserved per CTA).
+  const size_t fixed = 1024 + 256 + 4 * S4Cfg<KIND>::NWG * (size_t)S4Cfg<KIND>::ES_WARP_BYTES;
+  const size_t budget = (S4Cfg<KIND>::CTAS == 2 ? (size_t)112 * 1024 : (size_t)220 * 1024) - fixed;
+  int S = (int)(budget / stage);
+  if (S > 6) S = 6;
   p.stages = S;
-  p.tmem_cols = 512;
+  p.tmem_cols = S4Cfg<KIND>::TMEM_COLS;
   p.n_tiles = n_tiles;
   p.nbatch = nbatch;
   const int tiles = m_tiles * n_tiles;
@@ -835,7 +969,7 @@ static void s4_plan(S4Buffers* sb, int m_tiles, int n_tiles, int nbatch, int tar
   p.bpc = (nbatch + ns - 1) / ns;
   p.nsplit = (nbatch + p.bpc - 1) / p.bpc;
   sb->grid[KIND] = tiles * p.nsplit;
-  sb->smem[KIND] = 1024 + (size_t)S * stage + 256 + 4 * S4Cfg<KIND>::NWG * (size_t)S4Cfg<KIND>::ES_WARP_BYTES;
+  sb->smem[KIND] = fixed + (size_t)S * stage;
   p.persist = 0;
   p.ntiles = tiles;
   if (persist_ctas > 0 && nbatch == 1) {
@@ -861,17 +995,18 @@ int s4_init(donof_ri_ctx* ctx) {
     sb->encode = (PFN_cuTensorMapEncodeTiled_v12000)f;
   }
   const int nb = ctx->nbf, nx = ctx->naux, m = ctx->n_omega;
-  const int nbp = s4_round_up(nb, 8), nxp = s4_round_up(nx, 8), mp = s4_round_up(m, 4), ldo = s4_round_up(nb, 4);
+  // Digit rows padded to 16 elements (32 bytes) so that full-sector stores stay aligned.
+  const int nbp = s4_round_up(nb, 16), nxp = s4_round_up(nx, 16), mp = s4_round_up(m, 4), ldo = s4_round_up(nb, 4);
   sb->nbp = nbp; sb->nxp = nxp; sb->mp = mp; sb->ldo = ldo;
   const long long nbs = nb, nxs = nx, ms = m;
   const int sms = 152;
   const int KBb = (nb + S4_BK - 1) / S4_BK, KBx = (nx + S4_BK - 1) / S4_BK;
   const int bn = S4Cfg<S_HALF>::BN;  // 48 for every kind but the full transform (32)
-  s4_plan<S_HALF>(sb, ((nx + 15) / 16) * ((nb + 7) / 8), (m + bn - 1) / bn, 1, 1, sms);
+  s4_plan<S_HALF>(sb, ((nx + 7) / 8) * ((nb + 15) / 16), (m + bn - 1) / bn, 1, 1, S4Cfg<S_HALF>::CTAS * sms);
   s4_plan<S_FULLSQ>(sb, (m + S4_BM - 1) / S4_BM, (m + 31) / 32, nx, 2 * sms);
   s4_plan<S_JMO>(sb, (m + S4_BM - 1) / S4_BM, (m + bn - 1) / bn, (KBx + S4_CHUNK_KB - 1) / S4_CHUNK_KB, 2 * sms);
-  s4_plan<S_JAO>(sb, (nb * nb + S4_BM - 1) / S4_BM, (m + bn - 1) / bn, 1, 1, sms);
-  s4_plan<S_KAO>(sb, (nb + S4_BM - 1) / S4_BM, (nb + bn - 1) / bn, m, sms);
+  s4_plan<S_JAO>(sb, (nb * nb + S4_BM - 1) / S4_BM, (m + bn - 1) / bn, 1, 1, S4Cfg<S_JAO>::CTAS * sms);
+  s4_plan<S_KAO>(sb, (nb + S4_BM - 1) / S4_BM, (nb + bn - 1) / bn, m, S4Cfg<S_KAO>::CTAS * sms);
   s4_plan<S_FOCK>(sb, (nb + S4_BM - 1) / S4_BM, (m + bn - 1) / bn, 2 * m * ((KBb + S4_CHUNK_KB - 1) / S4_CHUNK_KB), sms);
   size_t pbytes = (size_t)sb->plan[S_FULLSQ].nsplit * m * m * sizeof(float2);
   size_t t = (size_t)sb->plan[S_JMO].nsplit * m * m * sizeof(long long);
@@ -891,6 +1026,7 @@ int s4_init(donof_ri_ctx* ctx) {
   ALLOC(sb->Ct, ms * 4 * nbp * 2);
   ALLOC(sb->L3, nxs * mp * 4 * nbp * 2);
   ALLOC(sb->L6, ms * nbs * 4 * nxp * 2);
+  ALLOC(sb->X6, nxs * ms * nbp * 4);
   ALLOC(sb->Dp, ms * 4 * nxp * 2);
   ALLOC(sb->JKp, 2 * ms * nbs * 4 * nbp * 2);
   ALLOC(sb->eB1, nxs * nbs * 4);
@@ -942,14 +1078,14 @@ int s4_init(donof_ri_ctx* ctx) {
   {  // HALF: A = B1 [nx][nb][4][nbp] rows (P, nu) over mu; B = C^T digits [m][4][nbp]
     S4Params& p = sb->plan[S_HALF];
     long long dA[4] = {nb, 4, nb, nx}, sA[3] = {nbp, 4LL * nbp, nbs * 4 * nbp};
-    int bA[4] = {S4_BK, 1, 8, 16};
+    int bA[4] = {S4_BK, 1, 16, 8};
     long long dB[3] = {nb, 4, m}, sB[2] = {nbp, 4LL * nbp};
     int bB[3] = {S4_BK, 1, bn};
     if ((rc = s4_map(sb, &p.a, sb->B1, 4, dA, sA, bA))) return rc;
     if ((rc = s4_map(sb, &p.b, sb->Ct, 3, dB, sB, bB))) return rc;
     p.ea = sb->eB1; p.eb = sb->eC;
     p.o3 = sb->L3; p.e3 = sb->e3;
-    p.o6 = sb->L6; p.e6 = sb->e6;
+    p.x6 = sb->X6; p.e6 = sb->e6;
   }
   {  // FULLSQ: A = L3 [nx][mp][4][nbp] rows p (per P) over nu; B = C^T digits
     S4Params& p = sb->plan[S_FULLSQ];
@@ -1007,7 +1143,9 @@ int s4_init(donof_ri_ctx* ctx) {
   }
 #define OPTIN(KIND)                                                                                           \
   if (cudaFuncSetAttribute(s4_gemm_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,                \
-                           (int)sb->smem[KIND]) != cudaSuccess)                                               \
+                           (int)sb->smem[KIND]) != cudaSuccess ||                                             \
+      cudaFuncSetAttribute(s4_gemm_kernel<KIND>, cudaFuncAttributePreferredSharedMemoryCarveout,             \
+                           (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)                               \
     return DONOF_RI_E_CUDA;
   OPTIN(S_HALF) OPTIN(S_FULLSQ) OPTIN(S_JMO) OPTIN(S_JAO) OPTIN(S_KAO) OPTIN(S_FOCK)
 #undef OPTIN
@@ -1017,7 +1155,7 @@ int s4_init(donof_ri_ctx* ctx) {
 void s4_free(donof_ri_ctx* ctx) {
   S4Buffers* sb = ctx->s4;
   if (!sb) return;
-  void* bufs[] = {sb->B1,    sb->B5,   sb->Ct,   sb->L3,   sb->L6, sb->Dp,  sb->JKp,  sb->eB1,   sb->eB5,
+  void* bufs[] = {sb->X6,    sb->B1,   sb->B5,   sb->Ct,   sb->L3,   sb->L6, sb->Dp,  sb->JKp,  sb->eB1,   sb->eB5,
                   sb->eC,    sb->e3,   sb->e6,   sb->ed,   sb->eJK, sb->rmaxB, sb->maxB, sb->absC, sb->absCt,
                   sb->Cdf,   sb->dmat, sb->JKhi, sb->JKlo, sb->W,  sb->HCt, sb->Yt,   sb->partial};
   for (void* b : bufs)
@@ -1054,6 +1192,9 @@ int s4_transform(donof_ri_ctx* ctx, int mode) {
   {
     ProfScope ps(ctx, DONOF_RI_ROW_HALF);
     if ((rc = launch_s4<S_HALF>(ctx))) return rc;
+    dim3 g((nb + 31) / 32, (nx + 31) / 32, m), b(32, 8);
+    x6_to_l6_kernel<<<g, b, 0, s>>>(sb->X6, nx, nb, m, sb->nbp, sb->nxp, sb->L6);
+    DONOF_LAUNCH_CHECK(ctx);
   }
   {
     ProfScope ps(ctx, DONOF_RI_ROW_DIAG);

@@ -275,8 +275,10 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_ge
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   // Work assignment.  Persistent kinds: unit u is tile blockIdx.x + u*gridDim.x (one batch
   // entry).  Other kinds: the CTA owns one tile and a contiguous range of its batch entries.
-  const int tile0 = p.persist ? (int)blockIdx.x : (int)blockIdx.x / p.nsplit;
-  const int split = p.persist ? 0 : (int)blockIdx.x % p.nsplit;
+  // Non-persistent kinds: tile fastest, so that the CTAs running at the same time
+  // cover every tile of the same batch range and share its A rows through L2.
+  const int tile0 = p.persist ? (int)blockIdx.x : (int)blockIdx.x % p.ntiles;
+  const int split = p.persist ? 0 : (int)blockIdx.x / p.ntiles;
   const int b0 = split * p.bpc;
   const int nunits = p.persist ? max(0, (p.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x)
                                : max(0, min(p.nbatch, b0 + p.bpc) - b0);
@@ -623,16 +625,28 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_ge
               }
             }
           } else if (KIND == S_KAO) {
+            // A thread's CW = 8 consecutive columns of one output row are one 32-byte
+            // sector of hi and one of lo (ldo is a multiple of 8): two 16-byte vector
+            // stores each instead of eight scattered 4-byte ones.
+            float h[CW], l[CW];
 #pragma unroll
-            for (int j = 0; j < CW; ++j) {
-              const int i = c * CW + j;
-              const int col = nt * BN + i;
-              if (col < p.nb) {
-                float h, l;
-                ll_to_df(v[j], ea + es_b[i] - S4_SHIFT, h, l);
-                const size_t o = ((size_t)(p.m + batch) * p.nb + mu) * p.ldo + col;
-                p.ohi[o] = h;
-                p.olo[o] = l;
+            for (int j = 0; j < CW; ++j) ll_to_df(v[j], ea + es_b[c * CW + j] - S4_SHIFT, h[j], l[j]);
+            const int col0 = nt * BN + c * CW;
+            const size_t o = ((size_t)(p.m + batch) * p.nb + mu) * p.ldo + col0;
+            if (CW == 8 && col0 + CW <= p.nb) {
+              float4* dh = (float4*)(p.ohi + o);
+              float4* dl = (float4*)(p.olo + o);
+              dh[0] = make_float4(h[0], h[1], h[2], h[3]);
+              dh[1] = make_float4(h[4], h[5], h[6], h[7]);
+              dl[0] = make_float4(l[0], l[1], l[2], l[3]);
+              dl[1] = make_float4(l[4], l[5], l[6], l[7]);
+            } else {
+#pragma unroll
+              for (int j = 0; j < CW; ++j) {
+                if (col0 + j < p.nb) {
+                  p.ohi[o + j] = h[j];
+                  p.olo[o + j] = l[j];
+                }
               }
             }
           }
@@ -996,7 +1010,7 @@ int s4_init(donof_ri_ctx* ctx) {
   }
   const int nb = ctx->nbf, nx = ctx->naux, m = ctx->n_omega;
   // Digit rows padded to 16 elements (32 bytes) so that full-sector stores stay aligned.
-  const int nbp = s4_round_up(nb, 16), nxp = s4_round_up(nx, 16), mp = s4_round_up(m, 4), ldo = s4_round_up(nb, 4);
+  const int nbp = s4_round_up(nb, 16), nxp = s4_round_up(nx, 16), mp = s4_round_up(m, 4), ldo = s4_round_up(nb, 8);
   sb->nbp = nbp; sb->nxp = nxp; sb->mp = mp; sb->ldo = ldo;
   const long long nbs = nb, nxs = nx, ms = m;
   const int sms = 152;

@@ -273,14 +273,15 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_ge
   int* es_6 = es_3 + 4 * BN;              // [BN][16]
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  // Work assignment.  Persistent kinds: unit u is tile blockIdx.x + u*gridDim.x (one batch
-  // entry).  Other kinds: the CTA owns one tile and a contiguous range of its batch entries.
-  // Non-persistent kinds: tile fastest, so that the CTAs running at the same time
-  // cover every tile of the same batch range and share its A rows through L2.
+  // Work assignment.  Persistent kinds (no sums across units): unit U = blockIdx.x +
+  // u*gridDim.x of ntiles x nbatch, tile U % ntiles of batch entry U / ntiles.  Other
+  // kinds: the CTA owns one tile and a contiguous range of its batch entries, with the
+  // tile fastest in blockIdx so that the CTAs running at the same time cover every
+  // tile of the same batch range and share its A rows through L2.
   const int tile0 = p.persist ? (int)blockIdx.x : (int)blockIdx.x % p.ntiles;
   const int split = p.persist ? 0 : (int)blockIdx.x / p.ntiles;
   const int b0 = split * p.bpc;
-  const int nunits = p.persist ? max(0, (p.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x)
+  const int nunits = p.persist ? max(0, (p.ntiles * p.nbatch - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x)
                                : max(0, min(p.nbatch, b0 + p.bpc) - b0);
   int mt = tile0 / p.n_tiles, nt = tile0 % p.n_tiles;
 
@@ -310,9 +311,10 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_ge
       bool ok = true;
       for (int u = 0; u < nunits && ok; ++u) {
         int batch, kb0, nkb;
-        s4_unit<KIND>(p, p.persist ? 0 : b0 + u, batch, kb0, nkb);
+        const int U = tile0 + u * (int)gridDim.x;
+        s4_unit<KIND>(p, p.persist ? U / p.ntiles : b0 + u, batch, kb0, nkb);
         if (p.persist) {
-          const int tl = tile0 + u * (int)gridDim.x;
+          const int tl = U % p.ntiles;
           mt = tl / p.n_tiles;
           nt = tl % p.n_tiles;
         }
@@ -339,7 +341,7 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_ge
       bool ok = true;
       for (int u = 0; u < nunits && ok; ++u) {
         int batch, kb0, nkb;
-        s4_unit<KIND>(p, p.persist ? 0 : b0 + u, batch, kb0, nkb);
+        s4_unit<KIND>(p, p.persist ? (tile0 + u * (int)gridDim.x) / p.ntiles : b0 + u, batch, kb0, nkb);
         for (int ch = 0; ch * S4_CHUNK_KB < nkb && ok; ++ch) {
           const int set = cc % NSETS;
           if (!mbar_wait(&acce[set], (uint32_t)(((cc / NSETS) & 1) ^ 1), abort_flag, p.status)) { ok = false; break; }
@@ -413,9 +415,10 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_ge
     bool ok = true;
     for (int u = 0; u < nunits && ok; ++u) {
       int batch, kb0, nkb;
-      s4_unit<KIND>(p, p.persist ? 0 : b0 + u, batch, kb0, nkb);
+      const int U = tile0 + u * (int)gridDim.x;
+      s4_unit<KIND>(p, p.persist ? U / p.ntiles : b0 + u, batch, kb0, nkb);
       if (p.persist) {
-        const int tl = tile0 + u * (int)gridDim.x;
+        const int tl = U % p.ntiles;
         mt = tl / p.n_tiles;
         nt = tl % p.n_tiles;
       }
@@ -977,7 +980,8 @@ static void s4_plan(S4Buffers* sb, int m_tiles, int n_tiles, int nbatch, int tar
   p.n_tiles = n_tiles;
   p.nbatch = nbatch;
   const int tiles = m_tiles * n_tiles;
-  int ns = (target_ctas + tiles - 1) / tiles;
+  // At most one wave: a second, partial wave would double the time of its CTAs' share.
+  int ns = target_ctas / tiles;
   if (ns < 1) ns = 1;
   if (ns > nbatch) ns = nbatch;
   p.bpc = (nbatch + ns - 1) / ns;
@@ -986,11 +990,12 @@ static void s4_plan(S4Buffers* sb, int m_tiles, int n_tiles, int nbatch, int tar
   sb->smem[KIND] = fixed + (size_t)S * stage;
   p.persist = 0;
   p.ntiles = tiles;
-  if (persist_ctas > 0 && nbatch == 1) {
+  if (persist_ctas > 0) {
     p.persist = 1;
     p.nsplit = 1;
     p.bpc = 1;
-    sb->grid[KIND] = tiles < persist_ctas ? tiles : persist_ctas;
+    const long long units = (long long)tiles * nbatch;
+    sb->grid[KIND] = units < persist_ctas ? (int)units : persist_ctas;
   }
 }
 
@@ -1017,10 +1022,12 @@ int s4_init(donof_ri_ctx* ctx) {
   const int KBb = (nb + S4_BK - 1) / S4_BK, KBx = (nx + S4_BK - 1) / S4_BK;
   const int bn = S4Cfg<S_HALF>::BN;  // 48 for every kind but the full transform (32)
   s4_plan<S_HALF>(sb, ((nx + 7) / 8) * ((nb + 15) / 16), (m + bn - 1) / bn, 1, 1, S4Cfg<S_HALF>::CTAS * sms);
-  s4_plan<S_FULLSQ>(sb, (m + S4_BM - 1) / S4_BM, (m + 31) / 32, nx, 2 * sms);
-  s4_plan<S_JMO>(sb, (m + S4_BM - 1) / S4_BM, (m + bn - 1) / bn, (KBx + S4_CHUNK_KB - 1) / S4_CHUNK_KB, 2 * sms);
+  s4_plan<S_FULLSQ>(sb, (m + S4_BM - 1) / S4_BM, (m + 31) / 32, nx, S4Cfg<S_FULLSQ>::CTAS * sms);
+  s4_plan<S_JMO>(sb, (m + S4_BM - 1) / S4_BM, (m + bn - 1) / bn, (KBx + S4_CHUNK_KB - 1) / S4_CHUNK_KB,
+                 S4Cfg<S_JMO>::CTAS * sms);
   s4_plan<S_JAO>(sb, (nb * nb + S4_BM - 1) / S4_BM, (m + bn - 1) / bn, 1, 1, S4Cfg<S_JAO>::CTAS * sms);
-  s4_plan<S_KAO>(sb, (nb + S4_BM - 1) / S4_BM, (nb + bn - 1) / bn, m, S4Cfg<S_KAO>::CTAS * sms);
+  s4_plan<S_KAO>(sb, (nb + S4_BM - 1) / S4_BM, (nb + bn - 1) / bn, m, S4Cfg<S_KAO>::CTAS * sms,
+                 S4Cfg<S_KAO>::CTAS * sms);
   s4_plan<S_FOCK>(sb, (nb + S4_BM - 1) / S4_BM, (m + bn - 1) / bn, 2 * m * ((KBb + S4_CHUNK_KB - 1) / S4_CHUNK_KB), sms);
   size_t pbytes = (size_t)sb->plan[S_FULLSQ].nsplit * m * m * sizeof(float2);
   size_t t = (size_t)sb->plan[S_JMO].nsplit * m * m * sizeof(long long);

@@ -38,6 +38,8 @@
 #include <cuda_bf16.h>
 #include <stdlib.h>
 
+#include <vector>
+
 namespace donof {
 int launch_dot64(donof_ri_ctx* ctx, int M, int N, int K, const double* A, int lda, const double* B, int ldb,
                  double* out, long long so_i, long long so_j);
@@ -95,6 +97,7 @@ struct S4Params {
   int* status;
   int persist;      // 1: units are whole tiles, CTA c takes tiles c, c + grid, ...
   int ntiles;       // total tiles (persistent kinds)
+  const int* tmap;  // optional list of the tiles to compute, (mt << 16) | nt (K^(q): upper triangle)
 };
 
 // ---------------------------------------------------------------------------
@@ -315,8 +318,8 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_ge
         s4_unit<KIND>(p, p.persist ? U / p.ntiles : b0 + u, batch, kb0, nkb);
         if (p.persist) {
           const int tl = U % p.ntiles;
-          mt = tl / p.n_tiles;
-          nt = tl % p.n_tiles;
+          mt = p.tmap ? p.tmap[tl] >> 16 : tl / p.n_tiles;
+          nt = p.tmap ? p.tmap[tl] & 0xFFFF : tl % p.n_tiles;
         }
         for (int kb = 0; kb < nkb; ++kb) {
           const int s = it % S;
@@ -419,8 +422,8 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_ge
       s4_unit<KIND>(p, p.persist ? U / p.ntiles : b0 + u, batch, kb0, nkb);
       if (p.persist) {
         const int tl = U % p.ntiles;
-        mt = tl / p.n_tiles;
-        nt = tl % p.n_tiles;
+        mt = p.tmap ? p.tmap[tl] >> 16 : tl / p.n_tiles;
+        nt = p.tmap ? p.tmap[tl] & 0xFFFF : tl % p.n_tiles;
       }
       // Stage this unit's column exponents (and weights) in shared memory: one pass of
       // coalesced loads per warp instead of a dependent global load per output column.
@@ -896,6 +899,36 @@ __global__ void x6_to_l6_kernel(const int* X6, int nx, int nb, int m, int nbp, i
   }
 }
 
+// K^(q) is symmetric: the GEMM skips the tiles (128 mu x 48 nu) that lie wholly
+// below the diagonal, and this kernel fills their elements from the transposed
+// ones, through a shared-memory tile so that reads and writes are coalesced.
+// hi/lo: [2m][nb][ldo] with K^(q) at rows m + q.
+__device__ __forceinline__ bool kao_tile_computed(int mu, int nu, int bn) {
+  return (nu / bn) * bn + bn - 1 >= (mu / 128) * 128;
+}
+
+__global__ void kao_mirror_kernel(float* hi, float* lo, int nb, int m, int ldo, int bn) {
+  __shared__ float th[32][33], tl[32][33];
+  const int bi = blockIdx.y, bj = blockIdx.x;  // destination block: rows mu (bi), columns nu (bj)
+  if (bj > bi) return;
+  const size_t base = (size_t)(m + blockIdx.z) * nb * ldo;
+  for (int r = threadIdx.y; r < 32; r += 8) {  // source rows nu = bj*32 + r, columns mu = bi*32 + x
+    const int nu = bj * 32 + r, mu = bi * 32 + threadIdx.x;
+    if (nu < nb && mu < nb) {
+      th[r][threadIdx.x] = hi[base + (size_t)nu * ldo + mu];
+      tl[r][threadIdx.x] = lo[base + (size_t)nu * ldo + mu];
+    }
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int mu = bi * 32 + r, nu = bj * 32 + threadIdx.x;
+    if (mu < nb && nu < nb && nu < mu && !kao_tile_computed(mu, nu, bn)) {
+      hi[base + (size_t)mu * ldo + nu] = th[threadIdx.x][r];
+      lo[base + (size_t)mu * ldo + nu] = tl[threadIdx.x][r];
+    }
+  }
+}
+
 __global__ void unslice_kernel(const __nv_bfloat16* planes, int ldp, const int* exps, long long rows, int cols,
                                double* out) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -926,6 +959,7 @@ struct donof::S4Buffers {
   int nbp, nxp, mp, ldo;
   __nv_bfloat16 *B1, *B5, *Ct, *L3, *L6, *Dp, *JKp;  // interleaved digits
   int* X6;                                            // L6 integers [nx][m][nbp] before digitisation
+  int* kao_tmap;                                      // K^(q) tiles on or above the diagonal
   int *eB1, *eB5, *eC, *e3, *e6, *ed, *eJK;          // row exponents
   float *rmaxB, *maxB, *absC, *absCt;
   float2* Cdf;    // C rows p (< N_O) as double-float pairs
@@ -1026,8 +1060,12 @@ int s4_init(donof_ri_ctx* ctx) {
   s4_plan<S_JMO>(sb, (m + S4_BM - 1) / S4_BM, (m + bn - 1) / bn, (KBx + S4_CHUNK_KB - 1) / S4_CHUNK_KB,
                  S4Cfg<S_JMO>::CTAS * sms);
   s4_plan<S_JAO>(sb, (nb * nb + S4_BM - 1) / S4_BM, (m + bn - 1) / bn, 1, 1, S4Cfg<S_JAO>::CTAS * sms);
-  s4_plan<S_KAO>(sb, (nb + S4_BM - 1) / S4_BM, (nb + bn - 1) / bn, m, S4Cfg<S_KAO>::CTAS * sms,
-                 S4Cfg<S_KAO>::CTAS * sms);
+  // K^(q): only the tiles that reach the diagonal or lie above it (the rest is mirrored).
+  std::vector<int> kao_tiles;
+  for (int mt = 0; mt < (nb + S4_BM - 1) / S4_BM; ++mt)
+    for (int nt = 0; nt < (nb + bn - 1) / bn; ++nt)
+      if (nt * bn + bn - 1 >= mt * S4_BM) kao_tiles.push_back((mt << 16) | nt);
+  s4_plan<S_KAO>(sb, 1, (int)kao_tiles.size(), m, S4Cfg<S_KAO>::CTAS * sms, S4Cfg<S_KAO>::CTAS * sms);
   s4_plan<S_FOCK>(sb, (nb + S4_BM - 1) / S4_BM, (m + bn - 1) / bn, 2 * m * ((KBb + S4_CHUNK_KB - 1) / S4_CHUNK_KB), sms);
   size_t pbytes = (size_t)sb->plan[S_FULLSQ].nsplit * m * m * sizeof(float2);
   size_t t = (size_t)sb->plan[S_JMO].nsplit * m * m * sizeof(long long);
@@ -1048,6 +1086,10 @@ int s4_init(donof_ri_ctx* ctx) {
   ALLOC(sb->L3, nxs * mp * 4 * nbp * 2);
   ALLOC(sb->L6, ms * nbs * 4 * nxp * 2);
   ALLOC(sb->X6, nxs * ms * nbp * 4);
+  ALLOC(sb->kao_tmap, kao_tiles.size() * sizeof(int));
+  if (cudaMemcpy(sb->kao_tmap, kao_tiles.data(), kao_tiles.size() * sizeof(int), cudaMemcpyHostToDevice) !=
+      cudaSuccess)
+    return DONOF_RI_E_CUDA;
   ALLOC(sb->Dp, ms * 4 * nxp * 2);
   ALLOC(sb->JKp, 2 * ms * nbs * 4 * nbp * 2);
   ALLOC(sb->eB1, nxs * nbs * 4);
@@ -1149,6 +1191,7 @@ int s4_init(donof_ri_ctx* ctx) {
     if ((rc = s4_map(sb, &p.b, sb->L6, 4, dA, sA, bB))) return rc;
     p.ea = sb->e6; p.eb = sb->e6;
     p.ohi = sb->JKhi; p.olo = sb->JKlo;
+    p.tmap = sb->kao_tmap;
   }
   {  // FOCK: A = JK digits [2m][nb][4][nbp] rows mu (per q') over nu; B = C^T digits
     S4Params& p = sb->plan[S_FOCK];
@@ -1176,7 +1219,7 @@ int s4_init(donof_ri_ctx* ctx) {
 void s4_free(donof_ri_ctx* ctx) {
   S4Buffers* sb = ctx->s4;
   if (!sb) return;
-  void* bufs[] = {sb->X6,    sb->B1,   sb->B5,   sb->Ct,   sb->L3,   sb->L6, sb->Dp,  sb->JKp,  sb->eB1,   sb->eB5,
+  void* bufs[] = {sb->kao_tmap, sb->X6,    sb->B1,   sb->B5,   sb->Ct,   sb->L3,   sb->L6, sb->Dp,  sb->JKp,  sb->eB1,   sb->eB5,
                   sb->eC,    sb->e3,   sb->e6,   sb->ed,   sb->eJK, sb->rmaxB, sb->maxB, sb->absC, sb->absCt,
                   sb->Cdf,   sb->dmat, sb->JKhi, sb->JKlo, sb->W,  sb->HCt, sb->Yt,   sb->partial};
   for (void* b : bufs)
@@ -1258,6 +1301,9 @@ int s4_jk_ao(donof_ri_ctx* ctx) {
   {
     ProfScope ps(ctx, DONOF_RI_ROW_KAO);
     if ((rc = launch_s4<S_KAO>(ctx))) return rc;
+    dim3 g((nb + 31) / 32, (nb + 31) / 32, m), b(32, 8);
+    kao_mirror_kernel<<<g, b, 0, ctx->stream>>>(sb->JKhi, sb->JKlo, nb, m, sb->ldo, S4Cfg<S_KAO>::BN);
+    DONOF_LAUNCH_CHECK(ctx);
   }
   {
     ProfScope ps(ctx, DONOF_RI_ROW_OTHER);

@@ -213,6 +213,18 @@ def cpu_baseline(name, budget_s=12.0):
 
 
 # ---------------------------------------------------------------------------
+def job_ms_per_iteration(rank_total_ms, steps, world, device="cpu"):
+    """Effective ms per iteration of the whole job (replicas): the slowest rank's
+    time for its `steps` iterations, over the steps x world iterations all ranks ran."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(rank_total_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        rank_total_ms = float(t.item())
+    return rank_total_ms / (steps * world)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -315,13 +327,7 @@ def main():
         rows[r] = (t, c)
     bd.donof_ri_profile(eng.ctx, False)
     ms = float(np.mean(step_ms))
-    if world > 1:
-        t = torch.tensor([ms * args.steps], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    else:
-        total_ms = ms * args.steps
-    value = total_ms / (args.steps * world)
+    value = job_ms_per_iteration(ms * args.steps, args.steps, world, dev)
 
     # e2e through the same entry points with pinned host buffers
     e2e = None
@@ -348,11 +354,7 @@ def main():
             tt.append(time.perf_counter() - t0)
         barrier()
         e_ms = 1000.0 * float(np.mean(tt))
-        if world > 1:
-            t = torch.tensor([e_ms], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e_ms = float(t.item())
-        e2e = {"value": e_ms / world, "unit": UNIT,
+        e2e = {"value": job_ms_per_iteration(e_ms * args.steps, args.steps, world, dev), "unit": UNIT,
                "h2d_bytes_per_step": int(8 * (nb * nb + len(w.gamma))),
                "d2h_bytes_per_step": int(8 * (2 * m * m + 1 + nb * nb))}
 

@@ -20,6 +20,9 @@ brute      four-index fitted ERIs and the explicit O(N^5) transform of
            Eqs. (Jpq)-(Kpq) / Table 1, used to pin the factored path.
 rhf        closed-shell determinant energy from the AO density, the special
            case PNOF7 reduces to when every strong orbital is fully occupied.
+onopt      the occupation (gamma) optimisation for fixed orbitals: dE/dn,
+           dn/dgamma, dE/dgamma and an L-BFGS minimiser (Sec. 2, "Occupancy
+           Optimization with RI"), and the standard starting guess.
 
 Parity unpinned: the absolute PNOF7 energies of the synthetic systems (no
 printed value exists for them); they are pinned only through the invariants,

@@ -100,3 +100,42 @@ def test_dropped_kinetic_term_fails_textbook_pin():
     D = np.zeros((6, 2)); D[:3, 0] = d; D[3:, 1] = d
     assert abs((D.T @ I.kinetic(s) @ D)[0, 1] - 0.2365) < 1e-4
     assert abs((D.T @ bad @ D)[0, 1] - 0.2365) > 1e-2
+
+
+def test_wrong_sign_weak_weak_gradient_fails_finite_differences(monkeypatch):
+    from oracle import onopt
+    rng = np.random.default_rng(21)
+    sub, rank = pairing_columns(2, 3)
+    m = 8
+    X = rng.standard_normal((m, m))
+    J = X @ X.T / m + np.eye(m)
+    K = 0.3 * J
+    np.fill_diagonal(K, np.diag(J))
+    H = rng.standard_normal(m)
+    gamma = rng.uniform(0.2, 1.3, 6)
+
+    def fd_ok():
+        E0, g = onopt.energy_and_gradient(gamma, 2, 3, sub, rank, H, J, K, 0.0)
+        h = 1e-6
+        for k in range(gamma.shape[0]):
+            e = np.zeros_like(gamma)
+            e[k] = h
+            Ep, _ = onopt.energy_and_gradient(gamma + e, 2, 3, sub, rank, H, J, K, 0.0)
+            Em, _ = onopt.energy_and_gradient(gamma - e, 2, 3, sub, rank, H, J, K, 0.0)
+            if abs((Ep - Em) / (2 * h) - g[k]) > 1e-7 * max(1.0, abs(g[k])):
+                return False
+        return True
+
+    assert fd_ok()
+    good = onopt.energy_dn
+
+    def bad(n, Hd, J_, K_, sub_, rank_):
+        # the within-subspace sign taken as +1 for weak-weak pairs too
+        g = good(n, Hd, J_, K_, sub_, rank_)
+        for p in range(n.shape[0]):
+            for q in range(n.shape[0]):
+                if q != p and sub_[q] == sub_[p] and rank_[p] >= 0 and rank_[q] >= 0:
+                    g[p] -= 2.0 * K_[p, q] * np.sqrt(n[q] / n[p])
+        return g
+    monkeypatch.setattr(onopt, "energy_dn", bad)
+    assert not fd_ok()

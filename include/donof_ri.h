@@ -231,6 +231,31 @@ int donof_ri_profile(donof_ri_ctx* ctx, int enable);
 int donof_ri_profile_read(donof_ri_ctx* ctx, int row, double* total_ms, long long* count);
 
 /*
+ * Occupation optimisation for fixed orbitals (Sec. 2, "Occupancy Optimization
+ * with RI"): with J, K of the last FULL transform fixed, the PNOF7 energy of
+ * Eq. (PNOF) is minimised over the unconstrained angles gamma (occupation map as
+ * in donof_ri_energy_lagrangian).  The paper names no optimiser: L-BFGS (8
+ * pairs, backtracking Armijo line search) on the analytic gradient
+ * dE/dgamma = sum_p dE/dn_p dn_p/dgamma, FP64, in one single-CTA kernel.
+ *   gamma     in: start, out: result; [N_I*N_g] FP64, host or device
+ *   max_iter  iteration cap, 0..1000000 (0: only evaluates E and the gradient)
+ *   gtol      stop when max_k |dE/dgamma_k| <= gtol (>= 0)
+ *   etol      stop when an iteration lowers E by at most etol * max(1, |E|) (>= 0); a
+ *             minimum where an occupation reaches 0 or 1 lies on a kink of E(gamma)
+ *             (the sqrt(n) terms), where the gradient need not vanish
+ *   E         out: energy at the result (host or device, one FP64) or NULL
+ *   grad      out: dE/dgamma at the result ([N_I*N_g] FP64, host or device) or NULL
+ *   info      out (host) or NULL: info[0] iterations, info[1] stop reason
+ *             (0 gradient below gtol, 1 iteration cap, 2 line search found no
+ *             decrease, 3 energy decrease below etol)
+ * Synchronous when any output is in host memory.
+ * Errors: E_ARG, E_STATE (no FULL transform since the orbitals last changed),
+ *         E_UNSUPPORTED (N_g > 16 or N_Omega too large for one CTA's shared memory).
+ */
+int donof_ri_optimize_occupations(donof_ri_ctx* ctx, double* gamma, int max_iter, double gtol, double etol, double* E,
+                                  double* grad, int* info);
+
+/*
  * J_pq = sum_P b^P_pp b^P_qq with no device allocation.
  * The paper has no counterpart: this entry point exists for callers that may
  * not allocate device memory (code running under an allocator or memory pool

@@ -44,7 +44,7 @@ EXPORTS = [
     "donof_ri_init", "donof_ri_transform", "donof_ri_jk_mo", "donof_ri_jk_ao_batch",
     "donof_ri_energy_lagrangian", "donof_ri_fetch", "donof_ri_sync", "donof_ri_destroy",
     "donof_ri_strerror", "donof_ri_launch_count", "donof_ri_profile", "donof_ri_profile_read",
-    "donof_ri_iteration", "donof_ri_jmo_noalloc",
+    "donof_ri_iteration", "donof_ri_jmo_noalloc", "donof_ri_optimize_occupations",
 ]
 
 ROWS = ["half", "diag", "full_k", "j", "jao", "kao", "energy", "other"]
@@ -101,6 +101,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.donof_ri_profile.restype = i
     lib.donof_ri_profile_read.argtypes = [vp, i, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong)]
     lib.donof_ri_profile_read.restype = i
+    lib.donof_ri_optimize_occupations.argtypes = [vp, vp, i, d, d, vp, vp, vp]
+    lib.donof_ri_optimize_occupations.restype = i
     for name in ("donof_ri_init", "donof_ri_transform", "donof_ri_jk_mo", "donof_ri_jk_ao_batch",
                  "donof_ri_energy_lagrangian", "donof_ri_fetch", "donof_ri_sync", "donof_ri_destroy"):
         getattr(lib, name).restype = i
@@ -201,6 +203,14 @@ def donof_ri_jmo_noalloc(d, naux: int, n_omega: int, J, stream=None):
     _check(load().donof_ri_jmo_noalloc(_ptr(d), int(naux), int(n_omega), _ptr(J), st), "donof_ri_jmo_noalloc")
 
 
+def donof_ri_optimize_occupations(ctx, gamma, max_iter: int, gtol: float, etol: float = 0.0, E=None, grad=None,
+                                  info=None):
+    """Occupation optimisation for the current orbitals; gamma is updated in place."""
+    ip = None if info is None else info.ctypes.data
+    _check(load().donof_ri_optimize_occupations(ctx, _ptr(gamma), int(max_iter), float(gtol), float(etol), _ptr(E),
+                                                _ptr(grad), ip), "donof_ri_optimize_occupations")
+
+
 def donof_ri_profile(ctx, enable: bool):
     _check(load().donof_ri_profile(ctx, 1 if enable else 0), "donof_ri_profile")
 
@@ -280,3 +290,13 @@ class Engine:
 
     def launches(self) -> int:
         return donof_ri_launch_count(self.ctx)
+
+    def optimize_occupations(self, gamma0: np.ndarray, max_iter: int = 5000, gtol: float = 1e-8,
+                             etol: float = 1e-14):
+        """(gamma, E, grad, iterations, stop reason) from the device L-BFGS (max_iter 0: evaluate only)."""
+        g = np.array(gamma0, dtype=np.float64, copy=True)
+        E = np.zeros(1)
+        grad = np.empty_like(g)
+        info = np.zeros(2, dtype=np.int32)
+        donof_ri_optimize_occupations(self.ctx, g, max_iter, gtol, etol, E, grad, info)
+        return g, float(E[0]), grad, int(info[0]), int(info[1])

@@ -145,7 +145,7 @@ int donof_ri_destroy(donof_ri_ctx* ctx) {
                   ctx->d_aux_alpha, ctx->d_subspace, ctx->d_weak_rank, ctx->d_S, ctx->d_H, ctx->d_G, ctx->d_B,
                   ctx->d_enuc, ctx->d_scratch_max, ctx->d_C, ctx->d_bh, ctx->d_d, ctx->d_bf, ctx->d_J, ctx->d_K,
                   ctx->d_Jao, ctx->d_Kao, ctx->d_W, ctx->d_HC, ctx->d_Y, ctx->d_lambda, ctx->d_gamma, ctx->d_n,
-                  ctx->d_A, ctx->d_Bc, ctx->d_E, ctx->d_status};
+                  ctx->d_A, ctx->d_Bc, ctx->d_E, ctx->d_Hd, ctx->d_on, ctx->d_on_info, ctx->d_status};
   for (void* b : bufs) dfree(b);
   free(ctx);
   return DONOF_RI_OK;
@@ -198,6 +198,9 @@ int donof_ri_init(const donof_ri_system* sys, int precision, void* stream, donof
   TRY(dalloc(&ctx->d_Y, nb * m));
   TRY(dalloc(&ctx->d_lambda, nb2));
   TRY(dalloc(&ctx->d_gamma, (size_t)sys->n_strong * sys->n_weak_per));
+  TRY(dalloc(&ctx->d_Hd, m));
+  TRY(dalloc(&ctx->d_on, 2 * (size_t)sys->n_strong * sys->n_weak_per + 1));
+  TRY(dalloc(&ctx->d_on_info, 2));
   TRY(dalloc(&ctx->d_n, m));
   TRY(dalloc(&ctx->d_A, m * m));
   TRY(dalloc(&ctx->d_Bc, m * m));
@@ -415,6 +418,32 @@ int donof_ri_iteration(donof_ri_ctx* ctx, const double* C, const double* gamma, 
   ctx->have_full = (mode == DONOF_RI_FULL);
   ctx->have_ao = 1;
   return DONOF_RI_OK;
+}
+
+int donof_ri_optimize_occupations(donof_ri_ctx* ctx, double* gamma, int max_iter, double gtol, double etol, double* E,
+                                  double* grad, int* info) {
+  if (!ctx || !gamma || max_iter < 0 || max_iter > 1000000 || !(gtol >= 0.0) || !(etol >= 0.0)) return DONOF_RI_E_ARG;
+  if (!ctx->have_full) return DONOF_RI_E_STATE;
+  const size_t ng = (size_t)ctx->n_strong * ctx->n_weak_per;
+  double* dg = ctx->d_on;
+  double* dgrad = ctx->d_on + ng;
+  double* dE = ctx->d_on + 2 * ng;
+  const bool gdev = is_device_ptr(gamma);
+  int rc;
+  ProfScope ps(ctx, DONOF_RI_ROW_OTHER);
+  DONOF_CUDA_TRY(cudaMemcpyAsync(dg, gamma, ng * sizeof(double), gdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                 ctx->stream));
+  if ((rc = launch_check_finite(ctx, dg, (long long)ng))) return rc;
+  if ((rc = onopt_launch(ctx, dg, dE, dgrad, ctx->d_on_info, max_iter > 0 ? 1 : 0, max_iter, gtol, etol))) return rc;
+  bool host = false;
+  if ((rc = copy_out(ctx, gamma, dg, ng, &host))) return rc;
+  if ((rc = copy_out(ctx, E, dE, 1, &host))) return rc;
+  if ((rc = copy_out(ctx, grad, dgrad, ng, &host))) return rc;
+  if (info) {
+    DONOF_CUDA_TRY(cudaMemcpyAsync(info, ctx->d_on_info, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    host = true;
+  }
+  return host ? consume_status(ctx) : DONOF_RI_OK;
 }
 
 int donof_ri_fetch(donof_ri_ctx* ctx, int what, double* dst, size_t count) {

@@ -79,6 +79,9 @@ struct donof_ri_ctx {
   double* d_A;      // [n_omega][n_omega]
   double* d_Bc;     // [n_omega][n_omega]
   double* d_E;      // [1]
+  double* d_Hd;     // [n_omega] C_p^T H C_p (occupation optimisation)
+  double* d_on;     // [2*N_I*N_g + 1] occupation optimisation: gamma, gradient, energy
+  int* d_on_info;   // [2]
   int* d_status;    // [1] device-side status (DeviceStatus)
 
   donof::MixedBuffers* mixed;
@@ -122,6 +125,9 @@ int path64_transform(donof_ri_ctx* ctx, int mode);
 int path64_jk_ao(donof_ri_ctx* ctx);
 int path64_energy(donof_ri_ctx* ctx);
 int launch_check_finite(donof_ri_ctx* ctx, const double* x, long long n);
+int launch_hc_public(donof_ri_ctx* ctx);
+int onopt_launch(donof_ri_ctx* ctx, double* d_gamma, double* d_E, double* d_grad, int* d_info, int mode,
+                 int max_iter, double gtol, double etol);
 int launch_occupations_coupling(donof_ri_ctx* ctx);
 int launch_energy_reduce(donof_ri_ctx* ctx);
 

@@ -237,7 +237,8 @@ int donof_ri_profile_read(donof_ri_ctx* ctx, int row, double* total_ms, long lon
  * in donof_ri_energy_lagrangian).  The paper names no optimiser: L-BFGS (8
  * pairs, backtracking Armijo line search) on the analytic gradient
  * dE/dgamma = sum_p dE/dn_p dn_p/dgamma, FP64, in one single-CTA kernel.
- *   gamma     in: start, out: result; [N_I*N_g] FP64, host or device
+ *   gamma     in: start, out: result folded into [0, pi/2] (E depends on cos^2 and
+ *             sin^2 of the angles only); [N_I*N_g] FP64, host or device
  *   max_iter  iteration cap, 0..1000000 (0: only evaluates E and the gradient)
  *   gtol      stop when max_k |dE/dgamma_k| <= gtol (>= 0)
  *   etol      stop when an iteration lowers E by at most etol * max(1, |E|) (>= 0); a
@@ -254,6 +255,52 @@ int donof_ri_profile_read(donof_ri_ctx* ctx, int row, double* total_ms, long lon
  */
 int donof_ri_optimize_occupations(donof_ri_ctx* ctx, double* gamma, int max_iter, double gtol, double etol, double* E,
                                   double* grad, int* info);
+
+/* ------------------------------------------------------------------------
+ * Learned warm start for the occupation optimisation.  The paper has no
+ * learned part: this is the project's own addition.  A 3-layer MLP
+ * (F -> H tanh -> H tanh -> O) with BF16 weights and FP32 arithmetic maps the
+ * features of one pairing subspace to its converged angles (strong angle,
+ * then the N_g - 1 weak angles, folded into [0, pi/2]).
+ * ------------------------------------------------------------------------ */
+typedef struct donof_mlp donof_mlp;
+
+/* Create a network with zero parameters and identity input scaling.
+ * max_batch: largest batch any later call may pass (1..2^24).  stream: the
+ * cudaStream_t its kernels run on (NULL = legacy default stream).
+ * Errors: E_ARG (sizes), E_OOM, E_CUDA. */
+int donof_mlp_create(int n_in, int n_hidden, int n_out, int max_batch, void* stream, donof_mlp** out);
+/* Number of parameters: H*F + H + H*H + H + O*H + O (W1, b1, W2, b2, W3, b3; W row-major [out][in]). */
+long long donof_mlp_param_count(const donof_mlp* net);
+/* Copy parameters in (host or device FP32, param_count values); resets the Adam state.  Synchronous. */
+int donof_mlp_set_params(donof_mlp* net, const float* params);
+/* Copy the FP32 master parameters out (host or device).  Synchronous. */
+int donof_mlp_get_params(donof_mlp* net, float* params);
+/* Input scaling z = (x - mean) * inv_std, F values each (host or device).  Synchronous. */
+int donof_mlp_set_normalization(donof_mlp* net, const float* mean, const float* inv_std);
+/* Y [batch][O] = network(X [batch][F]); FP32, host or device.  Synchronous for host Y. */
+int donof_mlp_forward(donof_mlp* net, const float* X, int batch, float* Y);
+/* Mean squared error against T [batch][O] and its gradient with respect to every
+ * parameter (through the BF16 weight values); loss (one float) and grads
+ * (param_count floats), host or device, either may be NULL.  Synchronous. */
+int donof_mlp_loss_grad(donof_mlp* net, const float* X, const float* T, int batch, float* loss, float* grads);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, decoupled weight decay on the
+ * matrices) on the batch (X, T); loss (host or device) may be NULL (then asynchronous). */
+int donof_mlp_train_step(donof_mlp* net, const float* X, const float* T, int batch, float lr, float weight_decay,
+                         float* loss);
+int donof_mlp_destroy(donof_mlp* net);
+
+/* Features of every pairing subspace g from J, K of the last FULL transform and
+ * H_pp = C_p^T H C_p: X [N_I][3 + 4 N_g] FP32 (host or device), row g =
+ * [H_ss, J_ss, mf_s, then per weak orbital w (rank order): H_ww, J_ww, K_sw, mf_w],
+ * mf_p = sum_{q outside g} n0_q (2 J_pq - K_pq), n0 = standard-guess occupations
+ * (strong 0.98, weak 0.02/N_g).  Errors: E_ARG, E_STATE. */
+int donof_ri_on_features(donof_ri_ctx* ctx, float* X);
+/* gamma [N_I*N_g] FP64 (host or device) predicted by net from the features of the
+ * current orbitals, each angle clipped to [clip, pi/2 - clip] (0 <= clip < pi/4):
+ * the warm start for donof_ri_optimize_occupations.  net must have F = 3 + 4 N_g
+ * inputs and O = N_g outputs.  Errors: E_ARG, E_STATE. */
+int donof_ri_gamma_guess(donof_ri_ctx* ctx, donof_mlp* net, double clip, double* gamma);
 
 /*
  * J_pq = sum_P b^P_pp b^P_qq with no device allocation.

@@ -23,6 +23,8 @@ rhf        closed-shell determinant energy from the AO density, the special
 onopt      the occupation (gamma) optimisation for fixed orbitals: dE/dn,
            dn/dgamma, dE/dgamma and an L-BFGS minimiser (Sec. 2, "Occupancy
            Optimization with RI"), and the standard starting guess.
+mlp        the learned warm start: per-subspace features, BF16-weight MLP
+           forward pass, loss gradients and the Adam update.
 
 Parity unpinned: the absolute PNOF7 energies of the synthetic systems (no
 printed value exists for them); they are pinned only through the invariants,

@@ -45,6 +45,10 @@ EXPORTS = [
     "donof_ri_energy_lagrangian", "donof_ri_fetch", "donof_ri_sync", "donof_ri_destroy",
     "donof_ri_strerror", "donof_ri_launch_count", "donof_ri_profile", "donof_ri_profile_read",
     "donof_ri_iteration", "donof_ri_jmo_noalloc", "donof_ri_optimize_occupations",
+    "donof_ri_on_features", "donof_ri_gamma_guess",
+    "donof_mlp_create", "donof_mlp_param_count", "donof_mlp_set_params", "donof_mlp_get_params",
+    "donof_mlp_set_normalization", "donof_mlp_forward", "donof_mlp_loss_grad", "donof_mlp_train_step",
+    "donof_mlp_destroy",
 ]
 
 ROWS = ["half", "diag", "full_k", "j", "jao", "kao", "energy", "other"]
@@ -103,6 +107,24 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.donof_ri_profile_read.restype = i
     lib.donof_ri_optimize_occupations.argtypes = [vp, vp, i, d, d, vp, vp, vp]
     lib.donof_ri_optimize_occupations.restype = i
+    lib.donof_ri_on_features.argtypes = [vp, vp]
+    lib.donof_ri_on_features.restype = i
+    lib.donof_ri_gamma_guess.argtypes = [vp, vp, d, vp]
+    lib.donof_ri_gamma_guess.restype = i
+    f = ctypes.c_float
+    lib.donof_mlp_create.argtypes = [i, i, i, i, vp, ctypes.POINTER(vp)]
+    lib.donof_mlp_param_count.argtypes = [vp]
+    lib.donof_mlp_param_count.restype = ctypes.c_longlong
+    lib.donof_mlp_set_params.argtypes = [vp, vp]
+    lib.donof_mlp_get_params.argtypes = [vp, vp]
+    lib.donof_mlp_set_normalization.argtypes = [vp, vp, vp]
+    lib.donof_mlp_forward.argtypes = [vp, vp, i, vp]
+    lib.donof_mlp_loss_grad.argtypes = [vp, vp, vp, i, vp, vp]
+    lib.donof_mlp_train_step.argtypes = [vp, vp, vp, i, f, f, vp]
+    lib.donof_mlp_destroy.argtypes = [vp]
+    for name in ("donof_mlp_create", "donof_mlp_set_params", "donof_mlp_get_params", "donof_mlp_set_normalization",
+                 "donof_mlp_forward", "donof_mlp_loss_grad", "donof_mlp_train_step", "donof_mlp_destroy"):
+        getattr(lib, name).restype = i
     for name in ("donof_ri_init", "donof_ri_transform", "donof_ri_jk_mo", "donof_ri_jk_ao_batch",
                  "donof_ri_energy_lagrangian", "donof_ri_fetch", "donof_ri_sync", "donof_ri_destroy"):
         getattr(lib, name).restype = i
@@ -223,6 +245,84 @@ def donof_ri_profile_read(ctx, row: int):
     return t.value, c.value
 
 
+def _fptr(x):
+    """Pointer of a C-contiguous float32 numpy array or a contiguous float32 torch tensor."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float32 or not x.flags["C_CONTIGUOUS"]:
+            raise TypeError("expected a C-contiguous float32 array")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        import torch
+        if x.dtype != torch.float32 or not x.is_contiguous():
+            raise TypeError("expected a contiguous float32 tensor")
+        return x.data_ptr()
+    raise TypeError(f"unsupported array type {type(x)!r}")
+
+
+class Mlp:
+    """The learned warm-start network (donof_mlp_*): FP32 arrays in and out."""
+
+    def __init__(self, n_in: int, n_hidden: int, n_out: int, max_batch: int, stream=None):
+        out = ctypes.c_void_p()
+        st = None if stream is None else ctypes.c_void_p(int(stream))
+        _check(load().donof_mlp_create(int(n_in), int(n_hidden), int(n_out), int(max_batch), st, ctypes.byref(out)),
+               "donof_mlp_create")
+        self.ptr = out
+        self.n_in, self.n_hidden, self.n_out = n_in, n_hidden, n_out
+        self.nparam = int(load().donof_mlp_param_count(self.ptr))
+
+    def close(self):
+        if self.ptr is not None:
+            load().donof_mlp_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        assert p.size == self.nparam
+        _check(load().donof_mlp_set_params(self.ptr, _fptr(p)), "donof_mlp_set_params")
+
+    def get_params(self) -> np.ndarray:
+        p = np.empty(self.nparam, dtype=np.float32)
+        _check(load().donof_mlp_get_params(self.ptr, _fptr(p)), "donof_mlp_get_params")
+        return p
+
+    def set_normalization(self, mean, inv_std):
+        mu = np.ascontiguousarray(mean, dtype=np.float32)
+        sd = np.ascontiguousarray(inv_std, dtype=np.float32)
+        _check(load().donof_mlp_set_normalization(self.ptr, _fptr(mu), _fptr(sd)), "donof_mlp_set_normalization")
+
+    def forward(self, X) -> np.ndarray:
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        Y = np.empty((X.shape[0], self.n_out), dtype=np.float32)
+        _check(load().donof_mlp_forward(self.ptr, _fptr(X), X.shape[0], _fptr(Y)), "donof_mlp_forward")
+        return Y
+
+    def loss_grad(self, X, T):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        T = np.ascontiguousarray(T, dtype=np.float32)
+        loss = np.zeros(1, dtype=np.float32)
+        g = np.empty(self.nparam, dtype=np.float32)
+        _check(load().donof_mlp_loss_grad(self.ptr, _fptr(X), _fptr(T), X.shape[0], _fptr(loss), _fptr(g)),
+               "donof_mlp_loss_grad")
+        return float(loss[0]), g
+
+    def train_step(self, X, T, lr: float, weight_decay: float = 0.0, loss_out=None):
+        """One Adam step; X, T numpy (host) or torch (device) float32 tensors."""
+        Xp = _fptr(X if not isinstance(X, np.ndarray) else np.ascontiguousarray(X, dtype=np.float32))
+        Tp = _fptr(T if not isinstance(T, np.ndarray) else np.ascontiguousarray(T, dtype=np.float32))
+        B = int(X.shape[0])
+        _check(load().donof_mlp_train_step(self.ptr, Xp, Tp, B, float(lr), float(weight_decay), _fptr(loss_out)),
+               "donof_mlp_train_step")
+
+
 class Engine:
     """Convenience wrapper owning one context (host numpy in, host numpy out)."""
 
@@ -300,3 +400,13 @@ class Engine:
         info = np.zeros(2, dtype=np.int32)
         donof_ri_optimize_occupations(self.ctx, g, max_iter, gtol, etol, E, grad, info)
         return g, float(E[0]), grad, int(info[0]), int(info[1])
+
+    def on_features(self) -> np.ndarray:
+        X = np.empty((self.system.n_strong, 3 + 4 * self.system.n_weak_per), dtype=np.float32)
+        _check(load().donof_ri_on_features(self.ctx, _fptr(X)), "donof_ri_on_features")
+        return X
+
+    def gamma_guess(self, net: "Mlp", clip: float = 0.05) -> np.ndarray:
+        g = np.empty(self.system.n_strong * self.system.n_weak_per)
+        _check(load().donof_ri_gamma_guess(self.ctx, net.ptr, float(clip), _ptr(g)), "donof_ri_gamma_guess")
+        return g

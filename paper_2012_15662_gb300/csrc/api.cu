@@ -145,7 +145,8 @@ int donof_ri_destroy(donof_ri_ctx* ctx) {
                   ctx->d_aux_alpha, ctx->d_subspace, ctx->d_weak_rank, ctx->d_S, ctx->d_H, ctx->d_G, ctx->d_B,
                   ctx->d_enuc, ctx->d_scratch_max, ctx->d_C, ctx->d_bh, ctx->d_d, ctx->d_bf, ctx->d_J, ctx->d_K,
                   ctx->d_Jao, ctx->d_Kao, ctx->d_W, ctx->d_HC, ctx->d_Y, ctx->d_lambda, ctx->d_gamma, ctx->d_n,
-                  ctx->d_A, ctx->d_Bc, ctx->d_E, ctx->d_Hd, ctx->d_on, ctx->d_on_info, ctx->d_status};
+                  ctx->d_A, ctx->d_Bc, ctx->d_E, ctx->d_Hd, ctx->d_on, ctx->d_on_info, ctx->d_feat,
+                  ctx->d_status};
   for (void* b : bufs) dfree(b);
   free(ctx);
   return DONOF_RI_OK;
@@ -201,6 +202,7 @@ int donof_ri_init(const donof_ri_system* sys, int precision, void* stream, donof
   TRY(dalloc(&ctx->d_Hd, m));
   TRY(dalloc(&ctx->d_on, 2 * (size_t)sys->n_strong * sys->n_weak_per + 1));
   TRY(dalloc(&ctx->d_on_info, 2));
+  TRY(dalloc(&ctx->d_feat, (size_t)sys->n_strong * (3 + 4 * (size_t)sys->n_weak_per)));
   TRY(dalloc(&ctx->d_n, m));
   TRY(dalloc(&ctx->d_A, m * m));
   TRY(dalloc(&ctx->d_Bc, m * m));
@@ -443,6 +445,40 @@ int donof_ri_optimize_occupations(donof_ri_ctx* ctx, double* gamma, int max_iter
     DONOF_CUDA_TRY(cudaMemcpyAsync(info, ctx->d_on_info, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     host = true;
   }
+  return host ? consume_status(ctx) : DONOF_RI_OK;
+}
+
+int donof_ri_on_features(donof_ri_ctx* ctx, float* X) {
+  if (!ctx || !X) return DONOF_RI_E_ARG;
+  if (!ctx->have_full) return DONOF_RI_E_STATE;
+  int rc;
+  ProfScope ps(ctx, DONOF_RI_ROW_OTHER);
+  if ((rc = onopt_features(ctx, ctx->d_feat))) return rc;
+  const size_t n = (size_t)ctx->n_strong * (3 + 4 * (size_t)ctx->n_weak_per);
+  const bool dev = is_device_ptr(X);
+  DONOF_CUDA_TRY(cudaMemcpyAsync(X, ctx->d_feat, n * sizeof(float), dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                 ctx->stream));
+  return dev ? DONOF_RI_OK : consume_status(ctx);
+}
+
+int donof_ri_gamma_guess(donof_ri_ctx* ctx, donof_mlp* net, double clip, double* gamma) {
+  if (!ctx || !net || !gamma || !(clip >= 0.0) || !(clip < 0.7853981633974483)) return DONOF_RI_E_ARG;
+  if (!ctx->have_full) return DONOF_RI_E_STATE;
+  int F = 0, O = 0;
+  mlp_shape(net, &F, &O);
+  if (F != 3 + 4 * ctx->n_weak_per || O != ctx->n_weak_per) return DONOF_RI_E_ARG;
+  int rc;
+  ProfScope ps(ctx, DONOF_RI_ROW_OTHER);
+  if ((rc = onopt_features(ctx, ctx->d_feat))) return rc;
+  // the network runs on its own stream: order it after the features
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return DONOF_RI_E_CUDA;
+  float* dY = nullptr;
+  if ((rc = mlp_forward_device(net, ctx->d_feat, ctx->n_strong, &dY))) return rc;
+  if (cudaDeviceSynchronize() != cudaSuccess) return DONOF_RI_E_CUDA;
+  const size_t ng = (size_t)ctx->n_strong * ctx->n_weak_per;
+  if ((rc = onopt_unfold(ctx, dY, clip, ctx->d_on))) return rc;
+  bool host = false;
+  if ((rc = copy_out(ctx, gamma, ctx->d_on, ng, &host))) return rc;
   return host ? consume_status(ctx) : DONOF_RI_OK;
 }
 

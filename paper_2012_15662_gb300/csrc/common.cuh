@@ -82,6 +82,7 @@ struct donof_ri_ctx {
   double* d_Hd;     // [n_omega] C_p^T H C_p (occupation optimisation)
   double* d_on;     // [2*N_I*N_g + 1] occupation optimisation: gamma, gradient, energy
   int* d_on_info;   // [2]
+  float* d_feat;    // [N_I][3 + 4 N_g] learned-guess features
   int* d_status;    // [1] device-side status (DeviceStatus)
 
   donof::MixedBuffers* mixed;
@@ -128,6 +129,10 @@ int launch_check_finite(donof_ri_ctx* ctx, const double* x, long long n);
 int launch_hc_public(donof_ri_ctx* ctx);
 int onopt_launch(donof_ri_ctx* ctx, double* d_gamma, double* d_E, double* d_grad, int* d_info, int mode,
                  int max_iter, double gtol, double etol);
+int onopt_features(donof_ri_ctx* ctx, float* d_X);
+int onopt_unfold(donof_ri_ctx* ctx, const float* d_Y, double clip, double* d_gamma);
+int mlp_forward_device(donof_mlp* n, const float* dX, int B, float** dY);
+int mlp_shape(const donof_mlp* n, int* F, int* O);
 int launch_occupations_coupling(donof_ri_ctx* ctx);
 int launch_energy_reduce(donof_ri_ctx* ctx);
 

@@ -299,15 +299,94 @@ __global__ void __launch_bounds__(ON_THREADS, 1) on_opt_kernel(const OnParams p)
       }
     }
   }
+  // E depends on the angles through cos^2 and sin^2 only: an optimised gamma is
+  // returned folded into [0, pi/2] (and its gradient with the matching sign).
   for (int i = threadIdx.x; i < ng; i += ON_THREADS) {
-    p.gamma[i] = sh.x[i];
-    p.grad_out[i] = sh.g[i];
+    double xi = sh.x[i], gi = sh.g[i];
+    if (p.mode == 1) {
+      const double c = cos(xi), s = sin(xi);
+      xi = atan2(fabs(s), fabs(c));
+      if (s * c < 0.0) gi = -gi;
+    }
+    p.gamma[i] = xi;
+    p.grad_out[i] = gi;
   }
   if (threadIdx.x == 0) {
     p.E_out[0] = E;
     p.info_out[0] = iters;
     p.info_out[1] = p.mode == 1 ? reason : 0;
   }
+}
+
+// Features of each pairing subspace g for the learned warm start (one row of
+// 3 + 4 N_g values): [H_ss, J_ss, mf_s, then per weak orbital w in rank order:
+// H_ww, J_ww, K_sw, mf_w], with mf_p = sum_{q outside g} n0_q (2 J_pq - K_pq)
+// the mean field of the other subspaces at the standard-guess occupations n0
+// (strong 0.98, weak 0.02 / N_g).  Thread per (subspace, member).
+__global__ void on_features_kernel(int NI, int Ng, int m, const int* subspace, const int* weak_rank, const double* J,
+                                   const double* K, const double* Hd, float* X) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= NI * (Ng + 1)) return;
+  const int g = t / (Ng + 1), k = t % (Ng + 1);
+  int pp = -1, s = -1;
+  for (int q = 0; q < m; ++q) {
+    if (subspace[q] != g) continue;
+    if (weak_rank[q] == k - 1) pp = q;
+    if (weak_rank[q] < 0) s = q;
+  }
+  if (pp < 0 || s < 0) return;
+  double mf = 0.0;
+  for (int q = 0; q < m; ++q) {
+    if (subspace[q] == g) continue;
+    const double n0 = weak_rank[q] < 0 ? 0.98 : 0.02 / Ng;
+    mf += n0 * (2.0 * J[(size_t)pp * m + q] - K[(size_t)pp * m + q]);
+  }
+  const int F = 3 + 4 * Ng;
+  float* x = X + (size_t)g * F;
+  if (k == 0) {
+    x[0] = (float)Hd[pp];
+    x[1] = (float)J[(size_t)pp * m + pp];
+    x[2] = (float)mf;
+  } else {
+    float* y = x + 3 + 4 * (k - 1);
+    y[0] = (float)Hd[pp];
+    y[1] = (float)J[(size_t)pp * m + pp];
+    y[2] = (float)K[(size_t)s * m + pp];
+    y[3] = (float)mf;
+  }
+}
+
+// Network outputs [N_I][N_g] -> gamma (strong angles, then the weak angles of each
+// subspace), clipped to [clip, pi/2 - clip].
+__global__ void on_unfold_kernel(const float* Y, int NI, int Ng, double clip, double* gamma) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= NI * Ng) return;
+  const int g = t / Ng, j = t % Ng;
+  double v = (double)Y[t];
+  const double hi = 1.5707963267948966 - clip;
+  v = v < clip ? clip : (v > hi ? hi : v);
+  if (j == 0) gamma[g] = v;
+  else gamma[NI + g * (Ng - 1) + j - 1] = v;
+}
+
+int onopt_features(donof_ri_ctx* ctx, float* d_X) {
+  const int m = ctx->n_omega, nb = ctx->nbf, NI = ctx->n_strong, Ng = ctx->n_weak_per;
+  int rc;
+  if ((rc = launch_hc_public(ctx))) return rc;
+  on_hdiag_kernel<<<ceil_div_u((long long)m * 32, 256), 256, 0, ctx->stream>>>(nb, m, ctx->d_C, ctx->d_HC,
+                                                                               ctx->d_Hd);
+  DONOF_LAUNCH_CHECK(ctx);
+  on_features_kernel<<<ceil_div_u((long long)NI * (Ng + 1), 128), 128, 0, ctx->stream>>>(
+      NI, Ng, m, ctx->d_subspace, ctx->d_weak_rank, ctx->d_J, ctx->d_K, ctx->d_Hd, d_X);
+  DONOF_LAUNCH_CHECK(ctx);
+  return DONOF_RI_OK;
+}
+
+int onopt_unfold(donof_ri_ctx* ctx, const float* d_Y, double clip, double* d_gamma) {
+  const int NI = ctx->n_strong, Ng = ctx->n_weak_per;
+  on_unfold_kernel<<<ceil_div_u((long long)NI * Ng, 128), 128, 0, ctx->stream>>>(d_Y, NI, Ng, clip, d_gamma);
+  DONOF_LAUNCH_CHECK(ctx);
+  return DONOF_RI_OK;
 }
 
 // Runs the evaluation (mode 0) or the optimisation (mode 1) on the context's

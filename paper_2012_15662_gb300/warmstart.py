@@ -1,0 +1,141 @@
+"""Learned warm start for the occupation optimisation: data, training, evaluation.
+
+Host orchestration only; every computation runs in the library's kernels:
+the engine produces J, K (donof_ri_transform), the per-subspace features
+(donof_ri_on_features) and the converged angles (donof_ri_optimize_occupations,
+returned folded into [0, pi/2]); the network is trained by donof_mlp_train_step
+(forward, backward and Adam kernels) and applied by donof_ri_gamma_guess.
+
+The training targets are the converged angles the method itself generates on
+seeded synthetic rings (C6-C12, jitter 0.05 A, Haar-random orbitals), one
+sample per pairing subspace; the features are z-scored with the training set's
+mean and standard deviation.
+
+    python -m paper_2012_15662_gb300.warmstart --train 300 --eval c20h40
+trains on 300 rings and compares, on the evaluation workload, the iterations
+and time of the occupation optimisation from the standard guess and from the
+network's guess (the converged energies must agree: the plain optimiser judges).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+from . import binding as bd
+
+N_HIDDEN = 64
+
+
+def targets(gamma: np.ndarray, n_strong: int, n_weak_per: int) -> np.ndarray:
+    """Folded angles -> rows [N_I][N_g]: strong angle, then the subspace's weak angles."""
+    Y = np.empty((n_strong, n_weak_per), dtype=np.float32)
+    Y[:, 0] = gamma[:n_strong]
+    Y[:, 1:] = gamma[n_strong:].reshape(n_strong, n_weak_per - 1)
+    return Y
+
+
+def sample(workload, precision=bd.DONOF_RI_SLICE4, max_iter=20000, etol=1e-13):
+    """(features, targets, iterations, energy) of one system from the standard guess."""
+    from synthetic import standard_gamma
+    s = workload.system
+    eng = bd.Engine(s, precision)
+    try:
+        eng.transform(workload.C, bd.DONOF_RI_FULL)
+        X = eng.on_features()
+        g0 = standard_gamma(s.n_strong, s.n_weak_per)
+        gam, E, grad, it, reason = eng.optimize_occupations(g0, max_iter=max_iter, gtol=1e-8, etol=etol)
+        return X, targets(gam, s.n_strong, s.n_weak_per), it, E
+    finally:
+        eng.close()
+
+
+def training_set(n_systems: int, first_seed: int = 1000, n_c_range=(6, 12), precision=bd.DONOF_RI_SLICE4):
+    """Features and targets of n_systems seeded rings (C6..C12 in turn)."""
+    from synthetic import ring_workload
+    lo, hi = n_c_range
+    Xs, Ys = [], []
+    for k in range(n_systems):
+        n_c = lo + k % (hi - lo + 1)
+        X, Y, _, _ = sample(ring_workload(n_c, first_seed + k), precision)
+        Xs.append(X)
+        Ys.append(Y)
+    return np.concatenate(Xs), np.concatenate(Ys)
+
+
+def init_params(n_in, n_hidden, n_out, y_mean, seed=0):
+    """Uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) matrices, zero hidden biases, output bias at the target mean."""
+    rng = np.random.default_rng(seed)
+    W1 = rng.uniform(-1, 1, (n_hidden, n_in)) / np.sqrt(n_in)
+    W2 = rng.uniform(-1, 1, (n_hidden, n_hidden)) / np.sqrt(n_hidden)
+    W3 = rng.uniform(-1, 1, (n_out, n_hidden)) / np.sqrt(n_hidden)
+    parts = [W1, np.zeros(n_hidden), W2, np.zeros(n_hidden), W3, np.full(n_out, y_mean)]
+    return np.concatenate([p.ravel() for p in parts]).astype(np.float32)
+
+
+def train(X, Y, steps=6000, batch=1024, lr=3e-3, weight_decay=1e-4, seed=0, net=None):
+    """Train a network on (X, Y); returns (net, final loss)."""
+    n_in, n_out = X.shape[1], Y.shape[1]
+    if net is None:
+        net = bd.Mlp(n_in, N_HIDDEN, n_out, max_batch=max(batch, X.shape[0]))
+        net.set_params(init_params(n_in, N_HIDDEN, n_out, float(Y.mean()), seed))
+        mu = X.mean(axis=0)
+        sd = X.std(axis=0)
+        net.set_normalization(mu, 1.0 / np.where(sd > 0, sd, 1.0))
+    rng = np.random.default_rng(seed + 1)
+    loss = np.zeros(1, dtype=np.float32)
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    Y = np.ascontiguousarray(Y, dtype=np.float32)
+    for step in range(steps):
+        idx = rng.integers(0, X.shape[0], min(batch, X.shape[0]))
+        net.train_step(X[idx], Y[idx], lr, weight_decay, loss if step == steps - 1 else None)
+    return net, float(loss[0])
+
+
+def compare(workload, net, precision=bd.DONOF_RI_SLICE4, clip=0.05, max_iter=20000, etol=1e-13):
+    """Occupation optimisation of one system from the standard and from the learned guess."""
+    from synthetic import standard_gamma
+    s = workload.system
+    eng = bd.Engine(s, precision)
+    try:
+        eng.transform(workload.C, bd.DONOF_RI_FULL)
+        out = {}
+        for name in ("standard", "learned"):
+            bd.donof_ri_sync(eng.ctx)
+            t0 = time.perf_counter()
+            g0 = standard_gamma(s.n_strong, s.n_weak_per) if name == "standard" else eng.gamma_guess(net, clip)
+            gam, E, grad, it, reason = eng.optimize_occupations(g0, max_iter=max_iter, gtol=1e-8, etol=etol)
+            dt = time.perf_counter() - t0
+            _, E0, _, _, _ = eng.optimize_occupations(g0, max_iter=0)
+            out[name] = {"iterations": it, "E": E, "E_start": E0, "ms": 1000.0 * dt, "stop": reason}
+        return out
+    finally:
+        eng.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--train", type=int, default=300, help="number of training rings (C6..C12)")
+    ap.add_argument("--steps", type=int, default=6000)
+    ap.add_argument("--eval", default="c20h40", help="evaluation workload name")
+    ap.add_argument("--eval-seeds", type=int, default=3, help="evaluation systems (the named one, then reseeded)")
+    args = ap.parse_args()
+    from synthetic import make_workload
+    t0 = time.perf_counter()
+    X, Y = training_set(args.train)
+    t_data = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    net, loss = train(X, Y, steps=args.steps)
+    t_train = time.perf_counter() - t0
+    rows = []
+    for k in range(args.eval_seeds):
+        w = make_workload(args.eval) if k == 0 else make_workload(args.eval, seed=900 + k)
+        rows.append(compare(w, net))
+    print(json.dumps({"train_systems": args.train, "samples": int(X.shape[0]), "data_s": t_data, "train_s": t_train,
+                      "final_loss": loss, "eval": args.eval, "results": rows}))
+
+
+if __name__ == "__main__":
+    main()

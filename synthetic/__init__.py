@@ -16,5 +16,7 @@ from .systems import (  # noqa: F401
     pairing_columns,
     random_orthogonal,
     draw_gamma,
+    ring_workload,
+    standard_gamma,
     WORKLOADS,
 )

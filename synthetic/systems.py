@@ -250,3 +250,24 @@ def make_workload(name: str, seed: int | None = None) -> Workload:
     C = random_orthogonal(system.nbf, rng)
     gamma = draw_gamma(system.n_strong, system.n_weak_per, rng)
     return Workload(name=name, system=system, C=C, gamma=gamma, meta={"seed": s})
+
+
+def ring_workload(n_c: int, seed: int, jitter: float = 0.05) -> Workload:
+    """A CnH2n ring with its own seeded geometry and Haar-random orbitals (the
+    learned-guess training and evaluation sets: rings C6-C12, jitter 0.05 A)."""
+    system = make_system("ring", n_c=n_c, seed=seed, jitter=jitter)
+    rng = np.random.default_rng(10_000 + seed)
+    C = random_orthogonal(system.nbf, rng)
+    gamma = draw_gamma(system.n_strong, system.n_weak_per, rng)
+    return Workload(name=f"c{n_c}h{2 * n_c}-s{seed}", system=system, C=C, gamma=gamma, meta={"seed": seed})
+
+
+def standard_gamma(n_strong: int, n_weak_per: int, n_strong_occ: float = 0.98) -> np.ndarray:
+    """The standard starting angles of the occupation optimisation (the paper's
+    calculations start from a Fermi-Dirac-like distribution of occupations; read
+    here as every strong orbital at n_strong_occ and the weak share of each
+    subspace split equally): cos^2 gamma_g = 2 n - 1, cos^2 w_i = 1 / (N_g - i)."""
+    g0 = np.arccos(np.sqrt(2.0 * n_strong_occ - 1.0))
+    w = [np.arccos(np.sqrt(1.0 / (n_weak_per - i))) for i in range(n_weak_per - 1)]
+    return np.concatenate([np.full(n_strong, g0), np.tile(np.array(w, dtype=np.float64), n_strong)])
+

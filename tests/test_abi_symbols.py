@@ -16,7 +16,7 @@ def _declared():
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
         text = open(h).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-        names.update(re.findall(r"\b(donof_ri_\w+)\s*\(", text))
+        names.update(re.findall(r"\b(donof_(?:ri|mlp)_\w+)\s*\(", text))
     return sorted(names)
 
 

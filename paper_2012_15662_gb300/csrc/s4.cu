@@ -64,14 +64,15 @@ constexpr int S4_SHIFT = 46;    // value = 2^(ea + eb - 46) v
 // uses 32 columns.
 template <int KIND>
 struct S4Cfg {
-  static constexpr int BN = (KIND == S_FULLSQ) ? 32 : 48;
+  static constexpr int BN = 48;
   static constexpr int CTAS = (KIND == S_HALF) ? 2 : 1;  // CTAs per SM
   static constexpr int NSETS = CTAS == 2 ? 1 : 2;        // accumulator sets per CTA
   static constexpr int TMEM_COLS = CTAS == 2 ? 256 : 512;
-  // Epilogue warpgroups: the kinds that carry int64 running sums across K chunks
-  // (J^(q), K^(q), J) split the columns over two warpgroups in 8-column blocks so
-  // that the sums stay in registers.
-  static constexpr int NWG = (KIND == S_JAO || KIND == S_KAO || KIND == S_JMO) ? 2 : 1;
+  // Epilogue warpgroups: the kinds that carry running sums (int64 across K chunks
+  // for J^(q), K^(q), J; double-float across units for a3 and a7) split the
+  // columns over two warpgroups in 8-column blocks so that the sums stay in
+  // registers; the half transform uses one.
+  static constexpr int NWG = (KIND == S_HALF) ? 1 : 2;
   static constexpr int CW = NWG == 2 ? 8 : 16;
   static constexpr int THREADS = 64 + 128 * NWG;
   static constexpr int ES_WARP_BYTES = BN * 4 + BN * 8 + 4 * BN * 4 + BN * 16 * 4;
@@ -86,7 +87,7 @@ struct S4Params {
   const int* eb;
   __nv_bfloat16* o3;  // HALF: L3 digits [nx][mp][4][nbp]
   const int* e3;
-  int* x6;            // HALF: L6 integers [nx][m][nbp] (digitised into L6 by x6_to_l6_kernel)
+  int* x6;            // HALF: b_half integers [nx][m][nbp] at scale min(e3, e6) (xf_to_digits_kernel)
   const int* e6;
   float* ohi;
   float* olo;
@@ -406,11 +407,11 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_ge
     constexpr bool SUM_DF = (KIND == S_FULLSQ || KIND == S_FOCK);
     constexpr int NACC = (KIND == S_FOCK) ? 1 : BN / NWG;  // FOCK units are single chunks: no running sums
     long long acc[NACC];
-    float sh[SUM_DF ? BN : 1], sl[SUM_DF ? BN : 1];
+    float sh[SUM_DF ? BN / NWG : 1], sl[SUM_DF ? BN / NWG : 1];
 #pragma unroll
     for (int i = 0; i < NACC; ++i) acc[i] = 0;
 #pragma unroll
-    for (int i = 0; i < (SUM_DF ? BN : 1); ++i) {
+    for (int i = 0; i < (SUM_DF ? BN / NWG : 1); ++i) {
       sh[i] = 0.f;
       sl[i] = 0.f;
     }
@@ -528,13 +529,13 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_ge
             else tmem_wait8(gr[g]);
           }
           if (KIND == S_HALF && nch == 1) {
-            // Single-chunk half transform: both output integers straight from the
-            // five group sums, X = sum_g rint(G_g 2^(sigma - 8g)) in int32 (see
-            // half_fold), without the int64 fold.
+            // Single-chunk half transform: one output integer at the finer of the two
+            // output scales (exponents e3, e6), Xf = sum_g rint(G_g 2^(sigma - 8g)) in
+            // int32 (see half_fold), without the int64 fold.  xf_to_digits_kernel
+            // derives both digit layouts from it.
             if (!rvalid) continue;
             const int lrow = lane / 16, l16 = lane % 16;
-            __nv_bfloat16* base3 = p.o3 + ((size_t)P * p.mp * 4) * p.nbp + nu;
-            int* base6 = p.x6 + (size_t)P * p.m * p.nbp + nu;
+            int* basef = p.x6 + (size_t)P * p.m * p.nbp + nu;
 #pragma unroll
             for (int j = 0; j < CW; ++j) {
               const int i = c * CW + j;
@@ -543,18 +544,8 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_ge
                 float H[S4_NG];
 #pragma unroll
                 for (int g = 0; g < S4_NG; ++g) H[g] = __uint_as_float(gr[g][j]) * exp2_int(-8 * g);
-                // One fold at the finer of the two output scales; the other output is
-                // a rounding right shift of it (at most one unit of double rounding).
-                const int sg = ea + es_b[i] + 17;
-                const int s3 = sg - es_3[lrow * BN + i], s6 = sg - es_6[i * 16 + l16];
-                const int sf = s3 > s6 ? s3 : s6;
-                const int Xf = half_fold(H, sf);
-                __nv_bfloat16 d[4];
-                digits_bf16(rshift_round(Xf, sf - s3), d);
-                __nv_bfloat16* o3 = base3 + (size_t)col * 4 * p.nbp;
-#pragma unroll
-                for (int t = 0; t < 4; ++t) o3[t * p.nbp] = d[t];
-                base6[(size_t)col * p.nbp] = rshift_round(Xf, sf - s6);
+                const int emin = min(es_3[lrow * BN + i], es_6[i * 16 + l16]);
+                basef[(size_t)col * p.nbp] = half_fold(H, ea + es_b[i] + 17 - emin);
               }
             }
             continue;
@@ -576,20 +567,14 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_ge
           if (!rvalid) continue;
           if (KIND == S_HALF) {
             const int lrow = lane / 16, l16 = lane % 16;
-            __nv_bfloat16* base3 = p.o3 + ((size_t)P * p.mp * 4) * p.nbp + nu;
-            int* base6 = p.x6 + (size_t)P * p.m * p.nbp + nu;
+            int* basef = p.x6 + (size_t)P * p.m * p.nbp + nu;
 #pragma unroll
             for (int j = 0; j < CW; ++j) {
               const int i = c * CW + j;
               const int col = nt * BN + i;
               if (col < p.m) {
-                const int sb = ea + es_b[i] - 15;
-                __nv_bfloat16 d[4];
-                digits_bf16(round_shift(v[j], sb - es_3[lrow * BN + i]), d);
-                __nv_bfloat16* o3 = base3 + (size_t)col * 4 * p.nbp;
-#pragma unroll
-                for (int t = 0; t < 4; ++t) o3[t * p.nbp] = d[t];
-                base6[(size_t)col * p.nbp] = round_shift(v[j], sb - es_6[i * 16 + l16]);
+                const int emin = min(es_3[lrow * BN + i], es_6[i * 16 + l16]);
+                basef[(size_t)col * p.nbp] = round_shift(v[j], ea + es_b[i] - 15 - emin);
               }
             }
           } else if (KIND == S_FULLSQ) {
@@ -601,7 +586,7 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_ge
                 ll_to_df(v[j], ea + es_b[i] - S4_SHIFT, xh, xl);
                 const float ph = xh * xh;
                 const float pl = fmaf(xh, xh, -ph) + 2.f * xh * xl;
-                df_add(sh[SUM_DF ? i : 0], sl[SUM_DF ? i : 0], ph, pl);
+                df_add(sh[SUM_DF ? cb * CW + j : 0], sl[SUM_DF ? cb * CW + j : 0], ph, pl);
               }
             }
           } else if (KIND == S_FOCK) {
@@ -614,7 +599,7 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_ge
                 const float2 wv = es_w[i];
                 const float ph = xh * wv.x;
                 const float pl = fmaf(xh, wv.x, -ph) + (xh * wv.y + xl * wv.x);
-                df_add(sh[SUM_DF ? i : 0], sl[SUM_DF ? i : 0], ph, pl);
+                df_add(sh[SUM_DF ? cb * CW + j : 0], sl[SUM_DF ? cb * CW + j : 0], ph, pl);
               }
             }
           } else if (KIND == S_JAO) {
@@ -678,8 +663,8 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_ge
         } else if (SUM_DF) {
           float2* dst = (float2*)p.partial + ((size_t)split * p.prow + r) * p.pcol;
 #pragma unroll
-          for (int i = 0; i < BN; ++i) {
-            const int col = nt * BN + i;
+          for (int i = 0; i < BN / NWG; ++i) {
+            const int col = nt * BN + ((i / CW) * NWG + wg) * CW + i % CW;
             if (col < p.pcol) dst[col] = make_float2(sh[SUM_DF ? i : 0], sl[SUM_DF ? i : 0]);
           }
         }
@@ -875,26 +860,66 @@ __global__ void fock_weights_df_kernel(const double* A, const double* Bc, int m,
 }
 
 // Interleaved digits + row exponents -> FP64 values (fetch / copy-out paths).
-// L6 digits [p][nu][t][P] from the half transform's integers X6 [P][p][nu]
-// (same exponents e6): a 32 x 32 (P, nu) tile per block, transposed in shared
-// memory so that both the reads (nu contiguous) and the digit stores (P
-// contiguous, 64 bytes per row) are full sectors.
-__global__ void x6_to_l6_kernel(const int* X6, int nx, int nb, int m, int nbp, int nxp, __nv_bfloat16* L6) {
-  __shared__ int tile[32][33];
-  const int p = blockIdx.z, nu0 = blockIdx.x * 32, P0 = blockIdx.y * 32;
-  for (int r = threadIdx.y; r < 32; r += 8) {
-    const int P = P0 + r, nu = nu0 + threadIdx.x;
-    tile[r][threadIdx.x] = (P < nx && nu < nb) ? X6[((size_t)P * m + p) * nbp + nu] : 0;
+// Both digit layouts of b_half from the half transform's integers Xf [P][p][nu]
+// (scale 2^(min(e3, e6) - 31)): L3 [P][p][t][nu] with exponent e3[P][p] and L6
+// [p][nu][t][P] with exponent e6[p][nu], each a rounding right shift of Xf by
+// the exponent difference.  A 64 x 64 (P, nu) tile per block, two adjacent
+// elements per thread (8-byte loads, BF16 pairs stored as 4 bytes); L6 goes
+// through a shared-memory transposition, so the reads and both digit stores are
+// 128 contiguous bytes per warp.  Row strides (nbp, nxp) are even.
+__global__ void __launch_bounds__(256) xf_to_digits_kernel(const int* Xf, const int* e3, const int* e6, int nx, int nb,
+                                                           int m, int mp, int nbp, int nxp, __nv_bfloat16* L3,
+                                                           __nv_bfloat16* L6) {
+  __shared__ int tile[64][65];
+  __shared__ int s3[64], s6[64];
+  const int p = blockIdx.z, nu0 = blockIdx.x * 64, P0 = blockIdx.y * 64;
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  if (tid < 64) s3[tid] = (P0 + tid < nx) ? e3[(size_t)(P0 + tid) * m + p] : 0;
+  else if (tid < 128) s6[tid - 64] = (nu0 + tid - 64 < nb) ? e6[(size_t)p * nb + nu0 + tid - 64] : 0;
+  __syncthreads();
+  const int c0 = 2 * threadIdx.x;  // this thread's column pair within the tile
+  for (int r = threadIdx.y; r < 64; r += 8) {
+    const int P = P0 + r, nu = nu0 + c0;
+    int x0 = 0, x1 = 0;
+    if (P < nx && nu < nb) {
+      const int* src = Xf + ((size_t)P * m + p) * nbp + nu;
+      if (nu + 1 < nb) {
+        const int2 v = *(const int2*)src;
+        x0 = v.x;
+        x1 = v.y;
+      } else {
+        x0 = src[0];
+      }
+      int d = s3[r] - s6[c0];
+      __nv_bfloat16 a[4], b[4];
+      digits_bf16(rshift_round(x0, d > 0 ? d : 0), a);
+      d = s3[r] - s6[c0 + 1];
+      digits_bf16(rshift_round(x1, d > 0 ? d : 0), b);
+      __nv_bfloat16* o = L3 + (((size_t)P * mp + p) * 4) * nbp + nu;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        if (nu + 1 < nb) *(__nv_bfloat162*)(o + (size_t)t * nbp) = __halves2bfloat162(a[t], b[t]);
+        else o[(size_t)t * nbp] = a[t];
+      }
+    }
+    tile[r][c0] = x0;
+    tile[r][c0 + 1] = x1;
   }
   __syncthreads();
-  for (int r = threadIdx.y; r < 32; r += 8) {
-    const int nu = nu0 + r, P = P0 + threadIdx.x;
+  for (int r = threadIdx.y; r < 64; r += 8) {
+    const int nu = nu0 + r, P = P0 + c0;
     if (nu < nb && P < nx) {
-      __nv_bfloat16 d[4];
-      digits_bf16(tile[threadIdx.x][r], d);
+      int d = s6[r] - s3[c0];
+      __nv_bfloat16 a[4], b[4];
+      digits_bf16(rshift_round(tile[c0][r], d > 0 ? d : 0), a);
+      d = s6[r] - s3[c0 + 1];
+      digits_bf16(rshift_round(tile[c0 + 1][r], d > 0 ? d : 0), b);
       __nv_bfloat16* o = L6 + ((size_t)p * nb + nu) * 4 * nxp + P;
 #pragma unroll
-      for (int t = 0; t < 4; ++t) o[(size_t)t * nxp] = d[t];
+      for (int t = 0; t < 4; ++t) {
+        if (P + 1 < nx) *(__nv_bfloat162*)(o + (size_t)t * nxp) = __halves2bfloat162(a[t], b[t]);
+        else o[(size_t)t * nxp] = a[t];
+      }
     }
   }
 }
@@ -1056,7 +1081,7 @@ int s4_init(donof_ri_ctx* ctx) {
   const int KBb = (nb + S4_BK - 1) / S4_BK, KBx = (nx + S4_BK - 1) / S4_BK;
   const int bn = S4Cfg<S_HALF>::BN;  // 48 for every kind but the full transform (32)
   s4_plan<S_HALF>(sb, ((nx + 7) / 8) * ((nb + 15) / 16), (m + bn - 1) / bn, 1, 1, S4Cfg<S_HALF>::CTAS * sms);
-  s4_plan<S_FULLSQ>(sb, (m + S4_BM - 1) / S4_BM, (m + 31) / 32, nx, S4Cfg<S_FULLSQ>::CTAS * sms);
+  s4_plan<S_FULLSQ>(sb, (m + S4_BM - 1) / S4_BM, (m + bn - 1) / bn, nx, S4Cfg<S_FULLSQ>::CTAS * sms);
   s4_plan<S_JMO>(sb, (m + S4_BM - 1) / S4_BM, (m + bn - 1) / bn, (KBx + S4_CHUNK_KB - 1) / S4_CHUNK_KB,
                  S4Cfg<S_JMO>::CTAS * sms);
   s4_plan<S_JAO>(sb, (nb * nb + S4_BM - 1) / S4_BM, (m + bn - 1) / bn, 1, 1, S4Cfg<S_JAO>::CTAS * sms);
@@ -1155,7 +1180,7 @@ int s4_init(donof_ri_ctx* ctx) {
     long long dA[4] = {nb, 4, m, nx}, sA[3] = {nbp, 4LL * nbp, (long long)mp * 4 * nbp};
     int bA[4] = {S4_BK, 1, S4_BM, 1};
     long long dB[3] = {nb, 4, m}, sB[2] = {nbp, 4LL * nbp};
-    int bB[3] = {S4_BK, 1, 32};
+    int bB[3] = {S4_BK, 1, bn};
     if ((rc = s4_map(sb, &p.a, sb->L3, 4, dA, sA, bA))) return rc;
     if ((rc = s4_map(sb, &p.b, sb->Ct, 3, dB, sB, bB))) return rc;
     p.ea = sb->e3; p.eb = sb->eC;
@@ -1256,8 +1281,8 @@ int s4_transform(donof_ri_ctx* ctx, int mode) {
   {
     ProfScope ps(ctx, DONOF_RI_ROW_HALF);
     if ((rc = launch_s4<S_HALF>(ctx))) return rc;
-    dim3 g((nb + 31) / 32, (nx + 31) / 32, m), b(32, 8);
-    x6_to_l6_kernel<<<g, b, 0, s>>>(sb->X6, nx, nb, m, sb->nbp, sb->nxp, sb->L6);
+    dim3 g((nb + 63) / 64, (nx + 63) / 64, m), b(32, 8);
+    xf_to_digits_kernel<<<g, b, 0, s>>>(sb->X6, sb->e3, sb->e6, nx, nb, m, sb->mp, sb->nbp, sb->nxp, sb->L3, sb->L6);
     DONOF_LAUNCH_CHECK(ctx);
   }
   {

@@ -924,19 +924,28 @@ __global__ void __launch_bounds__(256) xf_to_digits_kernel(const int* Xf, const 
   }
 }
 
-// K^(q) is symmetric: the GEMM skips the tiles (128 mu x 48 nu) that lie wholly
-// below the diagonal, and this kernel fills their elements from the transposed
-// ones, through a shared-memory tile so that reads and writes are coalesced.
-// hi/lo: [2m][nb][ldo] with K^(q) at rows m + q.
-__device__ __forceinline__ bool kao_tile_computed(int mu, int nu, int bn) {
+// J^(q) and K^(q) are symmetric: their GEMMs skip the tiles that lie wholly below
+// the diagonal, and this kernel fills those elements from the transposed ones,
+// through a shared-memory tile so that reads and writes are coalesced.
+// hi/lo: [2m][nb][ldo] with J^(q) at rows q and K^(q) at rows m + q.
+//   K^(q) tiles: 128 mu x bn nu; skipped when the tile's last nu is below its first mu.
+//   J^(q) tiles: 128 consecutive rows r = mu nb + nu of the output (one tile per
+//   row block); skipped when all of its rows lie in one mu and have nu < mu.
+__host__ __device__ __forceinline__ bool kao_tile_computed(int mu, int nu, int bn) {
   return (nu / bn) * bn + bn - 1 >= (mu / 128) * 128;
 }
 
-__global__ void kao_mirror_kernel(float* hi, float* lo, int nb, int m, int ldo, int bn) {
+__host__ __device__ __forceinline__ bool jao_block_skipped(long long r0, int nb) {
+  const long long r1 = r0 + 127 < (long long)nb * nb ? r0 + 127 : (long long)nb * nb - 1;
+  const long long mu0 = r0 / nb, mu1 = r1 / nb;
+  return mu0 == mu1 && (r1 - mu0 * nb) < mu0;
+}
+
+__global__ void sym_mirror_kernel(float* hi, float* lo, int nb, int row0, int ldo, int bn, int jao) {
   __shared__ float th[32][33], tl[32][33];
   const int bi = blockIdx.y, bj = blockIdx.x;  // destination block: rows mu (bi), columns nu (bj)
   if (bj > bi) return;
-  const size_t base = (size_t)(m + blockIdx.z) * nb * ldo;
+  const size_t base = (size_t)(row0 + blockIdx.z) * nb * ldo;
   for (int r = threadIdx.y; r < 32; r += 8) {  // source rows nu = bj*32 + r, columns mu = bi*32 + x
     const int nu = bj * 32 + r, mu = bi * 32 + threadIdx.x;
     if (nu < nb && mu < nb) {
@@ -947,7 +956,9 @@ __global__ void kao_mirror_kernel(float* hi, float* lo, int nb, int m, int ldo, 
   __syncthreads();
   for (int r = threadIdx.y; r < 32; r += 8) {
     const int mu = bi * 32 + r, nu = bj * 32 + threadIdx.x;
-    if (mu < nb && nu < nb && nu < mu && !kao_tile_computed(mu, nu, bn)) {
+    const bool computed = jao ? !jao_block_skipped(((long long)mu * nb + nu) / 128 * 128, nb)
+                              : kao_tile_computed(mu, nu, bn);
+    if (mu < nb && nu < nb && nu < mu && !computed) {
       hi[base + (size_t)mu * ldo + nu] = th[threadIdx.x][r];
       lo[base + (size_t)mu * ldo + nu] = tl[threadIdx.x][r];
     }
@@ -985,6 +996,8 @@ struct donof::S4Buffers {
   __nv_bfloat16 *B1, *B5, *Ct, *L3, *L6, *Dp, *JKp;  // interleaved digits
   int* X6;                                            // L6 integers [nx][m][nbp] before digitisation
   int* kao_tmap;                                      // K^(q) tiles on or above the diagonal
+  int* jao_tmap;                                      // J^(q) row blocks on or above the diagonal
+  int jao_sym;                                        // 1: J^(q) lower row blocks skipped and mirrored
   int *eB1, *eB5, *eC, *e3, *e6, *ed, *eJK;          // row exponents
   float *rmaxB, *maxB, *absC, *absCt;
   float2* Cdf;    // C rows p (< N_O) as double-float pairs
@@ -1084,7 +1097,14 @@ int s4_init(donof_ri_ctx* ctx) {
   s4_plan<S_FULLSQ>(sb, (m + S4_BM - 1) / S4_BM, (m + bn - 1) / bn, nx, S4Cfg<S_FULLSQ>::CTAS * sms);
   s4_plan<S_JMO>(sb, (m + S4_BM - 1) / S4_BM, (m + bn - 1) / bn, (KBx + S4_CHUNK_KB - 1) / S4_CHUNK_KB,
                  S4Cfg<S_JMO>::CTAS * sms);
-  s4_plan<S_JAO>(sb, (nb * nb + S4_BM - 1) / S4_BM, (m + bn - 1) / bn, 1, 1, S4Cfg<S_JAO>::CTAS * sms);
+  // J^(q): only the row blocks that reach the diagonal or lie above it, once the
+  // saving outweighs the extra mirror pass (measured: from nbf ~ 256 on).
+  sb->jao_sym = nb >= 256;
+  std::vector<int> jao_tiles;
+  for (long long mt = 0; mt < ((long long)nb * nb + S4_BM - 1) / S4_BM; ++mt)
+    if (!sb->jao_sym || !jao_block_skipped(mt * S4_BM, nb))
+      for (int nt = 0; nt < (m + bn - 1) / bn; ++nt) jao_tiles.push_back((int)((mt << 16) | nt));
+  s4_plan<S_JAO>(sb, 1, (int)jao_tiles.size(), 1, 1, S4Cfg<S_JAO>::CTAS * sms);
   // K^(q): only the tiles that reach the diagonal or lie above it (the rest is mirrored).
   std::vector<int> kao_tiles;
   for (int mt = 0; mt < (nb + S4_BM - 1) / S4_BM; ++mt)
@@ -1112,6 +1132,10 @@ int s4_init(donof_ri_ctx* ctx) {
   ALLOC(sb->L6, ms * nbs * 4 * nxp * 2);
   ALLOC(sb->X6, nxs * ms * nbp * 4);
   ALLOC(sb->kao_tmap, kao_tiles.size() * sizeof(int));
+  ALLOC(sb->jao_tmap, jao_tiles.size() * sizeof(int));
+  if (cudaMemcpy(sb->jao_tmap, jao_tiles.data(), jao_tiles.size() * sizeof(int), cudaMemcpyHostToDevice) !=
+      cudaSuccess)
+    return DONOF_RI_E_CUDA;
   if (cudaMemcpy(sb->kao_tmap, kao_tiles.data(), kao_tiles.size() * sizeof(int), cudaMemcpyHostToDevice) !=
       cudaSuccess)
     return DONOF_RI_E_CUDA;
@@ -1206,6 +1230,7 @@ int s4_init(donof_ri_ctx* ctx) {
     if ((rc = s4_map(sb, &p.b, sb->Dp, 3, dB, sB, bB))) return rc;
     p.ea = sb->eB5; p.eb = sb->ed;
     p.ohi = sb->JKhi; p.olo = sb->JKlo;
+    p.tmap = sb->jao_tmap;
   }
   {  // KAO: A = B = L6 [m][nb][4][nxp] rows (p, mu) over P
     S4Params& p = sb->plan[S_KAO];
@@ -1244,7 +1269,7 @@ int s4_init(donof_ri_ctx* ctx) {
 void s4_free(donof_ri_ctx* ctx) {
   S4Buffers* sb = ctx->s4;
   if (!sb) return;
-  void* bufs[] = {sb->kao_tmap, sb->X6,    sb->B1,   sb->B5,   sb->Ct,   sb->L3,   sb->L6, sb->Dp,  sb->JKp,  sb->eB1,   sb->eB5,
+  void* bufs[] = {sb->jao_tmap, sb->kao_tmap, sb->X6,    sb->B1,   sb->B5,   sb->Ct,   sb->L3,   sb->L6, sb->Dp,  sb->JKp,  sb->eB1,   sb->eB5,
                   sb->eC,    sb->e3,   sb->e6,   sb->ed,   sb->eJK, sb->rmaxB, sb->maxB, sb->absC, sb->absCt,
                   sb->Cdf,   sb->dmat, sb->JKhi, sb->JKlo, sb->W,  sb->HCt, sb->Yt,   sb->partial};
   for (void* b : bufs)
@@ -1322,12 +1347,17 @@ int s4_jk_ao(donof_ri_ctx* ctx) {
   {
     ProfScope ps(ctx, DONOF_RI_ROW_JAO);
     if ((rc = launch_s4<S_JAO>(ctx))) return rc;
+    if (sb->jao_sym) {
+      dim3 g((nb + 31) / 32, (nb + 31) / 32, m), b(32, 8);
+      sym_mirror_kernel<<<g, b, 0, ctx->stream>>>(sb->JKhi, sb->JKlo, nb, 0, sb->ldo, S4Cfg<S_JAO>::BN, 1);
+      DONOF_LAUNCH_CHECK(ctx);
+    }
   }
   {
     ProfScope ps(ctx, DONOF_RI_ROW_KAO);
     if ((rc = launch_s4<S_KAO>(ctx))) return rc;
     dim3 g((nb + 31) / 32, (nb + 31) / 32, m), b(32, 8);
-    kao_mirror_kernel<<<g, b, 0, ctx->stream>>>(sb->JKhi, sb->JKlo, nb, m, sb->ldo, S4Cfg<S_KAO>::BN);
+    sym_mirror_kernel<<<g, b, 0, ctx->stream>>>(sb->JKhi, sb->JKlo, nb, m, sb->ldo, S4Cfg<S_KAO>::BN, 0);
     DONOF_LAUNCH_CHECK(ctx);
   }
   {

@@ -787,40 +787,6 @@ __global__ void bmax_aux_kernel(const double* B, int nx, int nb, float* maxB) {
   maxB[i] = __double2float_ru(mx);
 }
 
-// b^P_pp = sum_nu b^P_{p nu} C_{nu p} (Table 3 step 3) from the L3 digits, compensated
-// double-float dot product per warp; writes d[p][P] in FP64.
-__global__ void diag_s4_kernel(const __nv_bfloat16* L3, const int* e3, const float2* Cdf, int nb, int nbp, int nx,
-                               int m, int mp, double* d) {
-  long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / 32;
-  int lane = threadIdx.x % 32;
-  if (w >= (long long)nx * m) return;
-  int P = (int)(w / m), pc = (int)(w % m);
-  const __nv_bfloat16* rb = L3 + ((size_t)P * mp + pc) * 4 * nbp;
-  float s = 0.f, c = 0.f;
-  for (int nu = lane; nu < nb; nu += 32) {
-    // Xint = d0 2^24 + d1 2^16 + d2 2^8 + d3 as xh + xl, both exact in FP32
-    const float d0 = __bfloat162float(rb[nu]), d1 = __bfloat162float(rb[nbp + nu]);
-    const float d2 = __bfloat162float(rb[2 * nbp + nu]), d3 = __bfloat162float(rb[3 * nbp + nu]);
-    const float xh = ((d0 * 65536.f + d1 * 256.f) + d2) * 256.f, xl = d3;
-    const float2 cv = Cdf[(size_t)pc * nb + nu];
-    const float p0 = xh * cv.x;
-    const float e0 = fmaf(xh, cv.x, -p0) + (xh * cv.y + xl * cv.x);
-    float ns, e;
-    two_sum_f(s, p0, ns, e);
-    s = ns;
-    c += e + e0;
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    float so = __shfl_xor_sync(0xffffffffu, s, o);
-    float co = __shfl_xor_sync(0xffffffffu, c, o);
-    float ns, e;
-    two_sum_f(s, so, ns, e);
-    s = ns;
-    c += co + e;
-  }
-  if (lane == 0) d[(size_t)pc * nx + P] = ldexp((double)s + (double)c, e3[(size_t)P * m + pc] - 31);
-}
-
 // J_pq = 2^(ed_p + ed_q - 46) x (sum over splits of the exact int64 partials).
 __global__ void reduce_jmo_kernel(const long long* partial, int nsplit, int m, const int* ed, double* J) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -867,9 +833,15 @@ __global__ void fock_weights_df_kernel(const double* A, const double* Bc, int m,
 // elements per thread (8-byte loads, BF16 pairs stored as 4 bytes); L6 goes
 // through a shared-memory transposition, so the reads and both digit stores are
 // 128 contiguous bytes per warp.  Row strides (nbp, nxp) are even.
+//
+// The same pass accumulates the diagonal b^P_pp = sum_nu C_{nu p} b^P_{p nu} (Table 3
+// step 3) from the L3 integers it has in hand: each warp sums its row's 64 nu in
+// double-float arithmetic (X3 = xh + xl exactly, C as a double-float pair) and
+// writes one partial per (nu tile, p, P) to dpart; diag_reduce_kernel adds the
+// tiles in a fixed order and applies the row scale.
 __global__ void __launch_bounds__(256) xf_to_digits_kernel(const int* Xf, const int* e3, const int* e6, int nx, int nb,
                                                            int m, int mp, int nbp, int nxp, __nv_bfloat16* L3,
-                                                           __nv_bfloat16* L6) {
+                                                           __nv_bfloat16* L6, const float2* Cdf, float2* dpart) {
   __shared__ int tile[64][65];
   __shared__ int s3[64], s6[64];
   const int p = blockIdx.z, nu0 = blockIdx.x * 64, P0 = blockIdx.y * 64;
@@ -878,9 +850,11 @@ __global__ void __launch_bounds__(256) xf_to_digits_kernel(const int* Xf, const 
   else if (tid < 128) s6[tid - 64] = (nu0 + tid - 64 < nb) ? e6[(size_t)p * nb + nu0 + tid - 64] : 0;
   __syncthreads();
   const int c0 = 2 * threadIdx.x;  // this thread's column pair within the tile
+  const float2 cv0 = (nu0 + c0 < nb) ? Cdf[(size_t)p * nb + nu0 + c0] : make_float2(0.f, 0.f);
+  const float2 cv1 = (nu0 + c0 + 1 < nb) ? Cdf[(size_t)p * nb + nu0 + c0 + 1] : make_float2(0.f, 0.f);
   for (int r = threadIdx.y; r < 64; r += 8) {
     const int P = P0 + r, nu = nu0 + c0;
-    int x0 = 0, x1 = 0;
+    int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
     if (P < nx && nu < nb) {
       const int* src = Xf + ((size_t)P * m + p) * nbp + nu;
       if (nu + 1 < nb) {
@@ -891,10 +865,12 @@ __global__ void __launch_bounds__(256) xf_to_digits_kernel(const int* Xf, const 
         x0 = src[0];
       }
       int d = s3[r] - s6[c0];
-      __nv_bfloat16 a[4], b[4];
-      digits_bf16(rshift_round(x0, d > 0 ? d : 0), a);
+      y0 = rshift_round(x0, d > 0 ? d : 0);
       d = s3[r] - s6[c0 + 1];
-      digits_bf16(rshift_round(x1, d > 0 ? d : 0), b);
+      y1 = rshift_round(x1, d > 0 ? d : 0);
+      __nv_bfloat16 a[4], b[4];
+      digits_bf16(y0, a);
+      digits_bf16(y1, b);
       __nv_bfloat16* o = L3 + (((size_t)P * mp + p) * 4) * nbp + nu;
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
@@ -904,6 +880,29 @@ __global__ void __launch_bounds__(256) xf_to_digits_kernel(const int* Xf, const 
     }
     tile[r][c0] = x0;
     tile[r][c0 + 1] = x1;
+    // diagonal partial of row P over this tile's 64 nu: y = yh + yl exactly in FP32
+    float sum = 0.f, cmp = 0.f;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int y = k ? y1 : y0;
+      const float2 cv = k ? cv1 : cv0;
+      const float yh = (float)(y >> 8) * 256.f, yl = (float)(y & 255);
+      const float p0 = yh * cv.x;
+      const float e0 = fmaf(yh, cv.x, -p0) + (yh * cv.y + yl * cv.x);
+      float ns, e;
+      two_sum_f(sum, p0, ns, e);
+      sum = ns;
+      cmp += e + e0;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const float so = __shfl_xor_sync(0xffffffffu, sum, o);
+      const float co = __shfl_xor_sync(0xffffffffu, cmp, o);
+      float ns, e;
+      two_sum_f(sum, so, ns, e);
+      sum = ns;
+      cmp += co + e;
+    }
+    if (threadIdx.x == 0 && P < nx) dpart[((size_t)blockIdx.x * m + p) * nx + P] = make_float2(sum, cmp);
   }
   __syncthreads();
   for (int r = threadIdx.y; r < 64; r += 8) {
@@ -922,6 +921,19 @@ __global__ void __launch_bounds__(256) xf_to_digits_kernel(const int* Xf, const 
       }
     }
   }
+}
+
+// d[p][P] = 2^(e3[P][p] - 31) sum over the nu tiles of the pass's double-float partials.
+__global__ void diag_reduce_kernel(const float2* dpart, int ntiles, int nx, int m, const int* e3, double* d) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= (long long)nx * m) return;
+  const int pc = (int)(i / nx), P = (int)(i % nx);
+  double s = 0.0;
+  for (int t = 0; t < ntiles; ++t) {
+    const float2 v = dpart[((size_t)t * m + pc) * nx + P];
+    s += (double)v.x + (double)v.y;
+  }
+  d[i] = ldexp(s, e3[(size_t)P * m + pc] - 31);
 }
 
 // J^(q) and K^(q) are symmetric: their GEMMs skip the tiles that lie wholly below
@@ -1001,6 +1013,7 @@ struct donof::S4Buffers {
   int *eB1, *eB5, *eC, *e3, *e6, *ed, *eJK;          // row exponents
   float *rmaxB, *maxB, *absC, *absCt;
   float2* Cdf;    // C rows p (< N_O) as double-float pairs
+  float2* dpart;  // diagonal partials [nu tile][m][nx] from the digit pass
   double* dmat;   // d [m][nx] FP64
   float *JKhi, *JKlo;
   float2* W;
@@ -1153,6 +1166,7 @@ int s4_init(donof_ri_ctx* ctx) {
   ALLOC(sb->absC, ms * nbs * 4);
   ALLOC(sb->absCt, ms * nbs * 4);
   ALLOC(sb->Cdf, ms * nbs * 8);
+  ALLOC(sb->dpart, (size_t)((nb + 63) / 64) * ms * nxs * 8);
   ALLOC(sb->dmat, ms * nxs * 8);
   ALLOC(sb->JKhi, 2 * ms * nbs * ldo * 4);
   ALLOC(sb->JKlo, 2 * ms * nbs * ldo * 4);
@@ -1271,7 +1285,7 @@ void s4_free(donof_ri_ctx* ctx) {
   if (!sb) return;
   void* bufs[] = {sb->jao_tmap, sb->kao_tmap, sb->X6,    sb->B1,   sb->B5,   sb->Ct,   sb->L3,   sb->L6, sb->Dp,  sb->JKp,  sb->eB1,   sb->eB5,
                   sb->eC,    sb->e3,   sb->e6,   sb->ed,   sb->eJK, sb->rmaxB, sb->maxB, sb->absC, sb->absCt,
-                  sb->Cdf,   sb->dmat, sb->JKhi, sb->JKlo, sb->W,  sb->HCt, sb->Yt,   sb->partial};
+                  sb->Cdf,   sb->dpart, sb->dmat, sb->JKhi, sb->JKlo, sb->W,  sb->HCt, sb->Yt,   sb->partial};
   for (void* b : bufs)
     if (b) cudaFree(b);
   free(sb);
@@ -1307,13 +1321,14 @@ int s4_transform(donof_ri_ctx* ctx, int mode) {
     ProfScope ps(ctx, DONOF_RI_ROW_HALF);
     if ((rc = launch_s4<S_HALF>(ctx))) return rc;
     dim3 g((nb + 63) / 64, (nx + 63) / 64, m), b(32, 8);
-    xf_to_digits_kernel<<<g, b, 0, s>>>(sb->X6, sb->e3, sb->e6, nx, nb, m, sb->mp, sb->nbp, sb->nxp, sb->L3, sb->L6);
+    xf_to_digits_kernel<<<g, b, 0, s>>>(sb->X6, sb->e3, sb->e6, nx, nb, m, sb->mp, sb->nbp, sb->nxp, sb->L3, sb->L6,
+                                        sb->Cdf, sb->dpart);
     DONOF_LAUNCH_CHECK(ctx);
   }
   {
     ProfScope ps(ctx, DONOF_RI_ROW_DIAG);
-    diag_s4_kernel<<<ceil_div_u((long long)nx * m * 32, 256), 256, 0, s>>>(sb->L3, sb->e3, sb->Cdf, nb, sb->nbp, nx, m,
-                                                                            sb->mp, sb->dmat);
+    diag_reduce_kernel<<<ceil_div_u((long long)nx * m, 256), 256, 0, s>>>(sb->dpart, (nb + 63) / 64, nx, m, sb->e3,
+                                                                           sb->dmat);
     DONOF_LAUNCH_CHECK(ctx);
     slice_f64_kernel<<<ceil_div_u((long long)m * 32, 256), 256, 0, s>>>(sb->dmat, m, nx, nx, 1, sb->Dp, sb->nxp,
                                                                           sb->ed, nullptr, nullptr, nullptr);

@@ -256,6 +256,22 @@ int donof_ri_profile_read(donof_ri_ctx* ctx, int row, double* total_ms, long lon
 int donof_ri_optimize_occupations(donof_ri_ctx* ctx, double* gamma, int max_iter, double gtol, double etol, double* E,
                                   double* grad, int* info);
 
+/*
+ * One orbital rotation step for fixed occupations (Sec. 2, "Orbital Optimization
+ * with RI"; the plain rotation driver's step, which the paper's iterative
+ * diagonalisation of F^lambda replaces): with G = lambda - lambda^T from the last
+ * donof_ri_energy_lagrangian (the rotation gradient dE/dkappa = 4 G),
+ *   C <- C expm(kappa),  kappa = -radius G / max|G|,
+ * then one Newton-Schulz re-orthonormalisation C <- C (3 I - C^T C) / 2 (FP64).
+ *   radius  largest rotation angle of the step, 0..3.2 (0: only reports max|G|)
+ *   C       out (host or device, [nbf*nbf] column-major) or NULL: the rotated orbitals,
+ *           also kept as the context's orbitals; the transforms must be redone
+ *   gmax    out (host) or NULL: max|lambda_qp - lambda_pq| before the step
+ * Synchronous.  Errors: E_ARG, E_STATE (no donof_ri_energy_lagrangian since the
+ * last transform), E_OOM (scratch of 4 nbf^2 doubles, allocated on first use).
+ */
+int donof_ri_rotate_orbitals(donof_ri_ctx* ctx, double radius, double* C, double* gmax);
+
 /* ------------------------------------------------------------------------
  * Learned warm start for the occupation optimisation.  The paper has no
  * learned part: this is the project's own addition.  A 3-layer MLP

@@ -1,0 +1,63 @@
+"""Orbital optimisation for fixed occupations (oracle, FP64).
+
+Test infrastructure only; see the package docstring.
+
+Sec. 2, "Orbital Optimization with RI": the energy is minimised over real
+orthonormal orbitals at fixed occupations, with J^(q), K^(q) recomputed at every
+inner iteration and the Lagrangian lambda driving the step.  The paper's own
+step (iterative diagonalisation of F^lambda) is a later addition; this module
+states the plain driver it replaces: the orbitals rotate as C -> C expm(kappa)
+with kappa a steepest-descent step on the rotation gradient
+  dE/dkappa_qp = 4 (lambda_qp - lambda_pq)          (pinned in test_oracle_pnof7)
+of length controlled by a trust radius: kappa = -r G / max|G|, G = lambda -
+lambda^T; a step that raises E is rejected and halves r, an accepted one grows r
+by 1.5 (up to r_max).
+"""
+from __future__ import annotations
+
+import numpy as np
+from scipy.linalg import expm
+
+from . import integrals as I, pnof7, ri
+
+
+def rotation_step(C: np.ndarray, lam: np.ndarray, radius: float) -> np.ndarray:
+    """C expm(kappa) with kappa = -radius (lam - lam^T) / max|lam - lam^T|."""
+    G = lam - lam.T
+    gmax = np.abs(G).max()
+    if gmax == 0.0:
+        return C.copy()
+    return C @ expm(-radius * G / gmax)
+
+
+def energy_lambda(system, B, H, e_nuc, C, gamma, subspace, weak_rank):
+    """(E, lambda) of Eq. (PNOF) and the Lagrangian at orbitals C and angles gamma."""
+    m = system.n_omega
+    r = ri.all_rows(B, C, m)
+    n = pnof7.occupations(gamma, system.n_strong, system.n_weak_per, subspace, weak_rank)
+    A, Bc = pnof7.coupling(n, subspace, weak_rank)
+    lam = pnof7.lagrangian(C, H, r["Jao"], r["Kao"], n, A, Bc)
+    Hd = np.einsum("mp,mn,np->p", C[:, :m], H, C[:, :m])
+    return pnof7.energy_from_lagrangian(lam, n, Hd, e_nuc), lam
+
+
+def optimize(system, C0, gamma, subspace, weak_rank, max_iter=500, gtol=1e-6, radius=0.05, r_max=0.3):
+    """Trust-radius steepest descent on the orbitals; returns (C, E, max|lam - lam^T|, iterations)."""
+    B, L, G = ri.setup(system)
+    H = I.core_hamiltonian(system)
+    e_nuc = I.nuclear_repulsion(system)
+    C = C0.copy()
+    E, lam = energy_lambda(system, B, H, e_nuc, C, gamma, subspace, weak_rank)
+    it = 0
+    for it in range(1, max_iter + 1):
+        g = np.abs(lam - lam.T).max()
+        if g <= gtol:
+            break
+        Cn = rotation_step(C, lam, radius)
+        En, lamn = energy_lambda(system, B, H, e_nuc, Cn, gamma, subspace, weak_rank)
+        if En < E:
+            C, E, lam = Cn, En, lamn
+            radius = min(1.5 * radius, r_max)
+        else:
+            radius *= 0.5
+    return C, E, float(np.abs(lam - lam.T).max()), it

@@ -45,7 +45,7 @@ EXPORTS = [
     "donof_ri_energy_lagrangian", "donof_ri_fetch", "donof_ri_sync", "donof_ri_destroy",
     "donof_ri_strerror", "donof_ri_launch_count", "donof_ri_profile", "donof_ri_profile_read",
     "donof_ri_iteration", "donof_ri_jmo_noalloc", "donof_ri_optimize_occupations",
-    "donof_ri_on_features", "donof_ri_gamma_guess",
+    "donof_ri_on_features", "donof_ri_gamma_guess", "donof_ri_rotate_orbitals",
     "donof_mlp_create", "donof_mlp_param_count", "donof_mlp_set_params", "donof_mlp_get_params",
     "donof_mlp_set_normalization", "donof_mlp_forward", "donof_mlp_loss_grad", "donof_mlp_train_step",
     "donof_mlp_destroy",
@@ -107,6 +107,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.donof_ri_profile_read.restype = i
     lib.donof_ri_optimize_occupations.argtypes = [vp, vp, i, d, d, vp, vp, vp]
     lib.donof_ri_optimize_occupations.restype = i
+    lib.donof_ri_rotate_orbitals.argtypes = [vp, d, vp, vp]
+    lib.donof_ri_rotate_orbitals.restype = i
     lib.donof_ri_on_features.argtypes = [vp, vp]
     lib.donof_ri_on_features.restype = i
     lib.donof_ri_gamma_guess.argtypes = [vp, vp, d, vp]
@@ -231,6 +233,12 @@ def donof_ri_optimize_occupations(ctx, gamma, max_iter: int, gtol: float, etol: 
     ip = None if info is None else info.ctypes.data
     _check(load().donof_ri_optimize_occupations(ctx, _ptr(gamma), int(max_iter), float(gtol), float(etol), _ptr(E),
                                                 _ptr(grad), ip), "donof_ri_optimize_occupations")
+
+
+def donof_ri_rotate_orbitals_dev(ctx, radius: float, C_out, gmax_out: np.ndarray):
+    """One rotation step; C_out a device tensor (column-major nbf*nbf) or None, gmax_out a 1-element float64 array."""
+    _check(load().donof_ri_rotate_orbitals(ctx, float(radius), _ptr(C_out), gmax_out.ctypes.data),
+           "donof_ri_rotate_orbitals")
 
 
 def donof_ri_profile(ctx, enable: bool):
@@ -400,6 +408,14 @@ class Engine:
         info = np.zeros(2, dtype=np.int32)
         donof_ri_optimize_occupations(self.ctx, g, max_iter, gtol, etol, E, grad, info)
         return g, float(E[0]), grad, int(info[0]), int(info[1])
+
+    def rotate(self, radius: float):
+        """One rotation step from the last energy_lagrangian: (rotated C [mu, p], max|lambda - lambda^T|)."""
+        Ccm = np.empty(self.nbf * self.nbf)
+        g = ctypes.c_double()
+        _check(load().donof_ri_rotate_orbitals(self.ctx, float(radius), _ptr(Ccm), ctypes.byref(g)),
+               "donof_ri_rotate_orbitals")
+        return Ccm.reshape(self.nbf, self.nbf).T.copy(), g.value
 
     def on_features(self) -> np.ndarray:
         X = np.empty((self.system.n_strong, 3 + 4 * self.system.n_weak_per), dtype=np.float32)

@@ -145,7 +145,7 @@ int donof_ri_destroy(donof_ri_ctx* ctx) {
                   ctx->d_aux_alpha, ctx->d_subspace, ctx->d_weak_rank, ctx->d_S, ctx->d_H, ctx->d_G, ctx->d_B,
                   ctx->d_enuc, ctx->d_scratch_max, ctx->d_C, ctx->d_bh, ctx->d_d, ctx->d_bf, ctx->d_J, ctx->d_K,
                   ctx->d_Jao, ctx->d_Kao, ctx->d_W, ctx->d_HC, ctx->d_Y, ctx->d_lambda, ctx->d_gamma, ctx->d_n,
-                  ctx->d_A, ctx->d_Bc, ctx->d_E, ctx->d_Hd, ctx->d_on, ctx->d_on_info, ctx->d_feat,
+                  ctx->d_A, ctx->d_Bc, ctx->d_E, ctx->d_Hd, ctx->d_on, ctx->d_on_info, ctx->d_feat, ctx->d_rot,
                   ctx->d_status};
   for (void* b : bufs) dfree(b);
   free(ctx);
@@ -288,7 +288,7 @@ int donof_ri_transform(donof_ri_ctx* ctx, const double* C, int mode) {
     rc = launch_check_finite(ctx, ctx->d_C, (long long)nb2);
     if (rc) return rc;
   }
-  ctx->have_half = ctx->have_full = ctx->have_ao = 0;
+  ctx->have_half = ctx->have_full = ctx->have_ao = ctx->have_lambda = 0;
   rc = ctx->precision == DONOF_RI_FP64     ? path64_transform(ctx, mode)
        : ctx->precision == DONOF_RI_TF32X3 ? mixed_transform(ctx, mode)
                                            : s4_transform(ctx, mode);
@@ -358,9 +358,28 @@ int donof_ri_energy_lagrangian(donof_ri_ctx* ctx, const double* gamma, double* E
        : ctx->precision == DONOF_RI_TF32X3 ? mixed_energy(ctx)
                                            : s4_energy(ctx);
   if (rc) return rc;
+  ctx->have_lambda = 1;
   bool host = false;
   if ((rc = copy_out(ctx, E, ctx->d_E, 1, &host))) return rc;
   if ((rc = copy_out(ctx, lambda, ctx->d_lambda, (size_t)ctx->nbf * ctx->nbf, &host))) return rc;
+  return host ? consume_status(ctx) : DONOF_RI_OK;
+}
+
+int donof_ri_rotate_orbitals(donof_ri_ctx* ctx, double radius, double* C, double* gmax) {
+  if (!ctx || !(radius >= 0.0) || !(radius <= 3.2)) return DONOF_RI_E_ARG;
+  if (!ctx->have_lambda) return DONOF_RI_E_STATE;
+  const size_t nb2 = (size_t)ctx->nbf * ctx->nbf;
+  int rc;
+  if (!ctx->d_rot && (rc = dalloc(&ctx->d_rot, 4 * nb2 + 2))) return rc;
+  double g = 0.0;
+  {
+    ProfScope ps(ctx, DONOF_RI_ROW_OTHER);
+    if ((rc = rotate_orbitals(ctx, radius, ctx->d_rot, &g))) return rc;
+  }
+  if (radius > 0.0 && g > 0.0) ctx->have_half = ctx->have_full = ctx->have_ao = ctx->have_lambda = 0;
+  if (gmax) *gmax = g;
+  bool host = false;
+  if ((rc = copy_out(ctx, C, ctx->d_C, nb2, &host))) return rc;
   return host ? consume_status(ctx) : DONOF_RI_OK;
 }
 

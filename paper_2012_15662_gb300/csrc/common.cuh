@@ -83,6 +83,7 @@ struct donof_ri_ctx {
   double* d_on;     // [2*N_I*N_g + 1] occupation optimisation: gamma, gradient, energy
   int* d_on_info;   // [2]
   float* d_feat;    // [N_I][3 + 4 N_g] learned-guess features
+  double* d_rot;    // [4 nbf^2 + 2] rotation-step scratch (allocated on first use)
   int* d_status;    // [1] device-side status (DeviceStatus)
 
   donof::MixedBuffers* mixed;
@@ -94,7 +95,7 @@ struct donof_ri_ctx {
   int prof_n, prof_cap;
 
   // call-order state
-  int have_half, have_full, have_ao;
+  int have_half, have_full, have_ao, have_lambda;
 
   // CUDA graph of donof_ri_iteration (see the header)
   int capturing;
@@ -130,6 +131,7 @@ int launch_hc_public(donof_ri_ctx* ctx);
 int onopt_launch(donof_ri_ctx* ctx, double* d_gamma, double* d_E, double* d_grad, int* d_info, int mode,
                  int max_iter, double gtol, double etol);
 int onopt_features(donof_ri_ctx* ctx, float* d_X);
+int rotate_orbitals(donof_ri_ctx* ctx, double radius, double* scratch, double* gnorm);
 int onopt_unfold(donof_ri_ctx* ctx, const float* d_Y, double clip, double* d_gamma);
 int mlp_forward_device(donof_mlp* n, const float* dX, int B, float** dY);
 int mlp_shape(const donof_mlp* n, int* F, int* O);

@@ -1,0 +1,105 @@
+"""PNOF7 energy minimisation with the engine: outer and inner iterations.
+
+Host orchestration only; every computation runs in the library's kernels.  The
+scheme is the paper's (Sec. 2, Fig. "general scheme"): an outer iteration
+optimises the occupations for fixed orbitals (J, K from one FULL transform,
+donof_ri_optimize_occupations), and inner iterations optimise the orbitals for
+fixed occupations (J^(q), K^(q) and the Lagrangian recomputed at every step).
+The inner step here is the plain rotation driver (donof_ri_rotate_orbitals:
+steepest descent on dE/dkappa = 4 (lambda - lambda^T) with a trust radius that
+grows by 1.5 after an accepted step and halves after a rejected one); the
+paper's iterative diagonalisation of F^lambda is a later replacement.
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+
+from . import binding as bd
+
+
+class _Inner:
+    """Device state of the inner iterations of one engine."""
+
+    def __init__(self, eng: "bd.Engine"):
+        import torch
+        self.eng = eng
+        nb = eng.nbf
+        self.dev = torch.device("cuda")
+        self.C = torch.empty(nb * nb, dtype=torch.float64, device=self.dev)
+        self.C_try = torch.empty_like(self.C)
+        self.E = np.zeros(1)
+
+    def evaluate(self, C_dev, gamma):
+        """E at orbitals C_dev (also leaves lambda in the context for the next rotation)."""
+        ctx = self.eng.ctx
+        bd.donof_ri_transform(ctx, C_dev, bd.DONOF_RI_HALF)
+        bd.donof_ri_jk_ao_batch(ctx)
+        bd.donof_ri_energy_lagrangian(ctx, gamma, self.E, None)
+        return float(self.E[0])
+
+
+def orbital_iterations(eng, C_colmajor, gamma, max_iter=100, gtol=1e-4, etol=1e-10, radius=0.05, r_max=0.3,
+                       state=None):
+    """Inner iterations from C (column-major numpy or device tensor) at fixed gamma.
+    Returns dict(C (column-major numpy), E, gmax, iterations, evaluations, ms_per_iteration, radius)."""
+    import torch
+    st = state or _Inner(eng)
+    gamma = np.ascontiguousarray(gamma, dtype=np.float64)
+    st.C.copy_(torch.as_tensor(np.ascontiguousarray(C_colmajor).reshape(-1)) if isinstance(C_colmajor, np.ndarray)
+               else C_colmajor.reshape(-1))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    E = st.evaluate(st.C, gamma)
+    evals, gmax, it = 1, float("inf"), 0
+    g = np.zeros(1)
+    for it in range(1, max_iter + 1):
+        # rotation from the lambda of the current orbitals (left by the last accepted evaluation)
+        bd.donof_ri_rotate_orbitals_dev(eng.ctx, radius, st.C_try, g)
+        gmax = float(g[0])
+        if gmax <= gtol:
+            it -= 1
+            break
+        En = st.evaluate(st.C_try, gamma)
+        evals += 1
+        if En < E:
+            dec = E - En
+            st.C, st.C_try = st.C_try, st.C
+            E = En
+            radius = min(1.5 * radius, r_max)
+            if dec <= etol * max(1.0, abs(E)):
+                break
+        else:
+            radius *= 0.5
+            E = st.evaluate(st.C, gamma)  # restore lambda at the accepted orbitals
+            evals += 1
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return dict(C=st.C.cpu().numpy().copy(), E=E, gmax=gmax, iterations=it, evaluations=evals,
+                ms_per_iteration=1000.0 * dt / max(it, 1), radius=radius)
+
+
+def solve(eng, C0, gamma0, max_outer=10, max_inner=50, etol=1e-6, gtol=1e-4, on_max_iter=20000):
+    """Outer / inner iterations from orbitals C0 ([mu, p] numpy) and angles gamma0.
+    Returns dict(C, gamma, E, outer, inner_total, history)."""
+    C = bd.Engine.colmajor(C0)
+    gamma = np.array(gamma0, dtype=np.float64)
+    hist = []
+    E_prev = None
+    st = _Inner(eng)
+    radius = 0.05
+    total_inner = 0
+    for o in range(1, max_outer + 1):
+        bd.donof_ri_transform(eng.ctx, C, bd.DONOF_RI_FULL)
+        gamma, E_on, _, it_on, _ = eng.optimize_occupations(gamma, max_iter=on_max_iter, gtol=1e-8, etol=1e-14)
+        r = orbital_iterations(eng, C, gamma, max_iter=max_inner, gtol=gtol, radius=radius, state=st)
+        C, radius = r["C"], max(r["radius"], 1e-3)
+        total_inner += r["iterations"]
+        hist.append(dict(outer=o, E_occ=E_on, on_iterations=it_on, E=r["E"], gmax=r["gmax"],
+                         inner=r["iterations"], ms_per_inner=r["ms_per_iteration"]))
+        if E_prev is not None and abs(r["E"] - E_prev) < etol and r["gmax"] < gtol:
+            break
+        E_prev = r["E"]
+    return dict(C=C.reshape(eng.nbf, eng.nbf).T.copy(), gamma=gamma, E=hist[-1]["E"], outer=len(hist),
+                inner_total=total_inner, history=hist)

@@ -103,3 +103,45 @@ def solve(eng, C0, gamma0, max_outer=10, max_inner=50, etol=1e-6, gtol=1e-4, on_
         E_prev = r["E"]
     return dict(C=C.reshape(eng.nbf, eng.nbf).T.copy(), gamma=gamma, E=hist[-1]["E"], outer=len(hist),
                 inner_total=total_inner, history=hist)
+
+
+def main():
+    """Compare the FP64 and SLICE4 engines and the learned occupation guess on one workload:
+    outer / inner iterations, energies, ms per inner iteration."""
+    import argparse
+    import json
+    from synthetic import make_workload, standard_gamma
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="c6h12")
+    ap.add_argument("--outer", type=int, default=4)
+    ap.add_argument("--inner", type=int, default=25)
+    ap.add_argument("--learned", type=int, default=0, help="train the warm-start network on this many rings first")
+    args = ap.parse_args()
+    w = make_workload(args.workload)
+    s = w.system
+    g0 = standard_gamma(s.n_strong, s.n_weak_per)
+    runs = [("fp64", bd.DONOF_RI_FP64, None), ("slice4", bd.DONOF_RI_SLICE4, None)]
+    net = None
+    if args.learned:
+        from . import warmstart
+        X, Y = warmstart.training_set(args.learned)
+        net, _ = warmstart.train(X, Y)
+        runs.append(("slice4+learned", bd.DONOF_RI_SLICE4, net))
+    out = []
+    for name, prec, nn in runs:
+        eng = bd.Engine(s, prec)
+        start = g0
+        if nn is not None:
+            eng.transform(w.C, bd.DONOF_RI_FULL)
+            start = eng.gamma_guess(nn)
+        t0 = time.perf_counter()
+        r = solve(eng, w.C, start, max_outer=args.outer, max_inner=args.inner)
+        dt = time.perf_counter() - t0
+        eng.close()
+        out.append(dict(form=name, E=r["E"], outer=r["outer"], inner_total=r["inner_total"], seconds=dt,
+                        history=r["history"]))
+    print(json.dumps({"workload": args.workload, "runs": out}))
+
+
+if __name__ == "__main__":
+    main()

@@ -236,6 +236,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="launch eagerly instead of replaying a CUDA graph")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default SLICE4 tile schedule")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -280,6 +281,16 @@ def main():
     L_dev = torch.empty(nb * nb, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     torch.cuda.synchronize()
+    tuned = None
+    if prec == bd.DONOF_RI_SLICE4 and not args.no_autotune:
+        # tile schedule tuned on this problem before any timing (donof_ri_autotune)
+        bd.donof_ri_transform(eng.ctx, C_dev, bd.DONOF_RI_FULL)
+        bd.donof_ri_jk_ao_batch(eng.ctx)
+        report, tried = bd.donof_ri_autotune(eng.ctx, reps=3)
+        tuned = {"settings_timed": tried,
+                 "per_kind": {k: {"stages": int(r[0]), "splits_or_sym": int(r[1]), "ctas": int(r[2]), "us": int(r[3])}
+                              for k, r in zip(["half", "full_k", "j", "jao", "kao", "fock"], report)}}
+        torch.cuda.synchronize()
 
     def step(graph=not args.no_graph):
         bd.donof_ri_iteration(eng.ctx, C_dev, g_dev, bd.DONOF_RI_FULL, J_dev, K_dev, E_dev, L_dev,
@@ -401,7 +412,7 @@ def main():
         "config": {"workload": desc, "precision": args.precision,
                    "l2": "flushed between steps (256 MB write, outside the step events)",
                    "launch": "eager" if args.no_graph else "one CUDA graph per step (donof_ri_iteration)",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}", "autotune": tuned},
         "rows_ms_per_step": {r: rows[r][0] / args.steps for r in ROWS},
         "roofline": roof, "clocks": clocks, "gpu_launches": int(launches), "e2e": e2e,
     }

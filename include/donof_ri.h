@@ -257,6 +257,25 @@ int donof_ri_optimize_occupations(donof_ri_ctx* ctx, double* gamma, int max_iter
                                   double* grad, int* info);
 
 /*
+ * Tile-schedule autotuner of the SLICE4 engine (the paper has no counterpart):
+ * times every digit-plane GEMM kind on the context's own problem (reps launches
+ * each) for every pipeline depth that fits its shared memory, the split kinds
+ * (full transform, J, F^(p)C_p) also for one and two waves of CTAs, and J^(q)
+ * with and without its symmetric skip-and-mirror (each launch timed from a
+ * flushed L2, as inside an iteration), and keeps for every later call the
+ * fastest setting of each kind when it beats the default by at least 3 %.  Needs a FULL transform and
+ * donof_ri_jk_ao_batch first (their data are the timing inputs); afterwards
+ * every result must be recomputed (the state returns to "no transform").
+ *   reps    launches timed per setting, 1..1000
+ *   report  out (host) or NULL: 6 x 4 ints, per kind (half, full, J, J^(q), K^(q),
+ *           F^(p)C_p): pipeline stages, split count (J^(q): 1 if symmetric),
+ *           CTAs, best time in microseconds
+ *   tried   out (host) or NULL: settings timed
+ * Synchronous.  Errors: E_ARG, E_STATE, E_UNSUPPORTED (precision other than SLICE4).
+ */
+int donof_ri_autotune(donof_ri_ctx* ctx, int reps, int* report, int* tried);
+
+/*
  * One orbital rotation step for fixed occupations (Sec. 2, "Orbital Optimization
  * with RI"; the plain rotation driver's step, which the paper's iterative
  * diagonalisation of F^lambda replaces): with G = lambda - lambda^T from the last

@@ -365,6 +365,23 @@ int donof_ri_energy_lagrangian(donof_ri_ctx* ctx, const double* gamma, double* E
   return host ? consume_status(ctx) : DONOF_RI_OK;
 }
 
+int donof_ri_autotune(donof_ri_ctx* ctx, int reps, int* report, int* tried) {
+  if (!ctx || reps < 1 || reps > 1000) return DONOF_RI_E_ARG;
+  if (ctx->precision != DONOF_RI_SLICE4) return DONOF_RI_E_UNSUPPORTED;
+  if (!ctx->have_full || !ctx->have_ao) return DONOF_RI_E_STATE;
+  int n = 0;
+  int rc = s4_autotune(ctx, reps, report, &n);
+  if (tried) *tried = n;
+  // the kernels ran alone and the captured graph holds the old launch parameters
+  ctx->have_half = ctx->have_full = ctx->have_ao = ctx->have_lambda = 0;
+  if (ctx->graph_exec) {
+    cudaGraphExecDestroy(ctx->graph_exec);
+    ctx->graph_exec = nullptr;
+  }
+  if (rc) return rc;
+  return consume_status(ctx);
+}
+
 int donof_ri_rotate_orbitals(donof_ri_ctx* ctx, double radius, double* C, double* gmax) {
   if (!ctx || !(radius >= 0.0) || !(radius <= 3.2)) return DONOF_RI_E_ARG;
   if (!ctx->have_lambda) return DONOF_RI_E_STATE;

@@ -1009,7 +1009,11 @@ struct donof::S4Buffers {
   int* X6;                                            // L6 integers [nx][m][nbp] before digitisation
   int* kao_tmap;                                      // K^(q) tiles on or above the diagonal
   int* jao_tmap;                                      // J^(q) row blocks on or above the diagonal
+  int* jao_tmap_full;                                 // every J^(q) row block
+  int jao_ntiles_sym, jao_ntiles_full;
   int jao_sym;                                        // 1: J^(q) lower row blocks skipped and mirrored
+  int max_stages[donof::S_NKINDS];                    // pipeline depth that fits the shared memory
+  int target[donof::S_NKINDS];                        // CTA count the split kinds aim at
   int *eB1, *eB5, *eC, *e3, *e6, *ed, *eJK;          // row exponents
   float *rmaxB, *maxB, *absC, *absCt;
   float2* Cdf;    // C rows p (< N_O) as double-float pairs
@@ -1111,13 +1115,18 @@ int s4_init(donof_ri_ctx* ctx) {
   s4_plan<S_JMO>(sb, (m + S4_BM - 1) / S4_BM, (m + bn - 1) / bn, (KBx + S4_CHUNK_KB - 1) / S4_CHUNK_KB,
                  S4Cfg<S_JMO>::CTAS * sms);
   // J^(q): only the row blocks that reach the diagonal or lie above it, once the
-  // saving outweighs the extra mirror pass (measured: from nbf ~ 256 on).
+  // saving outweighs the extra mirror pass (default from nbf 256 on; s4_autotune
+  // measures both).
   sb->jao_sym = nb >= 256;
-  std::vector<int> jao_tiles;
+  std::vector<int> jao_tiles, jao_full;
   for (long long mt = 0; mt < ((long long)nb * nb + S4_BM - 1) / S4_BM; ++mt)
-    if (!sb->jao_sym || !jao_block_skipped(mt * S4_BM, nb))
-      for (int nt = 0; nt < (m + bn - 1) / bn; ++nt) jao_tiles.push_back((int)((mt << 16) | nt));
-  s4_plan<S_JAO>(sb, 1, (int)jao_tiles.size(), 1, 1, S4Cfg<S_JAO>::CTAS * sms);
+    for (int nt = 0; nt < (m + bn - 1) / bn; ++nt) {
+      jao_full.push_back((int)((mt << 16) | nt));
+      if (!jao_block_skipped(mt * S4_BM, nb)) jao_tiles.push_back((int)((mt << 16) | nt));
+    }
+  sb->jao_ntiles_sym = (int)jao_tiles.size();
+  sb->jao_ntiles_full = (int)jao_full.size();
+  s4_plan<S_JAO>(sb, 1, sb->jao_sym ? sb->jao_ntiles_sym : sb->jao_ntiles_full, 1, 1, S4Cfg<S_JAO>::CTAS * sms);
   // K^(q): only the tiles that reach the diagonal or lie above it (the rest is mirrored).
   std::vector<int> kao_tiles;
   for (int mt = 0; mt < (nb + S4_BM - 1) / S4_BM; ++mt)
@@ -1125,10 +1134,15 @@ int s4_init(donof_ri_ctx* ctx) {
       if (nt * bn + bn - 1 >= mt * S4_BM) kao_tiles.push_back((mt << 16) | nt);
   s4_plan<S_KAO>(sb, 1, (int)kao_tiles.size(), m, S4Cfg<S_KAO>::CTAS * sms, S4Cfg<S_KAO>::CTAS * sms);
   s4_plan<S_FOCK>(sb, (nb + S4_BM - 1) / S4_BM, (m + bn - 1) / bn, 2 * m * ((KBb + S4_CHUNK_KB - 1) / S4_CHUNK_KB), sms);
-  size_t pbytes = (size_t)sb->plan[S_FULLSQ].nsplit * m * m * sizeof(float2);
-  size_t t = (size_t)sb->plan[S_JMO].nsplit * m * m * sizeof(long long);
+  for (int k = 0; k < S_NKINDS; ++k) sb->max_stages[k] = sb->plan[k].stages;
+  sb->target[S_FULLSQ] = S4Cfg<S_FULLSQ>::CTAS * sms;
+  sb->target[S_JMO] = S4Cfg<S_JMO>::CTAS * sms;
+  sb->target[S_FOCK] = sms;
+  // partial sums sized for twice the default split count (the autotuner may pick it)
+  size_t pbytes = 2 * (size_t)sb->plan[S_FULLSQ].nsplit * m * m * sizeof(float2);
+  size_t t = 2 * (size_t)sb->plan[S_JMO].nsplit * m * m * sizeof(long long);
   if (t > pbytes) pbytes = t;
-  t = (size_t)sb->plan[S_FOCK].nsplit * nb * m * sizeof(float2);
+  t = 2 * (size_t)sb->plan[S_FOCK].nsplit * nb * m * sizeof(float2);
   if (t > pbytes) pbytes = t;
 
 #define ALLOC(ptr, bytes)                                             \
@@ -1146,6 +1160,10 @@ int s4_init(donof_ri_ctx* ctx) {
   ALLOC(sb->X6, nxs * ms * nbp * 4);
   ALLOC(sb->kao_tmap, kao_tiles.size() * sizeof(int));
   ALLOC(sb->jao_tmap, jao_tiles.size() * sizeof(int));
+  ALLOC(sb->jao_tmap_full, jao_full.size() * sizeof(int));
+  if (cudaMemcpy(sb->jao_tmap_full, jao_full.data(), jao_full.size() * sizeof(int), cudaMemcpyHostToDevice) !=
+      cudaSuccess)
+    return DONOF_RI_E_CUDA;
   if (cudaMemcpy(sb->jao_tmap, jao_tiles.data(), jao_tiles.size() * sizeof(int), cudaMemcpyHostToDevice) !=
       cudaSuccess)
     return DONOF_RI_E_CUDA;
@@ -1244,7 +1262,7 @@ int s4_init(donof_ri_ctx* ctx) {
     if ((rc = s4_map(sb, &p.b, sb->Dp, 3, dB, sB, bB))) return rc;
     p.ea = sb->eB5; p.eb = sb->ed;
     p.ohi = sb->JKhi; p.olo = sb->JKlo;
-    p.tmap = sb->jao_tmap;
+    p.tmap = sb->jao_sym ? sb->jao_tmap : sb->jao_tmap_full;
   }
   {  // KAO: A = B = L6 [m][nb][4][nxp] rows (p, mu) over P
     S4Params& p = sb->plan[S_KAO];
@@ -1283,7 +1301,7 @@ int s4_init(donof_ri_ctx* ctx) {
 void s4_free(donof_ri_ctx* ctx) {
   S4Buffers* sb = ctx->s4;
   if (!sb) return;
-  void* bufs[] = {sb->jao_tmap, sb->kao_tmap, sb->X6,    sb->B1,   sb->B5,   sb->Ct,   sb->L3,   sb->L6, sb->Dp,  sb->JKp,  sb->eB1,   sb->eB5,
+  void* bufs[] = {sb->jao_tmap_full, sb->jao_tmap, sb->kao_tmap, sb->X6,    sb->B1,   sb->B5,   sb->Ct,   sb->L3,   sb->L6, sb->Dp,  sb->JKp,  sb->eB1,   sb->eB5,
                   sb->eC,    sb->e3,   sb->e6,   sb->ed,   sb->eJK, sb->rmaxB, sb->maxB, sb->absC, sb->absCt,
                   sb->Cdf,   sb->dpart, sb->dmat, sb->JKhi, sb->JKlo, sb->W,  sb->HCt, sb->Yt,   sb->partial};
   for (void* b : bufs)
@@ -1402,6 +1420,147 @@ int s4_energy(donof_ri_ctx* ctx) {
   DONOF_LAUNCH_CHECK(ctx);
   if ((rc = launch_dot64(ctx, m, nb, nb, sb->Yt, nb, ctx->d_C, nb, ctx->d_lambda, nb, 1))) return rc;
   return launch_energy_rows(ctx, sb->HCt);
+}
+
+// ---------------------------------------------------------------------------
+// Autotuning: every digit-plane GEMM kind is timed on the live problem for each
+// pipeline depth that fits its shared memory, the split kinds (a3, a4, a7) also
+// for one and two waves of CTAs, and J^(q) with and without the symmetric
+// skip-and-mirror.  Each timed launch starts from a flushed L2 (a 256 MB write
+// outside the events), as inside an iteration, and a setting replaces the
+// default only when it is at least 3 % faster.  Each launch rewrites its
+// outputs, so the inputs stay valid.
+// ---------------------------------------------------------------------------
+template <int KIND>
+static int s4_split(S4Buffers* sb, int target) {
+  S4Params& p = sb->plan[KIND];
+  const int tiles = p.ntiles;
+  int ns = target / tiles;
+  if (ns < 1) ns = 1;
+  if (ns > p.nbatch) ns = p.nbatch;
+  p.bpc = (p.nbatch + ns - 1) / ns;
+  p.nsplit = (p.nbatch + p.bpc - 1) / p.bpc;
+  sb->grid[KIND] = tiles * p.nsplit;
+  return p.nsplit;
+}
+
+template <int KIND>
+static int s4_time(donof_ri_ctx* ctx, int reps, cudaEvent_t a, cudaEvent_t b, void* flush, size_t flush_bytes,
+                   float* ms) {
+  S4Buffers* sb = ctx->s4;
+  int rc;
+  if ((rc = launch_s4<KIND>(ctx))) return rc;  // warm-up
+  float total = 0.f;
+  for (int r = 0; r < reps; ++r) {
+    DONOF_CUDA_TRY(cudaMemsetAsync(flush, r & 255, flush_bytes, ctx->stream));
+    DONOF_CUDA_TRY(cudaEventRecord(a, ctx->stream));
+    if ((rc = launch_s4<KIND>(ctx))) return rc;
+    if (KIND == S_JAO && sb->jao_sym) {
+      const int nb = ctx->nbf, m = ctx->n_omega;
+      dim3 g((nb + 31) / 32, (nb + 31) / 32, m), bl(32, 8);
+      sym_mirror_kernel<<<g, bl, 0, ctx->stream>>>(sb->JKhi, sb->JKlo, nb, 0, sb->ldo, S4Cfg<S_JAO>::BN, 1);
+      DONOF_LAUNCH_CHECK(ctx);
+    }
+    DONOF_CUDA_TRY(cudaEventRecord(b, ctx->stream));
+    DONOF_CUDA_TRY(cudaEventSynchronize(b));
+    float t = 0.f;
+    DONOF_CUDA_TRY(cudaEventElapsedTime(&t, a, b));
+    total += t;
+  }
+  *ms = total / reps;
+  return DONOF_RI_OK;
+}
+
+template <int KIND>
+static int s4_tune_kind(donof_ri_ctx* ctx, int reps, cudaEvent_t a, cudaEvent_t b, void* flush, size_t fbytes,
+                        int* report, int* tried) {
+  S4Buffers* sb = ctx->s4;
+  S4Params& p = sb->plan[KIND];
+  const bool split = (KIND == S_FULLSQ || KIND == S_JMO || KIND == S_FOCK);
+  const int nsym = (KIND == S_JAO) ? 2 : 1;
+  float best = 1e30f, dflt = 1e30f;
+  const int dS = p.stages, dT = split ? sb->target[KIND] : 0, dSym = sb->jao_sym;
+  int bestS = dS, bestT = dT, bestSym = dSym;
+  const int targets[2] = {split ? sb->target[KIND] : 0, split ? 2 * sb->target[KIND] : 0};
+  int rc;
+  for (int sym = 0; sym < nsym; ++sym) {
+    if (KIND == S_JAO) {
+      sb->jao_sym = sym;
+      p.tmap = sym ? sb->jao_tmap : sb->jao_tmap_full;
+      p.ntiles = p.n_tiles = sym ? sb->jao_ntiles_sym : sb->jao_ntiles_full;
+      const int units = p.ntiles * p.nbatch, pc = S4Cfg<S_JAO>::CTAS * 152;
+      sb->grid[KIND] = units < pc ? units : pc;
+    }
+    for (int ti = 0; ti < (split ? 2 : 1); ++ti) {
+      if (split) s4_split<KIND>(sb, targets[ti]);
+      for (int S = 2; S <= sb->max_stages[KIND]; ++S) {
+        p.stages = S;
+        float ms = 0.f;
+        if ((rc = s4_time<KIND>(ctx, reps, a, b, flush, fbytes, &ms))) return rc;
+        ++*tried;
+        if (S == dS && targets[ti] == dT && (KIND != S_JAO || sym == dSym)) dflt = ms;
+        if (ms < best) {
+          best = ms;
+          bestS = S;
+          bestT = targets[ti];
+          bestSym = sym;
+        }
+      }
+    }
+  }
+  if (!(best < 0.97f * dflt)) {  // keep the default unless clearly beaten
+    best = dflt;
+    bestS = dS;
+    bestT = dT;
+    bestSym = dSym;
+  }
+  if (KIND == S_JAO) {
+    sb->jao_sym = bestSym;
+    p.tmap = bestSym ? sb->jao_tmap : sb->jao_tmap_full;
+    p.ntiles = p.n_tiles = bestSym ? sb->jao_ntiles_sym : sb->jao_ntiles_full;
+    const int units = p.ntiles * p.nbatch, pc = S4Cfg<S_JAO>::CTAS * 152;
+    sb->grid[KIND] = units < pc ? units : pc;
+  }
+  p.stages = bestS;
+  if (split) s4_split<KIND>(sb, bestT);
+  if (report) {
+    report[KIND * 4 + 0] = bestS;
+    report[KIND * 4 + 1] = split ? p.nsplit : (KIND == S_JAO ? bestSym : 0);
+    report[KIND * 4 + 2] = sb->grid[KIND];
+    report[KIND * 4 + 3] = (int)(best * 1000.f + 0.5f);  // microseconds
+  }
+  return DONOF_RI_OK;
+}
+
+int s4_autotune(donof_ri_ctx* ctx, int reps, int* report, int* tried) {
+  const size_t fbytes = (size_t)256 << 20;
+  void* flush = nullptr;
+  if (cudaMalloc(&flush, fbytes) != cudaSuccess) {
+    cudaGetLastError();
+    return DONOF_RI_E_OOM;
+  }
+  cudaEvent_t a, b;
+  if (cudaEventCreate(&a) != cudaSuccess) {
+    cudaFree(flush);
+    return DONOF_RI_E_CUDA;
+  }
+  if (cudaEventCreate(&b) != cudaSuccess) {
+    cudaEventDestroy(a);
+    cudaFree(flush);
+    return DONOF_RI_E_CUDA;
+  }
+  int rc = DONOF_RI_OK;
+  *tried = 0;
+  if (!rc) rc = s4_tune_kind<S_HALF>(ctx, reps, a, b, flush, fbytes, report, tried);
+  if (!rc) rc = s4_tune_kind<S_FULLSQ>(ctx, reps, a, b, flush, fbytes, report, tried);
+  if (!rc) rc = s4_tune_kind<S_JMO>(ctx, reps, a, b, flush, fbytes, report, tried);
+  if (!rc) rc = s4_tune_kind<S_JAO>(ctx, reps, a, b, flush, fbytes, report, tried);
+  if (!rc) rc = s4_tune_kind<S_KAO>(ctx, reps, a, b, flush, fbytes, report, tried);
+  if (!rc) rc = s4_tune_kind<S_FOCK>(ctx, reps, a, b, flush, fbytes, report, tried);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(flush);
+  return rc;
 }
 
 int s4_fetch(donof_ri_ctx* ctx, int what, double* dst, size_t count) {

@@ -1,0 +1,57 @@
+"""The SLICE4 tile-schedule autotuner: call order, and results that still meet
+the parity bars after the tuned schedule (pipeline depth, split counts and the
+symmetric J^(q) choice all change the kernels' work assignment)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+from oracle import integrals as I, pnof7, ri  # noqa: E402
+from synthetic import make_workload, pairing_columns  # noqa: E402
+
+
+def test_autotune_call_order():
+    from paper_2012_15662_gb300 import binding as bd
+    w = make_workload("square4")
+    eng = bd.Engine(w.system, bd.DONOF_RI_SLICE4)
+    with pytest.raises(bd.DonofError) as e:
+        bd.donof_ri_autotune(eng.ctx)
+    assert e.value.status == bd.DONOF_RI_E_STATE
+    eng.close()
+    eng = bd.Engine(w.system, bd.DONOF_RI_FP64)
+    eng.transform(w.C, bd.DONOF_RI_FULL)
+    eng.jk_ao(want=False)
+    with pytest.raises(bd.DonofError) as e:
+        bd.donof_ri_autotune(eng.ctx)
+    assert e.value.status == bd.DONOF_RI_E_UNSUPPORTED
+    eng.close()
+
+
+@pytest.mark.parametrize("name", ["c6h12", "c10h20"])
+def test_tuned_schedule_keeps_parity(name):
+    from paper_2012_15662_gb300 import binding as bd
+    w = make_workload(name)
+    s = w.system
+    eng = bd.Engine(s, bd.DONOF_RI_SLICE4)
+    eng.transform(w.C, bd.DONOF_RI_FULL)
+    eng.jk_ao(want=False)
+    rep, tried = bd.donof_ri_autotune(eng.ctx, reps=3)
+    assert tried >= 6
+    assert (rep[:, 0] >= 2).all() and (rep[:, 3] > 0).all()
+    eng.transform(w.C, bd.DONOF_RI_FULL)
+    J, K = eng.jk_mo()
+    Jao, Kao = eng.jk_ao()
+    E, lam = eng.energy_lagrangian(w.gamma)
+    eng.close()
+    B, L, G = ri.setup(s)
+    m = s.n_omega
+    r = ri.all_rows(B, w.C, m)
+    H = I.core_hamiltonian(s)
+    sub, rank = pairing_columns(s.n_strong, s.n_weak_per)
+    n = pnof7.occupations(w.gamma, s.n_strong, s.n_weak_per, sub, rank)
+    A, Bc = pnof7.coupling(n, sub, rank)
+    Hd = np.einsum("mp,mn,np->p", w.C[:, :m], H, w.C[:, :m])
+    Eo = pnof7.energy(n, Hd, r["J"], r["K"], A, Bc, I.nuclear_repulsion(s))
+    assert np.abs(J - r["J"]).max() <= 1e-7 and np.abs(K - r["K"]).max() <= 1e-7
+    assert np.abs(Jao - r["Jao"]).max() <= 1e-7 and np.abs(Kao - r["Kao"]).max() <= 1e-7
+    assert abs(E - Eo) <= 1e-6

@@ -44,6 +44,9 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 NOMINAL = {"bf16": 2250.0, "tf32": 1100.0, "fp64": 1.25}
 
 ROWS = ["half", "diag", "full_k", "j", "jao", "kao", "energy", "other"]
+# Profile rows 8..13: the tensor-core GEMM kernel of a row, timed alone.
+GEMMS = ["half", "full_k", "j", "jao", "kao", "fock"]
+GEMM_KERNEL = {"slice4": "s4_gemm_kernel<{}>", "tf32x3": "tc_gemm_kernel<{}>"}
 
 
 def workload_desc(name):
@@ -65,6 +68,7 @@ def algorithmic_flops(s):
         "jao": 1.0 * nb * (nb + 1) * nx * m,
         "kao": 1.0 * nb * (nb + 1) * nx * m,
         "energy": 4.0 * nb * nb * m * m + 2.0 * nb * nb * m,
+        "fock": 4.0 * nb * nb * m * m,
     }
 
 
@@ -336,6 +340,11 @@ def main():
     for i, r in enumerate(ROWS):
         t, c = bd.donof_ri_profile_read(eng.ctx, i)
         rows[r] = (t, c)
+    gemms = {}
+    for i, r in enumerate(GEMMS):
+        t, c = bd.donof_ri_profile_read(eng.ctx, len(ROWS) + i)
+        if c > 0:
+            gemms[r] = (t, c)
     bd.donof_ri_profile(eng.ctx, False)
     ms = float(np.mean(step_ms))
     value = job_ms_per_iteration(ms * args.steps, args.steps, world, dev)
@@ -369,10 +378,20 @@ def main():
                "h2d_bytes_per_step": int(8 * (nb * nb + len(w.gamma))),
                "d2h_bytes_per_step": int(8 * (2 * m * m + 1 + nb * nb))}
 
-    # roofline of the dominant compute row
+    # roofline of the dominant kernel: the tensor-core GEMM kernel with the largest
+    # share of the step (its own event pair); the FP64 form, which has no such
+    # kernel, falls back to its dominant row
     flops = algorithmic_flops(s)
-    dom = max((r for r in flops if rows[r][1] > 0), key=lambda r: rows[r][0])
-    t_dom, c_dom = rows[dom]
+    if gemms:
+        dom = max(gemms, key=lambda r: gemms[r][0])
+        t_dom, c_dom = gemms[dom]
+        kernel = GEMM_KERNEL[args.precision].format(GEMMS.index(dom))
+        traffic_key = "gemm_" + dom
+    else:
+        dom = max((r for r in ROWS if r in flops and rows[r][1] > 0), key=lambda r: rows[r][0])
+        t_dom, c_dom = rows[dom]
+        kernel = "row " + dom
+        traffic_key = dom
     per_launch_ms = t_dom / max(c_dom, 1)
     achieved = flops[dom] / (per_launch_ms * 1e-3) / 1e12
     peaks, peak_src = read_peaks()
@@ -396,9 +415,10 @@ def main():
         peak = bf / mult
         bound, peak_note = "tensor", (f"BF16 dense, {peak_src} burst {bf:.0f}, / 13 BF16 digit-pair MMAs per "
                                       "algorithmic product")
-    traffic = read_traffic(args.workload, args.precision, dom)
+    traffic = read_traffic(args.workload, args.precision, traffic_key)
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": traffic, "kernel_row": dom, "launch_ms": per_launch_ms,
+            "traffic": traffic, "kernel": kernel, "kernel_row": dom, "launch_ms": per_launch_ms,
+            "share_of_step": t_dom / args.steps / ms,
             "algorithmic_flops_per_launch": flops[dom], "executed_tflops": achieved * mult,
             "peak_source": peak_note}
 
@@ -414,6 +434,7 @@ def main():
                    "launch": "eager" if args.no_graph else "one CUDA graph per step (donof_ri_iteration)",
                    "parallelism": f"replicas x{world}", "autotune": tuned},
         "rows_ms_per_step": {r: rows[r][0] / args.steps for r in ROWS},
+        "gemm_kernels_ms_per_step": {r: gemms[r][0] / args.steps for r in gemms},
         "roofline": roof, "clocks": clocks, "gpu_launches": int(launches), "e2e": e2e,
     }
     if world == 1 and not args.no_cpu_baseline:

@@ -166,12 +166,20 @@ int donof_ri_energy_lagrangian(donof_ri_ctx* ctx, const double* gamma, double* E
  * mode); for FULL, donof_ri_jk_mo(J, K); donof_ri_jk_ao_batch(NULL, NULL);
  * donof_ri_energy_lagrangian(gamma, E, lambda).  Arguments as in those calls
  * (J, K, E, lambda may be NULL).
- * use_graph != 0: when every non-NULL pointer is device memory and the
- * context's stream is not the legacy default stream, the launch sequence is
- * captured once into a CUDA graph, keyed by (C, gamma, mode, J, K, E, lambda),
- * and replayed on later calls with the same key (one graph launch per
- * iteration).  Otherwise the calls run eagerly.  Profiling events are not
- * recorded inside graphs.  Errors: as the four calls; E_CUDA if capture fails.
+ * use_graph != 0: when every non-NULL pointer is device memory or page-locked
+ * host memory (cudaHostAlloc, cudaHostRegister) and the context's stream is not
+ * the legacy default stream, the launch sequence, including the copies from and
+ * to host memory, is captured once into a CUDA graph, keyed by (C, gamma, mode,
+ * J, K, E, lambda), and replayed on later calls with the same key (one graph
+ * launch per iteration; a replay reads the inputs' current contents).  With a
+ * host output the call returns after the stream has written it.  Otherwise
+ * (pageable host memory, or use_graph == 0) the calls run eagerly.  Profiling events are not
+ * recorded inside graphs.  Unless per-row profiling is on, the part of the
+ * energy row that needs only C, H and gamma (occupations, couplings, Fock
+ * weights, H C) runs on an internal side stream concurrently with the
+ * transforms and is joined back before F^(p) C_p; the call is still ordered on
+ * the context's stream as a whole.  Errors: as the four calls; E_CUDA if
+ * capture fails.
  */
 int donof_ri_iteration(donof_ri_ctx* ctx, const double* C, const double* gamma, int mode, double* J, double* K,
                        double* E, double* lambda, int use_graph);
@@ -213,7 +221,15 @@ long long donof_ri_launch_count(const donof_ri_ctx* ctx);
 #define DONOF_RI_ROW_KAO 5       /* a6: per-orbital K^(q)                             */
 #define DONOF_RI_ROW_ENERGY 6    /* a7: occupations, F^(p) C_p, lambda and E          */
 #define DONOF_RI_ROW_OTHER 7     /* input copies, finiteness checks, conversions      */
-#define DONOF_RI_NUM_ROWS 8
+/* The tensor-core GEMM kernel of a row alone (SLICE4 and TF32X3; the FP64 form
+ * records none): one event pair around that one launch, nested inside the row's. */
+#define DONOF_RI_GEMM_HALF 8     /* a1 GEMM                                           */
+#define DONOF_RI_GEMM_FULL_K 9   /* a3 GEMM (full transform with the squares summed)  */
+#define DONOF_RI_GEMM_J 10       /* a4 GEMM                                           */
+#define DONOF_RI_GEMM_JAO 11     /* a5 GEMM                                           */
+#define DONOF_RI_GEMM_KAO 12     /* a6 GEMM                                           */
+#define DONOF_RI_GEMM_FOCK 13    /* a7 GEMM: sum_q (A_pq J^(q) - B_pq K^(q)) C_p      */
+#define DONOF_RI_NUM_ROWS 14
 
 /*
  * Enable (1) or disable (0) per-row timing.  While enabled, every launch group

@@ -71,8 +71,24 @@ static void dfree(void* p) {
   if (p) cudaFree(p);
 }
 
-// Read and clear the device-side status word; maps it to an ABI status.
+// Page-locked host memory (cudaHostAlloc / cudaHostRegister): copies from and to
+// it can be captured into a CUDA graph.
+static bool is_pinned_host_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
+
+// Read and clear the device-side status word; maps it to an ABI status.  While a
+// graph is being captured nothing can be waited for: the caller of the graph
+// launch reads the status afterwards.
 static int consume_status(donof_ri_ctx* ctx) {
+  if (ctx->capturing) return DONOF_RI_OK;
   int h = 0;
   if (cudaMemcpyAsync(&h, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
     return DONOF_RI_E_CUDA;
@@ -141,6 +157,9 @@ int donof_ri_destroy(donof_ri_ctx* ctx) {
   }
   free(ctx->prof);
   if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  if (ctx->side) cudaStreamDestroy(ctx->side);
   void* bufs[] = {ctx->d_atom_xyz, ctx->d_atom_charge, ctx->d_bf_atom, ctx->d_bf_alpha, ctx->d_aux_atom,
                   ctx->d_aux_alpha, ctx->d_subspace, ctx->d_weak_rank, ctx->d_S, ctx->d_H, ctx->d_G, ctx->d_B,
                   ctx->d_enuc, ctx->d_scratch_max, ctx->d_C, ctx->d_bh, ctx->d_d, ctx->d_bf, ctx->d_J, ctx->d_K,
@@ -236,6 +255,10 @@ int donof_ri_init(const donof_ri_system* sys, int precision, void* stream, donof
   if (precision == DONOF_RI_TF32X3) TRY(mixed_init(ctx));
   if (precision == DONOF_RI_SLICE4) TRY(s4_init(ctx));
   if (cudaStreamSynchronize(s) != cudaSuccess) TRY(DONOF_RI_E_CUDA);
+  if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess)
+    TRY(DONOF_RI_E_CUDA);
 #undef TRY
   *out = ctx;
   return DONOF_RI_OK;
@@ -277,25 +300,31 @@ int donof_ri_sync(donof_ri_ctx* ctx) {
   return consume_status(ctx);
 }
 
-int donof_ri_transform(donof_ri_ctx* ctx, const double* C, int mode) {
-  if (!ctx || !C || (mode != DONOF_RI_HALF && mode != DONOF_RI_FULL)) return DONOF_RI_E_ARG;
+// Copy the orbitals in and check them (first part of donof_ri_transform).
+static int transform_input(donof_ri_ctx* ctx, const double* C) {
   const size_t nb2 = (size_t)ctx->nbf * ctx->nbf;
   cudaMemcpyKind kind = is_device_ptr(C) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  int rc;
-  {
-    ProfScope ps(ctx, DONOF_RI_ROW_OTHER);
-    DONOF_CUDA_TRY(cudaMemcpyAsync(ctx->d_C, C, nb2 * sizeof(double), kind, ctx->stream));
-    rc = launch_check_finite(ctx, ctx->d_C, (long long)nb2);
-    if (rc) return rc;
-  }
+  ProfScope ps(ctx, DONOF_RI_ROW_OTHER);
+  DONOF_CUDA_TRY(cudaMemcpyAsync(ctx->d_C, C, nb2 * sizeof(double), kind, ctx->stream));
+  return launch_check_finite(ctx, ctx->d_C, (long long)nb2);
+}
+
+static int transform_compute(donof_ri_ctx* ctx, int mode) {
   ctx->have_half = ctx->have_full = ctx->have_ao = ctx->have_lambda = 0;
-  rc = ctx->precision == DONOF_RI_FP64     ? path64_transform(ctx, mode)
-       : ctx->precision == DONOF_RI_TF32X3 ? mixed_transform(ctx, mode)
-                                           : s4_transform(ctx, mode);
+  int rc = ctx->precision == DONOF_RI_FP64     ? path64_transform(ctx, mode)
+           : ctx->precision == DONOF_RI_TF32X3 ? mixed_transform(ctx, mode)
+                                               : s4_transform(ctx, mode);
   if (rc) return rc;
   ctx->have_half = 1;
   ctx->have_full = (mode == DONOF_RI_FULL);
   return DONOF_RI_OK;
+}
+
+int donof_ri_transform(donof_ri_ctx* ctx, const double* C, int mode) {
+  if (!ctx || !C || (mode != DONOF_RI_HALF && mode != DONOF_RI_FULL)) return DONOF_RI_E_ARG;
+  int rc = transform_input(ctx, C);
+  if (rc) return rc;
+  return transform_compute(ctx, mode);
 }
 
 static int copy_out(donof_ri_ctx* ctx, double* dst, const double* src, size_t count, bool* host_written) {
@@ -342,27 +371,37 @@ int donof_ri_jk_ao_batch(donof_ri_ctx* ctx, double* Jao, double* Kao) {
   return host ? consume_status(ctx) : DONOF_RI_OK;
 }
 
-int donof_ri_energy_lagrangian(donof_ri_ctx* ctx, const double* gamma, double* E, double* lambda) {
-  if (!ctx || !gamma) return DONOF_RI_E_ARG;
-  if (!ctx->have_ao) return DONOF_RI_E_STATE;
+// Copy the angles in and check them.
+static int gamma_input(donof_ri_ctx* ctx, const double* gamma) {
   const size_t ng = (size_t)ctx->n_strong * ctx->n_weak_per;
   cudaMemcpyKind kind = is_device_ptr(gamma) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  int rc;
-  {
-    ProfScope ps(ctx, DONOF_RI_ROW_OTHER);
-    DONOF_CUDA_TRY(cudaMemcpyAsync(ctx->d_gamma, gamma, ng * sizeof(double), kind, ctx->stream));
-    rc = launch_check_finite(ctx, ctx->d_gamma, (long long)ng);
-    if (rc) return rc;
-  }
-  rc = ctx->precision == DONOF_RI_FP64     ? path64_energy(ctx)
-       : ctx->precision == DONOF_RI_TF32X3 ? mixed_energy(ctx)
-                                           : s4_energy(ctx);
-  if (rc) return rc;
+  ProfScope ps(ctx, DONOF_RI_ROW_OTHER);
+  DONOF_CUDA_TRY(cudaMemcpyAsync(ctx->d_gamma, gamma, ng * sizeof(double), kind, ctx->stream));
+  return launch_check_finite(ctx, ctx->d_gamma, (long long)ng);
+}
+
+static int energy_part(donof_ri_ctx* ctx, int part) {
+  return ctx->precision == DONOF_RI_FP64     ? path64_energy(ctx, part)
+         : ctx->precision == DONOF_RI_TF32X3 ? mixed_energy(ctx, part)
+                                             : s4_energy(ctx, part);
+}
+
+static int energy_outputs(donof_ri_ctx* ctx, double* E, double* lambda) {
   ctx->have_lambda = 1;
   bool host = false;
+  int rc;
   if ((rc = copy_out(ctx, E, ctx->d_E, 1, &host))) return rc;
   if ((rc = copy_out(ctx, lambda, ctx->d_lambda, (size_t)ctx->nbf * ctx->nbf, &host))) return rc;
   return host ? consume_status(ctx) : DONOF_RI_OK;
+}
+
+int donof_ri_energy_lagrangian(donof_ri_ctx* ctx, const double* gamma, double* E, double* lambda) {
+  if (!ctx || !gamma) return DONOF_RI_E_ARG;
+  if (!ctx->have_ao) return DONOF_RI_E_STATE;
+  int rc = gamma_input(ctx, gamma);
+  if (rc) return rc;
+  if ((rc = energy_part(ctx, ENERGY_ALL))) return rc;
+  return energy_outputs(ctx, E, lambda);
 }
 
 int donof_ri_autotune(donof_ri_ctx* ctx, int reps, int* report, int* tried) {
@@ -400,8 +439,36 @@ int donof_ri_rotate_orbitals(donof_ri_ctx* ctx, double radius, double* C, double
   return host ? consume_status(ctx) : DONOF_RI_OK;
 }
 
+// One iteration with the energy row's prologue (occupations, couplings, Fock
+// weights and H C, which need only C and gamma) forked onto the side stream, so
+// that it runs concurrently with the transforms; joined before F^(p) C_p.  The
+// buffers it writes are read by no kernel of the transforms.  Not used while
+// per-row profiling is on (the row events are recorded on the main stream).
+static int iteration_forked(donof_ri_ctx* ctx, const double* C, const double* gamma, int mode, double* J, double* K,
+                            double* E, double* lambda) {
+  int rc = transform_input(ctx, C);
+  if (rc) return rc;
+  cudaStream_t main_stream = ctx->stream;
+  DONOF_CUDA_TRY(cudaEventRecord(ctx->ev_fork, main_stream));
+  DONOF_CUDA_TRY(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+  ctx->stream = ctx->side;
+  rc = gamma_input(ctx, gamma);
+  if (!rc) rc = energy_part(ctx, ENERGY_PREP);
+  ctx->stream = main_stream;
+  // joined even after an error so that a stream capture stays well formed
+  DONOF_CUDA_TRY(cudaEventRecord(ctx->ev_join, ctx->side));
+  if (!rc) rc = transform_compute(ctx, mode);
+  if (!rc && mode == DONOF_RI_FULL && (J || K)) rc = donof_ri_jk_mo(ctx, J, K);
+  if (!rc) rc = donof_ri_jk_ao_batch(ctx, nullptr, nullptr);
+  DONOF_CUDA_TRY(cudaStreamWaitEvent(main_stream, ctx->ev_join, 0));
+  if (rc) return rc;
+  if ((rc = energy_part(ctx, ENERGY_MAIN))) return rc;
+  return energy_outputs(ctx, E, lambda);
+}
+
 static int iteration_eager(donof_ri_ctx* ctx, const double* C, const double* gamma, int mode, double* J, double* K,
                            double* E, double* lambda) {
+  if (ctx->side && !ctx->prof_enabled) return iteration_forked(ctx, C, gamma, mode, J, K, E, lambda);
   int rc = donof_ri_transform(ctx, C, mode);
   if (rc) return rc;
   if (mode == DONOF_RI_FULL && (J || K)) {
@@ -416,8 +483,12 @@ int donof_ri_iteration(donof_ri_ctx* ctx, const double* C, const double* gamma, 
   if (!ctx || !C || !gamma || (mode != DONOF_RI_HALF && mode != DONOF_RI_FULL)) return DONOF_RI_E_ARG;
   const void* key[7] = {C, gamma, J, K, E, lambda, nullptr};
   bool graphable = use_graph && ctx->stream != nullptr;
-  for (int i = 0; i < 6 && graphable; ++i)
-    if (key[i] && !is_device_ptr(key[i])) graphable = false;
+  bool host_out = false;
+  for (int i = 0; i < 6 && graphable; ++i) {
+    if (!key[i] || is_device_ptr(key[i])) continue;
+    if (is_pinned_host_ptr(key[i])) host_out = host_out || i >= 2;
+    else graphable = false;
+  }
   if (!graphable) return iteration_eager(ctx, C, gamma, mode, J, K, E, lambda);
   bool hit = ctx->graph_exec && ctx->graph_mode == mode;
   for (int i = 0; i < 7 && hit; ++i) hit = ctx->graph_key[i] == key[i];
@@ -455,7 +526,9 @@ int donof_ri_iteration(donof_ri_ctx* ctx, const double* C, const double* gamma, 
   ctx->have_half = 1;
   ctx->have_full = (mode == DONOF_RI_FULL);
   ctx->have_ao = 1;
-  return DONOF_RI_OK;
+  ctx->have_lambda = 1;
+  // results in host memory are complete once the stream has reached them
+  return host_out ? consume_status(ctx) : DONOF_RI_OK;
 }
 
 int donof_ri_optimize_occupations(donof_ri_ctx* ctx, double* gamma, int max_iter, double gtol, double etol, double* E,

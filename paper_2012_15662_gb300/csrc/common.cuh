@@ -97,6 +97,11 @@ struct donof_ri_ctx {
   // call-order state
   int have_half, have_full, have_ao, have_lambda;
 
+  // Side stream of donof_ri_iteration: the occupation-dependent and orbital-only
+  // prologue of the energy row runs there, concurrently with the transforms.
+  cudaStream_t side;
+  cudaEvent_t ev_fork, ev_join;
+
   // CUDA graph of donof_ri_iteration (see the header)
   int capturing;
   cudaGraphExec_t graph_exec;
@@ -125,7 +130,10 @@ int setup_cholesky_and_fit(donof_ri_ctx* ctx);
 // ---- FP64 hot path (path64.cu) ----
 int path64_transform(donof_ri_ctx* ctx, int mode);
 int path64_jk_ao(donof_ri_ctx* ctx);
-int path64_energy(donof_ri_ctx* ctx);
+// Parts of the energy row: PREP needs only C, H and gamma (occupations, couplings,
+// Fock weights, H C); MAIN needs J^(q), K^(q) as well (F^(p) C_p, lambda, E).
+enum EnergyPart { ENERGY_PREP = 1, ENERGY_MAIN = 2, ENERGY_ALL = 3 };
+int path64_energy(donof_ri_ctx* ctx, int part);
 int launch_check_finite(donof_ri_ctx* ctx, const double* x, long long n);
 int launch_hc_public(donof_ri_ctx* ctx);
 int onopt_launch(donof_ri_ctx* ctx, double* d_gamma, double* d_E, double* d_grad, int* d_info, int mode,
@@ -144,14 +152,14 @@ int mixed_init(donof_ri_ctx* ctx);
 void mixed_free(donof_ri_ctx* ctx);
 int mixed_transform(donof_ri_ctx* ctx, int mode);
 int mixed_jk_ao(donof_ri_ctx* ctx);
-int mixed_energy(donof_ri_ctx* ctx);
+int mixed_energy(donof_ri_ctx* ctx, int part);
 
 // ---- digit-plane path (s4.cu) ----
 int s4_init(donof_ri_ctx* ctx);
 void s4_free(donof_ri_ctx* ctx);
 int s4_transform(donof_ri_ctx* ctx, int mode);
 int s4_jk_ao(donof_ri_ctx* ctx);
-int s4_energy(donof_ri_ctx* ctx);
+int s4_energy(donof_ri_ctx* ctx, int part);
 int s4_fetch(donof_ri_ctx* ctx, int what, double* dst, size_t count);
 int s4_copy_ao(donof_ri_ctx* ctx, double* Jao, double* Kao, bool jao_dev, bool kao_dev);
 

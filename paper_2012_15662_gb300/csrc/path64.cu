@@ -317,12 +317,16 @@ int launch_lambda(donof_ri_ctx* ctx) {
 
 int launch_hc_public(donof_ri_ctx* ctx) { return launch_hc(ctx); }
 
-int path64_energy(donof_ri_ctx* ctx) {
+int path64_energy(donof_ri_ctx* ctx, int part) {
   const int nb = ctx->nbf, m = ctx->n_omega;
   const long long nb2 = (long long)nb * nb;
   int rc;
   ProfScope ps(ctx, DONOF_RI_ROW_ENERGY);
-  if ((rc = launch_occupations_coupling(ctx))) return rc;
+  if (part & ENERGY_PREP) {
+    if ((rc = launch_occupations_coupling(ctx))) return rc;
+    if ((rc = launch_hc(ctx))) return rc;
+  }
+  if (!(part & ENERGY_MAIN)) return DONOF_RI_OK;
   // W[p] = sum_q A_pq J^(q) - B_pq K^(q)
   {
     Gemm64 g{};
@@ -337,7 +341,6 @@ int path64_energy(donof_ri_ctx* ctx) {
     g.alpha = -1.0; g.beta = 1.0;
     if ((rc = launch_dgemm(ctx, g))) return rc;
   }
-  if ((rc = launch_hc(ctx))) return rc;
   fock_apply64_kernel<<<ceil_div_u((long long)nb * m * 32, 256), 256, 0, ctx->stream>>>(nb, m, ctx->d_W, ctx->d_C,
                                                                                        ctx->d_HC, ctx->d_n, ctx->d_Y);
   DONOF_LAUNCH_CHECK(ctx);

@@ -46,6 +46,7 @@ int launch_dot64(donof_ri_ctx* ctx, int M, int N, int K, const double* A, int ld
 int launch_energy_rows(donof_ri_ctx* ctx, const double* HCt);
 
 enum S4Kind { S_HALF = 0, S_FULLSQ = 1, S_JMO = 2, S_JAO = 3, S_KAO = 4, S_FOCK = 5, S_NKINDS = 6 };
+static_assert(DONOF_RI_GEMM_FOCK - DONOF_RI_GEMM_HALF == S_FOCK, "GEMM profile rows follow the kind order");
 
 constexpr int S4_BM = 128;      // rows per tile
 constexpr int S4_BK = 32;       // BF16 elements per K block (one 64-byte swizzle row)
@@ -1314,6 +1315,7 @@ template <int KIND>
 static int launch_s4(donof_ri_ctx* ctx) {
   S4Buffers* sb = ctx->s4;
   if (sb->grid[KIND] <= 0) return DONOF_RI_OK;
+  ProfScope ps(ctx, DONOF_RI_GEMM_HALF + KIND);
   s4_gemm_kernel<KIND><<<sb->grid[KIND], S4Cfg<KIND>::THREADS, sb->smem[KIND], ctx->stream>>>(sb->plan[KIND]);
   DONOF_LAUNCH_CHECK(ctx);
   return DONOF_RI_OK;
@@ -1403,16 +1405,19 @@ int s4_jk_ao(donof_ri_ctx* ctx) {
   return DONOF_RI_OK;
 }
 
-int s4_energy(donof_ri_ctx* ctx) {
+int s4_energy(donof_ri_ctx* ctx, int part) {
   S4Buffers* sb = ctx->s4;
   const int nb = ctx->nbf, m = ctx->n_omega;
   cudaStream_t s = ctx->stream;
   int rc;
   ProfScope ps(ctx, DONOF_RI_ROW_ENERGY);
-  if ((rc = launch_occupations_coupling(ctx))) return rc;
-  fock_weights_df_kernel<<<ceil_div_u(2LL * m * m, 256), 256, 0, s>>>(ctx->d_A, ctx->d_Bc, m, sb->W);
-  DONOF_LAUNCH_CHECK(ctx);
-  if ((rc = launch_dot64(ctx, m, nb, nb, ctx->d_C, nb, ctx->d_H, nb, sb->HCt, nb, 1))) return rc;
+  if (part & ENERGY_PREP) {
+    if ((rc = launch_occupations_coupling(ctx))) return rc;
+    fock_weights_df_kernel<<<ceil_div_u(2LL * m * m, 256), 256, 0, s>>>(ctx->d_A, ctx->d_Bc, m, sb->W);
+    DONOF_LAUNCH_CHECK(ctx);
+    if ((rc = launch_dot64(ctx, m, nb, nb, ctx->d_C, nb, ctx->d_H, nb, sb->HCt, nb, 1))) return rc;
+  }
+  if (!(part & ENERGY_MAIN)) return DONOF_RI_OK;
   if ((rc = launch_s4<S_FOCK>(ctx))) return rc;
   const S4Params& p = sb->plan[S_FOCK];
   reduce_df_kernel<<<ceil_div_u((long long)nb * m, 256), 256, 0, s>>>((const float2*)sb->partial, p.nsplit, nb, m,

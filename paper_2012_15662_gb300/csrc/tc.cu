@@ -45,6 +45,7 @@ int launch_dot64(donof_ri_ctx* ctx, int M, int N, int K, const double* A, int ld
 int launch_energy_rows(donof_ri_ctx* ctx, const double* HCt);
 
 enum TcKind { K_HALF = 0, K_FULLSQ = 1, K_JMO = 2, K_JAO = 3, K_KAO = 4, K_FOCK = 5, K_NKINDS = 6 };
+static_assert(DONOF_RI_GEMM_FOCK - DONOF_RI_GEMM_HALF == K_FOCK, "GEMM profile rows follow the kind order");
 
 constexpr int TC_THREADS = 192;
 constexpr int TC_BM = 128;   // rows per tile (TMEM lanes)
@@ -793,6 +794,7 @@ template <int KIND>
 static int launch_tc(donof_ri_ctx* ctx) {
   const TcPlan& pl = ctx->mixed->plan[KIND];
   if (pl.grid <= 0) return DONOF_RI_OK;
+  ProfScope ps(ctx, DONOF_RI_GEMM_HALF + KIND);
   tc_gemm_kernel<KIND><<<pl.grid, TC_THREADS, pl.smem, ctx->stream>>>(pl.p);
   DONOF_LAUNCH_CHECK(ctx);
   return DONOF_RI_OK;
@@ -855,17 +857,20 @@ int mixed_jk_ao(donof_ri_ctx* ctx) {
   return DONOF_RI_OK;
 }
 
-int mixed_energy(donof_ri_ctx* ctx) {
+int mixed_energy(donof_ri_ctx* ctx, int part) {
   MixedBuffers* mb = ctx->mixed;
   const int m = ctx->n_omega;
+  const int nb = ctx->nbf;
   int rc;
   ProfScope ps(ctx, DONOF_RI_ROW_ENERGY);
-  if ((rc = launch_occupations_coupling(ctx))) return rc;
-  fock_weights_kernel<<<ceil_div_u(2LL * m * m, 256), 256, 0, ctx->stream>>>(ctx->d_A, ctx->d_Bc, m, mb->W);
-  DONOF_LAUNCH_CHECK(ctx);
-  const int nb = ctx->nbf;
-  // (H C)^T[p][mu] = sum_nu C_{nu p} H_{mu nu}
-  if ((rc = launch_dot64(ctx, m, nb, nb, ctx->d_C, nb, ctx->d_H, nb, mb->HCt, nb, 1))) return rc;
+  if (part & ENERGY_PREP) {
+    if ((rc = launch_occupations_coupling(ctx))) return rc;
+    fock_weights_kernel<<<ceil_div_u(2LL * m * m, 256), 256, 0, ctx->stream>>>(ctx->d_A, ctx->d_Bc, m, mb->W);
+    DONOF_LAUNCH_CHECK(ctx);
+    // (H C)^T[p][mu] = sum_nu C_{nu p} H_{mu nu}
+    if ((rc = launch_dot64(ctx, m, nb, nb, ctx->d_C, nb, ctx->d_H, nb, mb->HCt, nb, 1))) return rc;
+  }
+  if (!(part & ENERGY_MAIN)) return DONOF_RI_OK;
   if ((rc = launch_tc<K_FOCK>(ctx))) return rc;
   if ((rc = launch_reduce(ctx, K_FOCK, mb->Yt, 1))) return rc;
   // lambda_qp = sum_mu C_{mu q} Y_{mu p}, column-major lambda[p*nb + q]

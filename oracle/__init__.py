@@ -11,6 +11,8 @@ Modules
 -------
 integrals  closed-form s-type Gaussian integrals (overlap, kinetic, nuclear
            attraction, two-, three- and four-centre Coulomb) via Boys F0.
+modchol    the paper's modified Cholesky of the metric (Bunch-Kaufman LDL^T,
+           Cheng-Higham correction of D's blocks) and the fit it defines.
 ri         metric factorisation, fitted three-index tensor, the half / full
            MO transforms, J_pq / K_pq and the per-orbital AO J^(p) / K^(p)
            (Eq. AOERI and the RI equations of Sec. 2, Tables 2 and 3).

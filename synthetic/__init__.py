@@ -18,5 +18,6 @@ from .systems import (  # noqa: F401
     draw_gamma,
     ring_workload,
     standard_gamma,
+    with_near_duplicate_aux,
     WORKLOADS,
 )

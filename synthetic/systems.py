@@ -271,3 +271,16 @@ def standard_gamma(n_strong: int, n_weak_per: int, n_strong_occ: float = 0.98) -
     w = [np.arccos(np.sqrt(1.0 / (n_weak_per - i))) for i in range(n_weak_per - 1)]
     return np.concatenate([np.full(n_strong, g0), np.tile(np.array(w, dtype=np.float64), n_strong)])
 
+
+
+def with_near_duplicate_aux(system: System, count: int, rel: float) -> System:
+    """A copy of `system` whose first `count` auxiliary functions each get a twin
+    on the same centre with exponent alpha (1 + rel): an auxiliary set that is
+    linearly dependent to about rel, so that its Coulomb metric is numerically
+    singular (the ill-conditioned case the modified factorisation is for)."""
+    import dataclasses
+    idx = np.arange(count)
+    return dataclasses.replace(
+        system, name=f"{system.name}+dup{count}",
+        aux_atom=np.concatenate([system.aux_atom, system.aux_atom[idx]]).astype(np.int32),
+        aux_alpha=np.concatenate([system.aux_alpha, system.aux_alpha[idx] * (1.0 + rel)]))

@@ -385,7 +385,13 @@ def main():
     if gemms:
         dom = max(gemms, key=lambda r: gemms[r][0])
         t_dom, c_dom = gemms[dom]
-        kernel = GEMM_KERNEL[args.precision].format(GEMMS.index(dom))
+        kind = GEMMS.index(dom)
+        kernel = GEMM_KERNEL[args.precision].format(kind)
+        if args.precision == "slice4":
+            # second template argument: every unit a single K chunk (K <= 512)
+            kext = s.naux if dom in ("jao", "kao") else s.nbf
+            one = dom == "fock" or (dom in ("full_k", "jao", "kao") and kext <= 512)
+            kernel = f"s4_gemm_kernel<{kind}, {int(one)}>"
         traffic_key = "gemm_" + dom
     else:
         dom = max((r for r in ROWS if r in flops and rows[r][1] > 0), key=lambda r: rows[r][0])

@@ -121,6 +121,46 @@ typedef struct donof_ri_system {
  */
 int donof_ri_init(const donof_ri_system* sys, int precision, void* stream, donof_ri_ctx** out);
 
+/* Factorisations of the Coulomb metric G (Sec. 2, "Occupancy Optimization with RI"). */
+#define DONOF_RI_METRIC_CHOLESKY 0  /* G = L L^T, B = L^-1 (k|mu nu); E_METRIC_NOT_PD
+                                       below a pivot of 1e-14 max_k G_kk (the default) */
+#define DONOF_RI_METRIC_MODIFIED 1  /* the paper's modified Cholesky: G = P L D L^T P^T
+                                       (Bunch-Kaufman partial pivoting, alpha =
+                                       (1 + sqrt 17)/8, 1x1 and 2x2 blocks in D), every
+                                       eigenvalue of a D block below delta =
+                                       metric_tol * max_k G_kk raised to delta
+                                       (Cheng-Higham) giving D~, and b from
+                                       P L D~^(1/2) b^T = (mu nu|k) with D~^(1/2) the
+                                       symmetric square root of each block.  With a
+                                       positive-definite G and no raised eigenvalue, b
+                                       is the Cholesky fit up to an orthogonal rotation
+                                       of the auxiliary index (every J/K result equal). */
+
+/* Options of donof_ri_init_ex (host memory, read during the call). */
+typedef struct donof_ri_options {
+  int metric;         /* DONOF_RI_METRIC_CHOLESKY or DONOF_RI_METRIC_MODIFIED     */
+  double metric_tol;  /* MODIFIED: relative eigenvalue floor, 0 < metric_tol < 1  */
+} donof_ri_options;
+
+/*
+ * donof_ri_init with options; opt == NULL is donof_ri_init.  The modified
+ * factorisation runs one pivot step per pair of launches (O(naux^3) FP64 work,
+ * once per context) and uses a temporary copy of the three-centre tensor.
+ * After init, donof_ri_fetch(METRIC) returns L (unit lower triangular, in the
+ * pivoted order) in place of the Cholesky factor.
+ * Errors: as donof_ri_init; E_ARG for an unknown metric or a tolerance outside
+ * (0, 1).
+ */
+int donof_ri_init_ex(const donof_ri_system* sys, int precision, void* stream, const donof_ri_options* opt,
+                     donof_ri_ctx** out);
+
+/*
+ * Counts of the metric factorisation of a context (host outputs, any may be
+ * NULL): 2x2 pivot blocks, eigenvalues raised by the correction, symmetric
+ * interchanges.  All zero for the Cholesky factorisation.  Errors: E_ARG.
+ */
+int donof_ri_metric_info(const donof_ri_ctx* ctx, int* n_pivots_2x2, int* n_raised, int* n_interchanges);
+
 /*
  * Transform the fitted tensor to the orbitals C (host or device, [nbf*nbf]
  * column-major FP64).  HALF: b^P_{p nu} and b^P_pp for p < N_Omega (Tables

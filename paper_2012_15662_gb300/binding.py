@@ -39,9 +39,12 @@ DONOF_RI_FETCH_METRIC = 5
 DONOF_RI_FETCH_ENUC = 6
 DONOF_RI_FETCH_OCC = 7
 
+DONOF_RI_METRIC_CHOLESKY = 0
+DONOF_RI_METRIC_MODIFIED = 1
+
 # Names of every entry point declared in include/donof_ri.h.
 EXPORTS = [
-    "donof_ri_init", "donof_ri_transform", "donof_ri_jk_mo", "donof_ri_jk_ao_batch",
+    "donof_ri_init", "donof_ri_init_ex", "donof_ri_metric_info", "donof_ri_transform", "donof_ri_jk_mo", "donof_ri_jk_ao_batch",
     "donof_ri_energy_lagrangian", "donof_ri_fetch", "donof_ri_sync", "donof_ri_destroy",
     "donof_ri_strerror", "donof_ri_launch_count", "donof_ri_profile", "donof_ri_profile_read",
     "donof_ri_iteration", "donof_ri_jmo_noalloc", "donof_ri_optimize_occupations",
@@ -58,6 +61,10 @@ class DonofError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
         super().__init__(f"{where}: {strerror(status)} (status {status})")
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("metric", ctypes.c_int), ("metric_tol", ctypes.c_double)]
 
 
 class System(ctypes.Structure):
@@ -86,6 +93,10 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib = ctypes.CDLL(path)
     vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
     lib.donof_ri_init.argtypes = [ctypes.POINTER(System), i, vp, ctypes.POINTER(vp)]
+    lib.donof_ri_init_ex.argtypes = [ctypes.POINTER(System), i, vp, ctypes.POINTER(Options), ctypes.POINTER(vp)]
+    lib.donof_ri_init_ex.restype = i
+    lib.donof_ri_metric_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
+    lib.donof_ri_metric_info.restype = i
     lib.donof_ri_transform.argtypes = [vp, vp, i]
     lib.donof_ri_jk_mo.argtypes = [vp, vp, vp]
     lib.donof_ri_jk_ao_batch.argtypes = [vp, vp, vp]
@@ -162,8 +173,10 @@ def _check(rc: int, where: str):
         raise DonofError(rc, where)
 
 
-def donof_ri_init(system, subspace, weak_rank, precision: int = DONOF_RI_FP64, stream=None):
-    """Build a context for a system (attributes as in synthetic.System). Returns the handle."""
+def donof_ri_init(system, subspace, weak_rank, precision: int = DONOF_RI_FP64, stream=None, metric=None,
+                  metric_tol: float = 0.0):
+    """Build a context for a system (attributes as in synthetic.System). Returns the handle.
+    metric: None (plain Cholesky, donof_ri_init) or DONOF_RI_METRIC_* (donof_ri_init_ex)."""
     lib = load()
     keep = dict(
         xyz=np.ascontiguousarray(system.atom_xyz, dtype=np.float64),
@@ -181,8 +194,21 @@ def donof_ri_init(system, subspace, weak_rank, precision: int = DONOF_RI_FP64, s
                keep["axa"].ctypes.data, keep["axx"].ctypes.data, keep["sub"].ctypes.data, keep["rank"].ctypes.data)
     ctx = ctypes.c_void_p()
     st = None if stream is None else ctypes.c_void_p(int(stream))
-    _check(lib.donof_ri_init(ctypes.byref(s), int(precision), st, ctypes.byref(ctx)), "donof_ri_init")
+    if metric is None:
+        _check(lib.donof_ri_init(ctypes.byref(s), int(precision), st, ctypes.byref(ctx)), "donof_ri_init")
+    else:
+        opt = Options(int(metric), float(metric_tol))
+        _check(lib.donof_ri_init_ex(ctypes.byref(s), int(precision), st, ctypes.byref(opt), ctypes.byref(ctx)),
+               "donof_ri_init_ex")
     return ctx
+
+
+def donof_ri_metric_info(ctx):
+    """(2x2 pivot blocks, raised eigenvalues, interchanges) of the context's metric factorisation."""
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().donof_ri_metric_info(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+           "donof_ri_metric_info")
+    return a.value, b.value, c.value
 
 
 def donof_ri_transform(ctx, C, mode: int):
@@ -344,14 +370,14 @@ class Mlp:
 class Engine:
     """Convenience wrapper owning one context (host numpy in, host numpy out)."""
 
-    def __init__(self, system, precision: int = DONOF_RI_FP64, stream=None):
+    def __init__(self, system, precision: int = DONOF_RI_FP64, stream=None, metric=None, metric_tol: float = 0.0):
         from synthetic import pairing_columns
         self.system = system
         self.nbf = int(system.bf_alpha.shape[0])
         self.naux = int(system.aux_alpha.shape[0])
         self.n_omega = int(system.n_strong * (1 + system.n_weak_per))
         self.subspace, self.weak_rank = pairing_columns(system.n_strong, system.n_weak_per)
-        self.ctx = donof_ri_init(system, self.subspace, self.weak_rank, precision, stream)
+        self.ctx = donof_ri_init(system, self.subspace, self.weak_rank, precision, stream, metric, metric_tol)
 
     def close(self):
         if self.ctx is not None:

@@ -42,6 +42,28 @@ void prof_end(donof_ri_ctx* ctx, int slot) {
   if (slot < 0) return;
   cudaEventRecord(ctx->prof[slot].b, ctx->stream);
 }
+
+bool fork_begin(donof_ri_ctx* ctx, cudaStream_t* main_stream) {
+  *main_stream = ctx->stream;
+  if (!ctx->side2 || ctx->prof_enabled) return false;
+  if (cudaEventRecord(ctx->ev_fork2, ctx->stream) != cudaSuccess ||
+      cudaStreamWaitEvent(ctx->side2, ctx->ev_fork2, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  ctx->stream = ctx->side2;
+  return true;
+}
+
+void fork_end(donof_ri_ctx* ctx, cudaStream_t main_stream) {
+  ctx->stream = main_stream;
+  cudaEventRecord(ctx->ev_join2, ctx->side2);
+}
+
+int fork_join(donof_ri_ctx* ctx) {
+  DONOF_CUDA_TRY(cudaStreamWaitEvent(ctx->stream, ctx->ev_join2, 0));
+  return DONOF_RI_OK;
+}
 }  // namespace donof
 
 static bool is_device_ptr(const void* p) {
@@ -160,6 +182,9 @@ int donof_ri_destroy(donof_ri_ctx* ctx) {
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   if (ctx->side) cudaStreamDestroy(ctx->side);
+  if (ctx->ev_fork2) cudaEventDestroy(ctx->ev_fork2);
+  if (ctx->ev_join2) cudaEventDestroy(ctx->ev_join2);
+  if (ctx->side2) cudaStreamDestroy(ctx->side2);
   void* bufs[] = {ctx->d_atom_xyz, ctx->d_atom_charge, ctx->d_bf_atom, ctx->d_bf_alpha, ctx->d_aux_atom,
                   ctx->d_aux_alpha, ctx->d_subspace, ctx->d_weak_rank, ctx->d_S, ctx->d_H, ctx->d_G, ctx->d_B,
                   ctx->d_enuc, ctx->d_scratch_max, ctx->d_C, ctx->d_bh, ctx->d_d, ctx->d_bf, ctx->d_J, ctx->d_K,
@@ -172,10 +197,27 @@ int donof_ri_destroy(donof_ri_ctx* ctx) {
 }
 
 int donof_ri_init(const donof_ri_system* sys, int precision, void* stream, donof_ri_ctx** out) {
+  return donof_ri_init_ex(sys, precision, stream, nullptr, out);
+}
+
+int donof_ri_metric_info(const donof_ri_ctx* ctx, int* n_pivots_2x2, int* n_raised, int* n_interchanges) {
+  if (!ctx) return DONOF_RI_E_ARG;
+  if (n_pivots_2x2) *n_pivots_2x2 = ctx->metric_info[0];
+  if (n_raised) *n_raised = ctx->metric_info[1];
+  if (n_interchanges) *n_interchanges = ctx->metric_info[2];
+  return DONOF_RI_OK;
+}
+
+int donof_ri_init_ex(const donof_ri_system* sys, int precision, void* stream, const donof_ri_options* opt,
+                     donof_ri_ctx** out) {
   if (!out) return DONOF_RI_E_ARG;
   *out = nullptr;
   int rc = validate_system(sys);
   if (rc) return rc;
+  const int metric = opt ? opt->metric : DONOF_RI_METRIC_CHOLESKY;
+  const double metric_tol = opt ? opt->metric_tol : 0.0;
+  if (metric != DONOF_RI_METRIC_CHOLESKY && metric != DONOF_RI_METRIC_MODIFIED) return DONOF_RI_E_ARG;
+  if (metric == DONOF_RI_METRIC_MODIFIED && !(metric_tol > 0.0 && metric_tol < 1.0)) return DONOF_RI_E_ARG;
   if (precision != DONOF_RI_FP64 && precision != DONOF_RI_TF32X3 && precision != DONOF_RI_SLICE4) return DONOF_RI_E_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return DONOF_RI_E_UNSUPPORTED; }
@@ -193,6 +235,8 @@ int donof_ri_init(const donof_ri_system* sys, int precision, void* stream, donof
   ctx->n_omega = sys->n_strong * (1 + sys->n_weak_per);
   ctx->precision = precision;
   ctx->stream = (cudaStream_t)stream;
+  ctx->metric_mode = metric;
+  ctx->metric_tol = metric_tol;
   const size_t nb = ctx->nbf, nx = ctx->naux, m = ctx->n_omega, na = ctx->n_atoms;
   const size_t nb2 = nb * nb;
 
@@ -250,14 +294,17 @@ int donof_ri_init(const donof_ri_system* sys, int precision, void* stream, donof
   if (cudaMemsetAsync(ctx->d_status, 0, sizeof(int), s) != cudaSuccess) TRY(DONOF_RI_E_CUDA);
   if (cudaMemsetAsync(ctx->d_lambda, 0, nb2 * sizeof(double), s) != cudaSuccess) TRY(DONOF_RI_E_CUDA);
   TRY(setup_integrals(ctx));
-  TRY(setup_cholesky_and_fit(ctx));
+  TRY(metric == DONOF_RI_METRIC_MODIFIED ? setup_modified_and_fit(ctx, metric_tol) : setup_cholesky_and_fit(ctx));
   TRY(consume_status(ctx));
   if (precision == DONOF_RI_TF32X3) TRY(mixed_init(ctx));
   if (precision == DONOF_RI_SLICE4) TRY(s4_init(ctx));
   if (cudaStreamSynchronize(s) != cudaSuccess) TRY(DONOF_RI_E_CUDA);
   if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess)
+      cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ctx->side2, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_fork2, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_join2, cudaEventDisableTiming) != cudaSuccess)
     TRY(DONOF_RI_E_CUDA);
 #undef TRY
   *out = ctx;

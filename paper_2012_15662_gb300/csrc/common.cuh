@@ -85,6 +85,11 @@ struct donof_ri_ctx {
   float* d_feat;    // [N_I][3 + 4 N_g] learned-guess features
   double* d_rot;    // [4 nbf^2 + 2] rotation-step scratch (allocated on first use)
   int* d_status;    // [1] device-side status (DeviceStatus)
+  // metric factorisation (DONOF_RI_METRIC_*) and, for the modified one, its
+  // tolerance and counts: 2x2 pivots, raised eigenvalues, interchanges
+  int metric_mode;
+  double metric_tol;
+  int metric_info[3];
 
   donof::MixedBuffers* mixed;
   donof::S4Buffers* s4;
@@ -101,6 +106,10 @@ struct donof_ri_ctx {
   // prologue of the energy row runs there, concurrently with the transforms.
   cudaStream_t side;
   cudaEvent_t ev_fork, ev_join;
+  // Second side stream: independent launch groups inside one call (e.g. J_pq
+  // beside the full transform), forked and joined within that call.
+  cudaStream_t side2;
+  cudaEvent_t ev_fork2, ev_join2;
 
   // CUDA graph of donof_ri_iteration (see the header)
   int capturing;
@@ -111,6 +120,16 @@ struct donof_ri_ctx {
 };
 
 namespace donof {
+
+// ---- fork / join of a launch group onto ctx->side2 (api.cu) ----
+// fork_begin: when a second stream exists and per-row profiling is off, makes
+// side2 wait for the work issued so far and points ctx->stream at it (returns
+// true).  fork_end: points ctx->stream back and records side2's completion;
+// fork_join makes the main stream wait for it.  Row events are recorded on the
+// main stream, so nothing is forked while profiling.
+bool fork_begin(donof_ri_ctx* ctx, cudaStream_t* main_stream);
+void fork_end(donof_ri_ctx* ctx, cudaStream_t main_stream);
+int fork_join(donof_ri_ctx* ctx);
 
 // ---- profiling scope (api.cu): records an event pair around a launch group ----
 void prof_begin(donof_ri_ctx* ctx, int row, int* slot);
@@ -126,6 +145,10 @@ struct ProfScope {
 int launch_dgemm(donof_ri_ctx* ctx, const Gemm64& g);
 int setup_integrals(donof_ri_ctx* ctx);
 int setup_cholesky_and_fit(donof_ri_ctx* ctx);
+int fit_forward(donof_ri_ctx* ctx);
+void max_diag_public(donof_ri_ctx* ctx, const double* G, double* out);
+// modchol.cu: G = P L D L^T P^T with the Cheng-Higham correction, B from it
+int setup_modified_and_fit(donof_ri_ctx* ctx, double tol);
 
 // ---- FP64 hot path (path64.cu) ----
 int path64_transform(donof_ri_ctx* ctx, int mode);

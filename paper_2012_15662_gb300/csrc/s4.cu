@@ -157,6 +157,24 @@ __device__ __forceinline__ void df_add(float& sh, float& sl, float ph, float pl)
   sl = e - (sh - s);
 }
 
+// 2^k as an FP32 value for k in [-126, 127] (k is clamped to that range).
+__device__ __forceinline__ float exp2_int(int k) {
+  k = k < -126 ? -126 : (k > 127 ? 127 : k);
+  return __int_as_float((k + 127) << 23);
+}
+
+// (h, l) *= 2^k: one multiplication each while 2^k is a normal float, ldexpf beyond.
+__device__ __forceinline__ void df_scale(float& h, float& l, int k) {
+  if (k >= -126 && k <= 127) {
+    const float sc = exp2_int(k);
+    h *= sc;
+    l *= sc;
+  } else {
+    h = ldexpf(h, k);
+    l = ldexpf(l, k);
+  }
+}
+
 // int64 * 2^k as a double-float pair, built from 32-bit pieces only (|v| < 2^55):
 // v = a 2^32 + b1 2^16 + b0 with every piece exact in FP32, summed with TwoSum.
 __device__ __forceinline__ void ll_to_df(long long v, int k, float& h, float& l) {
@@ -168,16 +186,28 @@ __device__ __forceinline__ void ll_to_df(long long v, int k, float& h, float& l)
   float s2, e2;
   two_sum_f(s, f0, s2, e2);
   const float t = e + e2;
-  const float hh = s2 + t;
-  const float ll = t - (hh - s2);
-  h = ldexpf(hh, k);
-  l = ldexpf(ll, k);
+  h = s2 + t;
+  l = t - (h - s2);
+  df_scale(h, l, k);
 }
 
-// 2^k as an FP32 value for k in [-126, 127] (k is clamped to that range).
-__device__ __forceinline__ float exp2_int(int k) {
-  k = k < -126 ? -126 : (k > 127 ? 127 : k);
-  return __int_as_float((k + 127) << 23);
+// Double-float value of one chunk's five group sums, sum_g G_g 2^(32 - 8g + k),
+// without the int64 fold: every term G_g 2^(-8g) is exact in FP32 (a power-of-two
+// scaling), a TwoSum chain adds them with the rounding errors collected in e, and
+// the pair is scaled by 2^(32 + k) at the end.  Relative error about 2^-48, the same
+// order as the int64 fold followed by its conversion.
+__device__ __forceinline__ void groups_to_df(const uint32_t* G, int k, float& h, float& l) {
+  float sum = __uint_as_float(G[0]), e = 0.f;
+#pragma unroll
+  for (int g = 1; g < S4_NG; ++g) {
+    float t, err;
+    two_sum_f(sum, __uint_as_float(G[g]) * exp2_int(-8 * g), t, err);
+    sum = t;
+    e += err;
+  }
+  h = sum + e;
+  l = e - (h - sum);
+  df_scale(h, l, 32 + k);
 }
 
 // Output integer of the half transform from one chunk's group sums:
@@ -235,9 +265,12 @@ __device__ __forceinline__ void s4_loads(const S4Params& p, uint8_t* st, uint64_
       const int nvb = (p.nb + 15) / 16;
       tma_load_4d(da, &p.a, bar, k0, t, (mt % nvb) * 16, (mt / nvb) * 8);
       tma_load_3d(db, &p.b, bar, k0, t, n0);
-    } else if (KIND == S_FULLSQ || KIND == S_FOCK) {
+    } else if (KIND == S_FULLSQ) {
       tma_load_4d(da, &p.a, bar, k0, t, mt * S4_BM, batch);
       tma_load_3d(db, &p.b, bar, k0, t, n0);
+    } else if (KIND == S_FOCK) {
+      tma_load_3d(da, &p.a, bar, k0, t, mt * S4_BM);
+      tma_load_4d(db, &p.b, bar, k0, t, n0, batch);
     } else if (KIND == S_JMO || KIND == S_JAO) {
       tma_load_3d(da, &p.a, bar, k0, t, mt * S4_BM);
       tma_load_3d(db, &p.b, bar, k0, t, n0);
@@ -248,8 +281,11 @@ __device__ __forceinline__ void s4_loads(const S4Params& p, uint8_t* st, uint64_
   }
 }
 
-template <int KIND>
+template <int KIND, int ONE>
 __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_gemm_kernel(const __grid_constant__ S4Params p) {
+  // ONE: every unit is a single K chunk (K <= 512, and always for F^(p) C_p), so the
+  // epilogue converts group sums straight to double-float pairs and carries no int64
+  // running sums; chosen at launch from the problem's K extent.
   constexpr int BN = S4Cfg<KIND>::BN;
   constexpr int NWG = S4Cfg<KIND>::NWG, CW = S4Cfg<KIND>::CW;
   constexpr int NCBT = BN / CW / NWG;  // column blocks per epilogue thread
@@ -435,17 +471,14 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_ge
         __syncwarp();
         constexpr int NLB = (BN + 31) / 32;
         int rb[NLB];
-        float2 rw[KIND == S_FOCK ? NLB : 1];
 #pragma unroll
         for (int k = 0; k < NLB; ++k) {
           const int i = lane + 32 * k, col = nt * BN + i;
           rb[k] = 0;
           if (i < BN) {
-            if (KIND == S_KAO) rb[k] = col < p.nb ? p.eb[(size_t)batch * p.nb + col] : 0;
+            if (KIND == S_KAO || KIND == S_FOCK) rb[k] = col < p.nb ? p.eb[(size_t)batch * p.nb + col] : 0;
             else rb[k] = col < p.m ? p.eb[col] : 0;
           }
-          if (KIND == S_FOCK)
-            rw[KIND == S_FOCK ? k : 0] = (i < BN && col < p.m) ? p.w[(size_t)batch * p.m + col] : make_float2(0.f, 0.f);
         }
         if (KIND == S_HALF) {
           const int nvb = (p.nb + 15) / 16;
@@ -473,10 +506,7 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_ge
 #pragma unroll
         for (int k = 0; k < NLB; ++k) {
           const int i = lane + 32 * k;
-          if (i < BN) {
-            es_b[i] = rb[k];
-            if (KIND == S_FOCK) es_w[i] = rw[KIND == S_FOCK ? k : 0];
-          }
+          if (i < BN) es_b[i] = rb[k];
         }
         __syncwarp();
       }
@@ -502,10 +532,18 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_ge
         mu = r / p.nb;
         nu = r % p.nb;
         ea = rvalid ? p.ea[r] : 0;
-      } else if (KIND == S_KAO || KIND == S_FOCK) {
+      } else if (KIND == S_KAO) {
         mu = mt * S4_BM + row;
         rvalid = mu < p.nb;
         ea = rvalid ? p.ea[(size_t)batch * p.nb + mu] : 0;
+      }
+      // FOCK: the row is orbital p (C^T digits), the unit's weight W[batch][p] is per row
+      float2 wrow = make_float2(0.f, 0.f);
+      if (KIND == S_FOCK) {
+        mu = mt * S4_BM + row;
+        rvalid = mu < p.m;
+        ea = rvalid ? p.ea[mu] : 0;
+        wrow = rvalid ? p.w[(size_t)batch * p.m + mu] : wrow;
       }
       const int nch = (nkb + S4_CHUNK_KB - 1) / S4_CHUNK_KB;
       for (int ch = 0; ch < nch; ++ch) {
@@ -551,40 +589,72 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_ge
             }
             continue;
           }
-          long long v[CW];
+          if (KIND == S_HALF || KIND == S_JMO) {
+            // int64 fold: running sums over K chunks (J_pq's partials stay integers)
+            long long v[CW];
 #pragma unroll
-          for (int j = 0; j < CW; ++j) v[j] = (KIND != S_FOCK && (ch > 0 || KIND == S_JMO)) ? acc[NACC == 1 ? 0 : cb * CW + j] : 0;
+            for (int j = 0; j < CW; ++j) v[j] = (ch > 0 || KIND == S_JMO) ? acc[NACC == 1 ? 0 : cb * CW + j] : 0;
 #pragma unroll
-          for (int g = 0; g < S4_NG; ++g) {
+            for (int g = 0; g < S4_NG; ++g) {
 #pragma unroll
-            for (int j = 0; j < CW; ++j) v[j] += (long long)__float2int_rn(__uint_as_float(gr[g][j])) << (32 - 8 * g);
-          }
-          if (KIND != S_FOCK && (!last || KIND == S_JMO)) {
+              for (int j = 0; j < CW; ++j) v[j] += (long long)__float2int_rn(__uint_as_float(gr[g][j])) << (32 - 8 * g);
+            }
+            if (!last || KIND == S_JMO) {
 #pragma unroll
-            for (int j = 0; j < CW; ++j) acc[NACC == 1 ? 0 : cb * CW + j] = v[j];
+              for (int j = 0; j < CW; ++j) acc[NACC == 1 ? 0 : cb * CW + j] = v[j];
+              continue;
+            }
+            if (!rvalid) continue;
+            if (KIND == S_HALF) {
+              const int lrow = lane / 16, l16 = lane % 16;
+              int* basef = p.x6 + (size_t)P * p.m * p.nbp + nu;
+#pragma unroll
+              for (int j = 0; j < CW; ++j) {
+                const int i = c * CW + j;
+                const int col = nt * BN + i;
+                if (col < p.m) {
+                  const int emin = min(es_3[lrow * BN + i], es_6[i * 16 + l16]);
+                  basef[(size_t)col * p.nbp] = round_shift(v[j], ea + es_b[i] - 15 - emin);
+                }
+              }
+            }
             continue;
+          }
+          // The value of every output of the block as a double-float pair (h, l).  A
+          // single-chunk unit converts its five group sums directly (groups_to_df); a
+          // multi-chunk one keeps exact int64 running sums until its last chunk.
+          float hv[CW], lv[CW];
+          if (ONE) {
+#pragma unroll
+            for (int j = 0; j < CW; ++j) {
+              const uint32_t G[S4_NG] = {gr[0][j], gr[1][j], gr[2][j], gr[3][j], gr[4][j]};
+              groups_to_df(G, ea + es_b[c * CW + j] - S4_SHIFT, hv[j], lv[j]);
+            }
+          } else {
+            long long v[CW];
+#pragma unroll
+            for (int j = 0; j < CW; ++j) v[j] = ch > 0 ? acc[NACC == 1 ? 0 : cb * CW + j] : 0;
+#pragma unroll
+            for (int g = 0; g < S4_NG; ++g) {
+#pragma unroll
+              for (int j = 0; j < CW; ++j) v[j] += (long long)__float2int_rn(__uint_as_float(gr[g][j])) << (32 - 8 * g);
+            }
+            if (!last) {
+#pragma unroll
+              for (int j = 0; j < CW; ++j) acc[NACC == 1 ? 0 : cb * CW + j] = v[j];
+              continue;
+            }
+#pragma unroll
+            for (int j = 0; j < CW; ++j) ll_to_df(v[j], ea + es_b[c * CW + j] - S4_SHIFT, hv[j], lv[j]);
           }
           // ---- the block's values are final: unit action ----
           if (!rvalid) continue;
-          if (KIND == S_HALF) {
-            const int lrow = lane / 16, l16 = lane % 16;
-            int* basef = p.x6 + (size_t)P * p.m * p.nbp + nu;
-#pragma unroll
-            for (int j = 0; j < CW; ++j) {
-              const int i = c * CW + j;
-              const int col = nt * BN + i;
-              if (col < p.m) {
-                const int emin = min(es_3[lrow * BN + i], es_6[i * 16 + l16]);
-                basef[(size_t)col * p.nbp] = round_shift(v[j], ea + es_b[i] - 15 - emin);
-              }
-            }
-          } else if (KIND == S_FULLSQ) {
+          if (KIND == S_FULLSQ) {
 #pragma unroll
             for (int j = 0; j < CW; ++j) {
               const int i = c * CW + j;
               if (nt * BN + i < p.m) {
-                float xh, xl;
-                ll_to_df(v[j], ea + es_b[i] - S4_SHIFT, xh, xl);
+                const float xh = hv[j], xl = lv[j];
                 const float ph = xh * xh;
                 const float pl = fmaf(xh, xh, -ph) + 2.f * xh * xl;
                 df_add(sh[SUM_DF ? cb * CW + j : 0], sl[SUM_DF ? cb * CW + j : 0], ph, pl);
@@ -594,10 +664,9 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_ge
 #pragma unroll
             for (int j = 0; j < CW; ++j) {
               const int i = c * CW + j;
-              if (nt * BN + i < p.m) {
-                float xh, xl;
-                ll_to_df(v[j], ea + es_b[i] - S4_SHIFT, xh, xl);
-                const float2 wv = es_w[i];
+              if (nt * BN + i < p.nb) {
+                const float xh = hv[j], xl = lv[j];
+                const float2 wv = wrow;
                 const float ph = xh * wv.x;
                 const float pl = fmaf(xh, wv.x, -ph) + (xh * wv.y + xl * wv.x);
                 df_add(sh[SUM_DF ? cb * CW + j : 0], sl[SUM_DF ? cb * CW + j : 0], ph, pl);
@@ -609,35 +678,30 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_ge
               const int i = c * CW + j;
               const int col = nt * BN + i;
               if (col < p.m) {
-                float h, l;
-                ll_to_df(v[j], ea + es_b[i] - S4_SHIFT, h, l);
                 const size_t o = ((size_t)col * p.nb + mu) * p.ldo + nu;
-                p.ohi[o] = h;
-                p.olo[o] = l;
+                p.ohi[o] = hv[j];
+                p.olo[o] = lv[j];
               }
             }
           } else if (KIND == S_KAO) {
             // A thread's CW = 8 consecutive columns of one output row are one 32-byte
             // sector of hi and one of lo (ldo is a multiple of 8): two 16-byte vector
             // stores each instead of eight scattered 4-byte ones.
-            float h[CW], l[CW];
-#pragma unroll
-            for (int j = 0; j < CW; ++j) ll_to_df(v[j], ea + es_b[c * CW + j] - S4_SHIFT, h[j], l[j]);
             const int col0 = nt * BN + c * CW;
             const size_t o = ((size_t)(p.m + batch) * p.nb + mu) * p.ldo + col0;
             if (CW == 8 && col0 + CW <= p.nb) {
               float4* dh = (float4*)(p.ohi + o);
               float4* dl = (float4*)(p.olo + o);
-              dh[0] = make_float4(h[0], h[1], h[2], h[3]);
-              dh[1] = make_float4(h[4], h[5], h[6], h[7]);
-              dl[0] = make_float4(l[0], l[1], l[2], l[3]);
-              dl[1] = make_float4(l[4], l[5], l[6], l[7]);
+              dh[0] = make_float4(hv[0], hv[1], hv[2], hv[3]);
+              dh[1] = make_float4(hv[4], hv[5], hv[6], hv[7]);
+              dl[0] = make_float4(lv[0], lv[1], lv[2], lv[3]);
+              dl[1] = make_float4(lv[4], lv[5], lv[6], lv[7]);
             } else {
 #pragma unroll
               for (int j = 0; j < CW; ++j) {
                 if (col0 + j < p.nb) {
-                  p.ohi[o + j] = h[j];
-                  p.olo[o + j] = l[j];
+                  p.ohi[o + j] = hv[j];
+                  p.olo[o + j] = lv[j];
                 }
               }
             }
@@ -797,7 +861,8 @@ __global__ void reduce_jmo_kernel(const long long* partial, int nsplit, int m, c
   J[i] = ldexp((double)s, ed[i / m] + ed[i % m] - S4_SHIFT);
 }
 
-// sum over splits of double-float partials, FP64.  mode 1: Y^T with n_c HCt added.
+// sum over splits of double-float partials, FP64.  mode 1: the [rows = p][cols = mu]
+// partials of F^(p) C_p, written as Y^T [p][mu] with n_p (H C)^T added.
 __global__ void reduce_df_kernel(const float2* partial, int nsplit, int rows, int cols, double* out, int mode,
                                  const double* n, const double* HCt) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -809,8 +874,7 @@ __global__ void reduce_df_kernel(const float2* partial, int nsplit, int rows, in
     s += (double)v.x + (double)v.y;
   }
   if (mode == 1) {
-    int r = (int)(i / cols), c = (int)(i % cols);
-    out[(size_t)c * rows + r] = n[c] * HCt[(size_t)c * rows + r] + s;
+    out[i] = n[i / cols] * HCt[i] + s;
   } else {
     out[i] = s;
   }
@@ -1025,6 +1089,7 @@ struct donof::S4Buffers {
   double* HCt;
   double* Yt;
   void* partial;
+  void* partial_j;  // J_pq's int64 partials (its launch group may run beside a3's)
   donof::S4Params plan[donof::S_NKINDS];
   int grid[donof::S_NKINDS];
   size_t smem[donof::S_NKINDS];
@@ -1134,16 +1199,15 @@ int s4_init(donof_ri_ctx* ctx) {
     for (int nt = 0; nt < (nb + bn - 1) / bn; ++nt)
       if (nt * bn + bn - 1 >= mt * S4_BM) kao_tiles.push_back((mt << 16) | nt);
   s4_plan<S_KAO>(sb, 1, (int)kao_tiles.size(), m, S4Cfg<S_KAO>::CTAS * sms, S4Cfg<S_KAO>::CTAS * sms);
-  s4_plan<S_FOCK>(sb, (nb + S4_BM - 1) / S4_BM, (m + bn - 1) / bn, 2 * m * ((KBb + S4_CHUNK_KB - 1) / S4_CHUNK_KB), sms);
+  s4_plan<S_FOCK>(sb, (m + S4_BM - 1) / S4_BM, (nb + bn - 1) / bn, 2 * m * ((KBb + S4_CHUNK_KB - 1) / S4_CHUNK_KB), sms);
   for (int k = 0; k < S_NKINDS; ++k) sb->max_stages[k] = sb->plan[k].stages;
   sb->target[S_FULLSQ] = S4Cfg<S_FULLSQ>::CTAS * sms;
   sb->target[S_JMO] = S4Cfg<S_JMO>::CTAS * sms;
   sb->target[S_FOCK] = sms;
   // partial sums sized for twice the default split count (the autotuner may pick it)
   size_t pbytes = 2 * (size_t)sb->plan[S_FULLSQ].nsplit * m * m * sizeof(float2);
-  size_t t = 2 * (size_t)sb->plan[S_JMO].nsplit * m * m * sizeof(long long);
-  if (t > pbytes) pbytes = t;
-  t = 2 * (size_t)sb->plan[S_FOCK].nsplit * nb * m * sizeof(float2);
+  const size_t jbytes = 2 * (size_t)sb->plan[S_JMO].nsplit * m * m * sizeof(long long);
+  size_t t = 2 * (size_t)sb->plan[S_FOCK].nsplit * nb * m * sizeof(float2);
   if (t > pbytes) pbytes = t;
 
 #define ALLOC(ptr, bytes)                                             \
@@ -1193,6 +1257,7 @@ int s4_init(donof_ri_ctx* ctx) {
   ALLOC(sb->HCt, ms * nbs * 8);
   ALLOC(sb->Yt, ms * nbs * 8);
   ALLOC(sb->partial, pbytes);
+  ALLOC(sb->partial_j, jbytes);
 #undef ALLOC
 
   // one-time digitisation of B in both operand layouts, and its maxima for the bounds
@@ -1217,7 +1282,7 @@ int s4_init(donof_ri_ctx* ctx) {
     S4Params& p = sb->plan[k];
     p.nb = nb; p.nx = nx; p.m = m; p.nbp = nbp; p.nxp = nxp; p.mp = mp;
     p.status = ctx->d_status;
-    p.partial = sb->partial;
+    p.partial = k == S_JMO ? sb->partial_j : sb->partial;
     p.ldo = ldo;
   }
   {  // HALF: A = B1 [nx][nb][4][nbp] rows (P, nu) over mu; B = C^T digits [m][4][nbp]
@@ -1276,25 +1341,28 @@ int s4_init(donof_ri_ctx* ctx) {
     p.ohi = sb->JKhi; p.olo = sb->JKlo;
     p.tmap = sb->kao_tmap;
   }
-  {  // FOCK: A = JK digits [2m][nb][4][nbp] rows mu (per q') over nu; B = C^T digits
+  {  // FOCK: A = C^T digits [m][4][nbp] rows p over nu; B = JK digits [2m][nb][4][nbp]
+     // rows mu (per q') over nu.  Orbitals on the rows: N_Omega <= N_b fills the
+     // 128-row tiles at least as well as mu would, and the weight W[q'][p] is per row.
     S4Params& p = sb->plan[S_FOCK];
-    long long dA[4] = {nb, 4, nb, 2 * ms}, sA[3] = {nbp, 4LL * nbp, nbs * 4 * nbp};
-    int bA[4] = {S4_BK, 1, S4_BM, 1};
-    long long dB[3] = {nb, 4, m}, sB[2] = {nbp, 4LL * nbp};
-    int bB[3] = {S4_BK, 1, bn};
-    if ((rc = s4_map(sb, &p.a, sb->JKp, 4, dA, sA, bA))) return rc;
-    if ((rc = s4_map(sb, &p.b, sb->Ct, 3, dB, sB, bB))) return rc;
-    p.ea = sb->eJK; p.eb = sb->eC;
+    long long dA[3] = {nb, 4, m}, sA[2] = {nbp, 4LL * nbp};
+    int bA[3] = {S4_BK, 1, S4_BM};
+    long long dB[4] = {nb, 4, nb, 2 * ms}, sB[3] = {nbp, 4LL * nbp, nbs * 4 * nbp};
+    int bB[4] = {S4_BK, 1, bn, 1};
+    if ((rc = s4_map(sb, &p.a, sb->Ct, 3, dA, sA, bA))) return rc;
+    if ((rc = s4_map(sb, &p.b, sb->JKp, 4, dB, sB, bB))) return rc;
+    p.ea = sb->eC; p.eb = sb->eJK;
     p.w = sb->W;
-    p.prow = nb; p.pcol = m;
+    p.prow = m; p.pcol = nb;
   }
-#define OPTIN(KIND)                                                                                           \
-  if (cudaFuncSetAttribute(s4_gemm_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,                \
+#define OPTIN(KIND, ONE)                                                                                      \
+  if (cudaFuncSetAttribute(s4_gemm_kernel<KIND, ONE>, cudaFuncAttributeMaxDynamicSharedMemorySize,           \
                            (int)sb->smem[KIND]) != cudaSuccess ||                                             \
-      cudaFuncSetAttribute(s4_gemm_kernel<KIND>, cudaFuncAttributePreferredSharedMemoryCarveout,             \
+      cudaFuncSetAttribute(s4_gemm_kernel<KIND, ONE>, cudaFuncAttributePreferredSharedMemoryCarveout,        \
                            (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)                               \
     return DONOF_RI_E_CUDA;
-  OPTIN(S_HALF) OPTIN(S_FULLSQ) OPTIN(S_JMO) OPTIN(S_JAO) OPTIN(S_KAO) OPTIN(S_FOCK)
+  OPTIN(S_HALF, 0) OPTIN(S_FULLSQ, 0) OPTIN(S_FULLSQ, 1) OPTIN(S_JMO, 0) OPTIN(S_JAO, 0) OPTIN(S_JAO, 1)
+  OPTIN(S_KAO, 0) OPTIN(S_KAO, 1) OPTIN(S_FOCK, 1)
 #undef OPTIN
   return DONOF_RI_OK;
 }
@@ -1304,7 +1372,7 @@ void s4_free(donof_ri_ctx* ctx) {
   if (!sb) return;
   void* bufs[] = {sb->jao_tmap_full, sb->jao_tmap, sb->kao_tmap, sb->X6,    sb->B1,   sb->B5,   sb->Ct,   sb->L3,   sb->L6, sb->Dp,  sb->JKp,  sb->eB1,   sb->eB5,
                   sb->eC,    sb->e3,   sb->e6,   sb->ed,   sb->eJK, sb->rmaxB, sb->maxB, sb->absC, sb->absCt,
-                  sb->Cdf,   sb->dpart, sb->dmat, sb->JKhi, sb->JKlo, sb->W,  sb->HCt, sb->Yt,   sb->partial};
+                  sb->Cdf,   sb->dpart, sb->dmat, sb->JKhi, sb->JKlo, sb->W,  sb->HCt, sb->Yt,   sb->partial, sb->partial_j};
   for (void* b : bufs)
     if (b) cudaFree(b);
   free(sb);
@@ -1316,7 +1384,21 @@ static int launch_s4(donof_ri_ctx* ctx) {
   S4Buffers* sb = ctx->s4;
   if (sb->grid[KIND] <= 0) return DONOF_RI_OK;
   ProfScope ps(ctx, DONOF_RI_GEMM_HALF + KIND);
-  s4_gemm_kernel<KIND><<<sb->grid[KIND], S4Cfg<KIND>::THREADS, sb->smem[KIND], ctx->stream>>>(sb->plan[KIND]);
+  // single-chunk epilogue where every unit's K fits one chunk (F^(p) C_p: always)
+  const int kext = (KIND == S_JAO || KIND == S_KAO) ? ctx->naux : ctx->nbf;
+  const bool one = KIND == S_FOCK || ((KIND == S_FULLSQ || KIND == S_JAO || KIND == S_KAO) &&
+                                      kext <= S4_CHUNK_KB * S4_BK);
+  if constexpr (KIND == S_FOCK) {
+    s4_gemm_kernel<KIND, 1><<<sb->grid[KIND], S4Cfg<KIND>::THREADS, sb->smem[KIND], ctx->stream>>>(sb->plan[KIND]);
+  } else if constexpr (KIND == S_FULLSQ || KIND == S_JAO || KIND == S_KAO) {
+    if (one)
+      s4_gemm_kernel<KIND, 1><<<sb->grid[KIND], S4Cfg<KIND>::THREADS, sb->smem[KIND], ctx->stream>>>(sb->plan[KIND]);
+    else
+      s4_gemm_kernel<KIND, 0><<<sb->grid[KIND], S4Cfg<KIND>::THREADS, sb->smem[KIND], ctx->stream>>>(sb->plan[KIND]);
+  } else {
+    (void)one;
+    s4_gemm_kernel<KIND, 0><<<sb->grid[KIND], S4Cfg<KIND>::THREADS, sb->smem[KIND], ctx->stream>>>(sb->plan[KIND]);
+  }
   DONOF_LAUNCH_CHECK(ctx);
   return DONOF_RI_OK;
 }
@@ -1332,10 +1414,17 @@ int s4_transform(donof_ri_ctx* ctx, int mode) {
     slice_f64_kernel<<<ceil_div_u((long long)m * 32, 256), 256, 0, s>>>(ctx->d_C, m, nb, nb, 1, sb->Ct, sb->nbp,
                                                                           sb->eC, sb->absC, sb->absCt, sb->Cdf);
     DONOF_LAUNCH_CHECK(ctx);
+    // the two bound passes are independent: e6 on the second stream
+    cudaStream_t main_stream;
+    const bool forked = fork_begin(ctx, &main_stream);
+    bound6_kernel<<<m, 128, nb * sizeof(float), ctx->stream>>>(sb->maxB, sb->absC, nb, m, sb->e6);
+    rc = cudaGetLastError() == cudaSuccess ? DONOF_RI_OK : DONOF_RI_E_CUDA;
+    ctx->launches++;
+    if (forked) fork_end(ctx, main_stream);
     bound3_kernel<<<nx, 128, nb * sizeof(float), s>>>(sb->rmaxB, sb->absCt, nx, nb, m, sb->e3);
     DONOF_LAUNCH_CHECK(ctx);
-    bound6_kernel<<<m, 128, nb * sizeof(float), s>>>(sb->maxB, sb->absC, nb, m, sb->e6);
-    DONOF_LAUNCH_CHECK(ctx);
+    if (forked && (rc = fork_join(ctx))) return rc;
+    if (rc) return rc;
   }
   {
     ProfScope ps(ctx, DONOF_RI_ROW_HALF);
@@ -1355,22 +1444,34 @@ int s4_transform(donof_ri_ctx* ctx, int mode) {
     DONOF_LAUNCH_CHECK(ctx);
   }
   if (mode == DONOF_RI_FULL) {
+    // J_pq (a few CTAs, its own partial buffer) runs on the second stream beside the
+    // full transform, on the SMs the latter leaves free; the shared-memory footprint
+    // of both kinds keeps their CTAs off each other's SMs.
+    cudaStream_t main_stream;
+    const bool forked = fork_begin(ctx, &main_stream);
+    int rcj;
+    {
+      ProfScope ps(ctx, DONOF_RI_ROW_J);
+      rcj = launch_s4<S_JMO>(ctx);
+      if (!rcj) {
+        const S4Params& p = sb->plan[S_JMO];
+        reduce_jmo_kernel<<<ceil_div_u((long long)m * m, 256), 256, 0, ctx->stream>>>(
+            (const long long*)p.partial, p.nsplit, m, sb->ed, ctx->d_J);
+        rcj = cudaGetLastError() == cudaSuccess ? DONOF_RI_OK : DONOF_RI_E_CUDA;
+        ctx->launches++;
+      }
+    }
+    if (forked) fork_end(ctx, main_stream);
     {
       ProfScope ps(ctx, DONOF_RI_ROW_FULL_K);
       if ((rc = launch_s4<S_FULLSQ>(ctx))) return rc;
       const S4Params& p = sb->plan[S_FULLSQ];
-      reduce_df_kernel<<<ceil_div_u((long long)m * m, 256), 256, 0, s>>>((const float2*)sb->partial, p.nsplit, m, m,
+      reduce_df_kernel<<<ceil_div_u((long long)m * m, 256), 256, 0, s>>>((const float2*)p.partial, p.nsplit, m, m,
                                                                           ctx->d_K, 0, nullptr, nullptr);
       DONOF_LAUNCH_CHECK(ctx);
     }
-    {
-      ProfScope ps(ctx, DONOF_RI_ROW_J);
-      if ((rc = launch_s4<S_JMO>(ctx))) return rc;
-      const S4Params& p = sb->plan[S_JMO];
-      reduce_jmo_kernel<<<ceil_div_u((long long)m * m, 256), 256, 0, s>>>((const long long*)sb->partial, p.nsplit, m,
-                                                                           sb->ed, ctx->d_J);
-      DONOF_LAUNCH_CHECK(ctx);
-    }
+    if (forked && (rc = fork_join(ctx))) return rc;
+    if (rcj) return rcj;
   }
   return DONOF_RI_OK;
 }
@@ -1420,7 +1521,7 @@ int s4_energy(donof_ri_ctx* ctx, int part) {
   if (!(part & ENERGY_MAIN)) return DONOF_RI_OK;
   if ((rc = launch_s4<S_FOCK>(ctx))) return rc;
   const S4Params& p = sb->plan[S_FOCK];
-  reduce_df_kernel<<<ceil_div_u((long long)nb * m, 256), 256, 0, s>>>((const float2*)sb->partial, p.nsplit, nb, m,
+  reduce_df_kernel<<<ceil_div_u((long long)nb * m, 256), 256, 0, s>>>((const float2*)p.partial, p.nsplit, m, nb,
                                                                        sb->Yt, 1, ctx->d_n, sb->HCt);
   DONOF_LAUNCH_CHECK(ctx);
   if ((rc = launch_dot64(ctx, m, nb, nb, sb->Yt, nb, ctx->d_C, nb, ctx->d_lambda, nb, 1))) return rc;

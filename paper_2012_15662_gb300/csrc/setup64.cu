@@ -329,7 +329,20 @@ int setup_cholesky_and_fit(donof_ri_ctx* ctx) {
   }
   zero_upper_kernel<<<ceil_div_u((long long)nx * nx, 256), 256, 0, ctx->stream>>>(nx, G);
   DONOF_LAUNCH_CHECK(ctx);
-  // Forward substitution over row blocks of B (initially (k|mu nu)).
+  return fit_forward(ctx);
+}
+
+void max_diag_public(donof_ri_ctx* ctx, const double* G, double* out) {
+  max_diag_kernel<<<1, 256, 0, ctx->stream>>>(ctx->naux, G, out);
+  ctx->launches++;
+}
+
+// B <- L^-1 B for the lower-triangular L in ctx->d_G (row-major, zero upper
+// triangle): forward substitution over row blocks of B.
+int fit_forward(donof_ri_ctx* ctx) {
+  const int nx = ctx->naux;
+  const long long nb2 = (long long)ctx->nbf * ctx->nbf;
+  const double* G = ctx->d_G;
   double* R = ctx->d_B;
   for (int i0 = 0; i0 < nx; i0 += CH_NB) {
     int nbk = nx - i0 < CH_NB ? nx - i0 : CH_NB;

@@ -390,7 +390,7 @@ def main():
         if args.precision == "slice4":
             # second template argument: every unit a single K chunk (K <= 512)
             kext = s.naux if dom in ("jao", "kao") else s.nbf
-            one = dom == "fock" or (dom in ("full_k", "jao", "kao") and kext <= 512)
+            one = dom == "fock" or (dom in ("half", "full_k", "jao", "kao") and kext <= 512)
             kernel = f"s4_gemm_kernel<{kind}, {int(one)}>"
         traffic_key = "gemm_" + dom
     else:

@@ -316,20 +316,34 @@ int donof_ri_optimize_occupations(donof_ri_ctx* ctx, double* gamma, int max_iter
  * Tile-schedule autotuner of the SLICE4 engine (the paper has no counterpart):
  * times every digit-plane GEMM kind on the context's own problem (reps launches
  * each) for every pipeline depth that fits its shared memory, the split kinds
- * (full transform, J, F^(p)C_p) also for one and two waves of CTAs, and J^(q)
- * with and without its symmetric skip-and-mirror (each launch timed from a
- * flushed L2, as inside an iteration), and keeps for every later call the
- * fastest setting of each kind when it beats the default by at least 3 %.  Needs a FULL transform and
+ * (full transform, J, F^(p)C_p) also for one and two waves of CTAs, J^(q)
+ * with and without its symmetric skip-and-mirror and the half transform as the
+ * two-CTA-per-SM kernel or the one-CTA kernel with two accumulator sets (each
+ * launch timed from a flushed L2, as inside an iteration), and keeps for every
+ * later call the fastest setting of each kind when it beats the default by at
+ * least 3 %.  Needs a FULL transform and
  * donof_ri_jk_ao_batch first (their data are the timing inputs); afterwards
  * every result must be recomputed (the state returns to "no transform").
  *   reps    launches timed per setting, 1..1000
  *   report  out (host) or NULL: 6 x 4 ints, per kind (half, full, J, J^(q), K^(q),
- *           F^(p)C_p): pipeline stages, split count (J^(q): 1 if symmetric),
- *           CTAs, best time in microseconds
+ *           F^(p)C_p): pipeline stages, split count (J^(q): 1 if symmetric; half
+ *           transform: 1 for the one-CTA kernel), CTAs, best time in microseconds
  *   tried   out (host) or NULL: settings timed
  * Synchronous.  Errors: E_ARG, E_STATE, E_UNSUPPORTED (precision other than SLICE4).
  */
 int donof_ri_autotune(donof_ri_ctx* ctx, int reps, int* report, int* tried);
+
+/*
+ * Set one GEMM kind's schedule directly (a choice the autotuner can make):
+ *   kind     0 half transform, 1 full transform, 2 J, 3 J^(q), 4 K^(q), 5 F^(p)C_p
+ *   stages   pipeline depth, 2 .. what fits the kind's shared memory
+ *   option   half transform: 0 two CTAs per SM, 1 one CTA with two accumulator
+ *            sets; J^(q): 1 symmetric skip-and-mirror, 0 full; full transform,
+ *            J and F^(p)C_p: 1 or 2 waves of CTAs; K^(q): 0
+ * Takes effect at the next launch (a captured iteration graph is dropped).
+ * Errors: E_ARG, E_UNSUPPORTED (precision other than SLICE4).
+ */
+int donof_ri_set_schedule(donof_ri_ctx* ctx, int kind, int stages, int option);
 
 /*
  * One orbital rotation step for fixed occupations (Sec. 2, "Orbital Optimization

@@ -468,6 +468,19 @@ int donof_ri_autotune(donof_ri_ctx* ctx, int reps, int* report, int* tried) {
   return consume_status(ctx);
 }
 
+int donof_ri_set_schedule(donof_ri_ctx* ctx, int kind, int stages, int option) {
+  if (!ctx) return DONOF_RI_E_ARG;
+  if (ctx->precision != DONOF_RI_SLICE4) return DONOF_RI_E_UNSUPPORTED;
+  int rc = s4_set_schedule(ctx, kind, stages, option);
+  if (rc) return rc;
+  // the captured graph holds the old launch parameters
+  if (ctx->graph_exec) {
+    cudaGraphExecDestroy(ctx->graph_exec);
+    ctx->graph_exec = nullptr;
+  }
+  return DONOF_RI_OK;
+}
+
 int donof_ri_rotate_orbitals(donof_ri_ctx* ctx, double radius, double* C, double* gmax) {
   if (!ctx || !(radius >= 0.0) || !(radius <= 3.2)) return DONOF_RI_E_ARG;
   if (!ctx->have_lambda) return DONOF_RI_E_STATE;

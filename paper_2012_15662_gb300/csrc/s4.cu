@@ -45,7 +45,11 @@ int launch_dot64(donof_ri_ctx* ctx, int M, int N, int K, const double* A, int ld
                  double* out, long long so_i, long long so_j);
 int launch_energy_rows(donof_ri_ctx* ctx, const double* HCt);
 
-enum S4Kind { S_HALF = 0, S_FULLSQ = 1, S_JMO = 2, S_JAO = 3, S_KAO = 4, S_FOCK = 5, S_NKINDS = 6 };
+// S_HALF1: the half transform with one CTA per SM, two accumulator sets and two
+// epilogue warpgroups (the layout of the other kinds); the autotuner chooses
+// between it and the two-CTA S_HALF.
+enum S4Kind { S_HALF = 0, S_FULLSQ = 1, S_JMO = 2, S_JAO = 3, S_KAO = 4, S_FOCK = 5, S_HALF1 = 6, S_NKINDS = 7 };
+__host__ __device__ constexpr bool s4_half(int kind) { return kind == S_HALF || kind == S_HALF1; }
 static_assert(DONOF_RI_GEMM_FOCK - DONOF_RI_GEMM_HALF == S_FOCK, "GEMM profile rows follow the kind order");
 
 constexpr int S4_BM = 128;      // rows per tile
@@ -239,7 +243,7 @@ __device__ __forceinline__ int rshift_round(int X, int d) {
 template <int KIND>
 __device__ __forceinline__ void s4_unit(const S4Params& p, int b, int& batch, int& kb0, int& nkb) {
   const int KBb = (p.nb + S4_BK - 1) / S4_BK, KBx = (p.nx + S4_BK - 1) / S4_BK;
-  if (KIND == S_HALF) { batch = 0; kb0 = 0; nkb = KBb; }
+  if (s4_half(KIND)) { batch = 0; kb0 = 0; nkb = KBb; }
   else if (KIND == S_FULLSQ) { batch = b; kb0 = 0; nkb = KBb; }
   else if (KIND == S_JMO) { batch = 0; kb0 = b * S4_CHUNK_KB; nkb = min(S4_CHUNK_KB, KBx - kb0); }
   else if (KIND == S_JAO) { batch = 0; kb0 = 0; nkb = KBx; }
@@ -261,7 +265,7 @@ __device__ __forceinline__ void s4_loads(const S4Params& p, uint8_t* st, uint64_
   for (int t = 0; t < S4_PLANES; ++t) {
     uint8_t* da = st + t * (S4_BM * S4_BK * 2);
     uint8_t* db = st + S4_PLANES * (S4_BM * S4_BK * 2) + t * (BN * S4_BK * 2);
-    if (KIND == S_HALF) {
+    if (s4_half(KIND)) {
       const int nvb = (p.nb + 15) / 16;
       tma_load_4d(da, &p.a, bar, k0, t, (mt % nvb) * 16, (mt / nvb) * 8);
       tma_load_3d(db, &p.b, bar, k0, t, n0);
@@ -480,11 +484,11 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_ge
             else rb[k] = col < p.m ? p.eb[col] : 0;
           }
         }
-        if (KIND == S_HALF) {
+        if (s4_half(KIND)) {
           const int nvb = (p.nb + 15) / 16;
           const int Pb = mt / nvb, vb = mt % nvb;
           constexpr int N3 = 2 * BN / 32, N6 = BN * 16 / 32;
-          static_assert(KIND != S_HALF || (2 * BN) % 32 == 0, "staging assumes 2*BN divisible by 32");
+          static_assert(!s4_half(KIND) || (2 * BN) % 32 == 0, "staging assumes 2*BN divisible by 32");
           int r3[N3], r6[N6];
 #pragma unroll
           for (int k = 0; k < N3; ++k) {
@@ -514,7 +518,7 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_ge
       int ea = 0;
       bool rvalid = false;
       int P = 0, nu = 0, mu = 0;
-      if (KIND == S_HALF) {
+      if (s4_half(KIND)) {
         // M tile = 16 nu x 8 P with nu fastest: a warp holds 16 consecutive nu of two
         // auxiliary rows, so each L3 digit row it stores is one full 32-byte sector.
         const int nvb = (p.nb + 15) / 16;
@@ -567,7 +571,7 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_ge
             if (CW == 16) tmem_wait16(gr[g]);
             else tmem_wait8(gr[g]);
           }
-          if (KIND == S_HALF && nch == 1) {
+          if (s4_half(KIND) && (ONE || nch == 1)) {
             // Single-chunk half transform: one output integer at the finer of the two
             // output scales (exponents e3, e6), Xf = sum_g rint(G_g 2^(sigma - 8g)) in
             // int32 (see half_fold), without the int64 fold.  xf_to_digits_kernel
@@ -589,7 +593,7 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_ge
             }
             continue;
           }
-          if (KIND == S_HALF || KIND == S_JMO) {
+          if (s4_half(KIND) || KIND == S_JMO) {
             // int64 fold: running sums over K chunks (J_pq's partials stay integers)
             long long v[CW];
 #pragma unroll
@@ -605,7 +609,7 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_ge
               continue;
             }
             if (!rvalid) continue;
-            if (KIND == S_HALF) {
+            if (s4_half(KIND)) {
               const int lrow = lane / 16, l16 = lane % 16;
               int* basef = p.x6 + (size_t)P * p.m * p.nbp + nu;
 #pragma unroll
@@ -857,26 +861,38 @@ __global__ void reduce_jmo_kernel(const long long* partial, int nsplit, int m, c
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m * m) return;
   long long s = 0;
+#pragma unroll 8
   for (int k = 0; k < nsplit; ++k) s += partial[(size_t)k * m * m + i];
   J[i] = ldexp((double)s, ed[i / m] + ed[i % m] - S4_SHIFT);
 }
 
 // sum over splits of double-float partials, FP64.  mode 1: the [rows = p][cols = mu]
 // partials of F^(p) C_p, written as Y^T [p][mu] with n_p (H C)^T added.
-__global__ void reduce_df_kernel(const float2* partial, int nsplit, int rows, int cols, double* out, int mode,
-                                 const double* n, const double* HCt) {
-  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  long long rc = (long long)rows * cols;
-  if (i >= rc) return;
+__global__ void __launch_bounds__(256) reduce_df_kernel(const float2* partial, int nsplit, int rows, int cols,
+                                                       double* out, int mode, const double* n, const double* HCt) {
+  // 32 outputs per block, their splits dealt to 8 thread rows (split k to row
+  // k % 8), each row summing its share in FP64; the 8 row sums are then added in
+  // row order, so the result does not depend on the launch beyond that fixed order.
+  __shared__ double part[8][32];
+  const long long rc = (long long)rows * cols;
+  const long long i = blockIdx.x * 32LL + threadIdx.x;
   double s = 0.0;
-  for (int k = 0; k < nsplit; ++k) {
-    float2 v = partial[(size_t)k * rc + i];
-    s += (double)v.x + (double)v.y;
+  if (i < rc) {
+    for (int k = threadIdx.y; k < nsplit; k += 8) {
+      const float2 v = partial[(size_t)k * rc + i];
+      s += (double)v.x + (double)v.y;
+    }
   }
+  part[threadIdx.y][threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.y != 0 || i >= rc) return;
+  double t = part[0][threadIdx.x];
+#pragma unroll
+  for (int y = 1; y < 8; ++y) t += part[y][threadIdx.x];
   if (mode == 1) {
-    out[i] = n[i / cols] * HCt[i] + s;
+    out[i] = n[i / cols] * HCt[i] + t;
   } else {
-    out[i] = s;
+    out[i] = t;
   }
 }
 
@@ -900,26 +916,29 @@ __global__ void fock_weights_df_kernel(const double* A, const double* Bc, int m,
 // 128 contiguous bytes per warp.  Row strides (nbp, nxp) are even.
 //
 // The same pass accumulates the diagonal b^P_pp = sum_nu C_{nu p} b^P_{p nu} (Table 3
-// step 3) from the L3 integers it has in hand: each warp sums its row's 64 nu in
-// double-float arithmetic (X3 = xh + xl exactly, C as a double-float pair) and
-// writes one partial per (nu tile, p, P) to dpart; diag_reduce_kernel adds the
-// tiles in a fixed order and applies the row scale.
+// step 3) from the L3 integers it has in hand: in the transposed half each thread
+// sums its two rows P over its eight nu in double-float arithmetic (X3 = xh + xl
+// exactly, C as a double-float pair), the eight thread rows are added in a fixed
+// order through shared memory, and one partial per (nu tile, p, P) goes to dpart;
+// diag_reduce_kernel adds the tiles in a fixed order and applies the row scale.
 __global__ void __launch_bounds__(256) xf_to_digits_kernel(const int* Xf, const int* e3, const int* e6, int nx, int nb,
                                                            int m, int mp, int nbp, int nxp, __nv_bfloat16* L3,
                                                            __nv_bfloat16* L6, const float2* Cdf, float2* dpart) {
   __shared__ int tile[64][65];
   __shared__ int s3[64], s6[64];
+  __shared__ float2 sc[64];
+  __shared__ float2 red[8][64];
   const int p = blockIdx.z, nu0 = blockIdx.x * 64, P0 = blockIdx.y * 64;
   const int tid = threadIdx.y * 32 + threadIdx.x;
   if (tid < 64) s3[tid] = (P0 + tid < nx) ? e3[(size_t)(P0 + tid) * m + p] : 0;
   else if (tid < 128) s6[tid - 64] = (nu0 + tid - 64 < nb) ? e6[(size_t)p * nb + nu0 + tid - 64] : 0;
+  else if (tid < 192) sc[tid - 128] = (nu0 + tid - 128 < nb) ? Cdf[(size_t)p * nb + nu0 + tid - 128] : make_float2(0.f, 0.f);
   __syncthreads();
   const int c0 = 2 * threadIdx.x;  // this thread's column pair within the tile
-  const float2 cv0 = (nu0 + c0 < nb) ? Cdf[(size_t)p * nb + nu0 + c0] : make_float2(0.f, 0.f);
-  const float2 cv1 = (nu0 + c0 + 1 < nb) ? Cdf[(size_t)p * nb + nu0 + c0 + 1] : make_float2(0.f, 0.f);
+  // rows P of the tile: L3 digits (nu contiguous)
   for (int r = threadIdx.y; r < 64; r += 8) {
     const int P = P0 + r, nu = nu0 + c0;
-    int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
+    int x0 = 0, x1 = 0;
     if (P < nx && nu < nb) {
       const int* src = Xf + ((size_t)P * m + p) * nbp + nu;
       if (nu + 1 < nb) {
@@ -930,9 +949,9 @@ __global__ void __launch_bounds__(256) xf_to_digits_kernel(const int* Xf, const 
         x0 = src[0];
       }
       int d = s3[r] - s6[c0];
-      y0 = rshift_round(x0, d > 0 ? d : 0);
+      const int y0 = rshift_round(x0, d > 0 ? d : 0);
       d = s3[r] - s6[c0 + 1];
-      y1 = rshift_round(x1, d > 0 ? d : 0);
+      const int y1 = rshift_round(x1, d > 0 ? d : 0);
       __nv_bfloat16 a[4], b[4];
       digits_bf16(y0, a);
       digits_bf16(y1, b);
@@ -945,31 +964,12 @@ __global__ void __launch_bounds__(256) xf_to_digits_kernel(const int* Xf, const 
     }
     tile[r][c0] = x0;
     tile[r][c0 + 1] = x1;
-    // diagonal partial of row P over this tile's 64 nu: y = yh + yl exactly in FP32
-    float sum = 0.f, cmp = 0.f;
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      const int y = k ? y1 : y0;
-      const float2 cv = k ? cv1 : cv0;
-      const float yh = (float)(y >> 8) * 256.f, yl = (float)(y & 255);
-      const float p0 = yh * cv.x;
-      const float e0 = fmaf(yh, cv.x, -p0) + (yh * cv.y + yl * cv.x);
-      float ns, e;
-      two_sum_f(sum, p0, ns, e);
-      sum = ns;
-      cmp += e + e0;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      const float so = __shfl_xor_sync(0xffffffffu, sum, o);
-      const float co = __shfl_xor_sync(0xffffffffu, cmp, o);
-      float ns, e;
-      two_sum_f(sum, so, ns, e);
-      sum = ns;
-      cmp += co + e;
-    }
-    if (threadIdx.x == 0 && P < nx) dpart[((size_t)blockIdx.x * m + p) * nx + P] = make_float2(sum, cmp);
   }
   __syncthreads();
+  // columns nu of the tile: L6 digits (P contiguous), and the diagonal partials of the
+  // thread's two rows P over its eight nu in double-float arithmetic (the L3 value
+  // y = yh + yl exactly in FP32, C as a double-float pair)
+  float sum[2] = {0.f, 0.f}, cmp[2] = {0.f, 0.f};
   for (int r = threadIdx.y; r < 64; r += 8) {
     const int nu = nu0 + r, P = P0 + c0;
     if (nu < nb && P < nx) {
@@ -984,7 +984,34 @@ __global__ void __launch_bounds__(256) xf_to_digits_kernel(const int* Xf, const 
         if (P + 1 < nx) *(__nv_bfloat162*)(o + (size_t)t * nxp) = __halves2bfloat162(a[t], b[t]);
         else o[(size_t)t * nxp] = a[t];
       }
+      const float2 cv = sc[r];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int d3 = s3[c0 + k] - s6[r];
+        const int y = rshift_round(tile[c0 + k][r], d3 > 0 ? d3 : 0);
+        const float yh = (float)(y >> 8) * 256.f, yl = (float)(y & 255);
+        const float p0 = yh * cv.x;
+        const float e0 = fmaf(yh, cv.x, -p0) + (yh * cv.y + yl * cv.x);
+        float ns, e;
+        two_sum_f(sum[k], p0, ns, e);
+        sum[k] = ns;
+        cmp[k] += e + e0;
+      }
     }
+  }
+  red[threadIdx.y][c0] = make_float2(sum[0], cmp[0]);
+  red[threadIdx.y][c0 + 1] = make_float2(sum[1], cmp[1]);
+  __syncthreads();
+  if (tid < 64 && P0 + tid < nx) {
+    float sh = red[0][tid].x, sl = red[0][tid].y;
+#pragma unroll
+    for (int y = 1; y < 8; ++y) {
+      float ns, e;
+      two_sum_f(sh, red[y][tid].x, ns, e);
+      sh = ns;
+      sl += e + red[y][tid].y;
+    }
+    dpart[((size_t)blockIdx.x * m + p) * nx + P0 + tid] = make_float2(sh, sl);
   }
 }
 
@@ -1077,6 +1104,7 @@ struct donof::S4Buffers {
   int* jao_tmap_full;                                 // every J^(q) row block
   int jao_ntiles_sym, jao_ntiles_full;
   int jao_sym;                                        // 1: J^(q) lower row blocks skipped and mirrored
+  int half_variant;                                   // 1: the half transform runs as S_HALF1
   int max_stages[donof::S_NKINDS];                    // pipeline depth that fits the shared memory
   int target[donof::S_NKINDS];                        // CTA count the split kinds aim at
   int *eB1, *eB5, *eC, *e3, *e6, *ed, *eJK;          // row exponents
@@ -1177,6 +1205,7 @@ int s4_init(donof_ri_ctx* ctx) {
   const int KBb = (nb + S4_BK - 1) / S4_BK, KBx = (nx + S4_BK - 1) / S4_BK;
   const int bn = S4Cfg<S_HALF>::BN;  // 48 for every kind but the full transform (32)
   s4_plan<S_HALF>(sb, ((nx + 7) / 8) * ((nb + 15) / 16), (m + bn - 1) / bn, 1, 1, S4Cfg<S_HALF>::CTAS * sms);
+  s4_plan<S_HALF1>(sb, ((nx + 7) / 8) * ((nb + 15) / 16), (m + bn - 1) / bn, 1, 1, S4Cfg<S_HALF1>::CTAS * sms);
   s4_plan<S_FULLSQ>(sb, (m + S4_BM - 1) / S4_BM, (m + bn - 1) / bn, nx, S4Cfg<S_FULLSQ>::CTAS * sms);
   s4_plan<S_JMO>(sb, (m + S4_BM - 1) / S4_BM, (m + bn - 1) / bn, (KBx + S4_CHUNK_KB - 1) / S4_CHUNK_KB,
                  S4Cfg<S_JMO>::CTAS * sms);
@@ -1296,6 +1325,11 @@ int s4_init(donof_ri_ctx* ctx) {
     p.ea = sb->eB1; p.eb = sb->eC;
     p.o3 = sb->L3; p.e3 = sb->e3;
     p.x6 = sb->X6; p.e6 = sb->e6;
+    // the one-CTA variant: same operands, its own schedule
+    S4Params& p1 = sb->plan[S_HALF1];
+    const int st1 = p1.stages, tc1 = p1.tmem_cols, pe1 = p1.persist, nt1 = p1.ntiles, ntl1 = p1.n_tiles;
+    p1 = p;
+    p1.stages = st1; p1.tmem_cols = tc1; p1.persist = pe1; p1.ntiles = nt1; p1.n_tiles = ntl1;
   }
   {  // FULLSQ: A = L3 [nx][mp][4][nbp] rows p (per P) over nu; B = C^T digits
     S4Params& p = sb->plan[S_FULLSQ];
@@ -1361,7 +1395,7 @@ int s4_init(donof_ri_ctx* ctx) {
       cudaFuncSetAttribute(s4_gemm_kernel<KIND, ONE>, cudaFuncAttributePreferredSharedMemoryCarveout,        \
                            (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)                               \
     return DONOF_RI_E_CUDA;
-  OPTIN(S_HALF, 0) OPTIN(S_FULLSQ, 0) OPTIN(S_FULLSQ, 1) OPTIN(S_JMO, 0) OPTIN(S_JAO, 0) OPTIN(S_JAO, 1)
+  OPTIN(S_HALF, 0) OPTIN(S_HALF, 1) OPTIN(S_HALF1, 0) OPTIN(S_HALF1, 1) OPTIN(S_FULLSQ, 0) OPTIN(S_FULLSQ, 1) OPTIN(S_JMO, 0) OPTIN(S_JAO, 0) OPTIN(S_JAO, 1)
   OPTIN(S_KAO, 0) OPTIN(S_KAO, 1) OPTIN(S_FOCK, 1)
 #undef OPTIN
   return DONOF_RI_OK;
@@ -1386,9 +1420,18 @@ static int launch_s4(donof_ri_ctx* ctx) {
   ProfScope ps(ctx, DONOF_RI_GEMM_HALF + KIND);
   // single-chunk epilogue where every unit's K fits one chunk (F^(p) C_p: always)
   const int kext = (KIND == S_JAO || KIND == S_KAO) ? ctx->naux : ctx->nbf;
-  const bool one = KIND == S_FOCK || ((KIND == S_FULLSQ || KIND == S_JAO || KIND == S_KAO) &&
+  const bool one = KIND == S_FOCK || ((KIND == S_HALF || KIND == S_FULLSQ || KIND == S_JAO || KIND == S_KAO) &&
                                       kext <= S4_CHUNK_KB * S4_BK);
-  if constexpr (KIND == S_FOCK) {
+  if constexpr (KIND == S_HALF) {
+    const S4Params& p1 = sb->plan[S_HALF1];
+    const int g1 = sb->grid[S_HALF1];
+    const size_t m1 = sb->smem[S_HALF1];
+    constexpr int T1 = S4Cfg<S_HALF1>::THREADS;
+    if (sb->half_variant && one) s4_gemm_kernel<S_HALF1, 1><<<g1, T1, m1, ctx->stream>>>(p1);
+    else if (sb->half_variant) s4_gemm_kernel<S_HALF1, 0><<<g1, T1, m1, ctx->stream>>>(p1);
+    else if (one) s4_gemm_kernel<S_HALF, 1><<<sb->grid[KIND], S4Cfg<KIND>::THREADS, sb->smem[KIND], ctx->stream>>>(sb->plan[KIND]);
+    else s4_gemm_kernel<S_HALF, 0><<<sb->grid[KIND], S4Cfg<KIND>::THREADS, sb->smem[KIND], ctx->stream>>>(sb->plan[KIND]);
+  } else if constexpr (KIND == S_FOCK) {
     s4_gemm_kernel<KIND, 1><<<sb->grid[KIND], S4Cfg<KIND>::THREADS, sb->smem[KIND], ctx->stream>>>(sb->plan[KIND]);
   } else if constexpr (KIND == S_FULLSQ || KIND == S_JAO || KIND == S_KAO) {
     if (one)
@@ -1466,7 +1509,7 @@ int s4_transform(donof_ri_ctx* ctx, int mode) {
       ProfScope ps(ctx, DONOF_RI_ROW_FULL_K);
       if ((rc = launch_s4<S_FULLSQ>(ctx))) return rc;
       const S4Params& p = sb->plan[S_FULLSQ];
-      reduce_df_kernel<<<ceil_div_u((long long)m * m, 256), 256, 0, s>>>((const float2*)p.partial, p.nsplit, m, m,
+      reduce_df_kernel<<<ceil_div_u((long long)m * m, 32), dim3(32, 8), 0, s>>>((const float2*)p.partial, p.nsplit, m, m,
                                                                           ctx->d_K, 0, nullptr, nullptr);
       DONOF_LAUNCH_CHECK(ctx);
     }
@@ -1521,7 +1564,7 @@ int s4_energy(donof_ri_ctx* ctx, int part) {
   if (!(part & ENERGY_MAIN)) return DONOF_RI_OK;
   if ((rc = launch_s4<S_FOCK>(ctx))) return rc;
   const S4Params& p = sb->plan[S_FOCK];
-  reduce_df_kernel<<<ceil_div_u((long long)nb * m, 256), 256, 0, s>>>((const float2*)p.partial, p.nsplit, m, nb,
+  reduce_df_kernel<<<ceil_div_u((long long)nb * m, 32), dim3(32, 8), 0, s>>>((const float2*)p.partial, p.nsplit, m, nb,
                                                                        sb->Yt, 1, ctx->d_n, sb->HCt);
   DONOF_LAUNCH_CHECK(ctx);
   if ((rc = launch_dot64(ctx, m, nb, nb, sb->Yt, nb, ctx->d_C, nb, ctx->d_lambda, nb, 1))) return rc;
@@ -1583,9 +1626,12 @@ static int s4_tune_kind(donof_ri_ctx* ctx, int reps, cudaEvent_t a, cudaEvent_t 
   S4Buffers* sb = ctx->s4;
   S4Params& p = sb->plan[KIND];
   const bool split = (KIND == S_FULLSQ || KIND == S_JMO || KIND == S_FOCK);
-  const int nsym = (KIND == S_JAO) ? 2 : 1;
+  // J^(q): symmetric skip on / off; half transform: the two-CTA or the one-CTA kernel
+  const int nsym = (KIND == S_JAO || KIND == S_HALF) ? 2 : 1;
   float best = 1e30f, dflt = 1e30f;
-  const int dS = p.stages, dT = split ? sb->target[KIND] : 0, dSym = sb->jao_sym;
+  const int dS = p.stages, dT = split ? sb->target[KIND] : 0;
+  const int dSym = KIND == S_HALF ? sb->half_variant : sb->jao_sym;
+  const int dS1 = sb->plan[S_HALF1].stages;
   int bestS = dS, bestT = dT, bestSym = dSym;
   const int targets[2] = {split ? sb->target[KIND] : 0, split ? 2 * sb->target[KIND] : 0};
   int rc;
@@ -1597,14 +1643,18 @@ static int s4_tune_kind(donof_ri_ctx* ctx, int reps, cudaEvent_t a, cudaEvent_t 
       const int units = p.ntiles * p.nbatch, pc = S4Cfg<S_JAO>::CTAS * 152;
       sb->grid[KIND] = units < pc ? units : pc;
     }
+    if (KIND == S_HALF) sb->half_variant = sym;
+    S4Params& pv = (KIND == S_HALF && sym) ? sb->plan[S_HALF1] : p;
+    const int maxS = (KIND == S_HALF && sym) ? sb->max_stages[S_HALF1] : sb->max_stages[KIND];
+    const int defS = (KIND == S_HALF && sym) ? dS1 : dS;
     for (int ti = 0; ti < (split ? 2 : 1); ++ti) {
       if (split) s4_split<KIND>(sb, targets[ti]);
-      for (int S = 2; S <= sb->max_stages[KIND]; ++S) {
-        p.stages = S;
+      for (int S = 2; S <= maxS; ++S) {
+        pv.stages = S;
         float ms = 0.f;
         if ((rc = s4_time<KIND>(ctx, reps, a, b, flush, fbytes, &ms))) return rc;
         ++*tried;
-        if (S == dS && targets[ti] == dT && (KIND != S_JAO || sym == dSym)) dflt = ms;
+        if (S == defS && targets[ti] == dT && ((KIND != S_JAO && KIND != S_HALF) || sym == dSym)) dflt = ms;
         if (ms < best) {
           best = ms;
           bestS = S;
@@ -1613,10 +1663,11 @@ static int s4_tune_kind(donof_ri_ctx* ctx, int reps, cudaEvent_t a, cudaEvent_t 
         }
       }
     }
+    pv.stages = defS;
   }
   if (!(best < 0.97f * dflt)) {  // keep the default unless clearly beaten
     best = dflt;
-    bestS = dS;
+    bestS = (KIND == S_HALF && dSym) ? dS1 : dS;
     bestT = dT;
     bestSym = dSym;
   }
@@ -1627,13 +1678,53 @@ static int s4_tune_kind(donof_ri_ctx* ctx, int reps, cudaEvent_t a, cudaEvent_t 
     const int units = p.ntiles * p.nbatch, pc = S4Cfg<S_JAO>::CTAS * 152;
     sb->grid[KIND] = units < pc ? units : pc;
   }
-  p.stages = bestS;
+  if (KIND == S_HALF) {
+    sb->half_variant = bestSym;
+    (bestSym ? sb->plan[S_HALF1] : p).stages = bestS;
+  } else {
+    p.stages = bestS;
+  }
   if (split) s4_split<KIND>(sb, bestT);
   if (report) {
     report[KIND * 4 + 0] = bestS;
-    report[KIND * 4 + 1] = split ? p.nsplit : (KIND == S_JAO ? bestSym : 0);
-    report[KIND * 4 + 2] = sb->grid[KIND];
+    report[KIND * 4 + 1] = split ? p.nsplit : ((KIND == S_JAO || KIND == S_HALF) ? bestSym : 0);
+    report[KIND * 4 + 2] = (KIND == S_HALF && bestSym) ? sb->grid[S_HALF1] : sb->grid[KIND];
     report[KIND * 4 + 3] = (int)(best * 1000.f + 0.5f);  // microseconds
+  }
+  return DONOF_RI_OK;
+}
+
+// A kind's schedule set by the caller (the choices the autotuner makes): pipeline
+// depth, and option = waves of CTAs (1 or 2) for the split kinds, the symmetric
+// skip (0 / 1) for J^(q), the kernel variant (0: two CTAs per SM, 1: one) for the
+// half transform, 0 otherwise.
+int s4_set_schedule(donof_ri_ctx* ctx, int kind, int stages, int option) {
+  S4Buffers* sb = ctx->s4;
+  if (kind < 0 || kind > S_FOCK) return DONOF_RI_E_ARG;
+  const bool split = (kind == S_FULLSQ || kind == S_JMO || kind == S_FOCK);
+  const int var_kind = (kind == S_HALF && option == 1) ? S_HALF1 : kind;
+  if (stages < 2 || stages > sb->max_stages[var_kind]) return DONOF_RI_E_ARG;
+  if (split ? (option != 1 && option != 2) : ((kind == S_JAO || kind == S_HALF) ? (option != 0 && option != 1) : option != 0))
+    return DONOF_RI_E_ARG;
+  S4Params& p = sb->plan[kind];
+  if (kind == S_HALF) {
+    sb->half_variant = option;
+    sb->plan[var_kind].stages = stages;
+    return DONOF_RI_OK;
+  }
+  p.stages = stages;
+  if (kind == S_JAO) {
+    sb->jao_sym = option;
+    p.tmap = option ? sb->jao_tmap : sb->jao_tmap_full;
+    p.ntiles = p.n_tiles = option ? sb->jao_ntiles_sym : sb->jao_ntiles_full;
+    const int units = p.ntiles * p.nbatch, pc = S4Cfg<S_JAO>::CTAS * 152;
+    sb->grid[kind] = units < pc ? units : pc;
+  }
+  if (split) {
+    const int target = option * sb->target[kind];
+    if (kind == S_FULLSQ) s4_split<S_FULLSQ>(sb, target);
+    if (kind == S_JMO) s4_split<S_JMO>(sb, target);
+    if (kind == S_FOCK) s4_split<S_FOCK>(sb, target);
   }
   return DONOF_RI_OK;
 }

@@ -189,6 +189,36 @@ int s4_copy_ao(donof_ri_ctx* ctx, double* Jao, double* Kao, bool jao_dev, bool k
 
 }  // namespace donof
 
+namespace donof {
+// ---- programmatic dependent launch (the kernels of the iteration chain) ----
+// A kernel launched with launch_pdl may be scheduled while its predecessor in
+// the stream is still running.  It calls pdl_entry() before it touches global
+// memory: griddepcontrol.wait returns once the predecessor grid has completed
+// and its writes are visible, and griddepcontrol.launch_dependents then lets the
+// next grid be scheduled, so each launch's latency hides behind the running
+// kernel, one grid ahead.  Launched the ordinary way, both return at once.
+__device__ __forceinline__ void pdl_entry() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+}  // namespace donof
+
 #define DONOF_CUDA_TRY(expr)                         \
   do {                                               \
     cudaError_t _e = (expr);                         \

@@ -9,12 +9,13 @@
 namespace donof {
 
 __global__ void check_finite_kernel(const double* x, long long n, int* status) {
+  pdl_entry();
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i < n && !isfinite(x[i])) atomicCAS(status, 0, (int)DEV_NONFINITE);
 }
 
 int launch_check_finite(donof_ri_ctx* ctx, const double* x, long long n) {
-  check_finite_kernel<<<ceil_div_u(n, 256), 256, 0, ctx->stream>>>(x, n, ctx->d_status);
+  launch_pdl(check_finite_kernel, dim3(ceil_div_u(n, 256)), dim3(256), 0, ctx->stream, x, n, ctx->d_status);
   DONOF_LAUNCH_CHECK(ctx);
   return DONOF_RI_OK;
 }
@@ -135,6 +136,7 @@ int path64_jk_ao(donof_ri_ctx* ctx) {
 // ---------------------------------------------------------------------------
 __global__ void occupations_kernel(int n_strong, int n_weak_per, int n_om, const int* subspace,
                                    const int* weak_rank, const double* gamma, double* n) {
+  pdl_entry();
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n_om) return;
   const int g = subspace[p];
@@ -164,6 +166,7 @@ __global__ void occupations_kernel(int n_strong, int n_weak_per, int n_om, const
 
 __global__ void coupling_kernel(int n_om, const int* subspace, const int* weak_rank, const double* n, double* A,
                                 double* Bc) {
+  pdl_entry();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_om * n_om) return;
   int p = i / n_om, q = i % n_om;
@@ -184,11 +187,11 @@ __global__ void coupling_kernel(int n_om, const int* subspace, const int* weak_r
 
 int launch_occupations_coupling(donof_ri_ctx* ctx) {
   const int m = ctx->n_omega;
-  occupations_kernel<<<ceil_div_u(m, 128), 128, 0, ctx->stream>>>(
-      ctx->n_strong, ctx->n_weak_per, m, ctx->d_subspace, ctx->d_weak_rank, ctx->d_gamma, ctx->d_n);
+  launch_pdl(occupations_kernel, dim3(ceil_div_u(m, 128)), dim3(128), 0, ctx->stream, ctx->n_strong, ctx->n_weak_per, m,
+             (const int*)ctx->d_subspace, (const int*)ctx->d_weak_rank, (const double*)ctx->d_gamma, ctx->d_n);
   DONOF_LAUNCH_CHECK(ctx);
-  coupling_kernel<<<ceil_div_u((long long)m * m, 256), 256, 0, ctx->stream>>>(m, ctx->d_subspace, ctx->d_weak_rank,
-                                                                               ctx->d_n, ctx->d_A, ctx->d_Bc);
+  launch_pdl(coupling_kernel, dim3(ceil_div_u((long long)m * m, 256)), dim3(256), 0, ctx->stream, m,
+             (const int*)ctx->d_subspace, (const int*)ctx->d_weak_rank, (const double*)ctx->d_n, ctx->d_A, ctx->d_Bc);
   DONOF_LAUNCH_CHECK(ctx);
   return DONOF_RI_OK;
 }
@@ -240,6 +243,7 @@ int launch_energy_reduce(donof_ri_ctx* ctx) {
 // products of the energy row, where a 64x64-tile GEMM would leave most SMs idle.
 __global__ void dot64_kernel(int M, int N, int K, const double* A, int lda, const double* B, int ldb, double* out,
                              long long so_i, long long so_j) {
+  pdl_entry();
   long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / 32;
   int lane = threadIdx.x % 32;
   if (w >= (long long)M * N) return;
@@ -254,8 +258,8 @@ __global__ void dot64_kernel(int M, int N, int K, const double* A, int lda, cons
 
 int launch_dot64(donof_ri_ctx* ctx, int M, int N, int K, const double* A, int lda, const double* B, int ldb,
                  double* out, long long so_i, long long so_j) {
-  dot64_kernel<<<ceil_div_u((long long)M * N * 32, 256), 256, 0, ctx->stream>>>(M, N, K, A, lda, B, ldb, out, so_i,
-                                                                               so_j);
+  launch_pdl(dot64_kernel, dim3(ceil_div_u((long long)M * N * 32, 256)), dim3(256), 0, ctx->stream, M, N, K, A, lda, B,
+             ldb, out, so_i, so_j);
   DONOF_LAUNCH_CHECK(ctx);
   return DONOF_RI_OK;
 }
@@ -264,6 +268,7 @@ int launch_dot64(donof_ri_ctx* ctx, int M, int N, int K, const double* A, int ld
 // (rows p, stride nbf).  One block, one warp per p, fixed reduction order.
 __global__ void energy_rows_kernel(int nbf, int n_om, const double* C, const double* HCt, const double* n,
                                    const double* lambda, const double* enuc, double* E) {
+  pdl_entry();
   __shared__ double part[32];
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   double acc = 0.0;
@@ -285,8 +290,8 @@ __global__ void energy_rows_kernel(int nbf, int n_om, const double* C, const dou
 }
 
 int launch_energy_rows(donof_ri_ctx* ctx, const double* HCt) {
-  energy_rows_kernel<<<1, 1024, 0, ctx->stream>>>(ctx->nbf, ctx->n_omega, ctx->d_C, HCt, ctx->d_n, ctx->d_lambda,
-                                                  ctx->d_enuc, ctx->d_E);
+  launch_pdl(energy_rows_kernel, dim3(1), dim3(1024), 0, ctx->stream, ctx->nbf, ctx->n_omega, (const double*)ctx->d_C,
+             HCt, (const double*)ctx->d_n, (const double*)ctx->d_lambda, (const double*)ctx->d_enuc, ctx->d_E);
   DONOF_LAUNCH_CHECK(ctx);
   return DONOF_RI_OK;
 }

@@ -348,6 +348,8 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_ge
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
+  // barriers and TMEM are set up; global memory only from here on
+  pdl_entry();
 
   if (warp == 0) {
     if (lane == 0) {
@@ -757,6 +759,7 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_ge
 __global__ void slice_f64_kernel(const double* X, long long rows, int cols, long long rs, long long cs,
                                  __nv_bfloat16* planes, int ldp, int* exps, float* absout, float* absT,
                                  float2* dfout) {
+  pdl_entry();
   long long r = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / 32;
   int lane = threadIdx.x % 32;
   if (r >= rows) return;
@@ -786,6 +789,7 @@ __global__ void slice_f64_kernel(const double* X, long long rows, int cols, long
 // row exponents.
 __global__ void slice_pair_kernel(const float* hi, const float* lo, long long rows, int cols, int ld,
                                   __nv_bfloat16* planes, int ldp, int* exps) {
+  pdl_entry();
   long long r = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / 32;
   int lane = threadIdx.x % 32;
   if (r >= rows) return;
@@ -814,6 +818,7 @@ __global__ void slice_pair_kernel(const float* hi, const float* lo, long long ro
 // One block per P (resp. p); the row of the first factor is staged in shared memory and the
 // threads run over p (resp. nu) with coalesced reads of the second factor.
 __global__ void bound3_kernel(const float* rmaxB, const float* absCt, int nx, int nb, int m, int* e3) {
+  pdl_entry();
   extern __shared__ float srow[];
   const int P = blockIdx.x;
   for (int mu = threadIdx.x; mu < nb; mu += blockDim.x) srow[mu] = rmaxB[(size_t)P * nb + mu];
@@ -826,6 +831,7 @@ __global__ void bound3_kernel(const float* rmaxB, const float* absCt, int nx, in
 }
 
 __global__ void bound6_kernel(const float* maxB, const float* absC, int nb, int m, int* e6) {
+  pdl_entry();
   extern __shared__ float srow[];
   const int pc = blockIdx.x;
   for (int mu = threadIdx.x; mu < nb; mu += blockDim.x) srow[mu] = absC[(size_t)pc * nb + mu];
@@ -858,6 +864,7 @@ __global__ void bmax_aux_kernel(const double* B, int nx, int nb, float* maxB) {
 
 // J_pq = 2^(ed_p + ed_q - 46) x (sum over splits of the exact int64 partials).
 __global__ void reduce_jmo_kernel(const long long* partial, int nsplit, int m, const int* ed, double* J) {
+  pdl_entry();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m * m) return;
   long long s = 0;
@@ -870,6 +877,7 @@ __global__ void reduce_jmo_kernel(const long long* partial, int nsplit, int m, c
 // partials of F^(p) C_p, written as Y^T [p][mu] with n_p (H C)^T added.
 __global__ void __launch_bounds__(256) reduce_df_kernel(const float2* partial, int nsplit, int rows, int cols,
                                                        double* out, int mode, const double* n, const double* HCt) {
+  pdl_entry();
   // 32 outputs per block, their splits dealt to 8 thread rows (split k to row
   // k % 8), each row summing its share in FP64; the 8 row sums are then added in
   // row order, so the result does not depend on the launch beyond that fixed order.
@@ -898,6 +906,7 @@ __global__ void __launch_bounds__(256) reduce_df_kernel(const float2* partial, i
 
 // FOCK weights as double-float pairs: W[q][p] = A_pq, W[N_O + q][p] = -B_pq.
 __global__ void fock_weights_df_kernel(const double* A, const double* Bc, int m, float2* W) {
+  pdl_entry();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 2 * m * m) return;
   int qq = i / m, pc = i % m;
@@ -924,6 +933,7 @@ __global__ void fock_weights_df_kernel(const double* A, const double* Bc, int m,
 __global__ void __launch_bounds__(256) xf_to_digits_kernel(const int* Xf, const int* e3, const int* e6, int nx, int nb,
                                                            int m, int mp, int nbp, int nxp, __nv_bfloat16* L3,
                                                            __nv_bfloat16* L6, const float2* Cdf, float2* dpart) {
+  pdl_entry();
   __shared__ int tile[64][65];
   __shared__ int s3[64], s6[64];
   __shared__ float2 sc[64];
@@ -1017,6 +1027,7 @@ __global__ void __launch_bounds__(256) xf_to_digits_kernel(const int* Xf, const 
 
 // d[p][P] = 2^(e3[P][p] - 31) sum over the nu tiles of the pass's double-float partials.
 __global__ void diag_reduce_kernel(const float2* dpart, int ntiles, int nx, int m, const int* e3, double* d) {
+  pdl_entry();
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= (long long)nx * m) return;
   const int pc = (int)(i / nx), P = (int)(i % nx);
@@ -1046,6 +1057,7 @@ __host__ __device__ __forceinline__ bool jao_block_skipped(long long r0, int nb)
 }
 
 __global__ void sym_mirror_kernel(float* hi, float* lo, int nb, int row0, int ldo, int bn, int jao) {
+  pdl_entry();
   __shared__ float th[32][33], tl[32][33];
   const int bi = blockIdx.y, bj = blockIdx.x;  // destination block: rows mu (bi), columns nu (bj)
   if (bj > bi) return;
@@ -1427,20 +1439,25 @@ static int launch_s4(donof_ri_ctx* ctx) {
     const int g1 = sb->grid[S_HALF1];
     const size_t m1 = sb->smem[S_HALF1];
     constexpr int T1 = S4Cfg<S_HALF1>::THREADS;
-    if (sb->half_variant && one) s4_gemm_kernel<S_HALF1, 1><<<g1, T1, m1, ctx->stream>>>(p1);
-    else if (sb->half_variant) s4_gemm_kernel<S_HALF1, 0><<<g1, T1, m1, ctx->stream>>>(p1);
-    else if (one) s4_gemm_kernel<S_HALF, 1><<<sb->grid[KIND], S4Cfg<KIND>::THREADS, sb->smem[KIND], ctx->stream>>>(sb->plan[KIND]);
-    else s4_gemm_kernel<S_HALF, 0><<<sb->grid[KIND], S4Cfg<KIND>::THREADS, sb->smem[KIND], ctx->stream>>>(sb->plan[KIND]);
-  } else if constexpr (KIND == S_FOCK) {
-    s4_gemm_kernel<KIND, 1><<<sb->grid[KIND], S4Cfg<KIND>::THREADS, sb->smem[KIND], ctx->stream>>>(sb->plan[KIND]);
-  } else if constexpr (KIND == S_FULLSQ || KIND == S_JAO || KIND == S_KAO) {
-    if (one)
-      s4_gemm_kernel<KIND, 1><<<sb->grid[KIND], S4Cfg<KIND>::THREADS, sb->smem[KIND], ctx->stream>>>(sb->plan[KIND]);
-    else
-      s4_gemm_kernel<KIND, 0><<<sb->grid[KIND], S4Cfg<KIND>::THREADS, sb->smem[KIND], ctx->stream>>>(sb->plan[KIND]);
+    const dim3 g0(sb->grid[KIND]), t0(S4Cfg<KIND>::THREADS);
+    const size_t m0 = sb->smem[KIND];
+    if (sb->half_variant && one) launch_pdl(s4_gemm_kernel<S_HALF1, 1>, dim3(g1), dim3(T1), m1, ctx->stream, p1);
+    else if (sb->half_variant) launch_pdl(s4_gemm_kernel<S_HALF1, 0>, dim3(g1), dim3(T1), m1, ctx->stream, p1);
+    else if (one) launch_pdl(s4_gemm_kernel<S_HALF, 1>, g0, t0, m0, ctx->stream, sb->plan[KIND]);
+    else launch_pdl(s4_gemm_kernel<S_HALF, 0>, g0, t0, m0, ctx->stream, sb->plan[KIND]);
   } else {
-    (void)one;
-    s4_gemm_kernel<KIND, 0><<<sb->grid[KIND], S4Cfg<KIND>::THREADS, sb->smem[KIND], ctx->stream>>>(sb->plan[KIND]);
+    const dim3 g0(sb->grid[KIND]), t0(S4Cfg<KIND>::THREADS);
+    const size_t m0 = sb->smem[KIND];
+    if constexpr (KIND == S_FOCK) {
+      (void)one;
+      launch_pdl(s4_gemm_kernel<KIND, 1>, g0, t0, m0, ctx->stream, sb->plan[KIND]);
+    } else if constexpr (KIND == S_FULLSQ || KIND == S_JAO || KIND == S_KAO) {
+      if (one) launch_pdl(s4_gemm_kernel<KIND, 1>, g0, t0, m0, ctx->stream, sb->plan[KIND]);
+      else launch_pdl(s4_gemm_kernel<KIND, 0>, g0, t0, m0, ctx->stream, sb->plan[KIND]);
+    } else {
+      (void)one;
+      launch_pdl(s4_gemm_kernel<KIND, 0>, g0, t0, m0, ctx->stream, sb->plan[KIND]);
+    }
   }
   DONOF_LAUNCH_CHECK(ctx);
   return DONOF_RI_OK;
@@ -1454,17 +1471,19 @@ int s4_transform(donof_ri_ctx* ctx, int mode) {
   {
     ProfScope ps(ctx, DONOF_RI_ROW_OTHER);
     // C^T rows p over mu (C column-major = rows p contiguous)
-    slice_f64_kernel<<<ceil_div_u((long long)m * 32, 256), 256, 0, s>>>(ctx->d_C, m, nb, nb, 1, sb->Ct, sb->nbp,
-                                                                          sb->eC, sb->absC, sb->absCt, sb->Cdf);
+    launch_pdl(slice_f64_kernel, dim3(ceil_div_u((long long)m * 32, 256)), dim3(256), 0, s, (const double*)ctx->d_C,
+               (long long)m, nb, (long long)nb, 1LL, sb->Ct, sb->nbp, sb->eC, sb->absC, sb->absCt, sb->Cdf);
     DONOF_LAUNCH_CHECK(ctx);
     // the two bound passes are independent: e6 on the second stream
     cudaStream_t main_stream;
     const bool forked = fork_begin(ctx, &main_stream);
-    bound6_kernel<<<m, 128, nb * sizeof(float), ctx->stream>>>(sb->maxB, sb->absC, nb, m, sb->e6);
+    launch_pdl(bound6_kernel, dim3(m), dim3(128), nb * sizeof(float), ctx->stream, (const float*)sb->maxB,
+               (const float*)sb->absC, nb, m, sb->e6);
     rc = cudaGetLastError() == cudaSuccess ? DONOF_RI_OK : DONOF_RI_E_CUDA;
     ctx->launches++;
     if (forked) fork_end(ctx, main_stream);
-    bound3_kernel<<<nx, 128, nb * sizeof(float), s>>>(sb->rmaxB, sb->absCt, nx, nb, m, sb->e3);
+    launch_pdl(bound3_kernel, dim3(nx), dim3(128), nb * sizeof(float), s, (const float*)sb->rmaxB,
+               (const float*)sb->absCt, nx, nb, m, sb->e3);
     DONOF_LAUNCH_CHECK(ctx);
     if (forked && (rc = fork_join(ctx))) return rc;
     if (rc) return rc;
@@ -1473,17 +1492,18 @@ int s4_transform(donof_ri_ctx* ctx, int mode) {
     ProfScope ps(ctx, DONOF_RI_ROW_HALF);
     if ((rc = launch_s4<S_HALF>(ctx))) return rc;
     dim3 g((nb + 63) / 64, (nx + 63) / 64, m), b(32, 8);
-    xf_to_digits_kernel<<<g, b, 0, s>>>(sb->X6, sb->e3, sb->e6, nx, nb, m, sb->mp, sb->nbp, sb->nxp, sb->L3, sb->L6,
-                                        sb->Cdf, sb->dpart);
+    launch_pdl(xf_to_digits_kernel, g, b, 0, s, (const int*)sb->X6, (const int*)sb->e3, (const int*)sb->e6, nx, nb, m,
+               sb->mp, sb->nbp, sb->nxp, sb->L3, sb->L6, (const float2*)sb->Cdf, sb->dpart);
     DONOF_LAUNCH_CHECK(ctx);
   }
   {
     ProfScope ps(ctx, DONOF_RI_ROW_DIAG);
-    diag_reduce_kernel<<<ceil_div_u((long long)nx * m, 256), 256, 0, s>>>(sb->dpart, (nb + 63) / 64, nx, m, sb->e3,
-                                                                           sb->dmat);
+    launch_pdl(diag_reduce_kernel, dim3(ceil_div_u((long long)nx * m, 256)), dim3(256), 0, s, (const float2*)sb->dpart,
+               (nb + 63) / 64, nx, m, (const int*)sb->e3, sb->dmat);
     DONOF_LAUNCH_CHECK(ctx);
-    slice_f64_kernel<<<ceil_div_u((long long)m * 32, 256), 256, 0, s>>>(sb->dmat, m, nx, nx, 1, sb->Dp, sb->nxp,
-                                                                          sb->ed, nullptr, nullptr, nullptr);
+    launch_pdl(slice_f64_kernel, dim3(ceil_div_u((long long)m * 32, 256)), dim3(256), 0, s, (const double*)sb->dmat,
+               (long long)m, nx, (long long)nx, 1LL, sb->Dp, sb->nxp, sb->ed, (float*)nullptr, (float*)nullptr,
+               (float2*)nullptr);
     DONOF_LAUNCH_CHECK(ctx);
   }
   if (mode == DONOF_RI_FULL) {
@@ -1498,8 +1518,8 @@ int s4_transform(donof_ri_ctx* ctx, int mode) {
       rcj = launch_s4<S_JMO>(ctx);
       if (!rcj) {
         const S4Params& p = sb->plan[S_JMO];
-        reduce_jmo_kernel<<<ceil_div_u((long long)m * m, 256), 256, 0, ctx->stream>>>(
-            (const long long*)p.partial, p.nsplit, m, sb->ed, ctx->d_J);
+        launch_pdl(reduce_jmo_kernel, dim3(ceil_div_u((long long)m * m, 256)), dim3(256), 0, ctx->stream,
+                   (const long long*)p.partial, p.nsplit, m, (const int*)sb->ed, ctx->d_J);
         rcj = cudaGetLastError() == cudaSuccess ? DONOF_RI_OK : DONOF_RI_E_CUDA;
         ctx->launches++;
       }
@@ -1509,8 +1529,8 @@ int s4_transform(donof_ri_ctx* ctx, int mode) {
       ProfScope ps(ctx, DONOF_RI_ROW_FULL_K);
       if ((rc = launch_s4<S_FULLSQ>(ctx))) return rc;
       const S4Params& p = sb->plan[S_FULLSQ];
-      reduce_df_kernel<<<ceil_div_u((long long)m * m, 32), dim3(32, 8), 0, s>>>((const float2*)p.partial, p.nsplit, m, m,
-                                                                          ctx->d_K, 0, nullptr, nullptr);
+      launch_pdl(reduce_df_kernel, dim3(ceil_div_u((long long)m * m, 32)), dim3(32, 8), 0, s, (const float2*)p.partial,
+                 p.nsplit, m, m, ctx->d_K, 0, (const double*)nullptr, (const double*)nullptr);
       DONOF_LAUNCH_CHECK(ctx);
     }
     if (forked && (rc = fork_join(ctx))) return rc;
@@ -1528,7 +1548,7 @@ int s4_jk_ao(donof_ri_ctx* ctx) {
     if ((rc = launch_s4<S_JAO>(ctx))) return rc;
     if (sb->jao_sym) {
       dim3 g((nb + 31) / 32, (nb + 31) / 32, m), b(32, 8);
-      sym_mirror_kernel<<<g, b, 0, ctx->stream>>>(sb->JKhi, sb->JKlo, nb, 0, sb->ldo, S4Cfg<S_JAO>::BN, 1);
+      launch_pdl(sym_mirror_kernel, g, b, 0, ctx->stream, sb->JKhi, sb->JKlo, nb, 0, sb->ldo, S4Cfg<S_JAO>::BN, 1);
       DONOF_LAUNCH_CHECK(ctx);
     }
   }
@@ -1536,14 +1556,14 @@ int s4_jk_ao(donof_ri_ctx* ctx) {
     ProfScope ps(ctx, DONOF_RI_ROW_KAO);
     if ((rc = launch_s4<S_KAO>(ctx))) return rc;
     dim3 g((nb + 31) / 32, (nb + 31) / 32, m), b(32, 8);
-    sym_mirror_kernel<<<g, b, 0, ctx->stream>>>(sb->JKhi, sb->JKlo, nb, m, sb->ldo, S4Cfg<S_KAO>::BN, 0);
+    launch_pdl(sym_mirror_kernel, g, b, 0, ctx->stream, sb->JKhi, sb->JKlo, nb, m, sb->ldo, S4Cfg<S_KAO>::BN, 0);
     DONOF_LAUNCH_CHECK(ctx);
   }
   {
     ProfScope ps(ctx, DONOF_RI_ROW_OTHER);
     long long rows = 2LL * m * nb;
-    slice_pair_kernel<<<ceil_div_u(rows * 32, 256), 256, 0, ctx->stream>>>(sb->JKhi, sb->JKlo, rows, nb, sb->ldo,
-                                                                            sb->JKp, sb->nbp, sb->eJK);
+    launch_pdl(slice_pair_kernel, dim3(ceil_div_u(rows * 32, 256)), dim3(256), 0, ctx->stream, (const float*)sb->JKhi,
+               (const float*)sb->JKlo, rows, nb, sb->ldo, sb->JKp, sb->nbp, sb->eJK);
     DONOF_LAUNCH_CHECK(ctx);
   }
   return DONOF_RI_OK;
@@ -1557,15 +1577,16 @@ int s4_energy(donof_ri_ctx* ctx, int part) {
   ProfScope ps(ctx, DONOF_RI_ROW_ENERGY);
   if (part & ENERGY_PREP) {
     if ((rc = launch_occupations_coupling(ctx))) return rc;
-    fock_weights_df_kernel<<<ceil_div_u(2LL * m * m, 256), 256, 0, s>>>(ctx->d_A, ctx->d_Bc, m, sb->W);
+    launch_pdl(fock_weights_df_kernel, dim3(ceil_div_u(2LL * m * m, 256)), dim3(256), 0, s, (const double*)ctx->d_A,
+               (const double*)ctx->d_Bc, m, sb->W);
     DONOF_LAUNCH_CHECK(ctx);
     if ((rc = launch_dot64(ctx, m, nb, nb, ctx->d_C, nb, ctx->d_H, nb, sb->HCt, nb, 1))) return rc;
   }
   if (!(part & ENERGY_MAIN)) return DONOF_RI_OK;
   if ((rc = launch_s4<S_FOCK>(ctx))) return rc;
   const S4Params& p = sb->plan[S_FOCK];
-  reduce_df_kernel<<<ceil_div_u((long long)nb * m, 32), dim3(32, 8), 0, s>>>((const float2*)p.partial, p.nsplit, m, nb,
-                                                                       sb->Yt, 1, ctx->d_n, sb->HCt);
+  launch_pdl(reduce_df_kernel, dim3(ceil_div_u((long long)nb * m, 32)), dim3(32, 8), 0, s, (const float2*)p.partial,
+             p.nsplit, m, nb, sb->Yt, 1, (const double*)ctx->d_n, (const double*)sb->HCt);
   DONOF_LAUNCH_CHECK(ctx);
   if ((rc = launch_dot64(ctx, m, nb, nb, sb->Yt, nb, ctx->d_C, nb, ctx->d_lambda, nb, 1))) return rc;
   return launch_energy_rows(ctx, sb->HCt);

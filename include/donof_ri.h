@@ -224,6 +224,25 @@ int donof_ri_energy_lagrangian(donof_ri_ctx* ctx, const double* gamma, double* E
 int donof_ri_iteration(donof_ri_ctx* ctx, const double* C, const double* gamma, int mode, double* J, double* K,
                        double* E, double* lambda, int use_graph);
 
+/*
+ * Exact four-centre J and K for orbitals C (the conventional algorithm of Table 1,
+ * Eqs. (Jpq), (Pmat), (Kpq), with exact s-type integrals (mu nu|l s) in place of
+ * Eq. (AOERI)): the paper's RI -> exact restart finishes an RI-converged
+ * calculation with a few exact iterations (Sec. 1, Sec. 4).  Computes
+ * J^(q)_{mu nu} = sum_{l s} (mu nu|l s) C_{l q} C_{s q},
+ * K^(q)_{mu nu} = sum_{l s} (mu l|nu s) C_{l q} C_{s q} and
+ * J_pq = C_p^T J^(q) C_p, K_pq = C_p^T K^(q) C_p in FP64 and leaves them in the
+ * context in place of the RI ones, so that donof_ri_energy_lagrangian and
+ * donof_ri_optimize_occupations that follow use exact integrals (until the next
+ * transform).  The integrals are stored (nbf^4 doubles) together with one
+ * half-contracted copy (nbf^3 N_Omega doubles), allocated for the call.
+ *   C      [nbf][nbf] column-major orbitals, host or device
+ *   J, K   [N_Omega][N_Omega] outputs, host or device, or NULL
+ * Synchronous.  Errors: E_ARG, E_OOM, E_CUDA, E_NONFINITE, E_UNSUPPORTED (a
+ * precision other than DONOF_RI_FP64, or nbf > 256).
+ */
+int donof_ri_exact_jk(donof_ri_ctx* ctx, const double* C, double* J, double* K);
+
 /* Internal arrays readable through donof_ri_fetch (converted to FP64). */
 #define DONOF_RI_FETCH_B 0        /* [naux][nbf][nbf]   fitted tensor B^P_{mu nu}      */
 #define DONOF_RI_FETCH_BHALF 1    /* [naux][N_Omega][nbf] b^P_{p nu}                   */

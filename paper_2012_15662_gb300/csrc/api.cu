@@ -468,6 +468,24 @@ int donof_ri_autotune(donof_ri_ctx* ctx, int reps, int* report, int* tried) {
   return consume_status(ctx);
 }
 
+int donof_ri_exact_jk(donof_ri_ctx* ctx, const double* C, double* J, double* K) {
+  if (!ctx || !C) return DONOF_RI_E_ARG;
+  if (ctx->precision != DONOF_RI_FP64 || ctx->nbf > 256) return DONOF_RI_E_UNSUPPORTED;
+  int rc = transform_input(ctx, C);
+  if (rc) return rc;
+  ctx->have_half = ctx->have_full = ctx->have_ao = ctx->have_lambda = 0;
+  {
+    ProfScope ps(ctx, DONOF_RI_ROW_OTHER);
+    if ((rc = exact_jk(ctx))) return rc;
+  }
+  ctx->have_half = ctx->have_full = ctx->have_ao = 1;
+  const size_t m2 = (size_t)ctx->n_omega * ctx->n_omega;
+  bool host = false;
+  if ((rc = copy_out(ctx, J, ctx->d_J, m2, &host))) return rc;
+  if ((rc = copy_out(ctx, K, ctx->d_K, m2, &host))) return rc;
+  return consume_status(ctx);
+}
+
 int donof_ri_set_schedule(donof_ri_ctx* ctx, int kind, int stages, int option) {
   if (!ctx) return DONOF_RI_E_ARG;
   if (ctx->precision != DONOF_RI_SLICE4) return DONOF_RI_E_UNSUPPORTED;

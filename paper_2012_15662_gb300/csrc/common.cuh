@@ -165,6 +165,8 @@ int onopt_features(donof_ri_ctx* ctx, float* d_X);
 int rotate_orbitals(donof_ri_ctx* ctx, double radius, double* scratch, double* gnorm);
 int s4_autotune(donof_ri_ctx* ctx, int reps, int* report, int* tried);
 int s4_set_schedule(donof_ri_ctx* ctx, int kind, int stages, int option);
+// exact.cu: exact four-centre J^(q), K^(q), J, K into an FP64 context's buffers
+int exact_jk(donof_ri_ctx* ctx);
 int onopt_unfold(donof_ri_ctx* ctx, const float* d_Y, double clip, double* d_gamma);
 int mlp_forward_device(donof_mlp* n, const float* dX, int B, float** dY);
 int mlp_shape(const donof_mlp* n, int* F, int* O);

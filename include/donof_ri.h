@@ -340,13 +340,15 @@ int donof_ri_optimize_occupations(donof_ri_ctx* ctx, double* gamma, int max_iter
  * two-CTA-per-SM kernel or the one-CTA kernel with two accumulator sets (each
  * launch timed from a flushed L2, as inside an iteration), and keeps for every
  * later call the fastest setting of each kind when it beats the default by at
- * least 3 %.  Needs a FULL transform and
+ * least 3 %; finally J^(q) and K^(q) in one persistent launch (the default)
+ * against two launches.  Needs a FULL transform and
  * donof_ri_jk_ao_batch first (their data are the timing inputs); afterwards
  * every result must be recomputed (the state returns to "no transform").
  *   reps    launches timed per setting, 1..1000
  *   report  out (host) or NULL: 6 x 4 ints, per kind (half, full, J, J^(q), K^(q),
  *           F^(p)C_p): pipeline stages, split count (J^(q): 1 if symmetric; half
- *           transform: 1 for the one-CTA kernel), CTAs, best time in microseconds
+ *           transform: 1 for the one-CTA kernel; K^(q): 1 if in one launch with
+ *           J^(q)), CTAs, best time in microseconds
  *   tried   out (host) or NULL: settings timed
  * Synchronous.  Errors: E_ARG, E_STATE, E_UNSUPPORTED (precision other than SLICE4).
  */
@@ -358,7 +360,8 @@ int donof_ri_autotune(donof_ri_ctx* ctx, int reps, int* report, int* tried);
  *   stages   pipeline depth, 2 .. what fits the kind's shared memory
  *   option   half transform: 0 two CTAs per SM, 1 one CTA with two accumulator
  *            sets; J^(q): 1 symmetric skip-and-mirror, 0 full; full transform,
- *            J and F^(p)C_p: 1 or 2 waves of CTAs; K^(q): 0
+ *            J and F^(p)C_p: 1 or 2 waves of CTAs; K^(q): 1 in one persistent
+ *            launch together with J^(q) (the default), 0 in a launch of its own
  * Takes effect at the next launch (a captured iteration graph is dropped).
  * Errors: E_ARG, E_UNSUPPORTED (precision other than SLICE4).
  */

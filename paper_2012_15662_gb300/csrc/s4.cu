@@ -48,7 +48,11 @@ int launch_energy_rows(donof_ri_ctx* ctx, const double* HCt);
 // S_HALF1: the half transform with one CTA per SM, two accumulator sets and two
 // epilogue warpgroups (the layout of the other kinds); the autotuner chooses
 // between it and the two-CTA S_HALF.
-enum S4Kind { S_HALF = 0, S_FULLSQ = 1, S_JMO = 2, S_JAO = 3, S_KAO = 4, S_FOCK = 5, S_HALF1 = 6, S_NKINDS = 7 };
+// S_JKAO: J^(q) and K^(q) of one orbital iteration in one persistent launch (the
+// J^(q) tiles, then the K^(q) (tile, orbital) units).
+enum S4Kind {
+  S_HALF = 0, S_FULLSQ = 1, S_JMO = 2, S_JAO = 3, S_KAO = 4, S_FOCK = 5, S_HALF1 = 6, S_JKAO = 7, S_NKINDS = 8
+};
 __host__ __device__ constexpr bool s4_half(int kind) { return kind == S_HALF || kind == S_HALF1; }
 static_assert(DONOF_RI_GEMM_FOCK - DONOF_RI_GEMM_HALF == S_FOCK, "GEMM profile rows follow the kind order");
 
@@ -85,6 +89,7 @@ struct S4Cfg {
 
 struct S4Params {
   CUtensorMap a, b;  // digit planes; coordinate 1 selects the digit
+  CUtensorMap a2, b2;  // S_JKAO: the K^(q) operands (a, b: the J^(q) ones)
   int stages, tmem_cols;
   int n_tiles, nbatch, bpc, nsplit;
   int nb, nx, m, nbp, nxp, mp;  // nbp / nxp: BF16 row strides (multiples of 8)
@@ -104,6 +109,12 @@ struct S4Params {
   int persist;      // 1: units are whole tiles, CTA c takes tiles c, c + grid, ...
   int ntiles;       // total tiles (persistent kinds)
   const int* tmap;  // optional list of the tiles to compute, (mt << 16) | nt (K^(q): upper triangle)
+  // S_JKAO: units [0, u_split) are J^(q) tiles (tmap, exponents ea / eb), the rest
+  // (tile, orbital) units of K^(q) (tmap2 of ntiles2 tiles, exponents ea2 / eb2)
+  const int* tmap2;
+  const int* ea2;
+  const int* eb2;
+  int ntiles2, u_split;
 };
 
 // ---------------------------------------------------------------------------
@@ -246,7 +257,7 @@ __device__ __forceinline__ void s4_unit(const S4Params& p, int b, int& batch, in
   if (s4_half(KIND)) { batch = 0; kb0 = 0; nkb = KBb; }
   else if (KIND == S_FULLSQ) { batch = b; kb0 = 0; nkb = KBb; }
   else if (KIND == S_JMO) { batch = 0; kb0 = b * S4_CHUNK_KB; nkb = min(S4_CHUNK_KB, KBx - kb0); }
-  else if (KIND == S_JAO) { batch = 0; kb0 = 0; nkb = KBx; }
+  else if (KIND == S_JAO || KIND == S_JKAO) { batch = 0; kb0 = 0; nkb = KBx; }
   else if (KIND == S_KAO) { batch = b; kb0 = 0; nkb = KBx; }
   else {
     const int nc = (KBb + S4_CHUNK_KB - 1) / S4_CHUNK_KB;
@@ -256,9 +267,31 @@ __device__ __forceinline__ void s4_unit(const S4Params& p, int b, int& batch, in
   }
 }
 
+// Persistent unit U -> (K^(q) unit?, batch entry, tile (mt, nt)).
+template <int KIND>
+__device__ __forceinline__ void s4_persist_unit(const S4Params& p, int U, bool& kao, int& batch, int& mt, int& nt) {
+  const int* tm = p.tmap;
+  int ntl = p.ntiles, V = U;
+  kao = (KIND == S_KAO);
+  if (KIND == S_JKAO) {
+    if (U >= p.u_split) {
+      kao = true;
+      V = U - p.u_split;
+      tm = p.tmap2;
+      ntl = p.ntiles2;
+    } else {
+      ntl = p.u_split;
+    }
+  }
+  batch = V / ntl;
+  const int tl = V % ntl;
+  mt = tm ? tm[tl] >> 16 : tl / p.n_tiles;
+  nt = tm ? tm[tl] & 0xFFFF : tl % p.n_tiles;
+}
+
 template <int KIND>
 __device__ __forceinline__ void s4_loads(const S4Params& p, uint8_t* st, uint64_t* bar, int mt, int nt, int batch,
-                                         int kb) {
+                                         int kb, bool kao) {
   constexpr int BN = S4Cfg<KIND>::BN;
   const int k0 = kb * S4_BK, n0 = nt * BN;
 #pragma unroll
@@ -275,9 +308,12 @@ __device__ __forceinline__ void s4_loads(const S4Params& p, uint8_t* st, uint64_
     } else if (KIND == S_FOCK) {
       tma_load_3d(da, &p.a, bar, k0, t, mt * S4_BM);
       tma_load_4d(db, &p.b, bar, k0, t, n0, batch);
-    } else if (KIND == S_JMO || KIND == S_JAO) {
+    } else if (KIND == S_JMO || KIND == S_JAO || (KIND == S_JKAO && !kao)) {
       tma_load_3d(da, &p.a, bar, k0, t, mt * S4_BM);
       tma_load_3d(db, &p.b, bar, k0, t, n0);
+    } else if (KIND == S_JKAO) {  // K^(q) unit of the merged launch
+      tma_load_4d(da, &p.a2, bar, k0, t, mt * S4_BM, batch);
+      tma_load_4d(db, &p.b2, bar, k0, t, n0, batch);
     } else {  // S_KAO
       tma_load_4d(da, &p.a, bar, k0, t, mt * S4_BM, batch);
       tma_load_4d(db, &p.b, bar, k0, t, n0, batch);
@@ -358,18 +394,15 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_ge
       bool ok = true;
       for (int u = 0; u < nunits && ok; ++u) {
         int batch, kb0, nkb;
+        bool kao = (KIND == S_KAO);
         const int U = tile0 + u * (int)gridDim.x;
         s4_unit<KIND>(p, p.persist ? U / p.ntiles : b0 + u, batch, kb0, nkb);
-        if (p.persist) {
-          const int tl = U % p.ntiles;
-          mt = p.tmap ? p.tmap[tl] >> 16 : tl / p.n_tiles;
-          nt = p.tmap ? p.tmap[tl] & 0xFFFF : tl % p.n_tiles;
-        }
+        if (p.persist) s4_persist_unit<KIND>(p, U, kao, batch, mt, nt);
         for (int kb = 0; kb < nkb; ++kb) {
           const int s = it % S;
           if (!mbar_wait(&empty[s], (uint32_t)(((it / S) & 1) ^ 1), abort_flag, p.status)) { ok = false; break; }
           mbar_expect_tx(&full[s], stage_bytes);
-          s4_loads<KIND>(p, smem + (size_t)s * stage_bytes, &full[s], mt, nt, batch, kb0 + kb);
+          s4_loads<KIND>(p, smem + (size_t)s * stage_bytes, &full[s], mt, nt, batch, kb0 + kb, kao);
           ++it;
         }
       }
@@ -462,13 +495,13 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_ge
     bool ok = true;
     for (int u = 0; u < nunits && ok; ++u) {
       int batch, kb0, nkb;
+      bool kao = (KIND == S_KAO);
       const int U = tile0 + u * (int)gridDim.x;
       s4_unit<KIND>(p, p.persist ? U / p.ntiles : b0 + u, batch, kb0, nkb);
-      if (p.persist) {
-        const int tl = U % p.ntiles;
-        mt = p.tmap ? p.tmap[tl] >> 16 : tl / p.n_tiles;
-        nt = p.tmap ? p.tmap[tl] & 0xFFFF : tl % p.n_tiles;
-      }
+      if (p.persist) s4_persist_unit<KIND>(p, U, kao, batch, mt, nt);
+      // the merged kind's exponents for this unit
+      const int* eA = (KIND == S_JKAO && kao) ? p.ea2 : p.ea;
+      const int* eB = (KIND == S_JKAO && kao) ? p.eb2 : p.eb;
       // Stage this unit's column exponents (and weights) in shared memory: one pass of
       // coalesced loads per warp instead of a dependent global load per output column.
       if (KIND != S_JMO) {
@@ -482,8 +515,9 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_ge
           const int i = lane + 32 * k, col = nt * BN + i;
           rb[k] = 0;
           if (i < BN) {
-            if (KIND == S_KAO || KIND == S_FOCK) rb[k] = col < p.nb ? p.eb[(size_t)batch * p.nb + col] : 0;
-            else rb[k] = col < p.m ? p.eb[col] : 0;
+            if (KIND == S_KAO || KIND == S_FOCK || (KIND == S_JKAO && kao))
+              rb[k] = col < p.nb ? eB[(size_t)batch * p.nb + col] : 0;
+            else rb[k] = col < p.m ? eB[col] : 0;
           }
         }
         if (s4_half(KIND)) {
@@ -532,16 +566,16 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_ge
         mu = mt * S4_BM + row;
         rvalid = mu < p.m;
         ea = rvalid ? p.ea[(size_t)batch * p.m + mu] : 0;
-      } else if (KIND == S_JAO) {
+      } else if (KIND == S_JAO || (KIND == S_JKAO && !kao)) {
         const int r = mt * S4_BM + row;
         rvalid = r < p.nb * p.nb;
         mu = r / p.nb;
         nu = r % p.nb;
-        ea = rvalid ? p.ea[r] : 0;
-      } else if (KIND == S_KAO) {
+        ea = rvalid ? eA[r] : 0;
+      } else if (KIND == S_KAO || KIND == S_JKAO) {
         mu = mt * S4_BM + row;
         rvalid = mu < p.nb;
-        ea = rvalid ? p.ea[(size_t)batch * p.nb + mu] : 0;
+        ea = rvalid ? eA[(size_t)batch * p.nb + mu] : 0;
       }
       // FOCK: the row is orbital p (C^T digits), the unit's weight W[batch][p] is per row
       float2 wrow = make_float2(0.f, 0.f);
@@ -678,7 +712,7 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_ge
                 df_add(sh[SUM_DF ? cb * CW + j : 0], sl[SUM_DF ? cb * CW + j : 0], ph, pl);
               }
             }
-          } else if (KIND == S_JAO) {
+          } else if (KIND == S_JAO || (KIND == S_JKAO && !kao)) {
 #pragma unroll
             for (int j = 0; j < CW; ++j) {
               const int i = c * CW + j;
@@ -689,7 +723,7 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_ge
                 p.olo[o] = lv[j];
               }
             }
-          } else if (KIND == S_KAO) {
+          } else if (KIND == S_KAO || KIND == S_JKAO) {
             // A thread's CW = 8 consecutive columns of one output row are one 32-byte
             // sector of hi and one of lo (ldo is a multiple of 8): two 16-byte vector
             // stores each instead of eight scattered 4-byte ones.
@@ -1117,6 +1151,7 @@ struct donof::S4Buffers {
   int jao_ntiles_sym, jao_ntiles_full;
   int jao_sym;                                        // 1: J^(q) lower row blocks skipped and mirrored
   int half_variant;                                   // 1: the half transform runs as S_HALF1
+  int jk_merged;                                      // 1: J^(q) and K^(q) in one launch (S_JKAO)
   int max_stages[donof::S_NKINDS];                    // pipeline depth that fits the shared memory
   int target[donof::S_NKINDS];                        // CTA count the split kinds aim at
   int *eB1, *eB5, *eC, *e3, *e6, *ed, *eJK;          // row exponents
@@ -1192,6 +1227,33 @@ static void s4_plan(S4Buffers* sb, int m_tiles, int n_tiles, int nbatch, int tar
     const long long units = (long long)tiles * nbatch;
     sb->grid[KIND] = units < persist_ctas ? (int)units : persist_ctas;
   }
+}
+
+// The merged J^(q) + K^(q) launch: the current J^(q) plan (tile list, symmetric or
+// full) and the K^(q) plan in one persistent grid, one CTA per SM.
+static void s4_plan_jkao(S4Buffers* sb) {
+  const S4Params& pj = sb->plan[S_JAO];
+  const S4Params& pk = sb->plan[S_KAO];
+  S4Params& p = sb->plan[S_JKAO];
+  const int stages = p.stages > 0 ? p.stages : pj.stages;
+  p = pj;
+  p.a2 = pk.a;
+  p.b2 = pk.b;
+  p.ea2 = pk.ea;
+  p.eb2 = pk.eb;
+  p.tmap2 = pk.tmap;
+  p.ntiles2 = pk.ntiles;
+  p.u_split = pj.ntiles * pj.nbatch;
+  p.ntiles = p.u_split + pk.ntiles * pk.nbatch;  // every unit of the launch
+  p.nbatch = 1;
+  p.persist = 1;
+  p.stages = stages;
+  const int pc = S4Cfg<S_JKAO>::CTAS * 152;
+  sb->grid[S_JKAO] = p.ntiles < pc ? p.ntiles : pc;
+  sb->smem[S_JKAO] = sb->smem[S_JAO] > sb->smem[S_KAO] ? sb->smem[S_JAO] : sb->smem[S_KAO];
+  // the shared memory holds the deeper of the two pipelines' stages
+  const int sj = sb->plan[S_JAO].stages, sk = sb->plan[S_KAO].stages;
+  if (p.stages > (sj > sk ? sj : sk)) p.stages = sj > sk ? sj : sk;
 }
 
 int s4_init(donof_ri_ctx* ctx) {
@@ -1401,6 +1463,9 @@ int s4_init(donof_ri_ctx* ctx) {
     p.w = sb->W;
     p.prow = m; p.pcol = nb;
   }
+  sb->plan[S_JKAO].stages = 0;
+  s4_plan_jkao(sb);
+  sb->jk_merged = 1;
 #define OPTIN(KIND, ONE)                                                                                      \
   if (cudaFuncSetAttribute(s4_gemm_kernel<KIND, ONE>, cudaFuncAttributeMaxDynamicSharedMemorySize,           \
                            (int)sb->smem[KIND]) != cudaSuccess ||                                             \
@@ -1408,7 +1473,7 @@ int s4_init(donof_ri_ctx* ctx) {
                            (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)                               \
     return DONOF_RI_E_CUDA;
   OPTIN(S_HALF, 0) OPTIN(S_HALF, 1) OPTIN(S_HALF1, 0) OPTIN(S_HALF1, 1) OPTIN(S_FULLSQ, 0) OPTIN(S_FULLSQ, 1) OPTIN(S_JMO, 0) OPTIN(S_JAO, 0) OPTIN(S_JAO, 1)
-  OPTIN(S_KAO, 0) OPTIN(S_KAO, 1) OPTIN(S_FOCK, 1)
+  OPTIN(S_KAO, 0) OPTIN(S_KAO, 1) OPTIN(S_FOCK, 1) OPTIN(S_JKAO, 0) OPTIN(S_JKAO, 1)
 #undef OPTIN
   return DONOF_RI_OK;
 }
@@ -1429,11 +1494,13 @@ template <int KIND>
 static int launch_s4(donof_ri_ctx* ctx) {
   S4Buffers* sb = ctx->s4;
   if (sb->grid[KIND] <= 0) return DONOF_RI_OK;
-  ProfScope ps(ctx, DONOF_RI_GEMM_HALF + KIND);
+  ProfScope ps(ctx, KIND == S_JKAO ? DONOF_RI_GEMM_JAO : DONOF_RI_GEMM_HALF + KIND);
   // single-chunk epilogue where every unit's K fits one chunk (F^(p) C_p: always)
-  const int kext = (KIND == S_JAO || KIND == S_KAO) ? ctx->naux : ctx->nbf;
-  const bool one = KIND == S_FOCK || ((KIND == S_HALF || KIND == S_FULLSQ || KIND == S_JAO || KIND == S_KAO) &&
-                                      kext <= S4_CHUNK_KB * S4_BK);
+  const int kext = (KIND == S_JAO || KIND == S_KAO || KIND == S_JKAO) ? ctx->naux : ctx->nbf;
+  const bool one =
+      KIND == S_FOCK ||
+      ((KIND == S_HALF || KIND == S_FULLSQ || KIND == S_JAO || KIND == S_KAO || KIND == S_JKAO) &&
+       kext <= S4_CHUNK_KB * S4_BK);
   if constexpr (KIND == S_HALF) {
     const S4Params& p1 = sb->plan[S_HALF1];
     const int g1 = sb->grid[S_HALF1];
@@ -1451,7 +1518,7 @@ static int launch_s4(donof_ri_ctx* ctx) {
     if constexpr (KIND == S_FOCK) {
       (void)one;
       launch_pdl(s4_gemm_kernel<KIND, 1>, g0, t0, m0, ctx->stream, sb->plan[KIND]);
-    } else if constexpr (KIND == S_FULLSQ || KIND == S_JAO || KIND == S_KAO) {
+    } else if constexpr (KIND == S_FULLSQ || KIND == S_JAO || KIND == S_KAO || KIND == S_JKAO) {
       if (one) launch_pdl(s4_gemm_kernel<KIND, 1>, g0, t0, m0, ctx->stream, sb->plan[KIND]);
       else launch_pdl(s4_gemm_kernel<KIND, 0>, g0, t0, m0, ctx->stream, sb->plan[KIND]);
     } else {
@@ -1543,6 +1610,18 @@ int s4_jk_ao(donof_ri_ctx* ctx) {
   S4Buffers* sb = ctx->s4;
   const int nb = ctx->nbf, m = ctx->n_omega;
   int rc;
+  if (sb->jk_merged && !ctx->prof_enabled) {
+    // one persistent launch for every J^(q) and K^(q) unit, then the mirrors.  Per-row
+    // profiling keeps the two launches apart so that each row has its own events.
+    if ((rc = launch_s4<S_JKAO>(ctx))) return rc;
+    dim3 g((nb + 31) / 32, (nb + 31) / 32, m), b(32, 8);
+    if (sb->jao_sym) {
+      launch_pdl(sym_mirror_kernel, g, b, 0, ctx->stream, sb->JKhi, sb->JKlo, nb, 0, sb->ldo, S4Cfg<S_JAO>::BN, 1);
+      DONOF_LAUNCH_CHECK(ctx);
+    }
+    launch_pdl(sym_mirror_kernel, g, b, 0, ctx->stream, sb->JKhi, sb->JKlo, nb, m, sb->ldo, S4Cfg<S_KAO>::BN, 0);
+    DONOF_LAUNCH_CHECK(ctx);
+  } else {
   {
     ProfScope ps(ctx, DONOF_RI_ROW_JAO);
     if ((rc = launch_s4<S_JAO>(ctx))) return rc;
@@ -1558,6 +1637,7 @@ int s4_jk_ao(donof_ri_ctx* ctx) {
     dim3 g((nb + 31) / 32, (nb + 31) / 32, m), b(32, 8);
     launch_pdl(sym_mirror_kernel, g, b, 0, ctx->stream, sb->JKhi, sb->JKlo, nb, m, sb->ldo, S4Cfg<S_KAO>::BN, 0);
     DONOF_LAUNCH_CHECK(ctx);
+  }
   }
   {
     ProfScope ps(ctx, DONOF_RI_ROW_OTHER);
@@ -1725,7 +1805,8 @@ int s4_set_schedule(donof_ri_ctx* ctx, int kind, int stages, int option) {
   const bool split = (kind == S_FULLSQ || kind == S_JMO || kind == S_FOCK);
   const int var_kind = (kind == S_HALF && option == 1) ? S_HALF1 : kind;
   if (stages < 2 || stages > sb->max_stages[var_kind]) return DONOF_RI_E_ARG;
-  if (split ? (option != 1 && option != 2) : ((kind == S_JAO || kind == S_HALF) ? (option != 0 && option != 1) : option != 0))
+  if (split ? (option != 1 && option != 2)
+            : ((kind == S_JAO || kind == S_HALF || kind == S_KAO) ? (option != 0 && option != 1) : option != 0))
     return DONOF_RI_E_ARG;
   S4Params& p = sb->plan[kind];
   if (kind == S_HALF) {
@@ -1734,6 +1815,7 @@ int s4_set_schedule(donof_ri_ctx* ctx, int kind, int stages, int option) {
     return DONOF_RI_OK;
   }
   p.stages = stages;
+  if (kind == S_KAO) sb->jk_merged = option;
   if (kind == S_JAO) {
     sb->jao_sym = option;
     p.tmap = option ? sb->jao_tmap : sb->jao_tmap_full;
@@ -1747,6 +1829,42 @@ int s4_set_schedule(donof_ri_ctx* ctx, int kind, int stages, int option) {
     if (kind == S_JMO) s4_split<S_JMO>(sb, target);
     if (kind == S_FOCK) s4_split<S_FOCK>(sb, target);
   }
+  if (kind == S_JAO || kind == S_KAO) s4_plan_jkao(sb);
+  return DONOF_RI_OK;
+}
+
+// J^(q) and K^(q) as one launch or as two (with their mirrors), each timed from a
+// flushed L2; the merged launch stays unless the pair of launches is 3 % faster.
+static int s4_tune_jk_merge(donof_ri_ctx* ctx, int reps, cudaEvent_t a, cudaEvent_t b, void* flush, size_t fbytes,
+                            int* tried) {
+  S4Buffers* sb = ctx->s4;
+  const int nb = ctx->nbf, m = ctx->n_omega;
+  float t[2] = {0.f, 0.f};
+  int rc;
+  for (int merged = 0; merged < 2; ++merged) {
+    sb->jk_merged = merged;
+    for (int r = 0; r <= reps; ++r) {  // r = 0: warm-up
+      DONOF_CUDA_TRY(cudaMemsetAsync(flush, r & 255, fbytes, ctx->stream));
+      DONOF_CUDA_TRY(cudaEventRecord(a, ctx->stream));
+      if (merged) {
+        if ((rc = launch_s4<S_JKAO>(ctx))) return rc;
+      } else {
+        if ((rc = launch_s4<S_JAO>(ctx))) return rc;
+        if ((rc = launch_s4<S_KAO>(ctx))) return rc;
+      }
+      dim3 g((nb + 31) / 32, (nb + 31) / 32, m), bl(32, 8);
+      if (sb->jao_sym) sym_mirror_kernel<<<g, bl, 0, ctx->stream>>>(sb->JKhi, sb->JKlo, nb, 0, sb->ldo, S4Cfg<S_JAO>::BN, 1);
+      sym_mirror_kernel<<<g, bl, 0, ctx->stream>>>(sb->JKhi, sb->JKlo, nb, m, sb->ldo, S4Cfg<S_KAO>::BN, 0);
+      DONOF_LAUNCH_CHECK(ctx);
+      DONOF_CUDA_TRY(cudaEventRecord(b, ctx->stream));
+      DONOF_CUDA_TRY(cudaEventSynchronize(b));
+      float ms = 0.f;
+      DONOF_CUDA_TRY(cudaEventElapsedTime(&ms, a, b));
+      if (r > 0) t[merged] += ms;
+    }
+    ++*tried;
+  }
+  sb->jk_merged = (t[0] < 0.97f * t[1]) ? 0 : 1;
   return DONOF_RI_OK;
 }
 
@@ -1775,6 +1893,9 @@ int s4_autotune(donof_ri_ctx* ctx, int reps, int* report, int* tried) {
   if (!rc) rc = s4_tune_kind<S_JAO>(ctx, reps, a, b, flush, fbytes, report, tried);
   if (!rc) rc = s4_tune_kind<S_KAO>(ctx, reps, a, b, flush, fbytes, report, tried);
   if (!rc) rc = s4_tune_kind<S_FOCK>(ctx, reps, a, b, flush, fbytes, report, tried);
+  s4_plan_jkao(ctx->s4);  // the merged J^(q) + K^(q) launch follows the tuned tile lists
+  if (!rc) rc = s4_tune_jk_merge(ctx, reps, a, b, flush, fbytes, tried);
+  if (!rc && report) report[S_KAO * 4 + 1] = ctx->s4->jk_merged;
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   cudaFree(flush);

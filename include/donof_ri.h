@@ -225,6 +225,22 @@ int donof_ri_iteration(donof_ri_ctx* ctx, const double* C, const double* gamma, 
                        double* E, double* lambda, int use_graph);
 
 /*
+ * Energy and Lagrangian in the contracted form: F^(p) C_p straight from the RI
+ * transforms, without the per-orbital AO matrices J^(q), K^(q):
+ *   J^(q) C_p = sum_P b^P_qq b^P_{p .},   K^(q) C_p = sum_P b^P_{q .} b^P_qp,
+ * so F^(p) C_p = n_p H C_p + sum_P w_pP b^P_{p .} - sum_P sum_q B_pq b^P_qp b^P_{q .}
+ * with w_pP = sum_q A_pq b^P_qq (one batched DGEMM over P of N_b x N_Omega x
+ * N_Omega, N_b N_aux N_Omega^2 multiply-adds in place of 2 N_b^2 N_aux N_Omega for
+ * J^(q), K^(q) and the Fock sum).  lambda and E as in donof_ri_energy_lagrangian,
+ * which gives the same values.  Needs the full transform b^P_qp: call after a
+ * FULL donof_ri_transform (no donof_ri_jk_ao_batch needed).  FP64 contexts; its
+ * scratch (N_aux N_Omega (1 + N_Omega + N_b) doubles) is allocated on first use.
+ * Errors: E_ARG, E_OOM, E_STATE (no FULL transform since the orbitals changed),
+ * E_UNSUPPORTED (precision other than DONOF_RI_FP64).
+ */
+int donof_ri_energy_lagrangian_contracted(donof_ri_ctx* ctx, const double* gamma, double* E, double* lambda);
+
+/*
  * Exact four-centre J and K for orbitals C (the conventional algorithm of Table 1,
  * Eqs. (Jpq), (Pmat), (Kpq), with exact s-type integrals (mu nu|l s) in place of
  * Eq. (AOERI)): the paper's RI -> exact restart finishes an RI-converged

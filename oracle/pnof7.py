@@ -139,6 +139,25 @@ def lagrangian(C, H, Jao, Kao, n, A, Bc) -> np.ndarray:
     return lam
 
 
+def lagrangian_contracted(C, H, bh, d, bf, n, A, Bc) -> np.ndarray:
+    """The same lambda without the per-orbital AO matrices (contracted form).
+
+    With b^P_{p mu} (bh), b^P_pp (d) and b^P_qp (bf) of the RI transforms,
+      J^(q) C_p = sum_P b^P_qq b^P_{p .},   K^(q) C_p = sum_P b^P_{q .} b^P_qp,
+    so F^(p) C_p = n_p H C_p + sum_P w_pP b^P_{p .} - sum_P sum_q B_pq b^P_qp b^P_{q .}
+    with w_pP = sum_q A_pq b^P_qq, and lambda_qp = C_q^T F^(p) C_p.
+    """
+    nb = C.shape[0]
+    m = n.shape[0]
+    w = A @ d.T                                             # w[p, P]
+    YJ = np.einsum("pP,Ppm->mp", w, bh)                     # sum_P w_pP b^P_{p mu}
+    YK = np.einsum("pq,Pqm,Pqp->mp", Bc, bh, bf)            # sum_P sum_q B_pq b^P_{q mu} b^P_qp
+    Y = (H @ C[:, :m]) * n[None, :] + YJ - YK               # F^(p) C_p, columns p
+    lam = np.zeros((nb, nb))
+    lam[:, :m] = C.T @ Y
+    return lam
+
+
 def energy_from_lagrangian(lam, n, Hmo_diag, e_nuc) -> float:
     """E = E_nuc + sum_p (n_p H_pp + lambda_pp)."""
     m = n.shape[0]

@@ -189,7 +189,7 @@ int donof_ri_destroy(donof_ri_ctx* ctx) {
                   ctx->d_aux_alpha, ctx->d_subspace, ctx->d_weak_rank, ctx->d_S, ctx->d_H, ctx->d_G, ctx->d_B,
                   ctx->d_enuc, ctx->d_scratch_max, ctx->d_C, ctx->d_bh, ctx->d_d, ctx->d_bf, ctx->d_J, ctx->d_K,
                   ctx->d_Jao, ctx->d_Kao, ctx->d_W, ctx->d_HC, ctx->d_Y, ctx->d_lambda, ctx->d_gamma, ctx->d_n,
-                  ctx->d_A, ctx->d_Bc, ctx->d_E, ctx->d_Hd, ctx->d_on, ctx->d_on_info, ctx->d_feat, ctx->d_rot,
+                  ctx->d_A, ctx->d_Bc, ctx->d_E, ctx->d_Hd, ctx->d_on, ctx->d_on_info, ctx->d_feat, ctx->d_rot, ctx->d_ctr,
                   ctx->d_status};
   for (void* b : bufs) dfree(b);
   free(ctx);
@@ -466,6 +466,21 @@ int donof_ri_autotune(donof_ri_ctx* ctx, int reps, int* report, int* tried) {
   }
   if (rc) return rc;
   return consume_status(ctx);
+}
+
+int donof_ri_energy_lagrangian_contracted(donof_ri_ctx* ctx, const double* gamma, double* E, double* lambda) {
+  if (!ctx || !gamma) return DONOF_RI_E_ARG;
+  if (ctx->precision != DONOF_RI_FP64) return DONOF_RI_E_UNSUPPORTED;
+  if (!ctx->have_full) return DONOF_RI_E_STATE;
+  const size_t nb = ctx->nbf, nx = ctx->naux, m = ctx->n_omega;
+  int rc;
+  if (!ctx->d_ctr && (rc = dalloc(&ctx->d_ctr, m * nx + nx * m * m + nx * nb * m))) return rc;
+  if ((rc = gamma_input(ctx, gamma))) return rc;
+  double* w = ctx->d_ctr;
+  double* X = w + m * nx;
+  double* Yp = X + nx * m * m;
+  if ((rc = path64_energy_contracted(ctx, w, X, Yp))) return rc;
+  return energy_outputs(ctx, E, lambda);
 }
 
 int donof_ri_exact_jk(donof_ri_ctx* ctx, const double* C, double* J, double* K) {

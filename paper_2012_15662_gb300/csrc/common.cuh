@@ -84,6 +84,7 @@ struct donof_ri_ctx {
   int* d_on_info;   // [2]
   float* d_feat;    // [N_I][3 + 4 N_g] learned-guess features
   double* d_rot;    // [4 nbf^2 + 2] rotation-step scratch (allocated on first use)
+  double* d_ctr;    // contracted-Lagrangian scratch (allocated on first use)
   int* d_status;    // [1] device-side status (DeviceStatus)
   // metric factorisation (DONOF_RI_METRIC_*) and, for the modified one, its
   // tolerance and counts: 2x2 pivots, raised eigenvalues, interchanges
@@ -157,6 +158,8 @@ int path64_jk_ao(donof_ri_ctx* ctx);
 // Fock weights, H C); MAIN needs J^(q), K^(q) as well (F^(p) C_p, lambda, E).
 enum EnergyPart { ENERGY_PREP = 1, ENERGY_MAIN = 2, ENERGY_ALL = 3 };
 int path64_energy(donof_ri_ctx* ctx, int part);
+// contracted Lagrangian (no J^(q), K^(q)); scratch w [N_Omega][naux], X [naux][N_Omega]^2, Yp [naux][nbf][N_Omega]
+int path64_energy_contracted(donof_ri_ctx* ctx, double* w, double* X, double* Yp);
 int launch_check_finite(donof_ri_ctx* ctx, const double* x, long long n);
 int launch_hc_public(donof_ri_ctx* ctx);
 int onopt_launch(donof_ri_ctx* ctx, double* d_gamma, double* d_E, double* d_grad, int* d_info, int mode,

@@ -322,6 +322,72 @@ int launch_lambda(donof_ri_ctx* ctx) {
 
 int launch_hc_public(donof_ri_ctx* ctx) { return launch_hc(ctx); }
 
+// ---------------------------------------------------------------------------
+// Contracted Lagrangian (FP64): F^(p) C_p straight from the RI transforms, without
+// the per-orbital AO matrices.  With w_pP = sum_q A_pq b^P_qq,
+//   F^(p) C_p = n_p H C_p + sum_P w_pP b^P_{p .} - sum_P sum_q B_pq b^P_qp b^P_{q .}
+//             = n_p H C_p - sum_P sum_q b^P_{q .} X^P_qp,
+//   X^P_qp = B_pq b^P_qp - [q = p] w_pP,
+// one batched DGEMM over P (per P: N_b x N_Omega x N_Omega) and a fixed-order sum
+// over P; then lambda = C^T Y and E as in the per-orbital form.
+// ---------------------------------------------------------------------------
+__global__ void contract_x_kernel(int naux, int n_om, const double* Bc, const double* bf, const double* w, double* X) {
+  pdl_entry();
+  const long long m2 = (long long)n_om * n_om;
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)naux * m2) return;
+  const int P = (int)(idx / m2);
+  const long long r = idx % m2;
+  const int q = (int)(r / n_om), p = (int)(r % n_om);
+  double x = Bc[(long long)p * n_om + q] * bf[idx];
+  if (q == p) x -= w[(long long)p * naux + P];
+  X[idx] = x;
+}
+
+// Y[mu][p] = n_p HC[mu][p] - sum_P Yp[P][mu][p], P in increasing order.
+__global__ void contract_sum_kernel(int naux, int nbf, int n_om, const double* Yp, const double* HC, const double* n,
+                                    double* Y) {
+  pdl_entry();
+  const long long nm = (long long)nbf * n_om;
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= nm) return;
+  double s = 0.0;
+  for (int P = 0; P < naux; ++P) s += Yp[(long long)P * nm + idx];
+  Y[idx] = n[idx % n_om] * HC[idx] - s;
+}
+
+int path64_energy_contracted(donof_ri_ctx* ctx, double* w, double* X, double* Yp) {
+  const int nb = ctx->nbf, nx = ctx->naux, m = ctx->n_omega;
+  int rc;
+  ProfScope ps(ctx, DONOF_RI_ROW_ENERGY);
+  if ((rc = launch_occupations_coupling(ctx))) return rc;
+  if ((rc = launch_hc(ctx))) return rc;
+  // w[p][P] = sum_q A_pq b^P_qq
+  Gemm64 g{};
+  g.M = m; g.N = nx; g.K = m; g.batch = 1;
+  g.A = ctx->d_A; g.sAm = m; g.sAk = 1;
+  g.B = ctx->d_d; g.sBk = 1; g.sBn = m;
+  g.C = w; g.sCm = nx; g.sCn = 1;
+  g.alpha = 1.0; g.beta = 0.0;
+  if ((rc = launch_dgemm(ctx, g))) return rc;
+  launch_pdl(contract_x_kernel, dim3(ceil_div_u((long long)nx * m * m, 256)), dim3(256), 0, ctx->stream, nx, m,
+             (const double*)ctx->d_Bc, (const double*)ctx->d_bf, (const double*)w, X);
+  DONOF_LAUNCH_CHECK(ctx);
+  // Yp[P][mu][p] = sum_q b^P_{q mu} X^P_qp
+  Gemm64 h{};
+  h.M = nb; h.N = m; h.K = m; h.batch = nx;
+  h.A = ctx->d_bh; h.sAb = (long long)m * nb; h.sAm = 1; h.sAk = nb;
+  h.B = X; h.sBb = (long long)m * m; h.sBk = m; h.sBn = 1;
+  h.C = Yp; h.sCb = (long long)nb * m; h.sCm = m; h.sCn = 1;
+  h.alpha = 1.0; h.beta = 0.0;
+  if ((rc = launch_dgemm(ctx, h))) return rc;
+  launch_pdl(contract_sum_kernel, dim3(ceil_div_u((long long)nb * m, 256)), dim3(256), 0, ctx->stream, nx, nb, m,
+             (const double*)Yp, (const double*)ctx->d_HC, (const double*)ctx->d_n, ctx->d_Y);
+  DONOF_LAUNCH_CHECK(ctx);
+  if ((rc = launch_lambda(ctx))) return rc;
+  return launch_energy_reduce(ctx);
+}
+
 int path64_energy(donof_ri_ctx* ctx, int part) {
   const int nb = ctx->nbf, m = ctx->n_omega;
   const long long nb2 = (long long)nb * nb;

@@ -180,3 +180,23 @@ def test_energy_gradient_wrt_gamma_is_finite_and_consistent(sq):
         d1 = (e1(gp) - e1(gm)) / (2 * h)
         d2 = (e2(gp) - e2(gm)) / (2 * h)
         assert np.isfinite(d1) and abs(d1 - d2) < 1e-7
+
+
+@pytest.mark.parametrize("name", ["square4", "c6h12"])
+def test_contracted_lagrangian_equals_the_per_orbital_form(name):
+    """lambda from the RI transforms directly (no J^(q), K^(q)) equals lambda from
+    the per-orbital AO matrices: two routes through the same algebra."""
+    from oracle import integrals as I, pnof7, ri
+    from synthetic import make_workload, pairing_columns
+    w = make_workload(name)
+    s = w.system
+    m = s.n_omega
+    B, L, G = ri.setup(s)
+    r = ri.all_rows(B, w.C, m)
+    sub, rank = pairing_columns(s.n_strong, s.n_weak_per)
+    n = pnof7.occupations(w.gamma, s.n_strong, s.n_weak_per, sub, rank)
+    A, Bc = pnof7.coupling(n, sub, rank)
+    H = I.core_hamiltonian(s)
+    lam = pnof7.lagrangian(w.C, H, r["Jao"], r["Kao"], n, A, Bc)
+    lam_c = pnof7.lagrangian_contracted(w.C, H, r["bh"], r["d"], r["bf"], n, A, Bc)
+    np.testing.assert_allclose(lam_c, lam, atol=1e-11 * np.abs(lam).max())

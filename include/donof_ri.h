@@ -225,6 +225,31 @@ int donof_ri_iteration(donof_ri_ctx* ctx, const double* C, const double* gamma, 
                        double* E, double* lambda, int use_graph);
 
 /*
+ * The paper's orbital step (Sec. 2, "Orbital Optimization with RI"): diagonalise
+ * the symmetric matrix F^lambda built from the Lagrangian of the last
+ * donof_ri_energy_lagrangian and rotate the orbitals onto its eigenvectors, in
+ * increasing order of eigenvalue (aufbau):
+ *   F_qp = lambda_qp - lambda_pq for q > p (mirrored); an element larger than
+ *   `bound` in magnitude is scaled by the smallest power of 1/10 that brings it to
+ *   `bound` or below; F_pp = diag[p] (the previous step's eigenvalues), or
+ *   lambda_pp when `first` is nonzero.
+ * At a stationary point (lambda symmetric) the step changes nothing.  The
+ * eigenproblem is solved in FP32 by cyclic Jacobi in one CTA with the rotation
+ * kept as V - I; C V is formed in FP64 and re-orthonormalised by one
+ * Newton-Schulz step.  nbf <= 160.
+ *   diag    [nbf] in (unless first) / out: the eigenvalues, host or device
+ *   bound   > 0
+ *   C       out or NULL: the rotated orbitals (column-major, host or device); the
+ *           context keeps them, and the next transform must be called with them
+ *   gmax    out (host) or NULL: max |lambda_qp - lambda_pq| before the step
+ *   sweeps  out (host) or NULL: Jacobi sweeps used (at most 30)
+ * Synchronous.  Errors: E_ARG, E_OOM, E_STATE (no Lagrangian since the orbitals
+ * last changed), E_NONFINITE (diag), E_UNSUPPORTED (nbf > 160).
+ */
+int donof_ri_flambda_step(donof_ri_ctx* ctx, double* diag, int first, double bound, double* C, double* gmax,
+                          int* sweeps);
+
+/*
  * Energy and Lagrangian in the contracted form: F^(p) C_p straight from the RI
  * transforms, without the per-orbital AO matrices J^(q), K^(q):
  *   J^(q) C_p = sum_P b^P_qq b^P_{p .},   K^(q) C_p = sum_P b^P_{q .} b^P_qp,

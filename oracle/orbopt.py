@@ -5,9 +5,10 @@ Test infrastructure only; see the package docstring.
 Sec. 2, "Orbital Optimization with RI": the energy is minimised over real
 orthonormal orbitals at fixed occupations, with J^(q), K^(q) recomputed at every
 inner iteration and the Lagrangian lambda driving the step.  The paper's own
-step (iterative diagonalisation of F^lambda) is a later addition; this module
-states the plain driver it replaces: the orbitals rotate as C -> C expm(kappa)
-with kappa a steepest-descent step on the rotation gradient
+step, the iterative diagonalisation of a symmetric matrix F^lambda built from
+lambda (flambda_matrix, flambda_step), is stated here with the plain driver:
+the orbitals rotate as C -> C expm(kappa) with kappa a steepest-descent step on
+the rotation gradient
   dE/dkappa_qp = 4 (lambda_qp - lambda_pq)          (pinned in test_oracle_pnof7)
 of length controlled by a trust radius: kappa = -r G / max|G|, G = lambda -
 lambda^T; a step that raises E is rejected and halves r, an accepted one grows r
@@ -28,6 +29,34 @@ def rotation_step(C: np.ndarray, lam: np.ndarray, radius: float) -> np.ndarray:
     if gmax == 0.0:
         return C.copy()
     return C @ expm(-radius * G / gmax)
+
+
+def flambda_matrix(lam: np.ndarray, diag: np.ndarray, bound: float) -> np.ndarray:
+    """The symmetric matrix F^lambda of the iterative-diagonalisation step.
+
+    Off-diagonal F_qp = lambda_qp - lambda_pq for q > p, mirrored (the orbital
+    gradient, which vanishes at a stationary point); every off-diagonal element
+    larger than `bound` in magnitude is scaled by the smallest power of 1/10 that
+    brings it to `bound` or below (the paper gives no scaling rule; DoNOF damps the
+    large elements this way); the diagonal is `diag` (the aufbau ordering: the
+    previous step's eigenvalues, lambda_pp at the first step).
+    """
+    G = lam - lam.T
+    F = np.tril(G, -1)
+    F = F + F.T
+    a = np.abs(F)
+    k = np.where(a > bound, np.ceil(np.log10(np.maximum(a, 1e-300) / bound)), 0.0)
+    F = F * 10.0 ** (-k)
+    F[np.diag_indices_from(F)] = diag
+    return F
+
+
+def flambda_step(C: np.ndarray, lam: np.ndarray, diag: np.ndarray, bound: float):
+    """One step of the paper's orbital optimisation (Sec. 2, "Orbital Optimization
+    with RI"): diagonalise F^lambda and rotate the orbitals onto its eigenvectors,
+    taken in increasing order of eigenvalue (aufbau).  Returns (C U, eigenvalues)."""
+    eps, U = np.linalg.eigh(flambda_matrix(lam, diag, bound))
+    return C @ U, eps
 
 
 def energy_lambda(system, B, H, e_nuc, C, gamma, subspace, weak_rank):

@@ -49,7 +49,7 @@ EXPORTS = [
     "donof_ri_strerror", "donof_ri_launch_count", "donof_ri_profile", "donof_ri_profile_read",
     "donof_ri_iteration", "donof_ri_jmo_noalloc", "donof_ri_optimize_occupations",
     "donof_ri_on_features", "donof_ri_gamma_guess", "donof_ri_rotate_orbitals", "donof_ri_autotune", "donof_ri_set_schedule", "donof_ri_exact_jk",
-    "donof_ri_energy_lagrangian_contracted",
+    "donof_ri_energy_lagrangian_contracted", "donof_ri_flambda_step",
     "donof_mlp_create", "donof_mlp_param_count", "donof_mlp_set_params", "donof_mlp_get_params",
     "donof_mlp_set_normalization", "donof_mlp_forward", "donof_mlp_loss_grad", "donof_mlp_train_step",
     "donof_mlp_destroy",
@@ -126,6 +126,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.donof_ri_exact_jk.restype = i
     lib.donof_ri_energy_lagrangian_contracted.argtypes = [vp, vp, vp, vp]
     lib.donof_ri_energy_lagrangian_contracted.restype = i
+    lib.donof_ri_flambda_step.argtypes = [vp, vp, i, d, vp, ctypes.POINTER(d), ctypes.POINTER(i)]
+    lib.donof_ri_flambda_step.restype = i
     lib.donof_ri_set_schedule.restype = i
     lib.donof_ri_rotate_orbitals.argtypes = [vp, d, vp, vp]
     lib.donof_ri_rotate_orbitals.restype = i
@@ -288,6 +290,15 @@ def donof_ri_energy_lagrangian_contracted(ctx, gamma, E=None, lam=None):
     """E and lambda without the per-orbital AO matrices (after a FULL transform; FP64 contexts)."""
     _check(load().donof_ri_energy_lagrangian_contracted(ctx, _ptr(gamma), _ptr(E), _ptr(lam)),
            "donof_ri_energy_lagrangian_contracted")
+
+
+def donof_ri_flambda_step(ctx, diag, first: bool, bound: float, C=None):
+    """One F^lambda step: diag (float64 [nbf], in unless first, out: eigenvalues); returns (gmax, sweeps)."""
+    g = ctypes.c_double()
+    sw = ctypes.c_int()
+    _check(load().donof_ri_flambda_step(ctx, _ptr(diag), 1 if first else 0, float(bound), _ptr(C), ctypes.byref(g),
+                                        ctypes.byref(sw)), "donof_ri_flambda_step")
+    return g.value, sw.value
 
 
 def donof_ri_exact_jk(ctx, C, J=None, K=None):

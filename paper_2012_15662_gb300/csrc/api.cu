@@ -189,7 +189,7 @@ int donof_ri_destroy(donof_ri_ctx* ctx) {
                   ctx->d_aux_alpha, ctx->d_subspace, ctx->d_weak_rank, ctx->d_S, ctx->d_H, ctx->d_G, ctx->d_B,
                   ctx->d_enuc, ctx->d_scratch_max, ctx->d_C, ctx->d_bh, ctx->d_d, ctx->d_bf, ctx->d_J, ctx->d_K,
                   ctx->d_Jao, ctx->d_Kao, ctx->d_W, ctx->d_HC, ctx->d_Y, ctx->d_lambda, ctx->d_gamma, ctx->d_n,
-                  ctx->d_A, ctx->d_Bc, ctx->d_E, ctx->d_Hd, ctx->d_on, ctx->d_on_info, ctx->d_feat, ctx->d_rot, ctx->d_ctr,
+                  ctx->d_A, ctx->d_Bc, ctx->d_E, ctx->d_Hd, ctx->d_on, ctx->d_on_info, ctx->d_feat, ctx->d_rot, ctx->d_ctr, ctx->d_fl,
                   ctx->d_status};
   for (void* b : bufs) dfree(b);
   free(ctx);
@@ -537,6 +537,38 @@ int donof_ri_rotate_orbitals(donof_ri_ctx* ctx, double radius, double* C, double
 // that it runs concurrently with the transforms; joined before F^(p) C_p.  The
 // buffers it writes are read by no kernel of the transforms.  Not used while
 // per-row profiling is on (the row events are recorded on the main stream).
+int donof_ri_flambda_step(donof_ri_ctx* ctx, double* diag, int first, double bound, double* C, double* gmax,
+                          int* sweeps) {
+  if (!ctx || !(bound > 0.0) || (!first && !diag)) return DONOF_RI_E_ARG;
+  if (!ctx->have_lambda) return DONOF_RI_E_STATE;
+  if (ctx->nbf > 160) return DONOF_RI_E_UNSUPPORTED;
+  const size_t nb = ctx->nbf, nb2 = nb * nb;
+  int rc;
+  const size_t fls = flambda_scratch_doubles(ctx->nbf);
+  if (!ctx->d_fl && (rc = dalloc(&ctx->d_fl, fls + nb))) return rc;
+  double* dprev = ctx->d_fl + fls;  // previous eigenvalues (device copy)
+  if (!first) {
+    DONOF_CUDA_TRY(cudaMemcpyAsync(dprev, diag, nb * sizeof(double),
+                                   is_device_ptr(diag) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                   ctx->stream));
+    if ((rc = launch_check_finite(ctx, dprev, (long long)nb))) return rc;
+  }
+  double g = 0.0;
+  int sw = 0;
+  {
+    ProfScope ps(ctx, DONOF_RI_ROW_OTHER);
+    if ((rc = flambda_step(ctx, dprev, first ? 1 : 0, bound, ctx->d_fl, &g, &sw))) return rc;
+  }
+  ctx->have_half = ctx->have_full = ctx->have_ao = ctx->have_lambda = 0;
+  if (gmax) *gmax = g;
+  if (sweeps) *sweeps = sw;
+  bool host = false;
+  const double* eps = ctx->d_fl + 6 * nb2;
+  if (diag && (rc = copy_out(ctx, diag, eps, nb, &host))) return rc;
+  if ((rc = copy_out(ctx, C, ctx->d_C, nb2, &host))) return rc;
+  return consume_status(ctx);
+}
+
 static int iteration_forked(donof_ri_ctx* ctx, const double* C, const double* gamma, int mode, double* J, double* K,
                             double* E, double* lambda) {
   int rc = transform_input(ctx, C);

@@ -85,6 +85,7 @@ struct donof_ri_ctx {
   float* d_feat;    // [N_I][3 + 4 N_g] learned-guess features
   double* d_rot;    // [4 nbf^2 + 2] rotation-step scratch (allocated on first use)
   double* d_ctr;    // contracted-Lagrangian scratch (allocated on first use)
+  double* d_fl;     // F^lambda step scratch (allocated on first use)
   int* d_status;    // [1] device-side status (DeviceStatus)
   // metric factorisation (DONOF_RI_METRIC_*) and, for the modified one, its
   // tolerance and counts: 2x2 pivots, raised eigenvalues, interchanges
@@ -170,6 +171,10 @@ int s4_autotune(donof_ri_ctx* ctx, int reps, int* report, int* tried);
 int s4_set_schedule(donof_ri_ctx* ctx, int kind, int stages, int option);
 // exact.cu: exact four-centre J^(q), K^(q), J, K into an FP64 context's buffers
 int exact_jk(donof_ri_ctx* ctx);
+// flambda.cu: one F^lambda step on ctx->d_C (nbf <= 160); scratch flambda_scratch_doubles(nbf) doubles
+size_t flambda_scratch_doubles(int n);
+int flambda_step(donof_ri_ctx* ctx, const double* dprev, int first, double bound, double* scratch, double* gmax,
+                 int* sweeps);
 int onopt_unfold(donof_ri_ctx* ctx, const float* d_Y, double clip, double* d_gamma);
 int mlp_forward_device(donof_mlp* n, const float* dX, int B, float** dY);
 int mlp_shape(const donof_mlp* n, int* F, int* O);

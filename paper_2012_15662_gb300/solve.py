@@ -5,10 +5,11 @@ scheme is the paper's (Sec. 2, Fig. "general scheme"): an outer iteration
 optimises the occupations for fixed orbitals (J, K from one FULL transform,
 donof_ri_optimize_occupations), and inner iterations optimise the orbitals for
 fixed occupations (J^(q), K^(q) and the Lagrangian recomputed at every step).
-The inner step here is the plain rotation driver (donof_ri_rotate_orbitals:
-steepest descent on dE/dkappa = 4 (lambda - lambda^T) with a trust radius that
-grows by 1.5 after an accepted step and halves after a rejected one); the
-paper's iterative diagonalisation of F^lambda is a later replacement.
+Two inner steps: the plain rotation driver (donof_ri_rotate_orbitals: steepest
+descent on dE/dkappa = 4 (lambda - lambda^T) with a trust radius that grows by
+1.5 after an accepted step and halves after a rejected one), and the paper's
+iterative diagonalisation of F^lambda (donof_ri_flambda_step,
+flambda_iterations) with the same accept / reject control on its damping bound.
 """
 from __future__ import annotations
 
@@ -78,6 +79,55 @@ def orbital_iterations(eng, C_colmajor, gamma, max_iter=100, gtol=1e-4, etol=1e-
     dt = time.perf_counter() - t0
     return dict(C=st.C.cpu().numpy().copy(), E=E, gmax=gmax, iterations=it, evaluations=evals,
                 ms_per_iteration=1000.0 * dt / max(it, 1), radius=radius)
+
+
+def flambda_iterations(eng, C_colmajor, gamma, max_iter=100, gtol=1e-4, etol=1e-10, bound=0.1, bound_max=1.0):
+    """Inner iterations with the paper's step (donof_ri_flambda_step): F^lambda from the
+    Lagrangian, eigenvalues of the accepted step as the next diagonal (lambda_pp at the
+    first), off-diagonal elements damped to `bound`; a step that raises E is rejected
+    and halves the bound, an accepted one grows it by 1.5 (up to bound_max).
+    Returns dict(C, E, gmax, iterations, evaluations, energies, ms_per_iteration)."""
+    import torch
+    st = _Inner(eng)
+    nb = eng.nbf
+    gamma = np.ascontiguousarray(gamma, dtype=np.float64)
+    st.C.copy_(torch.as_tensor(np.ascontiguousarray(C_colmajor).reshape(-1)) if isinstance(C_colmajor, np.ndarray)
+               else C_colmajor.reshape(-1))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    E = st.evaluate(st.C, gamma)
+    energies = [E]
+    diag = np.zeros(nb)
+    have_diag = False
+    evals, gmax, it = 1, float("inf"), 0
+    for it in range(1, max_iter + 1):
+        trial = np.empty(nb)
+        if have_diag:
+            trial[:] = diag
+        gmax, _ = bd.donof_ri_flambda_step(eng.ctx, trial, not have_diag, bound, st.C_try)
+        if gmax <= gtol:
+            it -= 1
+            break
+        En = st.evaluate(st.C_try, gamma)
+        evals += 1
+        if En < E:
+            dec = E - En
+            st.C, st.C_try = st.C_try, st.C
+            E = En
+            diag[:] = trial
+            have_diag = True
+            bound = min(1.5 * bound, bound_max)
+            energies.append(E)
+            if dec <= etol * max(1.0, abs(E)):
+                break
+        else:
+            bound *= 0.5
+            E = st.evaluate(st.C, gamma)  # the Lagrangian of the accepted orbitals
+            evals += 1
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return dict(C=st.C.cpu().numpy().copy(), E=E, gmax=gmax, iterations=it, evaluations=evals, energies=energies,
+                ms_per_iteration=1000.0 * dt / max(it, 1))
 
 
 def solve(eng, C0, gamma0, max_outer=10, max_inner=50, etol=1e-6, gtol=1e-4, on_max_iter=20000):

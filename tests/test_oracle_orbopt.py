@@ -48,3 +48,40 @@ def test_driver_never_raises_energy(sq):
     assert E < E0
     g0 = np.abs(lam - lam.T).max()
     assert gmax < g0
+
+
+def test_flambda_step_is_the_identity_at_a_stationary_point(sq):
+    """lambda symmetric (a stationary point): F^lambda is diagonal, and with an
+    ascending diagonal the step keeps every orbital (up to its sign)."""
+    w, B, H, enuc, sub, rank = sq
+    nb = w.system.nbf
+    rng = np.random.default_rng(4)
+    S = rng.standard_normal((nb, nb))
+    lam = S + S.T
+    D = np.sort(rng.uniform(-3.0, 3.0, nb))
+    C1, eps = orbopt.flambda_step(w.C, lam, D, bound=0.1)
+    np.testing.assert_allclose(np.abs(C1.T @ w.C), np.eye(nb), atol=1e-12)
+    np.testing.assert_allclose(eps, D, atol=1e-12)
+
+
+def test_flambda_step_descends_by_the_first_order_amount(sq):
+    """With small off-diagonal elements and an ascending diagonal the eigenvectors are
+    U = I + kappa with kappa_qp = F_qp / (D_pp - D_qq), so E changes by
+    4 sum_{q>p} (lambda_qp - lambda_pq) U_qp to first order, and the change is a
+    descent (a reversed F^lambda off-diagonal would climb)."""
+    w, B, H, enuc, sub, rank = sq
+    s = w.system
+    nb = s.nbf
+    E0, lam = orbopt.energy_lambda(s, B, H, enuc, w.C, w.gamma, sub, rank)
+    G = lam - lam.T
+    D = np.arange(nb, dtype=np.float64)          # ascending, unit gaps
+    bound = 1e-5 * np.abs(G).max()
+    C1, eps = orbopt.flambda_step(w.C, lam, D, bound)
+    U = w.C.T @ C1
+    U = U * np.sign(np.diag(U))[None, :]         # eigenvector signs as near the identity
+    E1, _ = orbopt.energy_lambda(s, B, H, enuc, w.C @ U, w.gamma, sub, rank)
+    il = np.tril_indices(nb, -1)
+    predicted = 4.0 * np.sum(G[il] * U[il])
+    assert predicted < 0.0 and E1 < E0
+    assert abs((E1 - E0) - predicted) <= 2e-2 * abs(predicted)
+    np.testing.assert_allclose(U.T @ U, np.eye(nb), atol=1e-12)

@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(1024, 1) flambda_jacobi_kernel(int n, const do
   for (int o = 16; o > 0; o >>= 1) gm = fmax(gm, __shfl_xor_sync(0xffffffffu, gm, o));
   if (lane == 0) redd[wid] = gm;
   __syncthreads();
-  if (tid == 0) {
+  if (tid == 0 && gmax) {
     double m = 0.0;
     for (int w = 0; w < nt / 32; ++w) m = fmax(m, redd[w]);
     *gmax = m;
@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(1024, 1) flambda_jacobi_kernel(int n, const do
     const int j = perm[k];
     U[e] = (i == j ? 1.0 : 0.0) + (double)X[i * ld + j];  // U[i][k], row-major
   }
-  if (tid == 0) *sweeps_out = sweep;
+  if (tid == 0 && sweeps_out) *sweeps_out = sweep;
 }
 
 __global__ void fl_identity_axpy_kernel(int n, double a, double b, const double* X, double* M) {
@@ -248,6 +248,32 @@ static int fl_mm(donof_ri_ctx* ctx, int n, const double* A, bool at, const doubl
   return launch_dgemm(ctx, g);
 }
 
+// U <- U (3 I - U^T U) / 2, then two refinements U <- orth(U (I + K)) against the
+// FP64 matrix Fd; eps <- the refined eigenvalues.  T, W, Z, K: n x n scratch.
+static int eig_refine(donof_ri_ctx* ctx, int n, const double* Fd, double* U, double* T, double* W, double* Z,
+                      double* K, double* eps) {
+  const long long n2 = (long long)n * n;
+  const unsigned nblk = ceil_div_u(n2, 256);
+  int rc;
+  for (int pass = 0; pass < 3; ++pass) {
+    if (pass > 0) {
+      if ((rc = fl_mm(ctx, n, Fd, false, U, false, T, 1.0, 0.0))) return rc;   // T = F U
+      if ((rc = fl_mm(ctx, n, U, true, T, false, W, 1.0, 0.0))) return rc;    // A' = U^T F U
+      fl_refine_kernel<<<nblk, 256, 0, ctx->stream>>>(n, W, K, eps);
+      DONOF_LAUNCH_CHECK(ctx);
+      if ((rc = fl_mm(ctx, n, U, false, K, false, T, 1.0, 0.0))) return rc;   // T = U K
+      fl_add_kernel<<<nblk, 256, 0, ctx->stream>>>(n2, T, U);
+      DONOF_LAUNCH_CHECK(ctx);
+    }
+    if ((rc = fl_mm(ctx, n, U, true, U, false, W, 1.0, 0.0))) return rc;      // W = U^T U
+    fl_identity_axpy_kernel<<<nblk, 256, 0, ctx->stream>>>(n, 1.5, -0.5, W, Z);
+    DONOF_LAUNCH_CHECK(ctx);
+    if ((rc = fl_mm(ctx, n, U, false, Z, false, T, 1.0, 0.0))) return rc;     // T = U Z
+    DONOF_CUDA_TRY(cudaMemcpyAsync(U, T, n2 * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  return DONOF_RI_OK;
+}
+
 // One step on ctx->d_C (column-major = row-major C^T).  Scratch:
 // flambda_scratch_doubles(n) doubles.  The FP32 eigenvectors are orthonormalised
 // (Newton-Schulz) and refined twice in FP64 against the FP64 F^lambda by first-order
@@ -270,23 +296,7 @@ int flambda_step(donof_ri_ctx* ctx, const double* dprev, int first, double bound
   DONOF_LAUNCH_CHECK(ctx);
   ctx->launches++;
   int rc;
-  // U <- U (3 I - U^T U) / 2, then two refinements U <- orth(U (I + K))
-  for (int pass = 0; pass < 3; ++pass) {
-    if (pass > 0) {
-      if ((rc = fl_mm(ctx, n, Fd, false, U, false, T, 1.0, 0.0))) return rc;   // T = F U
-      if ((rc = fl_mm(ctx, n, U, true, T, false, W, 1.0, 0.0))) return rc;    // A' = U^T F U
-      fl_refine_kernel<<<nblk, 256, 0, ctx->stream>>>(n, W, K, eps);
-      DONOF_LAUNCH_CHECK(ctx);
-      if ((rc = fl_mm(ctx, n, U, false, K, false, T, 1.0, 0.0))) return rc;   // T = U K
-      fl_add_kernel<<<nblk, 256, 0, ctx->stream>>>(n2, T, U);
-      DONOF_LAUNCH_CHECK(ctx);
-    }
-    if ((rc = fl_mm(ctx, n, U, true, U, false, W, 1.0, 0.0))) return rc;      // W = U^T U
-    fl_identity_axpy_kernel<<<nblk, 256, 0, ctx->stream>>>(n, 1.5, -0.5, W, Z);
-    DONOF_LAUNCH_CHECK(ctx);
-    if ((rc = fl_mm(ctx, n, U, false, Z, false, T, 1.0, 0.0))) return rc;     // T = U Z
-    DONOF_CUDA_TRY(cudaMemcpyAsync(U, T, n2 * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
-  }
+  if ((rc = eig_refine(ctx, n, Fd, U, T, W, Z, K, eps))) return rc;
   // (C U)^T = U^T C^T, then one Newton-Schulz step on its rows
   if ((rc = fl_mm(ctx, n, U, true, ctx->d_C, false, T, 1.0, 0.0))) return rc;
   if ((rc = fl_mm(ctx, n, T, false, T, true, W, 1.0, 0.0))) return rc;        // W = T T^T

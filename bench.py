@@ -47,6 +47,18 @@ ROWS = ["half", "diag", "full_k", "j", "jao", "kao", "energy", "other"]
 # Profile rows 8..13: the tensor-core GEMM kernel of a row, timed alone.
 GEMMS = ["half", "full_k", "j", "jao", "kao", "fock"]
 GEMM_KERNEL = {"slice4": "s4_gemm_kernel<{}>", "tf32x3": "tc_gemm_kernel<{}>"}
+# Profile rows 14, 15: the memory-bound passes of SLICE4, timed alone.
+MEMS = {"digits": "xf_to_digits_kernel", "split": "slice_pair_kernel"}
+
+
+def algorithmic_bytes(s):
+    """Bytes each memory-bound pass must move per launch (unpadded element counts).
+    digits: b_half integers read (4 B), its L3 and L6 digit layouts written (8 B each),
+    the diagonal partials written (8 B per 64-wide nu tile); split: J^(q), K^(q) read as
+    FP32 pairs (8 B) and written as four BF16 digit planes (8 B), one exponent per row."""
+    nb, nx, m = s.nbf, s.naux, s.n_omega
+    return {"digits": nx * m * nb * (4 + 8 + 8) + ((nb + 63) // 64) * m * nx * 8,
+            "split": 2 * m * nb * nb * (8 + 8) + 2 * m * nb * 4}
 
 
 def workload_desc(name):
@@ -345,6 +357,11 @@ def main():
         t, c = bd.donof_ri_profile_read(eng.ctx, len(ROWS) + i)
         if c > 0:
             gemms[r] = (t, c)
+    mems = {}
+    for i, r in enumerate(MEMS):
+        t, c = bd.donof_ri_profile_read(eng.ctx, len(ROWS) + len(GEMMS) + i)
+        if c > 0:
+            mems[r] = (t, c)
     bd.donof_ri_profile(eng.ctx, False)
     ms = float(np.mean(step_ms))
     value = job_ms_per_iteration(ms * args.steps, args.steps, world, dev)
@@ -430,6 +447,16 @@ def main():
 
     if rank != 0:
         return 0
+    # the memory-bound passes against the measured copy bandwidth (algorithmic bytes
+    # over each launch's own events)
+    hbm_peak = _peak_value(peaks, "hbm_gbs") or FALLBACK_PEAKS["hbm_gbs"]
+    nbytes = algorithmic_bytes(s)
+    hbm_kernels = {}
+    for r, (t, c) in mems.items():
+        us = 1000.0 * t / c
+        gbs = nbytes[r] / (us * 1e-6) / 1e9
+        hbm_kernels[r] = {"kernel": MEMS[r], "bytes_per_launch": int(nbytes[r]), "us_per_launch": us,
+                          "achieved_gbs": gbs, "peak_gbs": hbm_peak, "frac": gbs / hbm_peak}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
@@ -441,6 +468,7 @@ def main():
                    "parallelism": f"replicas x{world}", "autotune": tuned},
         "rows_ms_per_step": {r: rows[r][0] / args.steps for r in ROWS},
         "gemm_kernels_ms_per_step": {r: gemms[r][0] / args.steps for r in gemms},
+        "hbm_kernels": hbm_kernels,
         "roofline": roof, "clocks": clocks, "gpu_launches": int(launches), "e2e": e2e,
     }
     if world == 1 and not args.no_cpu_baseline:

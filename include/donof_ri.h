@@ -329,7 +329,11 @@ long long donof_ri_launch_count(const donof_ri_ctx* ctx);
 #define DONOF_RI_GEMM_JAO 11     /* a5 GEMM                                           */
 #define DONOF_RI_GEMM_KAO 12     /* a6 GEMM                                           */
 #define DONOF_RI_GEMM_FOCK 13    /* a7 GEMM: sum_q (A_pq J^(q) - B_pq K^(q)) C_p      */
-#define DONOF_RI_NUM_ROWS 14
+/* The memory-bound passes of SLICE4 alone (one event pair around the launch, nested
+ * inside its row's; the other forms record none). */
+#define DONOF_RI_MEM_DIGITS 14   /* a1/a2: b_half's two digit layouts + diagonal partials */
+#define DONOF_RI_MEM_SPLIT 15    /* a5/a6: J^(q), K^(q) as digit planes for a7's GEMM    */
+#define DONOF_RI_NUM_ROWS 16
 
 /*
  * Enable (1) or disable (0) per-row timing.  While enabled, every launch group

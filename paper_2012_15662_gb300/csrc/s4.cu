@@ -41,9 +41,6 @@
 #include <vector>
 
 namespace donof {
-int launch_dot64(donof_ri_ctx* ctx, int M, int N, int K, const double* A, int lda, const double* B, int ldb,
-                 double* out, long long so_i, long long so_j);
-int launch_energy_rows(donof_ri_ctx* ctx, const double* HCt);
 
 // S_HALF1: the half transform with one CTA per SM, two accumulator sets and two
 // epilogue warpgroups (the layout of the other kinds); the autotuner chooses
@@ -149,6 +146,20 @@ __device__ __forceinline__ void digits_bf16(int X, __nv_bfloat16 d[4]) {
   }
 }
 
+// The digits of two integers at once, as BF16 pairs (d[t].x from X0, d[t].y from X1):
+// the same exact digit values, each pair rounded to BF16 by one packed conversion
+// (exact: every digit has at most 8 significant bits).
+__device__ __forceinline__ void digits_bf16x2(int X0, int X1, __nv_bfloat162 d[4]) {
+  const unsigned int U0 = (unsigned int)X0 + 0x80808080u, U1 = (unsigned int)X1 + 0x80808080u;
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const unsigned int sel = 0x7440u | (unsigned int)(3 - t);
+    const float x0 = __uint_as_float(__byte_perm(U0, 0x4B000000u, sel)) - 8388736.0f;
+    const float x1 = __uint_as_float(__byte_perm(U1, 0x4B000000u, sel)) - 8388736.0f;
+    d[t] = __floats2bfloat162_rn(x0, x1);
+  }
+}
+
 // Exponent e with |x| < 2^(e-1) for every |x| <= amax (amax >= 0); 0 for amax == 0.
 __device__ __forceinline__ int expo_of(double amax) {
   if (!(amax > 0.0)) return 0;
@@ -156,6 +167,36 @@ __device__ __forceinline__ int expo_of(double amax) {
   frexp(amax, &k);
   return k + 1;
 }
+
+// expo_of((double)mx * (1 + 2^-16)) for an FP32 bound mx, in integer arithmetic
+// (the product is exact in FP64: 24 x 17 significant bits).  With mx = I0 2^(E-150),
+// I0 = 2^23 + mantissa, the product is I0 (2^16 + 1) 2^(E-166), whose frexp
+// exponent is E - 126, or E - 125 once I0 (2^16 + 1) reaches 2^40.  Zero,
+// subnormal and non-finite bounds take the FP64 route.  (FP64 instructions run
+// at a small fraction of the FP32 rate; these bounds are taken once per row.)
+__device__ __forceinline__ int expo_of_inflated(float mx) {
+  const unsigned int b = __float_as_uint(mx);
+  const int E = (int)((b >> 23) & 0xFFu);
+  if (mx > 0.f && E > 0 && E < 255) {
+    const unsigned long long I = (unsigned long long)((b & 0x7FFFFFu) | 0x800000u) * 65537ull;
+    return E - 125 + (I >= (1ull << 40) ? 1 : 0);
+  }
+  return expo_of((double)mx * (1.0 + 1.0 / 65536.0));
+}
+
+// x 2^k for FP64 x: one multiplication by an exact power of two while 2^k is a
+// normal double (the same correctly rounded result as ldexp), ldexp beyond.
+__device__ __forceinline__ double scale_pow2(double x, int k) {
+  if (k >= -1022 && k <= 1023) return x * __longlong_as_double((long long)(k + 1023) << 52);
+  return ldexp(x, k);
+}
+
+// FP64 -> double-float pair (h + l = x to about 2^-48 relative).
+__device__ __forceinline__ float2 to_df(double x) {
+  const float h = (float)x;
+  return make_float2(h, (float)(x - (double)h));
+}
+__device__ __forceinline__ float2 to_df(float2 x) { return x; }
 
 __device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
   s = a + b;
@@ -807,7 +848,7 @@ __global__ void slice_f64_kernel(const double* X, long long rows, int cols, long
   for (int k = lane; k < cols; k += 32) {
     const double v = x[k * cs];
     __nv_bfloat16 d[4];
-    digits_bf16(__double2int_rn(ldexp(v, 31 - e)), d);
+    digits_bf16(__double2int_rn(scale_pow2(v, 31 - e)), d);
 #pragma unroll
     for (int t = 0; t < 4; ++t) out[t * ldp + k] = d[t];
     if (absout) absout[r * cols + k] = (float)fabs(v);
@@ -819,8 +860,70 @@ __global__ void slice_f64_kernel(const double* X, long long rows, int cols, long
   }
 }
 
-// Rows of a double-float matrix (hi, lo; row stride ld) -> interleaved digits with exact
-// row exponents.
+// The per-iteration form of slice_f64_kernel (unit column stride): one block per
+// row, so that a row's loads are spread over many threads and its FP64 work over
+// the SMs.  Rows r in [rows, rows_df) only write their double-float copy.
+constexpr int SLICE_ROWS_THREADS = 128;
+__global__ void __launch_bounds__(SLICE_ROWS_THREADS) slice_rows_kernel(const double* __restrict__ X, int rows,
+                                                                        int cols, long long rs,
+                                                                        __nv_bfloat16* __restrict__ planes, int ldp,
+                                                                        int* __restrict__ exps, float* absout,
+                                                                        float* absT, float2* dfout) {
+  pdl_entry();
+  __shared__ double wmax[SLICE_ROWS_THREADS / 32];
+  __shared__ int se;
+  const int r = blockIdx.x, tid = threadIdx.x;
+  const double* x = X + (long long)r * rs;
+  if (r >= rows) {
+    for (int k = tid; k < cols; k += SLICE_ROWS_THREADS) dfout[(long long)r * cols + k] = to_df(x[k]);
+    return;
+  }
+  double mx = 0.0;
+#pragma unroll 4
+  for (int k = tid; k < cols; k += SLICE_ROWS_THREADS) mx = fmax(mx, fabs(x[k]));
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((tid & 31) == 0) wmax[tid >> 5] = mx;
+  __syncthreads();
+  if (tid == 0) {
+    double m2 = wmax[0];
+    for (int w = 1; w < SLICE_ROWS_THREADS / 32; ++w) m2 = fmax(m2, wmax[w]);
+    se = expo_of(m2);
+    exps[r] = se;
+  }
+  __syncthreads();
+  const int e = se;
+  __nv_bfloat16* out = planes + (size_t)r * 4 * ldp;
+#pragma unroll 4
+  for (int k = tid; k < cols; k += SLICE_ROWS_THREADS) {
+    const double v = x[k];
+    __nv_bfloat16 d[4];
+    digits_bf16(__double2int_rn(scale_pow2(v, 31 - e)), d);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) out[t * ldp + k] = d[t];
+    if (absout) absout[(long long)r * cols + k] = (float)fabs(v);
+    if (absT) absT[(long long)k * rows + r] = (float)fabs(v);
+    if (dfout) dfout[(long long)r * cols + k] = to_df(v);
+  }
+}
+
+// FP64 -> double-float pairs, elementwise.
+__global__ void to_df_kernel(const double* __restrict__ x, long long n, float2* __restrict__ out) {
+  pdl_entry();
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = to_df(x[i]);
+}
+
+// Rows of a double-float matrix (hi, lo; row stride ld, a multiple of 2) ->
+// interleaved digits with exact row exponents.  One warp per row, two adjacent
+// columns per lane (8-byte loads, BF16 pairs stored as 4 bytes; ldp even).
+__device__ __forceinline__ float scale_pow2f(float x, int k) {
+  return (k >= -126 && k <= 127) ? x * exp2_int(k) : ldexpf(x, k);
+}
+__device__ __forceinline__ int pair_to_int(float h, float l, int k) {
+  const float hs = scale_pow2f(h, k), ls = scale_pow2f(l, k);  // |hs| < 2^30
+  const float ih = rintf(hs);
+  return __float2int_rn(ih) + __float2int_rn((hs - ih) + ls);
+}
 __global__ void slice_pair_kernel(const float* hi, const float* lo, long long rows, int cols, int ld,
                                   __nv_bfloat16* planes, int ldp, int* exps) {
   pdl_entry();
@@ -830,51 +933,65 @@ __global__ void slice_pair_kernel(const float* hi, const float* lo, long long ro
   const float* h = hi + r * ld;
   const float* l = lo + r * ld;
   float mx = 0.f;
-  for (int k = lane; k < cols; k += 32) mx = fmaxf(mx, fabsf(h[k]) + fabsf(l[k]));
+  for (int k = 2 * lane; k < cols; k += 64) {
+    if (k + 1 < cols) {
+      const float2 hv = *(const float2*)(h + k), lv = *(const float2*)(l + k);
+      mx = fmaxf(mx, fmaxf(fabsf(hv.x) + fabsf(lv.x), fabsf(hv.y) + fabsf(lv.y)));
+    } else {
+      mx = fmaxf(mx, fabsf(h[k]) + fabsf(l[k]));
+    }
+  }
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  const int e = expo_of((double)mx * (1.0 + 1.0 / 65536.0));
+  const int e = expo_of_inflated(mx);
   if (lane == 0) exps[r] = e;
   __nv_bfloat16* out = planes + (size_t)r * 4 * ldp;
-  for (int k = lane; k < cols; k += 32) {
-    const float hs = ldexpf(h[k], 31 - e), ls = ldexpf(l[k], 31 - e);  // |hs| < 2^30
-    const float ih = rintf(hs);
-    const int X = __float2int_rn(ih) + __float2int_rn((hs - ih) + ls);
-    __nv_bfloat16 d[4];
-    digits_bf16(X, d);
+  for (int k = 2 * lane; k < cols; k += 64) {
+    if (k + 1 < cols) {
+      const float2 hv = *(const float2*)(h + k), lv = *(const float2*)(l + k);
+      __nv_bfloat162 dd[4];
+      digits_bf16x2(pair_to_int(hv.x, lv.x, 31 - e), pair_to_int(hv.y, lv.y, 31 - e), dd);
 #pragma unroll
-    for (int t = 0; t < 4; ++t) out[t * ldp + k] = d[t];
+      for (int t = 0; t < 4; ++t) *(__nv_bfloat162*)(out + (size_t)t * ldp + k) = dd[t];
+    } else {
+      __nv_bfloat16 d[4];
+      digits_bf16(pair_to_int(h[k], l[k], 31 - e), d);
+#pragma unroll
+      for (int t = 0; t < 4; ++t) out[(size_t)t * ldp + k] = d[t];
+    }
   }
 }
 
 // Upper bounds on |b^P_{p nu}| (Table 2/3 step 2), FP32 sums inflated by (1 + 2^-16):
 //   e3[P][p] = expo(sum_mu rmaxB[P][mu] |C_{mu p}|)   (rows (P,p) of the full-transform operand)
 //   e6[p][nu] = expo(sum_mu |C_{mu p}| maxB[mu][nu])   (rows (p,nu) of the K^(p) operand)
-// One block per P (resp. p); the row of the first factor is staged in shared memory and the
-// threads run over p (resp. nu) with coalesced reads of the second factor.
-__global__ void bound3_kernel(const float* rmaxB, const float* absCt, int nx, int nb, int m, int* e3) {
+// Both are out[i][j] = expo(sum_k A[i][k] B[k][j]) over a small FP32 product: 16 x 16
+// outputs per block, K staged through shared memory in slices of 64, every sum
+// taken in k order with one FMA chain (the bounds do not depend on the launch).
+constexpr int BOUND_TILE = 16, BOUND_KC = 64;
+__global__ void __launch_bounds__(256) bound_kernel(int M, int N, int K, const float* __restrict__ A, int lda,
+                                                    const float* __restrict__ B, int ldb, int* __restrict__ out,
+                                                    int ldo) {
   pdl_entry();
-  extern __shared__ float srow[];
-  const int P = blockIdx.x;
-  for (int mu = threadIdx.x; mu < nb; mu += blockDim.x) srow[mu] = rmaxB[(size_t)P * nb + mu];
-  __syncthreads();
-  for (int pc = threadIdx.x; pc < m; pc += blockDim.x) {
-    float s = 0.f;
-    for (int mu = 0; mu < nb; ++mu) s = fmaf(srow[mu], absCt[(size_t)mu * m + pc], s);
-    e3[(size_t)P * m + pc] = expo_of((double)s * (1.0 + 1.0 / 65536.0));
+  __shared__ float As[BOUND_TILE][BOUND_KC + 1];
+  __shared__ float Bs[BOUND_KC][BOUND_TILE + 1];
+  const int tid = threadIdx.x, tx = tid % BOUND_TILE, ty = tid / BOUND_TILE;
+  const int i0 = blockIdx.y * BOUND_TILE, j0 = blockIdx.x * BOUND_TILE;
+  float acc = 0.f;
+  for (int k0 = 0; k0 < K; k0 += BOUND_KC) {
+#pragma unroll
+    for (int u = 0; u < BOUND_TILE * BOUND_KC / 256; ++u) {
+      const int idx = tid + 256 * u;
+      const int ar = idx / BOUND_KC, ac = idx % BOUND_KC;  // A: row i0 + ar, column k0 + ac
+      As[ar][ac] = (i0 + ar < M && k0 + ac < K) ? A[(size_t)(i0 + ar) * lda + k0 + ac] : 0.f;
+      const int br = idx / BOUND_TILE, bc = idx % BOUND_TILE;  // B: row k0 + br, column j0 + bc
+      Bs[br][bc] = (k0 + br < K && j0 + bc < N) ? B[(size_t)(k0 + br) * ldb + j0 + bc] : 0.f;
+    }
+    __syncthreads();
+    const int kn = K - k0 < BOUND_KC ? K - k0 : BOUND_KC;
+    for (int kk = 0; kk < kn; ++kk) acc = fmaf(As[ty][kk], Bs[kk][tx], acc);
+    __syncthreads();
   }
-}
-
-__global__ void bound6_kernel(const float* maxB, const float* absC, int nb, int m, int* e6) {
-  pdl_entry();
-  extern __shared__ float srow[];
-  const int pc = blockIdx.x;
-  for (int mu = threadIdx.x; mu < nb; mu += blockDim.x) srow[mu] = absC[(size_t)pc * nb + mu];
-  __syncthreads();
-  for (int nu = threadIdx.x; nu < nb; nu += blockDim.x) {
-    float s = 0.f;
-    for (int mu = 0; mu < nb; ++mu) s = fmaf(srow[mu], maxB[(size_t)mu * nb + nu], s);
-    e6[(size_t)pc * nb + nu] = expo_of((double)s * (1.0 + 1.0 / 65536.0));
-  }
+  if (i0 + ty < M && j0 + tx < N) out[(size_t)(i0 + ty) * ldo + j0 + tx] = expo_of_inflated(acc);
 }
 
 // max over nu of |B^P_{mu nu}| -> rmaxB[P][mu], max over P -> maxB[mu][nu] (FP32, rounded up).
@@ -907,34 +1024,151 @@ __global__ void reduce_jmo_kernel(const long long* partial, int nsplit, int m, c
   J[i] = ldexp((double)s, ed[i / m] + ed[i % m] - S4_SHIFT);
 }
 
-// sum over splits of double-float partials, FP64.  mode 1: the [rows = p][cols = mu]
-// partials of F^(p) C_p, written as Y^T [p][mu] with n_p (H C)^T added.
+// Sum over splits of double-float partials, in double-float arithmetic (FP64 only
+// for the final value).  Without outdf: out[i] = the sum (FP64).  With outdf: the
+// [rows = p][cols = mu] partials of F^(p) C_p, written as the double-float Y^T
+// [p][mu] with n_p (H C)^T added (HCt double-float).
 __global__ void __launch_bounds__(256) reduce_df_kernel(const float2* partial, int nsplit, int rows, int cols,
-                                                       double* out, int mode, const double* n, const double* HCt) {
+                                                       double* out, float2* outdf, const double* n,
+                                                       const float2* HCt) {
   pdl_entry();
   // 32 outputs per block, their splits dealt to 8 thread rows (split k to row
-  // k % 8), each row summing its share in FP64; the 8 row sums are then added in
-  // row order, so the result does not depend on the launch beyond that fixed order.
-  __shared__ double part[8][32];
+  // k % 8), each row summing its share in split order; the 8 row sums are then
+  // added in row order, so the result does not depend on the launch beyond that
+  // fixed order.
+  __shared__ float2 part[8][32];
   const long long rc = (long long)rows * cols;
   const long long i = blockIdx.x * 32LL + threadIdx.x;
-  double s = 0.0;
+  float sh = 0.f, sl = 0.f;
   if (i < rc) {
     for (int k = threadIdx.y; k < nsplit; k += 8) {
       const float2 v = partial[(size_t)k * rc + i];
-      s += (double)v.x + (double)v.y;
+      df_add(sh, sl, v.x, v.y);
     }
   }
-  part[threadIdx.y][threadIdx.x] = s;
+  part[threadIdx.y][threadIdx.x] = make_float2(sh, sl);
   __syncthreads();
   if (threadIdx.y != 0 || i >= rc) return;
-  double t = part[0][threadIdx.x];
+  float th = part[0][threadIdx.x].x, tl = part[0][threadIdx.x].y;
 #pragma unroll
-  for (int y = 1; y < 8; ++y) t += part[y][threadIdx.x];
-  if (mode == 1) {
-    out[i] = n[i / cols] * HCt[i] + t;
+  for (int y = 1; y < 8; ++y) df_add(th, tl, part[y][threadIdx.x].x, part[y][threadIdx.x].y);
+  if (outdf) {
+    const float2 np = to_df(n[i / cols]), h = HCt[i];
+    const float ph = np.x * h.x;
+    const float pl = fmaf(np.x, h.x, -ph) + fmaf(np.x, h.y, np.y * h.x);
+    df_add(th, tl, ph, pl);
+    outdf[i] = make_float2(th, tl);
   } else {
-    out[i] = t;
+    out[i] = (double)th + (double)tl;
+  }
+}
+
+// out[i][j] = sum_k A[i][k] B[j][k] in double-float arithmetic: each product as
+// an FP32 pair (about 2^-46 relative), the high parts summed with TwoSum in k
+// order and the low parts and rounding errors collected beside them.  A and B are
+// double-float; out double-float or FP64.  The small products of the energy row
+// (H C, lambda = Y^T C) run here rather than in DFMA, whose rate is a small
+// fraction of FP32's on this part.  16 x 16 outputs per block, K staged through
+// shared memory in slices of 64, the loads of a slice issued together.
+__device__ __forceinline__ void df_store(float2& o, float h, float l) { o = make_float2(h, l); }
+__device__ __forceinline__ void df_store(double& o, float h, float l) { o = (double)h + (double)l; }
+
+constexpr int DFG_KC = 64, DFG_TI = 16, DFG_TJ = 16, DFG_THREADS = DFG_TI * DFG_TJ;
+template <typename TO>
+__global__ void __launch_bounds__(DFG_THREADS) df_gemm_nt_kernel(int M, int N, int K, const float2* __restrict__ A,
+                                                                 int lda, const float2* __restrict__ B, int ldb,
+                                                                 TO* __restrict__ out, int ldo) {
+  pdl_entry();
+  __shared__ float2 As[DFG_TI][DFG_KC + 1];  // [i][k]
+  __shared__ float2 Bs[DFG_KC][DFG_TJ + 1];  // [k][j]
+  const int tid = threadIdx.x, tx = tid % DFG_TJ, ty = tid / DFG_TJ;
+  const int i0 = blockIdx.y * DFG_TI, j0 = blockIdx.x * DFG_TJ;
+  constexpr int NA = DFG_TI * DFG_KC / DFG_THREADS, NB = DFG_TJ * DFG_KC / DFG_THREADS;
+  float sum = 0.f, cmp = 0.f;
+  for (int k0 = 0; k0 < K; k0 += DFG_KC) {
+    float2 av[NA], bv[NB];
+#pragma unroll
+    for (int u = 0; u < NA; ++u) {
+      const int idx = tid + DFG_THREADS * u, r = idx / DFG_KC, c = idx % DFG_KC;
+      av[u] = (i0 + r < M && k0 + c < K) ? A[(size_t)(i0 + r) * lda + k0 + c] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+      const int idx = tid + DFG_THREADS * u, r = idx / DFG_KC, c = idx % DFG_KC;
+      bv[u] = (j0 + r < N && k0 + c < K) ? B[(size_t)(j0 + r) * ldb + k0 + c] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < NA; ++u) {
+      const int idx = tid + DFG_THREADS * u;
+      As[idx / DFG_KC][idx % DFG_KC] = av[u];
+    }
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+      const int idx = tid + DFG_THREADS * u;
+      Bs[idx % DFG_KC][idx / DFG_KC] = bv[u];
+    }
+    __syncthreads();
+    const int kn = K - k0 < DFG_KC ? K - k0 : DFG_KC;
+#pragma unroll 8
+    for (int kk = 0; kk < kn; ++kk) {
+      const float2 a = As[ty][kk], b = Bs[kk][tx];
+      const float ph = a.x * b.x;
+      const float pl = fmaf(a.x, b.x, -ph) + fmaf(a.x, b.y, a.y * b.x);
+      float ns, e;
+      two_sum_f(sum, ph, ns, e);
+      sum = ns;
+      cmp += e + pl;
+    }
+    __syncthreads();
+  }
+  if (i0 + ty < M && j0 + tx < N) {
+    const float h = sum + cmp;
+    df_store(out[(size_t)(i0 + ty) * ldo + j0 + tx], h, cmp - (h - sum));
+  }
+}
+
+// E = E_nuc + sum_p (n_p H_pp + lambda_pp).  One warp per p: H_pp = C_p . (H C)_p
+// in double-float arithmetic (lanes over mu, a fixed shuffle tree), the term in
+// FP64 into eterm[p].  The last warp to finish (a ticket counter, which that warp
+// resets for the next launch) adds the terms in a fixed order (lanes over p, then
+// a shuffle tree).  No FP64 loop runs on one SM over a whole matrix, and no block
+// waits for another.
+__global__ void energy_terms_kernel(int nbf, int n_om, const float2* Cdf, const float2* HCt, const double* n,
+                                    const double* lambda, const double* enuc, double* eterm, unsigned int* ticket,
+                                    double* E) {
+  pdl_entry();
+  __shared__ int last;
+  const int p = blockIdx.x, lane = threadIdx.x;
+  float sum = 0.f, cmp = 0.f;
+  for (int mu = lane; mu < nbf; mu += 32) {
+    const float2 c = Cdf[(size_t)p * nbf + mu], h = HCt[(size_t)p * nbf + mu];
+    const float ph = c.x * h.x;
+    const float pl = fmaf(c.x, h.x, -ph) + fmaf(c.x, h.y, c.y * h.x);
+    float ns, e;
+    two_sum_f(sum, ph, ns, e);
+    sum = ns;
+    cmp += e + pl;
+  }
+  float sh = sum + cmp, sl = cmp - (sh - sum);
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, sh, o), ol = __shfl_xor_sync(0xffffffffu, sl, o);
+    df_add(sh, sl, oh, ol);
+  }
+  if (lane == 0) {
+    eterm[p] = n[p] * ((double)sh + (double)sl) + lambda[(size_t)p * nbf + p];
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == (unsigned int)(n_om - 1);
+  }
+  __syncwarp();
+  if (!last) return;
+  __threadfence();
+  // lane l adds the terms q = l, l + 32, ... in order; then a fixed shuffle tree
+  double v = 0.0;
+  for (int q = lane; q < n_om; q += 32) v += __ldcg(eterm + q);
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) {
+    *E = *enuc + v;
+    *ticket = 0u;
   }
 }
 
@@ -979,31 +1213,36 @@ __global__ void __launch_bounds__(256) xf_to_digits_kernel(const int* Xf, const 
   else if (tid < 192) sc[tid - 128] = (nu0 + tid - 128 < nb) ? Cdf[(size_t)p * nb + nu0 + tid - 128] : make_float2(0.f, 0.f);
   __syncthreads();
   const int c0 = 2 * threadIdx.x;  // this thread's column pair within the tile
-  // rows P of the tile: L3 digits (nu contiguous)
-  for (int r = threadIdx.y; r < 64; r += 8) {
-    const int P = P0 + r, nu = nu0 + c0;
-    int x0 = 0, x1 = 0;
+  // rows P of the tile: L3 digits (nu contiguous).  The eight rows' loads are
+  // issued before any of their stores, so that they are in flight together.
+  int2 xv[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int P = P0 + threadIdx.y + 8 * i, nu = nu0 + c0;
+    xv[i] = make_int2(0, 0);
     if (P < nx && nu < nb) {
       const int* src = Xf + ((size_t)P * m + p) * nbp + nu;
-      if (nu + 1 < nb) {
-        const int2 v = *(const int2*)src;
-        x0 = v.x;
-        x1 = v.y;
-      } else {
-        x0 = src[0];
-      }
+      if (nu + 1 < nb) xv[i] = *(const int2*)src;
+      else xv[i].x = src[0];
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int r = threadIdx.y + 8 * i;
+    const int P = P0 + r, nu = nu0 + c0;
+    const int x0 = xv[i].x, x1 = xv[i].y;
+    if (P < nx && nu < nb) {
       int d = s3[r] - s6[c0];
       const int y0 = rshift_round(x0, d > 0 ? d : 0);
       d = s3[r] - s6[c0 + 1];
       const int y1 = rshift_round(x1, d > 0 ? d : 0);
-      __nv_bfloat16 a[4], b[4];
-      digits_bf16(y0, a);
-      digits_bf16(y1, b);
+      __nv_bfloat162 dd[4];
+      digits_bf16x2(y0, y1, dd);
       __nv_bfloat16* o = L3 + (((size_t)P * mp + p) * 4) * nbp + nu;
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
-        if (nu + 1 < nb) *(__nv_bfloat162*)(o + (size_t)t * nbp) = __halves2bfloat162(a[t], b[t]);
-        else o[(size_t)t * nbp] = a[t];
+        if (nu + 1 < nb) *(__nv_bfloat162*)(o + (size_t)t * nbp) = dd[t];
+        else o[(size_t)t * nbp] = dd[t].x;
       }
     }
     tile[r][c0] = x0;
@@ -1018,15 +1257,16 @@ __global__ void __launch_bounds__(256) xf_to_digits_kernel(const int* Xf, const 
     const int nu = nu0 + r, P = P0 + c0;
     if (nu < nb && P < nx) {
       int d = s6[r] - s3[c0];
-      __nv_bfloat16 a[4], b[4];
-      digits_bf16(rshift_round(tile[c0][r], d > 0 ? d : 0), a);
+      const int z0 = rshift_round(tile[c0][r], d > 0 ? d : 0);
       d = s6[r] - s3[c0 + 1];
-      digits_bf16(rshift_round(tile[c0 + 1][r], d > 0 ? d : 0), b);
+      const int z1 = rshift_round(tile[c0 + 1][r], d > 0 ? d : 0);
+      __nv_bfloat162 dd[4];
+      digits_bf16x2(z0, z1, dd);
       __nv_bfloat16* o = L6 + ((size_t)p * nb + nu) * 4 * nxp + P;
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
-        if (P + 1 < nx) *(__nv_bfloat162*)(o + (size_t)t * nxp) = __halves2bfloat162(a[t], b[t]);
-        else o[(size_t)t * nxp] = a[t];
+        if (P + 1 < nx) *(__nv_bfloat162*)(o + (size_t)t * nxp) = dd[t];
+        else o[(size_t)t * nxp] = dd[t].x;
       }
       const float2 cv = sc[r];
 #pragma unroll
@@ -1059,18 +1299,20 @@ __global__ void __launch_bounds__(256) xf_to_digits_kernel(const int* Xf, const 
   }
 }
 
-// d[p][P] = 2^(e3[P][p] - 31) sum over the nu tiles of the pass's double-float partials.
+// d[p][P] = 2^(e3[P][p] - 31) sum over the nu tiles of the pass's double-float
+// partials, added in tile order in double-float arithmetic; FP64 only for the
+// final value.
 __global__ void diag_reduce_kernel(const float2* dpart, int ntiles, int nx, int m, const int* e3, double* d) {
   pdl_entry();
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= (long long)nx * m) return;
   const int pc = (int)(i / nx), P = (int)(i % nx);
-  double s = 0.0;
+  float sh = 0.f, sl = 0.f;
   for (int t = 0; t < ntiles; ++t) {
     const float2 v = dpart[((size_t)t * m + pc) * nx + P];
-    s += (double)v.x + (double)v.y;
+    df_add(sh, sl, v.x, v.y);
   }
-  d[i] = ldexp(s, e3[(size_t)P * m + pc] - 31);
+  d[i] = scale_pow2((double)sh + (double)sl, e3[(size_t)P * m + pc] - 31);
 }
 
 // J^(q) and K^(q) are symmetric: their GEMMs skip the tiles that lie wholly below
@@ -1090,12 +1332,23 @@ __host__ __device__ __forceinline__ bool jao_block_skipped(long long r0, int nb)
   return mu0 == mu1 && (r1 - mu0 * nb) < mu0;
 }
 
-__global__ void sym_mirror_kernel(float* hi, float* lo, int nb, int row0, int ldo, int bn, int jao) {
+// Launched over the 32 x 32 destination blocks that hold skipped elements only
+// (tiles[] = (bi << 16) | bj, built on the host from the same predicates), one
+// grid row per matrix.
+__global__ void sym_mirror_kernel(float* hi, float* lo, int nb, int row0, int ldo, int bn, int jao, const int* tiles) {
   pdl_entry();
   __shared__ float th[32][33], tl[32][33];
-  const int bi = blockIdx.y, bj = blockIdx.x;  // destination block: rows mu (bi), columns nu (bj)
+  const int bi = tiles[blockIdx.x] >> 16, bj = tiles[blockIdx.x] & 0xFFFF;  // rows mu (bi), columns nu (bj)
   if (bj > bi) return;
-  const size_t base = (size_t)(row0 + blockIdx.z) * nb * ldo;
+  // most blocks below the diagonal were computed by the GEMM: leave before any load
+  int work = 0;
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int mu = bi * 32 + r, nu = bj * 32 + threadIdx.x;
+    if (mu < nb && nu < nb && nu < mu)
+      work |= !(jao ? !jao_block_skipped(((long long)mu * nb + nu) / 128 * 128, nb) : kao_tile_computed(mu, nu, bn));
+  }
+  if (!__syncthreads_or(work)) return;
+  const size_t base = (size_t)(row0 + blockIdx.y) * nb * ldo;
   for (int r = threadIdx.y; r < 32; r += 8) {  // source rows nu = bj*32 + r, columns mu = bi*32 + x
     const int nu = bj * 32 + r, mu = bi * 32 + threadIdx.x;
     if (nu < nb && mu < nb) {
@@ -1150,19 +1403,26 @@ struct donof::S4Buffers {
   int* jao_tmap_full;                                 // every J^(q) row block
   int jao_ntiles_sym, jao_ntiles_full;
   int jao_sym;                                        // 1: J^(q) lower row blocks skipped and mirrored
+  int *mir_jao, *mir_kao;                             // 32 x 32 blocks the mirrors fill, (bi << 16) | bj
+  int mir_n_jao, mir_n_kao;
   int half_variant;                                   // 1: the half transform runs as S_HALF1
   int jk_merged;                                      // 1: J^(q) and K^(q) in one launch (S_JKAO)
   int max_stages[donof::S_NKINDS];                    // pipeline depth that fits the shared memory
   int target[donof::S_NKINDS];                        // CTA count the split kinds aim at
   int *eB1, *eB5, *eC, *e3, *e6, *ed, *eJK;          // row exponents
   float *rmaxB, *maxB, *absC, *absCt;
-  float2* Cdf;    // C rows p (< N_O) as double-float pairs
+  float2* Cdf;    // C rows p (every p < nbf) as double-float pairs
+  float2* Hdf;    // H as double-float pairs (fixed at init)
+  float2* Cdfp;   // C rows p (< N_O) as double-float pairs, the energy prep's own copy (its stream
+                  // may run ahead of the transform that writes Cdf)
   float2* dpart;  // diagonal partials [nu tile][m][nx] from the digit pass
   double* dmat;   // d [m][nx] FP64
   float *JKhi, *JKlo;
   float2* W;
-  double* HCt;
-  double* Yt;
+  float2* HCt;  // (H C)^T [p][mu], double-float
+  float2* Yt;   // Y^T [p][mu] = (F^(p) C_p)^T, double-float
+  double* eterm;          // the energy's per-orbital terms
+  unsigned int* ticket;   // energy_terms_kernel's completion counter (zero between launches)
   void* partial;
   void* partial_j;  // J_pq's int64 partials (its launch group may run beside a3's)
   donof::S4Params plan[donof::S_NKINDS];
@@ -1338,6 +1598,35 @@ int s4_init(donof_ri_ctx* ctx) {
   if (cudaMemcpy(sb->kao_tmap, kao_tiles.data(), kao_tiles.size() * sizeof(int), cudaMemcpyHostToDevice) !=
       cudaSuccess)
     return DONOF_RI_E_CUDA;
+  {
+    // the 32 x 32 destination blocks of the mirrors: those holding an element below
+    // the diagonal that the J^(q) (resp. K^(q)) GEMM skips
+    std::vector<int> lists[2];
+    const int nbk = (nb + 31) / 32;
+    for (int jao = 0; jao < 2; ++jao) {
+      const int bn = jao ? S4Cfg<S_JAO>::BN : S4Cfg<S_KAO>::BN;
+      for (int bi = 0; bi < nbk; ++bi)
+        for (int bj = 0; bj <= bi; ++bj) {
+          bool work = false;
+          for (int r = 0; r < 32 && !work; ++r)
+            for (int x = 0; x < 32 && !work; ++x) {
+              const int mu = bi * 32 + r, nu = bj * 32 + x;
+              if (mu < nb && nu < nb && nu < mu)
+                work = jao ? jao_block_skipped(((long long)mu * nb + nu) / 128 * 128, nb) : !kao_tile_computed(mu, nu, bn);
+            }
+          if (work) lists[jao].push_back((bi << 16) | bj);
+        }
+    }
+    sb->mir_n_kao = (int)lists[0].size();
+    sb->mir_n_jao = (int)lists[1].size();
+    ALLOC(sb->mir_kao, (lists[0].size() + 1) * sizeof(int));
+    ALLOC(sb->mir_jao, (lists[1].size() + 1) * sizeof(int));
+    if ((!lists[0].empty() && cudaMemcpy(sb->mir_kao, lists[0].data(), lists[0].size() * sizeof(int),
+                                         cudaMemcpyHostToDevice) != cudaSuccess) ||
+        (!lists[1].empty() && cudaMemcpy(sb->mir_jao, lists[1].data(), lists[1].size() * sizeof(int),
+                                         cudaMemcpyHostToDevice) != cudaSuccess))
+      return DONOF_RI_E_CUDA;
+  }
   ALLOC(sb->Dp, ms * 4 * nxp * 2);
   ALLOC(sb->JKp, 2 * ms * nbs * 4 * nbp * 2);
   ALLOC(sb->eB1, nxs * nbs * 4);
@@ -1351,7 +1640,11 @@ int s4_init(donof_ri_ctx* ctx) {
   ALLOC(sb->maxB, nbs * nbs * 4);
   ALLOC(sb->absC, ms * nbs * 4);
   ALLOC(sb->absCt, ms * nbs * 4);
-  ALLOC(sb->Cdf, ms * nbs * 8);
+  ALLOC(sb->Cdf, nbs * nbs * 8);
+  ALLOC(sb->Hdf, nbs * nbs * 8);
+  ALLOC(sb->Cdfp, ms * nbs * 8);
+  ALLOC(sb->eterm, ms * 8);
+  ALLOC(sb->ticket, 4);
   ALLOC(sb->dpart, (size_t)((nb + 63) / 64) * ms * nxs * 8);
   ALLOC(sb->dmat, ms * nxs * 8);
   ALLOC(sb->JKhi, 2 * ms * nbs * ldo * 4);
@@ -1365,6 +1658,8 @@ int s4_init(donof_ri_ctx* ctx) {
 
   // one-time digitisation of B in both operand layouts, and its maxima for the bounds
   cudaStream_t s = ctx->stream;
+  to_df_kernel<<<ceil_div_u(nbs * nbs, 256), 256, 0, s>>>(ctx->d_H, nbs * nbs, sb->Hdf);
+  if (cudaMemsetAsync(sb->ticket, 0, sizeof(unsigned int), s) != cudaSuccess) return DONOF_RI_E_CUDA;
   {
     long long rows = nxs * nbs;  // rows (P, nu) over mu (B symmetric)
     slice_f64_kernel<<<ceil_div_u(rows * 32, 256), 256, 0, s>>>(ctx->d_B, rows, nb, nb, 1, sb->B1, nbp, sb->eB1,
@@ -1481,9 +1776,9 @@ int s4_init(donof_ri_ctx* ctx) {
 void s4_free(donof_ri_ctx* ctx) {
   S4Buffers* sb = ctx->s4;
   if (!sb) return;
-  void* bufs[] = {sb->jao_tmap_full, sb->jao_tmap, sb->kao_tmap, sb->X6,    sb->B1,   sb->B5,   sb->Ct,   sb->L3,   sb->L6, sb->Dp,  sb->JKp,  sb->eB1,   sb->eB5,
+  void* bufs[] = {sb->mir_jao, sb->mir_kao, sb->jao_tmap_full, sb->jao_tmap, sb->kao_tmap, sb->X6,    sb->B1,   sb->B5,   sb->Ct,   sb->L3,   sb->L6, sb->Dp,  sb->JKp,  sb->eB1,   sb->eB5,
                   sb->eC,    sb->e3,   sb->e6,   sb->ed,   sb->eJK, sb->rmaxB, sb->maxB, sb->absC, sb->absCt,
-                  sb->Cdf,   sb->dpart, sb->dmat, sb->JKhi, sb->JKlo, sb->W,  sb->HCt, sb->Yt,   sb->partial, sb->partial_j};
+                  sb->Cdf,   sb->Hdf,   sb->Cdfp,  sb->eterm, sb->ticket, sb->dpart, sb->dmat, sb->JKhi, sb->JKlo, sb->W,  sb->HCt, sb->Yt,   sb->partial, sb->partial_j};
   for (void* b : bufs)
     if (b) cudaFree(b);
   free(sb);
@@ -1538,19 +1833,20 @@ int s4_transform(donof_ri_ctx* ctx, int mode) {
   {
     ProfScope ps(ctx, DONOF_RI_ROW_OTHER);
     // C^T rows p over mu (C column-major = rows p contiguous)
-    launch_pdl(slice_f64_kernel, dim3(ceil_div_u((long long)m * 32, 256)), dim3(256), 0, s, (const double*)ctx->d_C,
-               (long long)m, nb, (long long)nb, 1LL, sb->Ct, sb->nbp, sb->eC, sb->absC, sb->absCt, sb->Cdf);
+    // (and every row of C as double-float pairs, for lambda)
+    launch_pdl(slice_rows_kernel, dim3(nb), dim3(SLICE_ROWS_THREADS), 0, s, (const double*)ctx->d_C, m, nb,
+               (long long)nb, sb->Ct, sb->nbp, sb->eC, sb->absC, sb->absCt, sb->Cdf);
     DONOF_LAUNCH_CHECK(ctx);
     // the two bound passes are independent: e6 on the second stream
     cudaStream_t main_stream;
     const bool forked = fork_begin(ctx, &main_stream);
-    launch_pdl(bound6_kernel, dim3(m), dim3(128), nb * sizeof(float), ctx->stream, (const float*)sb->maxB,
-               (const float*)sb->absC, nb, m, sb->e6);
+    launch_pdl(bound_kernel, dim3((nb + BOUND_TILE - 1) / BOUND_TILE, (m + BOUND_TILE - 1) / BOUND_TILE), dim3(256), 0,
+               ctx->stream, m, nb, nb, (const float*)sb->absC, nb, (const float*)sb->maxB, nb, sb->e6, nb);
     rc = cudaGetLastError() == cudaSuccess ? DONOF_RI_OK : DONOF_RI_E_CUDA;
     ctx->launches++;
     if (forked) fork_end(ctx, main_stream);
-    launch_pdl(bound3_kernel, dim3(nx), dim3(128), nb * sizeof(float), s, (const float*)sb->rmaxB,
-               (const float*)sb->absCt, nx, nb, m, sb->e3);
+    launch_pdl(bound_kernel, dim3((m + BOUND_TILE - 1) / BOUND_TILE, (nx + BOUND_TILE - 1) / BOUND_TILE), dim3(256), 0, s,
+               nx, m, nb, (const float*)sb->rmaxB, nb, (const float*)sb->absCt, m, sb->e3, m);
     DONOF_LAUNCH_CHECK(ctx);
     if (forked && (rc = fork_join(ctx))) return rc;
     if (rc) return rc;
@@ -1559,6 +1855,7 @@ int s4_transform(donof_ri_ctx* ctx, int mode) {
     ProfScope ps(ctx, DONOF_RI_ROW_HALF);
     if ((rc = launch_s4<S_HALF>(ctx))) return rc;
     dim3 g((nb + 63) / 64, (nx + 63) / 64, m), b(32, 8);
+    ProfScope pm(ctx, DONOF_RI_MEM_DIGITS);
     launch_pdl(xf_to_digits_kernel, g, b, 0, s, (const int*)sb->X6, (const int*)sb->e3, (const int*)sb->e6, nx, nb, m,
                sb->mp, sb->nbp, sb->nxp, sb->L3, sb->L6, (const float2*)sb->Cdf, sb->dpart);
     DONOF_LAUNCH_CHECK(ctx);
@@ -1568,9 +1865,8 @@ int s4_transform(donof_ri_ctx* ctx, int mode) {
     launch_pdl(diag_reduce_kernel, dim3(ceil_div_u((long long)nx * m, 256)), dim3(256), 0, s, (const float2*)sb->dpart,
                (nb + 63) / 64, nx, m, (const int*)sb->e3, sb->dmat);
     DONOF_LAUNCH_CHECK(ctx);
-    launch_pdl(slice_f64_kernel, dim3(ceil_div_u((long long)m * 32, 256)), dim3(256), 0, s, (const double*)sb->dmat,
-               (long long)m, nx, (long long)nx, 1LL, sb->Dp, sb->nxp, sb->ed, (float*)nullptr, (float*)nullptr,
-               (float2*)nullptr);
+    launch_pdl(slice_rows_kernel, dim3(m), dim3(SLICE_ROWS_THREADS), 0, s, (const double*)sb->dmat, m, nx,
+               (long long)nx, sb->Dp, sb->nxp, sb->ed, (float*)nullptr, (float*)nullptr, (float2*)nullptr);
     DONOF_LAUNCH_CHECK(ctx);
   }
   if (mode == DONOF_RI_FULL) {
@@ -1597,12 +1893,29 @@ int s4_transform(donof_ri_ctx* ctx, int mode) {
       if ((rc = launch_s4<S_FULLSQ>(ctx))) return rc;
       const S4Params& p = sb->plan[S_FULLSQ];
       launch_pdl(reduce_df_kernel, dim3(ceil_div_u((long long)m * m, 32)), dim3(32, 8), 0, s, (const float2*)p.partial,
-                 p.nsplit, m, m, ctx->d_K, 0, (const double*)nullptr, (const double*)nullptr);
+                 p.nsplit, m, m, ctx->d_K, (float2*)nullptr, (const double*)nullptr, (const float2*)nullptr);
       DONOF_LAUNCH_CHECK(ctx);
     }
     if (forked && (rc = fork_join(ctx))) return rc;
     if (rcj) return rcj;
   }
+  return DONOF_RI_OK;
+}
+
+// The mirrors after the J^(q) (jao = 1) or K^(q) GEMM: only the blocks in the list.
+static int launch_mirror(donof_ri_ctx* ctx, int jao, bool pdl) {
+  S4Buffers* sb = ctx->s4;
+  const int n = jao ? sb->mir_n_jao : sb->mir_n_kao;
+  if (n == 0) return DONOF_RI_OK;
+  const dim3 g(n, ctx->n_omega), b(32, 8);
+  const int* tl = jao ? sb->mir_jao : sb->mir_kao;
+  const int row0 = jao ? 0 : ctx->n_omega;
+  const int bn = jao ? S4Cfg<S_JAO>::BN : S4Cfg<S_KAO>::BN;
+  if (pdl)
+    launch_pdl(sym_mirror_kernel, g, b, 0, ctx->stream, sb->JKhi, sb->JKlo, ctx->nbf, row0, sb->ldo, bn, jao, tl);
+  else
+    sym_mirror_kernel<<<g, b, 0, ctx->stream>>>(sb->JKhi, sb->JKlo, ctx->nbf, row0, sb->ldo, bn, jao, tl);
+  DONOF_LAUNCH_CHECK(ctx);
   return DONOF_RI_OK;
 }
 
@@ -1614,34 +1927,24 @@ int s4_jk_ao(donof_ri_ctx* ctx) {
     // one persistent launch for every J^(q) and K^(q) unit, then the mirrors.  Per-row
     // profiling keeps the two launches apart so that each row has its own events.
     if ((rc = launch_s4<S_JKAO>(ctx))) return rc;
-    dim3 g((nb + 31) / 32, (nb + 31) / 32, m), b(32, 8);
-    if (sb->jao_sym) {
-      launch_pdl(sym_mirror_kernel, g, b, 0, ctx->stream, sb->JKhi, sb->JKlo, nb, 0, sb->ldo, S4Cfg<S_JAO>::BN, 1);
-      DONOF_LAUNCH_CHECK(ctx);
-    }
-    launch_pdl(sym_mirror_kernel, g, b, 0, ctx->stream, sb->JKhi, sb->JKlo, nb, m, sb->ldo, S4Cfg<S_KAO>::BN, 0);
-    DONOF_LAUNCH_CHECK(ctx);
+    if (sb->jao_sym && (rc = launch_mirror(ctx, 1, true))) return rc;
+    if ((rc = launch_mirror(ctx, 0, true))) return rc;
   } else {
   {
     ProfScope ps(ctx, DONOF_RI_ROW_JAO);
     if ((rc = launch_s4<S_JAO>(ctx))) return rc;
-    if (sb->jao_sym) {
-      dim3 g((nb + 31) / 32, (nb + 31) / 32, m), b(32, 8);
-      launch_pdl(sym_mirror_kernel, g, b, 0, ctx->stream, sb->JKhi, sb->JKlo, nb, 0, sb->ldo, S4Cfg<S_JAO>::BN, 1);
-      DONOF_LAUNCH_CHECK(ctx);
-    }
+    if (sb->jao_sym && (rc = launch_mirror(ctx, 1, true))) return rc;
   }
   {
     ProfScope ps(ctx, DONOF_RI_ROW_KAO);
     if ((rc = launch_s4<S_KAO>(ctx))) return rc;
-    dim3 g((nb + 31) / 32, (nb + 31) / 32, m), b(32, 8);
-    launch_pdl(sym_mirror_kernel, g, b, 0, ctx->stream, sb->JKhi, sb->JKlo, nb, m, sb->ldo, S4Cfg<S_KAO>::BN, 0);
-    DONOF_LAUNCH_CHECK(ctx);
+    if ((rc = launch_mirror(ctx, 0, true))) return rc;
   }
   }
   {
     ProfScope ps(ctx, DONOF_RI_ROW_OTHER);
     long long rows = 2LL * m * nb;
+    ProfScope pm(ctx, DONOF_RI_MEM_SPLIT);
     launch_pdl(slice_pair_kernel, dim3(ceil_div_u(rows * 32, 256)), dim3(256), 0, ctx->stream, (const float*)sb->JKhi,
                (const float*)sb->JKlo, rows, nb, sb->ldo, sb->JKp, sb->nbp, sb->eJK);
     DONOF_LAUNCH_CHECK(ctx);
@@ -1660,16 +1963,32 @@ int s4_energy(donof_ri_ctx* ctx, int part) {
     launch_pdl(fock_weights_df_kernel, dim3(ceil_div_u(2LL * m * m, 256)), dim3(256), 0, s, (const double*)ctx->d_A,
                (const double*)ctx->d_Bc, m, sb->W);
     DONOF_LAUNCH_CHECK(ctx);
-    if ((rc = launch_dot64(ctx, m, nb, nb, ctx->d_C, nb, ctx->d_H, nb, sb->HCt, nb, 1))) return rc;
+    // (H C)^T [p][mu] as double-float pairs, from the prep's own double-float copy of C
+    // (this part may run on a second stream beside the transform)
+    launch_pdl(to_df_kernel, dim3(ceil_div_u((long long)m * nb, 256)), dim3(256), 0, s, (const double*)ctx->d_C,
+               (long long)m * nb, sb->Cdfp);
+    DONOF_LAUNCH_CHECK(ctx);
+    launch_pdl(df_gemm_nt_kernel<float2>, dim3((nb + DFG_TJ - 1) / DFG_TJ, (m + DFG_TI - 1) / DFG_TI), dim3(DFG_THREADS),
+               0, s, m, nb, nb,
+               (const float2*)sb->Cdfp, nb, (const float2*)sb->Hdf, nb, sb->HCt, nb);
+    DONOF_LAUNCH_CHECK(ctx);
   }
   if (!(part & ENERGY_MAIN)) return DONOF_RI_OK;
   if ((rc = launch_s4<S_FOCK>(ctx))) return rc;
   const S4Params& p = sb->plan[S_FOCK];
   launch_pdl(reduce_df_kernel, dim3(ceil_div_u((long long)nb * m, 32)), dim3(32, 8), 0, s, (const float2*)p.partial,
-             p.nsplit, m, nb, sb->Yt, 1, (const double*)ctx->d_n, (const double*)sb->HCt);
+             p.nsplit, m, nb, (double*)nullptr, sb->Yt, (const double*)ctx->d_n, (const float2*)sb->HCt);
   DONOF_LAUNCH_CHECK(ctx);
-  if ((rc = launch_dot64(ctx, m, nb, nb, sb->Yt, nb, ctx->d_C, nb, ctx->d_lambda, nb, 1))) return rc;
-  return launch_energy_rows(ctx, sb->HCt);
+  // lambda[p][q] = Y^T_p . C_q for every q < nbf
+  launch_pdl(df_gemm_nt_kernel<double>, dim3((nb + DFG_TJ - 1) / DFG_TJ, (m + DFG_TI - 1) / DFG_TI), dim3(DFG_THREADS),
+             0, s, m, nb, nb,
+             (const float2*)sb->Yt, nb, (const float2*)sb->Cdf, nb, ctx->d_lambda, nb);
+  DONOF_LAUNCH_CHECK(ctx);
+  launch_pdl(energy_terms_kernel, dim3(m), dim3(32), 0, s, nb, m, (const float2*)sb->Cdf, (const float2*)sb->HCt,
+             (const double*)ctx->d_n, (const double*)ctx->d_lambda, (const double*)ctx->d_enuc, sb->eterm, sb->ticket,
+             ctx->d_E);
+  DONOF_LAUNCH_CHECK(ctx);
+  return DONOF_RI_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -1705,12 +2024,7 @@ static int s4_time(donof_ri_ctx* ctx, int reps, cudaEvent_t a, cudaEvent_t b, vo
     DONOF_CUDA_TRY(cudaMemsetAsync(flush, r & 255, flush_bytes, ctx->stream));
     DONOF_CUDA_TRY(cudaEventRecord(a, ctx->stream));
     if ((rc = launch_s4<KIND>(ctx))) return rc;
-    if (KIND == S_JAO && sb->jao_sym) {
-      const int nb = ctx->nbf, m = ctx->n_omega;
-      dim3 g((nb + 31) / 32, (nb + 31) / 32, m), bl(32, 8);
-      sym_mirror_kernel<<<g, bl, 0, ctx->stream>>>(sb->JKhi, sb->JKlo, nb, 0, sb->ldo, S4Cfg<S_JAO>::BN, 1);
-      DONOF_LAUNCH_CHECK(ctx);
-    }
+    if (KIND == S_JAO && sb->jao_sym && (rc = launch_mirror(ctx, 1, false))) return rc;
     DONOF_CUDA_TRY(cudaEventRecord(b, ctx->stream));
     DONOF_CUDA_TRY(cudaEventSynchronize(b));
     float t = 0.f;
@@ -1852,10 +2166,8 @@ static int s4_tune_jk_merge(donof_ri_ctx* ctx, int reps, cudaEvent_t a, cudaEven
         if ((rc = launch_s4<S_JAO>(ctx))) return rc;
         if ((rc = launch_s4<S_KAO>(ctx))) return rc;
       }
-      dim3 g((nb + 31) / 32, (nb + 31) / 32, m), bl(32, 8);
-      if (sb->jao_sym) sym_mirror_kernel<<<g, bl, 0, ctx->stream>>>(sb->JKhi, sb->JKlo, nb, 0, sb->ldo, S4Cfg<S_JAO>::BN, 1);
-      sym_mirror_kernel<<<g, bl, 0, ctx->stream>>>(sb->JKhi, sb->JKlo, nb, m, sb->ldo, S4Cfg<S_KAO>::BN, 0);
-      DONOF_LAUNCH_CHECK(ctx);
+      if (sb->jao_sym && (rc = launch_mirror(ctx, 1, false))) return rc;
+      if ((rc = launch_mirror(ctx, 0, false))) return rc;
       DONOF_CUDA_TRY(cudaEventRecord(b, ctx->stream));
       DONOF_CUDA_TRY(cudaEventSynchronize(b));
       float ms = 0.f;

@@ -72,8 +72,8 @@ def test_graph_matches_eager(prec_name):
 
 
 def test_gemm_kernel_profile_rows():
-    """Per-row profiling records one event pair per tensor-core GEMM launch (rows 8..13),
-    nested inside its row, and the profiled (serial) iteration gives the forked one's bits."""
+    """Per-row profiling records one event pair per tensor-core GEMM launch (rows 8..13)
+    and per memory-bound pass (rows 14, 15), nested inside its row, and the profiled (serial) iteration gives the forked one's bits."""
     import torch
     from paper_2012_15662_gb300 import binding as bd
     from synthetic import make_workload
@@ -95,6 +95,7 @@ def test_gemm_kernel_profile_rows():
         outs.append((E.cpu().numpy(), L.cpu().numpy()))
     rows = [bd.donof_ri_profile_read(eng.ctx, r) for r in range(8)]
     gemms = [bd.donof_ri_profile_read(eng.ctx, 8 + k) for k in range(6)]
+    mems = [bd.donof_ri_profile_read(eng.ctx, 14 + k) for k in range(2)]
     bd.donof_ri_profile(eng.ctx, False)
     eng.close()
     np.testing.assert_array_equal(outs[0][0], outs[1][0])
@@ -103,6 +104,10 @@ def test_gemm_kernel_profile_rows():
     # each GEMM lies inside its row: half, full_k, j, jao, kao, energy
     for k, r in enumerate([0, 2, 3, 4, 5, 6]):
         assert 0.0 < gemms[k][0] <= rows[r][0] + 1e-3, (k, gemms[k], rows[r])
+    # the digit pass inside the half-transform row, the J^(q)/K^(q) split inside "other"
+    assert all(c == 1 for _, c in mems), mems
+    for k, r in enumerate([0, 7]):
+        assert 0.0 < mems[k][0] <= rows[r][0] + 1e-3, (k, mems[k], rows[r])
 
 
 @pytest.mark.parametrize("prec_name", ["fp64", "slice4"])

@@ -234,9 +234,11 @@ int donof_ri_iteration(donof_ri_ctx* ctx, const double* C, const double* gamma, 
  *   `bound` or below; F_pp = diag[p] (the previous step's eigenvalues), or
  *   lambda_pp when `first` is nonzero.
  * At a stationary point (lambda symmetric) the step changes nothing.  The
- * eigenproblem is solved in FP32 by cyclic Jacobi in one CTA with the rotation
- * kept as V - I; C V is formed in FP64 and re-orthonormalised by one
- * Newton-Schulz step.  nbf <= 160.
+ * eigenproblem is solved in FP32 with the rotation kept as V - I: cyclic Jacobi
+ * in one CTA for nbf <= 160, two-sided block Jacobi (32-wide blocks, one launch per
+ * round for the 64 x 64 sub-problems and one for the update) above; the
+ * eigenvectors are then refined in FP64 against F^lambda, C V is formed in FP64
+ * and re-orthonormalised by one Newton-Schulz step.  nbf <= 2048.
  *   diag    [nbf] in (unless first) / out: the eigenvalues, host or device
  *   bound   > 0
  *   C       out or NULL: the rotated orbitals (column-major, host or device); the
@@ -244,7 +246,7 @@ int donof_ri_iteration(donof_ri_ctx* ctx, const double* C, const double* gamma, 
  *   gmax    out (host) or NULL: max |lambda_qp - lambda_pq| before the step
  *   sweeps  out (host) or NULL: Jacobi sweeps used (at most 30)
  * Synchronous.  Errors: E_ARG, E_OOM, E_STATE (no Lagrangian since the orbitals
- * last changed), E_NONFINITE (diag), E_UNSUPPORTED (nbf > 160).
+ * last changed), E_NONFINITE (diag), E_UNSUPPORTED (nbf > 2048).
  */
 int donof_ri_flambda_step(donof_ri_ctx* ctx, double* diag, int first, double bound, double* C, double* gmax,
                           int* sweeps);

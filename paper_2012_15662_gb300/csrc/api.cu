@@ -541,7 +541,7 @@ int donof_ri_flambda_step(donof_ri_ctx* ctx, double* diag, int first, double bou
                           int* sweeps) {
   if (!ctx || !(bound > 0.0) || (!first && !diag)) return DONOF_RI_E_ARG;
   if (!ctx->have_lambda) return DONOF_RI_E_STATE;
-  if (ctx->nbf > 160) return DONOF_RI_E_UNSUPPORTED;
+  if (ctx->nbf > FLAMBDA_MAX_NBF) return DONOF_RI_E_UNSUPPORTED;
   const size_t nb = ctx->nbf, nb2 = nb * nb;
   int rc;
   const size_t fls = flambda_scratch_doubles(ctx->nbf);

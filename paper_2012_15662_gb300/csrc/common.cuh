@@ -172,6 +172,7 @@ int s4_set_schedule(donof_ri_ctx* ctx, int kind, int stages, int option);
 // exact.cu: exact four-centre J^(q), K^(q), J, K into an FP64 context's buffers
 int exact_jk(donof_ri_ctx* ctx);
 // flambda.cu: one F^lambda step on ctx->d_C (nbf <= 160); scratch flambda_scratch_doubles(nbf) doubles
+constexpr int FLAMBDA_MAX_NBF = 2048;  // largest basis of the F^lambda step
 size_t flambda_scratch_doubles(int n);
 int flambda_step(donof_ri_ctx* ctx, const double* dprev, int first, double bound, double* scratch, double* gmax,
                  int* sweeps);

@@ -6,6 +6,9 @@ device's rotated orbitals match the oracle's column by column (to the FP32
 precision of the device eigensolver), stay orthonormal to FP64 rounding, and give
 the oracle's energy after the step.  With the first-step diagonal (lambda_pp) the
 eigenvalues match.  The F^lambda driver lowers the energy monotonically.
+square4 and C6H12 (nbf 24, 144) run the one-CTA Jacobi; C10H20 (nbf 240) the
+block Jacobi, against the same oracle; C16H32 (nbf 480) checks the block path on
+properties that hold at any size.
 """
 import numpy as np
 import pytest
@@ -16,7 +19,7 @@ from oracle import integrals as I, orbopt, ri  # noqa: E402
 from synthetic import make_workload, pairing_columns  # noqa: E402
 
 
-@pytest.mark.parametrize("name", ["square4", "c6h12"])
+@pytest.mark.parametrize("name", ["square4", "c6h12", "c10h20"])
 def test_flambda_step_matches_oracle(name):
     from paper_2012_15662_gb300 import binding as bd
     w = make_workload(name)
@@ -90,3 +93,53 @@ def test_flambda_call_order():
         bd.donof_ri_flambda_step(eng.ctx, np.zeros(w.system.nbf), True, 0.1)
     assert e.value.status == bd.DONOF_RI_E_STATE
     eng.close()
+
+
+def test_flambda_block_path_properties():
+    """nbf 480 (block Jacobi): the step's rotation U = C0^T C1 is orthogonal and
+    diagonalises F^lambda (built here from the engine's own lambda by the stated
+    rule), with the returned eigenvalues on the diagonal in increasing order (to the
+    FP32 solver's accuracy)."""
+    from paper_2012_15662_gb300 import binding as bd
+    w = make_workload("c16h32")
+    s = w.system
+    nb = s.nbf
+    eng = bd.Engine(s, bd.DONOF_RI_SLICE4)
+    eng.transform(w.C, bd.DONOF_RI_HALF)
+    eng.jk_ao(want=False)
+    _, lam = eng.energy_lagrangian(w.gamma)
+    g = np.abs(lam - lam.T).max()
+    bound = 1.234e-2 * g
+    diag = np.empty(nb)
+    Ccm = np.empty(nb * nb)
+    gmax, sweeps = bd.donof_ri_flambda_step(eng.ctx, diag, True, bound, Ccm)
+    eng.close()
+    assert gmax == pytest.approx(g, rel=1e-12)
+    assert 1 <= sweeps < 30
+    # ordered by the FP32 solve; the returned values are the FP64-refined ones
+    assert np.diff(diag).min() >= -2e-6 * np.abs(diag).max()
+    C1 = Ccm.reshape(nb, nb).T
+    np.testing.assert_allclose(C1.T @ C1, np.eye(nb), atol=1e-12)
+    # F^lambda: F_qp = lambda_qp - lambda_pq below the diagonal, mirrored, each element
+    # above the bound multiplied by 1/10 until it is not
+    F = np.tril(lam - lam.T, -1)
+    a = np.abs(F)
+    for _ in range(700):
+        big = a > bound
+        if not big.any():
+            break
+        F[big] *= 0.1
+        a[big] *= 0.1
+    F = F + F.T + np.diag(np.diag(lam))
+    U = w.C.T @ C1
+    A = U.T @ F @ U
+    off = A - np.diag(np.diag(A))
+    scale = np.abs(F).max()
+    # pairs of separated eigenvalues are refined to FP64; a nearly degenerate pair the
+    # first-order refinement cannot resolve keeps the FP32 solver's accuracy
+    sep = np.abs(diag[:, None] - diag[None, :]) > 1e-3 * scale
+    np.fill_diagonal(sep, False)
+    assert sep.sum() >= nb * (nb - 1) // 2
+    assert np.abs(off[sep]).max() <= 1e-9 * scale
+    assert np.abs(off).max() <= 2e-6 * scale
+    np.testing.assert_allclose(np.diag(A), diag, atol=1e-8 * scale)

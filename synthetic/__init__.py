@@ -19,5 +19,6 @@ from .systems import (  # noqa: F401
     ring_workload,
     standard_gamma,
     with_near_duplicate_aux,
+    without_basis_functions,
     WORKLOADS,
 )

@@ -284,3 +284,18 @@ def with_near_duplicate_aux(system: System, count: int, rel: float) -> System:
         system, name=f"{system.name}+dup{count}",
         aux_atom=np.concatenate([system.aux_atom, system.aux_atom[idx]]).astype(np.int32),
         aux_alpha=np.concatenate([system.aux_alpha, system.aux_alpha[idx] * (1.0 + rel)]))
+
+
+def without_basis_functions(system: System, count: int, naux_drop: int = 0) -> System:
+    """A copy of `system` without its last `count` basis functions (and its last
+    `naux_drop` auxiliary functions): odd and otherwise ragged sizes for the
+    kernels' edge paths.  N_Omega must still fit: N_I (1 + N_g) <= nbf."""
+    import dataclasses
+    nb = system.nbf - count
+    nx = system.naux - naux_drop
+    out = dataclasses.replace(system, name=f"{system.name}-{count}bf-{naux_drop}aux",
+                              bf_atom=system.bf_atom[:nb].copy(), bf_alpha=system.bf_alpha[:nb].copy(),
+                              aux_atom=system.aux_atom[:nx].copy(), aux_alpha=system.aux_alpha[:nx].copy())
+    if out.n_omega > out.nbf:
+        raise ValueError("N_Omega exceeds nbf")
+    return out

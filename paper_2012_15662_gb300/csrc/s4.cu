@@ -1202,7 +1202,8 @@ __global__ void __launch_bounds__(256) xf_to_digits_kernel(const int* Xf, const 
                                                            int m, int mp, int nbp, int nxp, __nv_bfloat16* L3,
                                                            __nv_bfloat16* L6, const float2* Cdf, float2* dpart) {
   pdl_entry();
-  __shared__ int tile[64][65];
+  __shared__ int tile[64][65];   // the integers Xf of the tile
+  __shared__ int ytile[64][65];  // their L3 values (scale e3), for the diagonal partials
   __shared__ int s3[64], s6[64];
   __shared__ float2 sc[64];
   __shared__ float2 red[8][64];
@@ -1244,6 +1245,11 @@ __global__ void __launch_bounds__(256) xf_to_digits_kernel(const int* Xf, const 
         if (nu + 1 < nb) *(__nv_bfloat162*)(o + (size_t)t * nbp) = dd[t];
         else o[(size_t)t * nbp] = dd[t].x;
       }
+      ytile[r][c0] = y0;
+      ytile[r][c0 + 1] = y1;
+    } else {
+      ytile[r][c0] = 0;
+      ytile[r][c0 + 1] = 0;
     }
     tile[r][c0] = x0;
     tile[r][c0 + 1] = x1;
@@ -1271,8 +1277,7 @@ __global__ void __launch_bounds__(256) xf_to_digits_kernel(const int* Xf, const 
       const float2 cv = sc[r];
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
-        const int d3 = s3[c0 + k] - s6[r];
-        const int y = rshift_round(tile[c0 + k][r], d3 > 0 ? d3 : 0);
+        const int y = ytile[c0 + k][r];
         const float yh = (float)(y >> 8) * 256.f, yl = (float)(y & 255);
         const float p0 = yh * cv.x;
         const float e0 = fmaf(yh, cv.x, -p0) + (yh * cv.y + yl * cv.x);

@@ -139,3 +139,50 @@ def test_wrong_sign_weak_weak_gradient_fails_finite_differences(monkeypatch):
         return g
     monkeypatch.setattr(onopt, "energy_dn", bad)
     assert not fd_ok()
+
+
+def _flambda_fixture():
+    from oracle import orbopt
+    w = make_workload("square4")
+    s = w.system
+    B, L, G = ri.setup(s)
+    H = I.core_hamiltonian(s)
+    sub, rank = pairing_columns(s.n_strong, s.n_weak_per)
+    return orbopt, w, s, B, H, I.nuclear_repulsion(s), sub, rank
+
+
+def test_reversed_flambda_off_diagonal_fails_descent_pin(monkeypatch):
+    """F_qp = lambda_pq - lambda_qp (the gradient's sign flipped): the step that the
+    descent pin of test_oracle_orbopt requires to lower E raises it instead."""
+    orbopt, w, s, B, H, enuc, sub, rank = _flambda_fixture()
+    nb = s.nbf
+    E0, lam = orbopt.energy_lambda(s, B, H, enuc, w.C, w.gamma, sub, rank)
+    D = np.arange(nb, dtype=np.float64)
+    bound = 1e-5 * np.abs(lam - lam.T).max()
+    good = orbopt.flambda_matrix
+    monkeypatch.setattr(orbopt, "flambda_matrix", lambda lam_, diag, b: good(lam_.T, diag, b))
+    C1, _ = orbopt.flambda_step(w.C, lam, D, bound)
+    U = w.C.T @ C1
+    U = U * np.sign(np.diag(U))[None, :]
+    E1, _ = orbopt.energy_lambda(s, B, H, enuc, w.C @ U, w.gamma, sub, rank)
+    assert E1 > E0
+
+
+def test_descending_eigenvector_order_fails_stationary_pin(monkeypatch):
+    """Eigenvectors taken in decreasing order of eigenvalue (aufbau reversed): at a
+    stationary point the step no longer keeps the orbitals."""
+    orbopt, w, s, B, H, enuc, sub, rank = _flambda_fixture()
+    nb = s.nbf
+    rng = np.random.default_rng(4)
+    S = rng.standard_normal((nb, nb))
+    lam = S + S.T
+    D = np.sort(rng.uniform(-3.0, 3.0, nb))
+
+    def reversed_step(C, lam_, diag, bound):
+        eps, U = np.linalg.eigh(orbopt.flambda_matrix(lam_, diag, bound))
+        return C @ U[:, ::-1], eps[::-1]
+
+    monkeypatch.setattr(orbopt, "flambda_step", reversed_step)
+    C1, eps = orbopt.flambda_step(w.C, lam, D, bound=0.1)
+    assert not np.allclose(np.abs(C1.T @ w.C), np.eye(nb), atol=1e-6)
+    assert not np.allclose(eps, D, atol=1e-6)

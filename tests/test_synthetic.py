@@ -45,3 +45,14 @@ def test_ring_geometry():
     assert np.all(np.abs(d - 1.54) < 0.08)
     sub, rank = pairing_columns(24, 4)
     assert sub.max() == 23
+
+
+def test_without_basis_functions_trims_the_tail():
+    from synthetic import make_system, without_basis_functions
+    s = make_system("ring", n_c=5, seed=77, jitter=0.02, n_weak_per=3)
+    t = without_basis_functions(s, 3, 5)
+    assert (t.nbf, t.naux) == (s.nbf - 3, s.naux - 5)
+    assert (t.bf_alpha == s.bf_alpha[:-3]).all() and (t.aux_atom == s.aux_atom[:-5]).all()
+    assert t.n_omega == s.n_omega and t.atom_xyz is s.atom_xyz
+    with pytest.raises(ValueError):
+        without_basis_functions(s, s.nbf - s.n_omega + 1)

@@ -21,7 +21,9 @@ pnof7      occupation map, PNOF7 coupling coefficients, energy (Eq. PNOF) and
 brute      four-index fitted ERIs and the explicit O(N^5) transform of
            Eqs. (Jpq)-(Kpq) / Table 1, used to pin the factored path.
 rhf        closed-shell determinant energy from the AO density, the special
-           case PNOF7 reduces to when every strong orbital is fully occupied.
+           case PNOF7 reduces to when every strong orbital is fully occupied;
+           the closed-shell Hartree-Fock orbitals of the NO guess (Sec. 4), by
+           Roothaan-Hall iterations in the overlap metric with DIIS.
 onopt      the occupation (gamma) optimisation for fixed orbitals: dE/dn,
            dn/dgamma, dE/dgamma and an L-BFGS minimiser (Sec. 2, "Occupancy
            Optimization with RI"), and the standard starting guess.

@@ -186,3 +186,21 @@ def test_descending_eigenvector_order_fails_stationary_pin(monkeypatch):
     C1, eps = orbopt.flambda_step(w.C, lam, D, bound=0.1)
     assert not np.allclose(np.abs(C1.T @ w.C), np.eye(nb), atol=1e-6)
     assert not np.allclose(eps, D, atol=1e-6)
+
+
+def test_full_weight_exchange_fails_printed_h2_scf():
+    """F = H + J - K (the exchange's 1/2 dropped, a plausible slip): the SCF no
+    longer reproduces the printed minimal-basis H2 energies."""
+    import json
+    import os
+    from tests.test_oracle_rhf import GOLDEN, _h2_sto3g
+    g = json.load(open(os.path.join(GOLDEN, "sto3g_h2_scf.json")))
+    S, H, eri, enuc = _h2_sto3g()
+    good = rhf.jk_exact(eri)
+
+    def bad(D):
+        Jd, Kd = good(D)
+        return Jd, 2.0 * Kd
+
+    r = rhf.scf(H, S, bad, 1, enuc)
+    assert abs(r["E"] - g["E_total"]) > 10 * g["tolerance"] or abs(r["eps"][0] - g["eps1"]) > 10 * g["tolerance"]

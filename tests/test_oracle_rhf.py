@@ -85,3 +85,24 @@ def test_ri_scf_energy_is_a_minimum(sq_scf):
         C1 = C @ expm(kappa)                     # stays S-orthonormal
         E1 = rhf.closed_shell_energy(B, H, C1[:, :no], enuc)
         assert E1 > r["E"]
+
+
+def test_pnof7_at_hf_orbitals(sq_scf):
+    """At the SCF orbitals PNOF7 with every strong orbital full (gamma = 0) is the
+    SCF energy; optimising the occupations from the standard guess then gives a
+    small negative correlation energy (gamma = 0 is itself a feasible point)."""
+    from oracle import onopt, pnof7
+    from synthetic import pairing_columns
+    s, B, H, S, enuc, r = sq_scf
+    m = s.n_omega
+    C = r["C"]
+    rows = ri.all_rows(B, C, m)
+    Hd = np.einsum("mp,mn,np->p", C[:, :m], H, C[:, :m])
+    sub, rank = pairing_columns(s.n_strong, s.n_weak_per)
+    g0 = np.zeros(s.n_strong * s.n_weak_per)
+    n0 = pnof7.occupations(g0, s.n_strong, s.n_weak_per, sub, rank)
+    A, Bc = pnof7.coupling(n0, sub, rank)
+    assert pnof7.energy(n0, Hd, rows["J"], rows["K"], A, Bc, enuc) == pytest.approx(r["E"], abs=1e-10)
+    _, E_opt, _, _, _ = onopt.optimize(onopt.standard_guess(s.n_strong, s.n_weak_per), s.n_strong, s.n_weak_per,
+                                       sub, rank, Hd, rows["J"], rows["K"], enuc)
+    assert -1.0 < E_opt - r["E"] < 0.0

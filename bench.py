@@ -62,11 +62,19 @@ def algorithmic_bytes(s):
 
 
 def workload_desc(name):
-    from synthetic import make_workload
-    w = make_workload(name)
-    s = w.system
-    return w, (f"{name}: s-type ring, nbf={s.nbf}, naux={s.naux}, N_I={s.n_strong}, "
+    from synthetic import workload_system
+    s = workload_system(name)
+    return s, (f"{name}: s-type ring, nbf={s.nbf}, naux={s.naux}, N_I={s.n_strong}, "
                f"N_g={s.n_weak_per}, N_Omega={s.n_omega}")
+
+
+def engine_workload(bd, name, precision, stream=None):
+    """A context for the named workload and the workload itself, its orbitals
+    C = S^-1/2 Q built from the overlap matrix the engine evaluated at init."""
+    from synthetic import make_workload, workload_system
+    eng = bd.Engine(workload_system(name), precision, stream=stream)
+    w = make_workload(name, eng.fetch(bd.DONOF_RI_FETCH_OVERLAP))
+    return eng, w
 
 
 def algorithmic_flops(s):
@@ -185,31 +193,69 @@ def read_traffic(workload, precision, row):
 # ---------------------------------------------------------------------------
 # CPU oracle (baseline and reference arm)
 # ---------------------------------------------------------------------------
+# Largest auxiliary set the oracle sample evaluates whole; beyond it the sample runs
+# rows a1-a6 on the leading auxiliary functions and scales them (all of a1-a6 are sums
+# over the auxiliary index, so their cost is proportional to the number of P).
+ORACLE_WHOLE_NAUX = 1000
+ORACLE_SLICE_NAUX = 48
+
+
 def _oracle_sample(name, budget_s):
-    """Run whole iterations of the oracle until budget_s is spent; return ms/iteration and count."""
+    """Time the oracle on the workload until budget_s is spent; returns
+    (ms per iteration, repetitions, description of the sample)."""
+    from scipy.linalg import solve_triangular
     from oracle import integrals as I, pnof7, ri
     from synthetic import make_workload, pairing_columns
-    w = make_workload(name)
+    w = make_workload(name, I.overlap)
     s = w.system
-    B, L, G = ri.setup(s)
     H = I.core_hamiltonian(s)
     e_nuc = I.nuclear_repulsion(s)
     sub, rank = pairing_columns(s.n_strong, s.n_weak_per)
     m = s.n_omega
-    times = []
-    t_end = time.perf_counter() + budget_s
-    while True:
-        t0 = time.perf_counter()
-        r = ri.all_rows(B, w.C, m)
-        n = pnof7.occupations(w.gamma, s.n_strong, s.n_weak_per, sub, rank)
+    n = pnof7.occupations(w.gamma, s.n_strong, s.n_weak_per, sub, rank)
+
+    def a7(r):
         A, Bc = pnof7.coupling(n, sub, rank)
         pnof7.lagrangian(w.C, H, r["Jao"], r["Kao"], n, A, Bc)
         Hd = np.einsum("mp,mn,np->p", w.C[:, :m], H, w.C[:, :m])
         pnof7.energy(n, Hd, r["J"], r["K"], A, Bc, e_nuc)
-        times.append(time.perf_counter() - t0)
-        if time.perf_counter() > t_end:
-            break
-    return 1000.0 * float(np.mean(times)), len(times)
+
+    if s.naux <= ORACLE_WHOLE_NAUX:
+        B, L, G = ri.setup(s)
+        times = []
+        t_end = time.perf_counter() + budget_s
+        while True:
+            t0 = time.perf_counter()
+            a7(ri.all_rows(B, w.C, m))
+            times.append(time.perf_counter() - t0)
+            if time.perf_counter() > t_end:
+                break
+        return (1000.0 * float(np.mean(times)), len(times),
+                f"{len(times)} whole iterations of {name} (all rows, FP64 numpy/BLAS) in ~{budget_s:.0f} s")
+    # B^P of the leading k auxiliary functions needs only the leading block of the
+    # metric's Cholesky factor and the matching (P|mu nu) (forward substitution)
+    k = ORACLE_SLICE_NAUX
+    G = I.metric(s)
+    Lk = np.linalg.cholesky(G[:k, :k])
+    e3 = I.eri3(s, slice(0, k))
+    Bk = solve_triangular(Lk, e3.reshape(k, -1), lower=True).reshape(k, s.nbf, s.nbf)
+    del e3
+    t0 = time.perf_counter()
+    r = ri.all_rows(Bk, w.C, m)
+    t_rows = [time.perf_counter() - t0]
+    t0 = time.perf_counter()
+    a7(r)
+    t_a7 = time.perf_counter() - t0
+    t_end = time.perf_counter() + max(0.0, budget_s - t_rows[0] - t_a7)
+    while time.perf_counter() < t_end:
+        t0 = time.perf_counter()
+        ri.all_rows(Bk, w.C, m)
+        t_rows.append(time.perf_counter() - t0)
+    scale = s.naux / k
+    ms = 1000.0 * (float(np.mean(t_rows)) * scale + t_a7)
+    return (ms, len(t_rows),
+            f"rows a1-a6 of {name} on the first {k} of {s.naux} auxiliary functions ({len(t_rows)} repetitions, "
+            f"time x {scale:.2f}) plus the energy and Lagrangian (a7) once at full size; FP64 numpy/BLAS")
 
 
 def cpu_baseline(name, budget_s=12.0):
@@ -223,9 +269,8 @@ def cpu_baseline(name, budget_s=12.0):
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
     if out.returncode != 0:
         return {"value": None, "unit": UNIT, "cores": cores, "kind": "oracle", "error": out.stderr[-300:]}
-    ms, iters = json.loads(out.stdout.strip().splitlines()[-1])
-    return {"value": ms, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{iters} whole iterations of {name} (all rows, FP64 numpy/BLAS) in ~{budget_s:.0f} s"}
+    ms, iters, sample = json.loads(out.stdout.strip().splitlines()[-1])
+    return {"value": ms, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
 
 
 # ---------------------------------------------------------------------------
@@ -247,12 +292,17 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c6h12")
+    ap.add_argument("--workload", default="c20h40",
+                    help="timed workload (default: C20H40, the largest one-GPU configuration)")
     ap.add_argument("--precision", default="slice4", choices=["slice4", "tf32x3", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="launch eagerly instead of replaying a CUDA graph")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default SLICE4 tile schedule")
+    ap.add_argument("--fp64-steps", type=int, default=2,
+                    help="iterations of the plain FP64 form on the same workload (mixed vs FP64 key; 0: skip)")
+    ap.add_argument("--extra-workloads", default="c6h12,c16h32",
+                    help="comma-separated workloads also timed (CUDA-graph iterations) as extra keys")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -263,7 +313,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return 0
-        w, desc = workload_desc(args.workload)
+        _, desc = workload_desc(args.workload)
         budget = max(2.0, min(20.0, 0.5 * (args.steps + args.warmup)))
         cb = cpu_baseline(args.workload, budget_s=budget)
         line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
@@ -283,11 +333,11 @@ def main():
         dist.init_process_group("nccl", rank=rank, world_size=world)
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    w, desc = workload_desc(args.workload)
-    s = w.system
+    _, desc = workload_desc(args.workload)
     prec = {"slice4": bd.DONOF_RI_SLICE4, "tf32x3": bd.DONOF_RI_TF32X3, "fp64": bd.DONOF_RI_FP64}[args.precision]
     stream = torch.cuda.Stream(device=dev)
-    eng = bd.Engine(s, prec, stream=stream.cuda_stream)
+    eng, w = engine_workload(bd, args.workload, prec, stream=stream.cuda_stream)
+    s = w.system
     nb, m = s.nbf, s.n_omega
     C_dev = torch.from_numpy(bd.Engine.colmajor(w.C)).to(dev)
     g_dev = torch.from_numpy(np.ascontiguousarray(w.gamma)).to(dev)
@@ -471,11 +521,83 @@ def main():
         "hbm_kernels": hbm_kernels,
         "roofline": roof, "clocks": clocks, "gpu_launches": int(launches), "e2e": e2e,
     }
+    # the result of the last timed iteration (for the mixed vs FP64 comparison)
+    torch.cuda.synchronize()
+    res = {"E": float(E_dev.item()), "J": J_dev.cpu().numpy(), "K": K_dev.cpu().numpy(),
+           "lam": L_dev.cpu().numpy()}
+    eng.close()
+    del flush
+    torch.cuda.empty_cache()
+    if args.fp64_steps > 0 and prec != bd.DONOF_RI_FP64:
+        line["mixed_vs_fp64"] = fp64_comparison(bd, torch, dev, args, w, res, value)
+    extra = [x for x in args.extra_workloads.split(",") if x and x != args.workload]
+    if extra and world == 1:
+        line["other_workloads"] = {x: time_workload(bd, torch, dev, x, prec) for x in extra}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload)
     print(json.dumps(line))
-    eng.close()
     return 0
+
+
+def _graph_iterations(bd, torch, eng, w, stream, steps, warmup):
+    """ms per CUDA-graph iteration (device events, L2 flushed between steps) and the last outputs."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    nb, m = eng.nbf, eng.n_omega
+    C_dev = torch.from_numpy(bd.Engine.colmajor(w.C)).to(dev)
+    g_dev = torch.from_numpy(np.ascontiguousarray(w.gamma)).to(dev)
+    J = torch.empty((m, m), dtype=torch.float64, device=dev)
+    K = torch.empty((m, m), dtype=torch.float64, device=dev)
+    E = torch.empty(1, dtype=torch.float64, device=dev)
+    L = torch.empty(nb * nb, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            bd.donof_ri_iteration(eng.ctx, C_dev, g_dev, bd.DONOF_RI_FULL, J, K, E, L)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        for a, b in evs:
+            flush.zero_()
+            a.record(stream)
+            bd.donof_ri_iteration(eng.ctx, C_dev, g_dev, bd.DONOF_RI_FULL, J, K, E, L)
+            b.record(stream)
+    torch.cuda.synchronize()
+    bd.donof_ri_sync(eng.ctx)
+    ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+    return ms, {"E": float(E.item()), "J": J.cpu().numpy(), "K": K.cpu().numpy(), "lam": L.cpu().numpy()}
+
+
+def fp64_comparison(bd, torch, dev, args, w, res, mixed_ms):
+    """The plain FP64 GPU form on the same workload and orbitals: ms per iteration
+    (one CUDA graph per iteration, like the mixed form) and the mixed form's
+    deviation from it in E, J, K and lambda."""
+    stream = torch.cuda.Stream(device=dev)
+    t0 = time.perf_counter()
+    from synthetic import workload_system
+    eng = bd.Engine(workload_system(args.workload), bd.DONOF_RI_FP64, stream=stream.cuda_stream)
+    init_s = time.perf_counter() - t0
+    ms, r64 = _graph_iterations(bd, torch, eng, w, stream, args.fp64_steps, 1)
+    eng.close()
+    torch.cuda.empty_cache()
+    return {"fp64_ms_per_iteration": ms, "mixed_ms_per_iteration": mixed_ms, "speedup": ms / mixed_ms,
+            "fp64_iterations_timed": args.fp64_steps, "fp64_init_s": init_s,
+            "abs_dE_eh": abs(res["E"] - r64["E"]), "E_fp64_eh": r64["E"],
+            "max_abs_dJ": float(np.abs(res["J"] - r64["J"]).max()),
+            "max_abs_dK": float(np.abs(res["K"] - r64["K"]).max()),
+            "max_abs_dlambda": float(np.abs(res["lam"] - r64["lam"]).max()),
+            "note": "same orbitals and angles; FP64 form = DONOF_RI_FP64 (DFMA), mixed = the timed form"}
+
+
+def time_workload(bd, torch, dev, name, prec, steps=10):
+    """ms per CUDA-graph iteration of another workload (default schedule, no autotuning)."""
+    stream = torch.cuda.Stream(device=dev)
+    eng, w = engine_workload(bd, name, prec, stream=stream.cuda_stream)
+    ms, r = _graph_iterations(bd, torch, eng, w, stream, steps, 3)
+    eng.close()
+    torch.cuda.empty_cache()
+    s = w.system
+    return {"ms_per_iteration": ms, "steps": steps, "E_eh": r["E"],
+            "shape": f"nbf={s.nbf}, naux={s.naux}, N_Omega={s.n_omega}"}
 
 
 if __name__ == "__main__":

@@ -314,6 +314,20 @@ const char* donof_ri_strerror(int status);
 /* Number of kernels the context has launched since init (for launch accounting). */
 long long donof_ri_launch_count(const donof_ri_ctx* ctx);
 
+/*
+ * Check of the fault path of the bounded device-side waits (the paper has no
+ * counterpart: this is the engine's own failure detection).  Every mbarrier wait
+ * in the engine's tensor-core kernels gives up after about two seconds, records
+ * a timeout in the context's status word and lets its CTA exit with no copy or
+ * MMA in flight; the next synchronising call returns DONOF_RI_E_TIMEOUT and the
+ * context stays usable.  This call launches one CTA on the context's stream whose
+ * wait, on an mbarrier that nothing completes, runs out after limit_ns
+ * nanoseconds (1e3 <= limit_ns <= 5e9), so that the same path can be tested
+ * without faulting or hanging the GPU.  Asynchronous; the timeout is reported by
+ * the next synchronising call (e.g. donof_ri_sync).  Errors: E_ARG, E_CUDA.
+ */
+int donof_ri_check_wait_timeout(donof_ri_ctx* ctx, long long limit_ns);
+
 /* Hot-path rows timed by the profiler (CUDA events on the context's stream). */
 #define DONOF_RI_ROW_HALF 0      /* a1: half transform b^P_{p nu}                     */
 #define DONOF_RI_ROW_DIAG 1      /* a2: diagonal b^P_pp                               */
@@ -493,11 +507,14 @@ int donof_ri_gamma_guess(donof_ri_ctx* ctx, donof_mlp* net, double clip, double*
  * naux floats, naux rounded up to 4) and up to 16 chunk partials (n_omega^2
  * floats each).  Sizes that do not fit return DONOF_RI_E_ARG before any work.
  * The first call on a device (the current one) looks up the array's device
- * address and prepares the kernel; make that first call before any stream
- * capture.  Every call uses the same array, which keeps the last call's
- * contents; calls whose work overlaps on the GPU (other streams, other host
- * threads) race on it and must be serialised by the caller.  A device-side
- * wait that times out leaves J incomplete and is not reported.
+ * address and the tensor-map encoder; make that first call before any stream
+ * capture.  First calls from several host threads are serialised inside the
+ * library.  Every call uses the same array, which keeps the last call's
+ * contents (the status word is cleared by each call); calls whose work
+ * overlaps on the GPU (other streams, other host threads) race on it and must
+ * be serialised by the caller.  A device-side wait that times out (a bounded
+ * spin of about two seconds) is not returned as a status, since the call does
+ * not synchronise: every element of J is then set to NaN instead.
  * Errors: E_ARG (null pointer, sizes), E_CUDA, E_UNSUPPORTED.
  */
 int donof_ri_jmo_noalloc(const double* d, int naux, int n_omega, double* J, void* stream);

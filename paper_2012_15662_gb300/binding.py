@@ -49,7 +49,7 @@ EXPORTS = [
     "donof_ri_strerror", "donof_ri_launch_count", "donof_ri_profile", "donof_ri_profile_read",
     "donof_ri_iteration", "donof_ri_jmo_noalloc", "donof_ri_optimize_occupations",
     "donof_ri_on_features", "donof_ri_gamma_guess", "donof_ri_rotate_orbitals", "donof_ri_autotune", "donof_ri_set_schedule", "donof_ri_exact_jk",
-    "donof_ri_energy_lagrangian_contracted", "donof_ri_flambda_step",
+    "donof_ri_energy_lagrangian_contracted", "donof_ri_flambda_step", "donof_ri_check_wait_timeout",
     "donof_mlp_create", "donof_mlp_param_count", "donof_mlp_set_params", "donof_mlp_get_params",
     "donof_mlp_set_normalization", "donof_mlp_forward", "donof_mlp_loss_grad", "donof_mlp_train_step",
     "donof_mlp_destroy",
@@ -109,6 +109,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.donof_ri_strerror.restype = ctypes.c_char_p
     lib.donof_ri_launch_count.argtypes = [vp]
     lib.donof_ri_launch_count.restype = ctypes.c_longlong
+    lib.donof_ri_check_wait_timeout.argtypes = [vp, ctypes.c_longlong]
+    lib.donof_ri_check_wait_timeout.restype = i
     lib.donof_ri_jmo_noalloc.argtypes = [vp, i, i, vp, vp]
     lib.donof_ri_jmo_noalloc.restype = i
     lib.donof_ri_iteration.argtypes = [vp, vp, vp, i, vp, vp, vp, vp, i]
@@ -251,6 +253,11 @@ def donof_ri_destroy(ctx):
 
 def donof_ri_launch_count(ctx) -> int:
     return int(load().donof_ri_launch_count(ctx))
+
+
+def donof_ri_check_wait_timeout(ctx, limit_ns: int):
+    """Launch the bounded-wait check (reported as DONOF_RI_E_TIMEOUT by the next sync)."""
+    _check(load().donof_ri_check_wait_timeout(ctx, int(limit_ns)), "donof_ri_check_wait_timeout")
 
 
 def donof_ri_iteration(ctx, C, gamma, mode: int, J=None, K=None, E=None, lam=None, use_graph: bool = True):
@@ -468,6 +475,18 @@ class Engine:
 
     def launches(self) -> int:
         return donof_ri_launch_count(self.ctx)
+
+    def overlap(self) -> np.ndarray:
+        """The basis overlap matrix S the context evaluated at init."""
+        return self.fetch(DONOF_RI_FETCH_OVERLAP)
+
+
+def engine_and_workload(name: str, precision: int = DONOF_RI_FP64, seed=None, stream=None):
+    """A context for a named synthetic workload and the workload, whose orbitals
+    C = S^-1/2 Q are built from the overlap matrix this context evaluated."""
+    from synthetic import make_workload, workload_system
+    eng = Engine(workload_system(name, seed), precision, stream=stream)
+    return eng, make_workload(name, eng.overlap(), seed=seed)
 
     def optimize_occupations(self, gamma0: np.ndarray, max_iter: int = 5000, gtol: float = 1e-8,
                              etol: float = 1e-14):

@@ -3,6 +3,7 @@
 // dispatched to the FP64 path (path64.cu) or the split-precision tensor-core
 // path (tc.cu); nothing here computes.
 #include "common.cuh"
+#include "tcgen05.cuh"
 
 #include <stdlib.h>
 #include <string.h>
@@ -167,6 +168,31 @@ const char* donof_ri_strerror(int status) {
 }
 
 long long donof_ri_launch_count(const donof_ri_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+namespace donof {
+// One thread waits, through the engine's bounded mbarrier wait, for phase 0 of a
+// barrier that nothing arrives on: the wait runs out after limit_ns and records
+// DEV_TIMEOUT in the context's status word, exactly as a timed-out wait inside a
+// GEMM kernel does.  No copy or MMA is in flight, so the CTA exits cleanly.
+__global__ void wait_timeout_check_kernel(unsigned long long limit_ns, int* status) {
+  __shared__ uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    abort_flag = 0;
+    fence_barrier_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_wait_for(&bar, 0, &abort_flag, status, limit_ns);
+}
+}  // namespace donof
+
+int donof_ri_check_wait_timeout(donof_ri_ctx* ctx, long long limit_ns) {
+  if (!ctx || limit_ns < 1000 || limit_ns > 5000000000LL) return DONOF_RI_E_ARG;
+  donof::wait_timeout_check_kernel<<<1, 32, 0, ctx->stream>>>((unsigned long long)limit_ns, ctx->d_status);
+  DONOF_LAUNCH_CHECK(ctx);
+  return DONOF_RI_OK;
+}
 
 int donof_ri_destroy(donof_ri_ctx* ctx) {
   if (!ctx) return DONOF_RI_OK;

@@ -15,8 +15,8 @@
 // rotation is kept as X = V - I so that small rotations keep their relative
 // precision.  The eigenvectors, sorted by eigenvalue, are then refined in FP64
 // (orthonormalisation and two first-order corrections against F^lambda in FP64),
-// C U is formed in FP64 and one Newton-Schulz step restores orthonormality to
-// FP64 rounding.
+// C U is formed in FP64 and one Newton-Schulz step in the overlap metric restores
+// C^T S C = I to FP64 rounding (the orbitals are orthonormal functions).
 #include "common.cuh"
 
 #include <math.h>
@@ -638,9 +638,11 @@ int flambda_step(donof_ri_ctx* ctx, const double* dprev, int first, double bound
   }
   int rc;
   if ((rc = eig_refine(ctx, n, Fd, U, T, W, Z, K, eps))) return rc;
-  // (C U)^T = U^T C^T, then one Newton-Schulz step on its rows
+  // (C U)^T = U^T C^T, then one Newton-Schulz step in the overlap metric:
+  // W = (C U)^T S (C U) = T S T^T (K is free after the refinement)
   if ((rc = fl_mm(ctx, n, U, true, ctx->d_C, false, T, 1.0, 0.0))) return rc;
-  if ((rc = fl_mm(ctx, n, T, false, T, true, W, 1.0, 0.0))) return rc;        // W = T T^T
+  if ((rc = fl_mm(ctx, n, ctx->d_S, false, T, true, K, 1.0, 0.0))) return rc;  // K = S T^T
+  if ((rc = fl_mm(ctx, n, T, false, K, false, W, 1.0, 0.0))) return rc;        // W = T S T^T
   fl_identity_axpy_kernel<<<nblk, 256, 0, ctx->stream>>>(n, 1.5, -0.5, W, Z);
   DONOF_LAUNCH_CHECK(ctx);
   if ((rc = fl_mm(ctx, n, Z, false, T, false, ctx->d_C, 1.0, 0.0))) return rc;

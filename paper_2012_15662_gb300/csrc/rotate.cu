@@ -7,8 +7,11 @@
 //
 // expm by scaling and squaring: X = kappa / 2^s with ||X||_1 <= 1/4, Taylor
 // series to order 12 in Horner form (truncation below 1e-17), then s squarings;
-// the rotated orbitals are re-orthonormalised by one Newton-Schulz step
-// C <- C (3 I - C^T C) / 2, which removes the rounding drift of repeated steps.
+// the rotated orbitals are re-orthonormalised in the overlap metric by one
+// Newton-Schulz step C <- C (3 I - C^T S C) / 2, which removes the rounding drift
+// of repeated steps (the orbitals are orthonormal functions, C^T S C = I; a
+// rotation in orbital space keeps that exactly, so the step only corrects
+// rounding and expects orbitals that are S-orthonormal on entry).
 // All FP64, with the library's tiled DGEMM.
 #include "common.cuh"
 
@@ -115,15 +118,18 @@ int rotate_orbitals(donof_ri_ctx* ctx, double radius, double* scratch, double* g
   }
   // d_C is column-major, i.e. row-major C^T: (C U)^T = U^T C^T
   if ((rc = gemm_rr(ctx, n, U, true, ctx->d_C, T, 1.0, 0.0))) return rc;
-  // Newton-Schulz: C <- C (3 I - C^T C) / 2; with Ct = C^T (row-major): S = Ct Ct^T, Ct <- Z Ct
+  // Newton-Schulz in the overlap metric: C <- C (3 I - C^T S C) / 2.  With Ct = C^T
+  // (row-major, in T): X = S C = S Ct^T (into K, free after the exponential), then
+  // W = Ct X = C^T S C; Ct <- Z Ct with Z = (3 I - W) / 2 (symmetric).
   {
     Gemm64 g{};
     g.M = n; g.N = n; g.K = n; g.batch = 1;
-    g.A = T; g.sAm = n; g.sAk = 1;
+    g.A = ctx->d_S; g.sAm = n; g.sAk = 1;
     g.B = T; g.sBk = 1; g.sBn = n;
-    g.C = W; g.sCm = n; g.sCn = 1;
+    g.C = K; g.sCm = n; g.sCn = 1;
     g.alpha = 1.0; g.beta = 0.0;
-    if ((rc = launch_dgemm(ctx, g))) return rc;  // W = Ct Ct^T = C^T C
+    if ((rc = launch_dgemm(ctx, g))) return rc;  // K = S C
+    if ((rc = gemm_rr(ctx, n, T, false, K, W, 1.0, 0.0))) return rc;  // W = C^T S C
   }
   rot_axpy_identity_kernel<<<nblk, 256, 0, ctx->stream>>>(n, 1.5, -0.5, W, U);  // Z = (3 I - W) / 2
   DONOF_LAUNCH_CHECK(ctx);

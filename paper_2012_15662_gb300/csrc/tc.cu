@@ -34,8 +34,10 @@
 #include "common.cuh"
 #include "tcgen05.cuh"
 
+#include <atomic>
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <mutex>
 #include <stdlib.h>
 #include <string.h>
 
@@ -949,11 +951,30 @@ constexpr size_t NOALLOC_SCRATCH_FLOATS = (size_t)6 << 20;  // 24 MiB
 static __device__ __align__(256) float g_noalloc_scratch[NOALLOC_SCRATCH_FLOATS];
 
 struct NoallocDevice {
-  bool ready;
+  std::atomic<bool> ready;
   float* scratch;  // device address of g_noalloc_scratch on this device
   PFN_cuTensorMapEncodeTiled_v12000 encode;
 };
 static NoallocDevice g_noalloc_dev[64];
+// Serialises the one-time set-up of a device when several host threads make their
+// first call at once; later calls read `ready` (acquire) and take no lock.
+static std::mutex g_noalloc_setup_mu;
+
+// J = sum of the chunk partials (fixed order), or NaN everywhere when a device-side
+// wait of the GEMM timed out (its status word is non-zero): an aborted CTA leaves its
+// partials unwritten, and the scratch array still holds an earlier call's.
+__global__ void noalloc_reduce_kernel(const float* partial, int nsplit, int m, const int* status, double* J) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long mm = (long long)m * m;
+  if (i >= mm) return;
+  if (*status != 0) {
+    J[i] = __longlong_as_double(0x7FF8000000000000LL);
+    return;
+  }
+  double s = 0.0;
+  for (int k = 0; k < nsplit; ++k) s += (double)partial[(size_t)k * mm + i];
+  J[i] = s;
+}
 
 // d (FP64 [naux][m]) -> split rows [m][nxp] (hi, lo).
 __global__ void noalloc_split_diag_kernel(const double* d, int nx, int m, int nxp, float* hi, float* lo) {
@@ -997,17 +1018,20 @@ extern "C" int donof_ri_jmo_noalloc(const double* d, int naux, int n_omega, doub
     return DONOF_RI_E_CUDA;
   }
   NoallocDevice& nd = g_noalloc_dev[dev];
-  if (!nd.ready) {
+  if (!nd.ready.load(std::memory_order_acquire)) {
     // One-time set-up for this device (the current one): the device address of the
-    // scratch array, the tensor-map encoder and the kernel's shared-memory opt-in.
-    void* ptr = nullptr;
-    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
-      cudaGetLastError();
-      return DONOF_RI_E_CUDA;
+    // scratch array and the tensor-map encoder.
+    std::lock_guard<std::mutex> lock(g_noalloc_setup_mu);
+    if (!nd.ready.load(std::memory_order_relaxed)) {
+      void* ptr = nullptr;
+      if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
+        cudaGetLastError();
+        return DONOF_RI_E_CUDA;
+      }
+      if (get_encode(&nd.encode)) return DONOF_RI_E_UNSUPPORTED;
+      nd.scratch = (float*)ptr;
+      nd.ready.store(true, std::memory_order_release);
     }
-    if (get_encode(&nd.encode)) return DONOF_RI_E_UNSUPPORTED;
-    nd.scratch = (float*)ptr;
-    nd.ready = true;
   }
   float* d_hi = nd.scratch;
   float* d_lo = nd.scratch + split_floats;
@@ -1037,7 +1061,6 @@ extern "C" int donof_ri_jmo_noalloc(const double* d, int naux, int n_omega, doub
   if (cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess) return DONOF_RI_E_CUDA;
   noalloc_split_diag_kernel<<<ceil_div_u((long long)nx * m, 256), 256, 0, s>>>(d, nx, m, nxp, d_hi, d_lo);
   tc_gemm_kernel<K_JMO><<<pl.grid, TC_THREADS, pl.smem, s>>>(p);
-  reduce_partials_kernel<<<ceil_div_u((long long)m * m, 256), 256, 0, s>>>(partial, p.nsplit, m, m, J, 0, nullptr,
-                                                                            nullptr);
+  noalloc_reduce_kernel<<<ceil_div_u((long long)m * m, 256), 256, 0, s>>>(partial, p.nsplit, m, status, J);
   return cudaGetLastError() == cudaSuccess ? DONOF_RI_OK : DONOF_RI_E_CUDA;
 }

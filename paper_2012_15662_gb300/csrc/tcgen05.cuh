@@ -52,20 +52,26 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Wait for phase `parity` of an mbarrier with a time limit; on timeout the CTA's
-// abort flag and the context's status word are set and false is returned.
-static __device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status) {
+// Wait for phase `parity` of an mbarrier with a time limit of limit_ns; on timeout
+// the CTA's abort flag and the context's status word are set and false is returned.
+static __device__ __noinline__ bool mbar_wait_for(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                                  int* status, unsigned long long limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   unsigned long long t0 = globaltimer();
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
     if (abort_flag && *abort_flag) return false;
-    if (globaltimer() - t0 > TC_TIMEOUT_NS) {
+    if (globaltimer() - t0 > limit_ns) {
       if (abort_flag) *abort_flag = 1;
       atomicCAS(status, 0, (int)DEV_TIMEOUT);
       return false;
     }
   }
+}
+
+// The engine's kernels wait with the TC_TIMEOUT_NS limit.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status) {
+  return mbar_wait_for(bar, parity, abort_flag, status, TC_TIMEOUT_NS);
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1) {

@@ -23,11 +23,10 @@ from . import binding as bd
 
 
 def run(name: str, gtol: float = 1e-8) -> dict:
-    from synthetic import make_workload, standard_gamma
-    w = make_workload(name)
+    from synthetic import standard_gamma
+    eng, w = bd.engine_and_workload(name, bd.DONOF_RI_FP64)
     s = w.system
     m = s.n_omega
-    eng = bd.Engine(s, bd.DONOF_RI_FP64)
     g0 = standard_gamma(s.n_strong, s.n_weak_per)
     eng.transform(w.C, bd.DONOF_RI_FULL)
     J_ri, K_ri = eng.jk_mo()

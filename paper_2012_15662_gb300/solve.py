@@ -160,14 +160,15 @@ def main():
     outer / inner iterations, energies, ms per inner iteration."""
     import argparse
     import json
-    from synthetic import make_workload, standard_gamma
+    from synthetic import standard_gamma
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="c6h12")
     ap.add_argument("--outer", type=int, default=4)
     ap.add_argument("--inner", type=int, default=25)
     ap.add_argument("--learned", type=int, default=0, help="train the warm-start network on this many rings first")
     args = ap.parse_args()
-    w = make_workload(args.workload)
+    eng0, w = bd.engine_and_workload(args.workload, bd.DONOF_RI_FP64)
+    eng0.close()
     s = w.system
     g0 = standard_gamma(s.n_strong, s.n_weak_per)
     runs = [("fp64", bd.DONOF_RI_FP64, None), ("slice4", bd.DONOF_RI_SLICE4, None)]

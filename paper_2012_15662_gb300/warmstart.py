@@ -7,7 +7,8 @@ returned folded into [0, pi/2]); the network is trained by donof_mlp_train_step
 (forward, backward and Adam kernels) and applied by donof_ri_gamma_guess.
 
 The training targets are the converged angles the method itself generates on
-seeded synthetic rings (C6-C12, jitter 0.05 A, Haar-random orbitals), one
+seeded synthetic rings (C6-C12, jitter 0.05 A, orbitals S^-1/2 Q with Q
+Haar-random and S the overlap the engine evaluates for each ring), one
 sample per pairing subspace; the features are z-scored with the training set's
 mean and standard deviation.
 
@@ -37,12 +38,13 @@ def targets(gamma: np.ndarray, n_strong: int, n_weak_per: int) -> np.ndarray:
     return Y
 
 
-def sample(workload, precision=bd.DONOF_RI_SLICE4, max_iter=20000, etol=1e-13):
-    """(features, targets, iterations, energy) of one system from the standard guess."""
-    from synthetic import standard_gamma
-    s = workload.system
-    eng = bd.Engine(s, precision)
+def sample(n_c, seed, precision=bd.DONOF_RI_SLICE4, max_iter=20000, etol=1e-13, jitter=0.05):
+    """(features, targets, iterations, energy) of one seeded ring from the standard guess."""
+    from synthetic import make_system, ring_workload, standard_gamma
+    eng = bd.Engine(make_system("ring", n_c=n_c, seed=seed, jitter=jitter), precision)
     try:
+        workload = ring_workload(n_c, seed, eng.overlap(), jitter=jitter)
+        s = workload.system
         eng.transform(workload.C, bd.DONOF_RI_FULL)
         X = eng.on_features()
         g0 = standard_gamma(s.n_strong, s.n_weak_per)
@@ -54,12 +56,11 @@ def sample(workload, precision=bd.DONOF_RI_SLICE4, max_iter=20000, etol=1e-13):
 
 def training_set(n_systems: int, first_seed: int = 1000, n_c_range=(6, 12), precision=bd.DONOF_RI_SLICE4):
     """Features and targets of n_systems seeded rings (C6..C12 in turn)."""
-    from synthetic import ring_workload
     lo, hi = n_c_range
     Xs, Ys = [], []
     for k in range(n_systems):
         n_c = lo + k % (hi - lo + 1)
-        X, Y, _, _ = sample(ring_workload(n_c, first_seed + k), precision)
+        X, Y, _, _ = sample(n_c, first_seed + k, precision)
         Xs.append(X)
         Ys.append(Y)
     return np.concatenate(Xs), np.concatenate(Ys)
@@ -94,11 +95,14 @@ def train(X, Y, steps=6000, batch=1024, lr=3e-3, weight_decay=1e-4, seed=0, net=
     return net, float(loss[0])
 
 
-def compare(workload, net, precision=bd.DONOF_RI_SLICE4, clip=0.05, max_iter=20000, etol=1e-13):
-    """Occupation optimisation of one system from the standard and from the learned guess."""
+def compare(workload, net, precision=bd.DONOF_RI_SLICE4, clip=0.05, max_iter=20000, etol=1e-13, eng=None):
+    """Occupation optimisation of one system (a synthetic.Workload) from the standard
+    and from the learned guess; `eng` a context of that system (made and closed here
+    when None)."""
     from synthetic import standard_gamma
     s = workload.system
-    eng = bd.Engine(s, precision)
+    if eng is None:
+        eng = bd.Engine(s, precision)
     try:
         eng.transform(workload.C, bd.DONOF_RI_FULL)
         out = {}
@@ -122,7 +126,6 @@ def main():
     ap.add_argument("--eval", default="c20h40", help="evaluation workload name")
     ap.add_argument("--eval-seeds", type=int, default=3, help="evaluation systems (the named one, then reseeded)")
     args = ap.parse_args()
-    from synthetic import make_workload
     t0 = time.perf_counter()
     X, Y = training_set(args.train)
     t_data = time.perf_counter() - t0
@@ -131,8 +134,8 @@ def main():
     t_train = time.perf_counter() - t0
     rows = []
     for k in range(args.eval_seeds):
-        w = make_workload(args.eval) if k == 0 else make_workload(args.eval, seed=900 + k)
-        rows.append(compare(w, net))
+        eng, w = bd.engine_and_workload(args.eval, bd.DONOF_RI_SLICE4, seed=None if k == 0 else 900 + k)
+        rows.append(compare(w, net, eng=eng))
     print(json.dumps({"train_systems": args.train, "samples": int(X.shape[0]), "data_s": t_data, "train_s": t_train,
                       "final_loss": loss, "eval": args.eval, "results": rows}))
 

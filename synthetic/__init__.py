@@ -13,6 +13,8 @@ from .systems import (  # noqa: F401
     Workload,
     make_system,
     make_workload,
+    orthonormal_orbitals,
+    workload_system,
     pairing_columns,
     random_orthogonal,
     draw_gamma,

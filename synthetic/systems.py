@@ -12,12 +12,17 @@ synthetic stand-in with the same shape:
 * basis: normalised s-type Gaussians centred on the atoms, with
   even-tempered exponent tables per element;
 * auxiliary basis: s-type Gaussians, even-tempered, per element;
-* orbitals: a seeded Haar-random orthogonal matrix (columns = orbitals);
+* orbitals: C = S^-1/2 Q, a seeded Haar-random rotation Q of the symmetric
+  (Loewdin) orthonormalisation of the basis, so that the columns are
+  orthonormal functions (C^T S C = I); the overlap S is supplied by the
+  caller (the oracle's integrals in the tests, the engine's own in the
+  benchmark and the drivers);
 * occupations: the PNOF7 electron-pairing angles gamma, drawn uniformly.
 
 Nothing in this module evaluates an integral or any other part of the
 method: it only produces numbers that both the oracle and the GPU engine
-take as inputs.
+take as inputs (the one matrix function here, S^-1/2 of a given overlap,
+is the input recipe's orthonormalisation, not a step of the method).
 """
 from __future__ import annotations
 
@@ -219,8 +224,9 @@ class Workload:
 
     name: str
     system: System
-    C: np.ndarray            # [nbf, nbf], column p is orbital p
+    C: np.ndarray            # [nbf, nbf], column p is orbital p; C^T S C = I
     gamma: np.ndarray        # [N_I * N_g]
+    Q: np.ndarray = None     # the seeded rotation, C = S^-1/2 Q
     meta: dict = field(default_factory=dict)
 
 
@@ -239,27 +245,56 @@ WORKLOADS = {
 }
 
 
-def make_workload(name: str, seed: int | None = None) -> Workload:
-    """Build a named workload; `seed` overrides the stored seed."""
+def orthonormal_orbitals(S: np.ndarray, Q: np.ndarray) -> np.ndarray:
+    """C = S^-1/2 Q for a symmetric positive definite overlap S and an orthogonal
+    Q: the symmetric (Loewdin) orthonormalisation of the basis followed by the
+    rotation Q, so that C^T S C = Q^T Q = I.  S^-1/2 from the eigenvectors of S."""
+    S = np.asarray(S, dtype=np.float64)
+    ev, U = np.linalg.eigh(0.5 * (S + S.T))
+    if not ev.min() > 0.0:
+        raise ValueError("the overlap matrix is not positive definite")
+    return np.ascontiguousarray((U * ev ** -0.5) @ (U.T @ Q))
+
+
+def _overlap_of(overlap, system: System) -> np.ndarray:
+    S = overlap(system) if callable(overlap) else overlap
+    S = np.asarray(S, dtype=np.float64)
+    if S.shape != (system.nbf, system.nbf):
+        raise ValueError(f"overlap has shape {S.shape}, expected {(system.nbf, system.nbf)}")
+    return S
+
+
+def workload_system(name: str, seed: int | None = None) -> System:
+    """The system of a named workload alone (the same object make_workload builds)."""
     spec = dict(WORKLOADS[name])
     kind = spec.pop("kind")
-    s = spec.pop("seed") if seed is None else seed
-    spec.pop("seed", None)
-    system = make_system(kind, seed=s, **spec)
+    stored = spec.pop("seed")
+    return make_system(kind, seed=stored if seed is None else seed, **spec)
+
+
+def make_workload(name: str, overlap, seed: int | None = None) -> Workload:
+    """Build a named workload; `seed` overrides the stored seed.
+
+    `overlap` is the basis overlap matrix S of the workload's system, or a
+    callable system -> S.  The orbitals are C = S^-1/2 Q with Q Haar-random."""
+    s = WORKLOADS[name]["seed"] if seed is None else seed
+    system = workload_system(name, seed)
     rng = np.random.default_rng(10_000 + s)
-    C = random_orthogonal(system.nbf, rng)
+    Q = random_orthogonal(system.nbf, rng)
     gamma = draw_gamma(system.n_strong, system.n_weak_per, rng)
-    return Workload(name=name, system=system, C=C, gamma=gamma, meta={"seed": s})
+    C = orthonormal_orbitals(_overlap_of(overlap, system), Q)
+    return Workload(name=name, system=system, C=C, gamma=gamma, Q=Q, meta={"seed": s})
 
 
-def ring_workload(n_c: int, seed: int, jitter: float = 0.05) -> Workload:
-    """A CnH2n ring with its own seeded geometry and Haar-random orbitals (the
+def ring_workload(n_c: int, seed: int, overlap, jitter: float = 0.05) -> Workload:
+    """A CnH2n ring with its own seeded geometry and orbitals S^-1/2 Q (the
     learned-guess training and evaluation sets: rings C6-C12, jitter 0.05 A)."""
     system = make_system("ring", n_c=n_c, seed=seed, jitter=jitter)
     rng = np.random.default_rng(10_000 + seed)
-    C = random_orthogonal(system.nbf, rng)
+    Q = random_orthogonal(system.nbf, rng)
     gamma = draw_gamma(system.n_strong, system.n_weak_per, rng)
-    return Workload(name=f"c{n_c}h{2 * n_c}-s{seed}", system=system, C=C, gamma=gamma, meta={"seed": seed})
+    C = orthonormal_orbitals(_overlap_of(overlap, system), Q)
+    return Workload(name=f"c{n_c}h{2 * n_c}-s{seed}", system=system, C=C, gamma=gamma, Q=Q, meta={"seed": seed})
 
 
 def standard_gamma(n_strong: int, n_weak_per: int, n_strong_occ: float = 0.98) -> np.ndarray:

@@ -8,7 +8,7 @@ so a slip here would mis-state every fraction.
 import pytest
 
 import bench
-from synthetic import make_workload
+from tests.workloads import make_workload
 
 # (workload, a1, a3, a5 or a6, a7 GEMM), three significant digits
 TABLE = [

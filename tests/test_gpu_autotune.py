@@ -7,7 +7,8 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 from oracle import integrals as I, pnof7, ri  # noqa: E402
-from synthetic import make_workload, pairing_columns  # noqa: E402
+from synthetic import pairing_columns  # noqa: E402
+from tests.workloads import make_workload  # noqa: E402
 
 
 def test_autotune_call_order():

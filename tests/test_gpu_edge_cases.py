@@ -17,8 +17,9 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 from oracle import integrals as I, onopt, pnof7, rhf, ri  # noqa: E402
-from synthetic import (draw_gamma, make_system, make_workload, pairing_columns,  # noqa: E402
+from synthetic import (draw_gamma, make_system, orthonormal_orbitals, pairing_columns,   # noqa: E402
                        random_orthogonal, standard_gamma, without_basis_functions)
+from tests.workloads import make_workload  # noqa: E402
 
 
 @pytest.mark.parametrize("prec", ["fp64", "slice4"])
@@ -44,7 +45,7 @@ def test_pairing_shapes_on_a_ragged_ring(n_weak):
     from paper_2012_15662_gb300 import binding as bd
     s = make_system("ring", n_c=5, seed=77, jitter=0.02, n_weak_per=n_weak)
     rng = np.random.default_rng(177)
-    C = random_orthogonal(s.nbf, rng)
+    C = orthonormal_orbitals(I.overlap(s), random_orthogonal(s.nbf, rng))
     gamma = draw_gamma(s.n_strong, s.n_weak_per, rng)
     m = s.n_omega
     B, L, G = ri.setup(s)
@@ -79,7 +80,7 @@ def test_odd_sizes(prec):
     s = without_basis_functions(make_system("ring", n_c=5, seed=77, jitter=0.02, n_weak_per=3), 3, 5)
     assert s.nbf % 2 == 1 and s.naux % 2 == 1
     rng = np.random.default_rng(178)
-    C = random_orthogonal(s.nbf, rng)
+    C = orthonormal_orbitals(I.overlap(s), random_orthogonal(s.nbf, rng))
     gamma = draw_gamma(s.n_strong, s.n_weak_per, rng)
     m = s.n_omega
     B, L, G = ri.setup(s)

@@ -16,7 +16,8 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 from oracle import brute, integrals as I, onopt, pnof7  # noqa: E402
-from synthetic import make_workload, pairing_columns  # noqa: E402
+from synthetic import pairing_columns  # noqa: E402
+from tests.workloads import make_workload  # noqa: E402
 
 
 def test_exact_square4_matches_conventional_oracle():

@@ -16,7 +16,8 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 from oracle import integrals as I, orbopt, ri  # noqa: E402
-from synthetic import make_workload, pairing_columns  # noqa: E402
+from synthetic import pairing_columns  # noqa: E402
+from tests.workloads import make_workload  # noqa: E402
 
 
 @pytest.mark.parametrize("name", ["square4", "c6h12", "c10h20"])
@@ -46,7 +47,7 @@ def test_flambda_step_matches_oracle(name):
     C_g = Ccm.reshape(nb, nb).T
     assert abs(gmax - gmax_o) <= 1e-10 * gmax_o
     assert 1 <= sweeps < 30
-    np.testing.assert_allclose(C_g.T @ C_g, np.eye(nb), atol=1e-13)
+    np.testing.assert_allclose(C_g.T @ I.overlap(s) @ C_g, np.eye(nb), atol=1e-13)
     np.testing.assert_allclose(diag, eps_o, atol=1e-9 * np.abs(eps_o).max())
     # eigenvectors column by column where the eigenvalue is separated (FP32 Jacobi,
     # then two FP64 first-order refinements)
@@ -96,7 +97,7 @@ def test_flambda_call_order():
 
 
 def test_flambda_block_path_properties():
-    """nbf 480 (block Jacobi): the step's rotation U = C0^T C1 is orthogonal and
+    """nbf 480 (block Jacobi): the step's rotation U = C0^T S C1 is orthogonal and
     diagonalises F^lambda (built here from the engine's own lambda by the stated
     rule), with the returned eigenvalues on the diagonal in increasing order (to the
     FP32 solver's accuracy)."""
@@ -119,7 +120,8 @@ def test_flambda_block_path_properties():
     # ordered by the FP32 solve; the returned values are the FP64-refined ones
     assert np.diff(diag).min() >= -2e-6 * np.abs(diag).max()
     C1 = Ccm.reshape(nb, nb).T
-    np.testing.assert_allclose(C1.T @ C1, np.eye(nb), atol=1e-12)
+    S = I.overlap(s)
+    np.testing.assert_allclose(C1.T @ S @ C1, np.eye(nb), atol=1e-12)
     # F^lambda: F_qp = lambda_qp - lambda_pq below the diagonal, mirrored, each element
     # above the bound multiplied by 1/10 until it is not
     F = np.tril(lam - lam.T, -1)
@@ -131,7 +133,7 @@ def test_flambda_block_path_properties():
         F[big] *= 0.1
         a[big] *= 0.1
     F = F + F.T + np.diag(np.diag(lam))
-    U = w.C.T @ C1
+    U = w.C.T @ S @ C1
     A = U.T @ F @ U
     off = A - np.diag(np.diag(A))
     scale = np.abs(F).max()

@@ -12,7 +12,7 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 from oracle import integrals as I, pnof7, ri  # noqa: E402
-from synthetic import make_workload  # noqa: E402
+from tests.workloads import make_workload  # noqa: E402
 
 
 def _oracle(w):

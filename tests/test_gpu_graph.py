@@ -16,7 +16,9 @@ pytestmark = pytest.mark.gpu
 def test_graph_matches_eager(prec_name):
     import torch
     from paper_2012_15662_gb300 import binding as bd
-    from synthetic import make_workload, random_orthogonal
+    from oracle import integrals as I
+    from synthetic import orthonormal_orbitals, random_orthogonal
+    from tests.workloads import make_workload
     prec = {"fp64": bd.DONOF_RI_FP64, "tf32x3": bd.DONOF_RI_TF32X3, "slice4": bd.DONOF_RI_SLICE4}[prec_name]
     w = make_workload("c6h12")
     s = w.system
@@ -24,7 +26,7 @@ def test_graph_matches_eager(prec_name):
     stream = torch.cuda.Stream(device=dev)
     eng = bd.Engine(s, prec, stream=stream.cuda_stream)
     nb, m = s.nbf, s.n_omega
-    C2 = random_orthogonal(nb, np.random.default_rng(77))
+    C2 = orthonormal_orbitals(I.overlap(w.system), random_orthogonal(nb, np.random.default_rng(77)))
     C_dev = torch.from_numpy(bd.Engine.colmajor(w.C)).to(dev)
     g_dev = torch.from_numpy(np.ascontiguousarray(w.gamma)).to(dev)
     out = {k: torch.zeros(sz, dtype=torch.float64, device=dev)
@@ -76,7 +78,7 @@ def test_gemm_kernel_profile_rows():
     and per memory-bound pass (rows 14, 15), nested inside its row, and the profiled (serial) iteration gives the forked one's bits."""
     import torch
     from paper_2012_15662_gb300 import binding as bd
-    from synthetic import make_workload
+    from tests.workloads import make_workload
     w = make_workload("square4")
     s = w.system
     eng = bd.Engine(s, bd.DONOF_RI_SLICE4)
@@ -117,7 +119,9 @@ def test_graph_with_pinned_host_buffers(prec_name):
     current contents."""
     import torch
     from paper_2012_15662_gb300 import binding as bd
-    from synthetic import make_workload, random_orthogonal
+    from oracle import integrals as I
+    from synthetic import orthonormal_orbitals, random_orthogonal
+    from tests.workloads import make_workload
     prec = {"fp64": bd.DONOF_RI_FP64, "slice4": bd.DONOF_RI_SLICE4}[prec_name]
     w = make_workload("square4")
     s = w.system
@@ -149,7 +153,7 @@ def test_graph_with_pinned_host_buffers(prec_name):
     for k in ref:
         np.testing.assert_array_equal(h1[k], ref[k])
         np.testing.assert_array_equal(h2[k], ref[k])
-    C2 = random_orthogonal(nb, np.random.default_rng(78))
+    C2 = orthonormal_orbitals(I.overlap(w.system), random_orthogonal(nb, np.random.default_rng(78)))
     C_h.copy_(torch.from_numpy(bd.Engine.colmajor(C2)))
     h3 = run(C_h, g_h, host_out, True)
     C_dev.copy_(torch.from_numpy(bd.Engine.colmajor(C2)).to(dev))

@@ -24,7 +24,7 @@ def _oracle_rows(system, C, B):
 def test_modified_fit_nothing_raised(name):
     from paper_2012_15662_gb300 import binding as bd
     from oracle import integrals as I, modchol, pnof7, ri
-    from synthetic import make_workload
+    from tests.workloads import make_workload
     w = make_workload(name)
     s = w.system
     eng = bd.Engine(s, bd.DONOF_RI_FP64, metric=bd.DONOF_RI_METRIC_MODIFIED, metric_tol=1e-10)
@@ -64,7 +64,7 @@ def eng_fetch(eng, what, dst):
 def test_modified_fit_with_raised_eigenvalues():
     from paper_2012_15662_gb300 import binding as bd
     from oracle import integrals as I, modchol
-    from synthetic import make_workload
+    from tests.workloads import make_workload
     w = make_workload("square4")
     s = w.system
     tol = 1e-3
@@ -90,7 +90,8 @@ def test_modified_fit_with_raised_eigenvalues():
 def test_redundant_auxiliary_set(rel):
     from paper_2012_15662_gb300 import binding as bd
     from oracle import ri
-    from synthetic import make_workload, with_near_duplicate_aux
+    from synthetic import with_near_duplicate_aux
+    from tests.workloads import make_workload
     w = make_workload("square4")
     s = w.system
     sd = with_near_duplicate_aux(s, 8, rel)
@@ -111,7 +112,7 @@ def test_redundant_auxiliary_set(rel):
 def test_slice4_on_the_modified_fit():
     from paper_2012_15662_gb300 import binding as bd
     from oracle import ri
-    from synthetic import make_workload
+    from tests.workloads import make_workload
     w = make_workload("c6h12")
     s = w.system
     eng = bd.Engine(s, bd.DONOF_RI_SLICE4, metric=bd.DONOF_RI_METRIC_MODIFIED, metric_tol=1e-10)
@@ -126,7 +127,7 @@ def test_slice4_on_the_modified_fit():
 
 def test_init_ex_rejects_bad_options():
     from paper_2012_15662_gb300 import binding as bd
-    from synthetic import make_workload
+    from tests.workloads import make_workload
     s = make_workload("square4").system
     for metric, tol in ((7, 1e-8), (bd.DONOF_RI_METRIC_MODIFIED, 0.0), (bd.DONOF_RI_METRIC_MODIFIED, 1.5)):
         with pytest.raises(bd.DonofError) as ei:

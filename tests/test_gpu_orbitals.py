@@ -1,7 +1,10 @@
 """GPU orbital rotation step and the outer / inner iterations.
 
 * donof_ri_rotate_orbitals against oracle/orbopt.rotation_step (scipy's expm) at
-  the oracle's own Lagrangian: the FP64 engine to 1e-10, orthonormal to 1e-13;
+  the oracle's own Lagrangian: the FP64 engine to 1e-10, orthonormal in the
+  overlap metric (C^T S C = I) to 1e-13;
+* 100 inner iterations of the rotation driver follow the oracle's driver
+  (oracle/orbopt.optimize) and keep C^T S C = I to 1e-12;
 * the inner iterations never raise the energy and shrink the rotation gradient;
 * the outer / inner driver (solve.py) lowers the energy over its iterations, and
   the FP64 and SLICE4 engines follow the same path within the energy bar.
@@ -12,7 +15,8 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 from oracle import integrals as I, orbopt, ri  # noqa: E402
-from synthetic import make_workload, pairing_columns, standard_gamma  # noqa: E402
+from synthetic import pairing_columns, standard_gamma  # noqa: E402
+from tests.workloads import make_workload  # noqa: E402
 
 
 @pytest.mark.parametrize("name", ["square4", "c6h12"])
@@ -32,7 +36,26 @@ def test_rotation_step_matches_oracle(name):
     assert gmax == pytest.approx(np.abs(lamo - lamo.T).max(), rel=1e-10)
     Co = orbopt.rotation_step(w.C, lamo, 0.1)
     assert np.abs(C1 - Co).max() <= 1e-10
-    assert np.abs(C1.T @ C1 - np.eye(s.nbf)).max() <= 1e-13
+    S = I.overlap(s)
+    assert np.abs(C1.T @ S @ C1 - np.eye(s.nbf)).max() <= 1e-13
+
+
+@pytest.mark.parametrize("name,iters", [("square4", 100), ("c6h12", 25)])
+def test_inner_iterations_follow_oracle_and_stay_orthonormal(name, iters):
+    from paper_2012_15662_gb300 import binding as bd, solve
+    w = make_workload(name)
+    s = w.system
+    sub, rank = pairing_columns(s.n_strong, s.n_weak_per)
+    Co, Eo, go, ito = orbopt.optimize(s, w.C, w.gamma, sub, rank, max_iter=iters, gtol=0.0)
+    eng = bd.Engine(s, bd.DONOF_RI_FP64)
+    r = solve.orbital_iterations(eng, bd.Engine.colmajor(w.C), w.gamma, max_iter=iters, gtol=0.0, etol=0.0)
+    eng.close()
+    C = r["C"].reshape(s.nbf, s.nbf).T
+    S = I.overlap(s)
+    assert r["iterations"] == ito == iters
+    assert np.abs(C.T @ S @ C - np.eye(s.nbf)).max() <= 1e-12
+    assert abs(r["E"] - Eo) <= 1e-9 * max(1.0, abs(Eo))
+    assert np.abs(C - Co).max() <= 1e-8
 
 
 def test_inner_iterations_descend():

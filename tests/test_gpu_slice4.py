@@ -17,7 +17,8 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 from oracle import integrals as I, pnof7, ri  # noqa: E402
-from synthetic import make_workload, pairing_columns  # noqa: E402
+from synthetic import pairing_columns  # noqa: E402
+from tests.workloads import make_workload  # noqa: E402
 
 TOL_JK = 1e-7
 TOL_E = 1e-6

@@ -15,7 +15,8 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 from oracle import integrals as I, mlp as omlp, ri  # noqa: E402
-from synthetic import make_workload, pairing_columns, ring_workload  # noqa: E402
+from synthetic import pairing_columns  # noqa: E402
+from tests.workloads import make_workload, ring_workload  # noqa: E402
 
 F, H, O = 19, 64, 4
 

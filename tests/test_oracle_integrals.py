@@ -17,7 +17,8 @@ from scipy.integrate import quad
 from scipy.special import erf
 
 from oracle import integrals as I
-from synthetic.systems import System, make_workload
+from synthetic.systems import System
+from tests.workloads import make_workload
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 

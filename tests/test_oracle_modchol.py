@@ -18,7 +18,8 @@ import pytest
 import scipy.linalg as sl
 
 from oracle import integrals as I, modchol, ri
-from synthetic import make_workload, with_near_duplicate_aux
+from synthetic import with_near_duplicate_aux
+from tests.workloads import make_workload
 
 
 def _random_symmetric(n, seed):

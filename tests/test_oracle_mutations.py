@@ -8,7 +8,8 @@ import numpy as np
 import pytest
 
 from oracle import brute, integrals as I, pnof7, rhf, ri
-from synthetic.systems import make_workload, pairing_columns
+from synthetic.systems import pairing_columns
+from tests.workloads import make_workload
 
 
 @pytest.fixture(scope="module")

@@ -14,7 +14,8 @@ import numpy as np
 import pytest
 
 from oracle import integrals as I, onopt, pnof7, ri
-from synthetic import make_workload, pairing_columns
+from synthetic import pairing_columns
+from tests.workloads import make_workload
 
 
 def _random_problem(rng, n_strong=3, n_weak=3):

@@ -4,14 +4,15 @@
   rotation gradient dE/dkappa_qp = 4 (lambda_qp - lambda_pq), itself pinned by
   finite differences in test_oracle_pnof7 (a wrong sign or scale of the step
   fails this);
-* the rotated orbitals stay orthonormal;
+* the rotated orbitals stay orthonormal in the overlap metric (C^T S C = I);
 * the trust-radius driver never raises E.
 """
 import numpy as np
 import pytest
 
 from oracle import integrals as I, orbopt, ri
-from synthetic import make_workload, pairing_columns
+from synthetic import pairing_columns
+from tests.workloads import make_workload
 
 
 @pytest.fixture(scope="module")
@@ -37,7 +38,8 @@ def test_small_step_lowers_energy_by_the_first_order_amount(sq):
     predicted = -4.0 * r / gmax * np.sum(G[iu] ** 2)
     assert E1 < E0
     assert abs((E1 - E0) - predicted) <= 1e-2 * abs(predicted)
-    assert np.abs(C1.T @ C1 - np.eye(s.nbf)).max() < 1e-13
+    S = I.overlap(s)
+    assert np.abs(C1.T @ S @ C1 - np.eye(s.nbf)).max() < 1e-13
 
 
 def test_driver_never_raises_energy(sq):
@@ -56,11 +58,12 @@ def test_flambda_step_is_the_identity_at_a_stationary_point(sq):
     w, B, H, enuc, sub, rank = sq
     nb = w.system.nbf
     rng = np.random.default_rng(4)
-    S = rng.standard_normal((nb, nb))
-    lam = S + S.T
+    X = rng.standard_normal((nb, nb))
+    lam = X + X.T
     D = np.sort(rng.uniform(-3.0, 3.0, nb))
     C1, eps = orbopt.flambda_step(w.C, lam, D, bound=0.1)
-    np.testing.assert_allclose(np.abs(C1.T @ w.C), np.eye(nb), atol=1e-12)
+    # the rotation in orbital space is C^T S C1 (orbitals orthonormal in the overlap metric)
+    np.testing.assert_allclose(np.abs(C1.T @ I.overlap(w.system) @ w.C), np.eye(nb), atol=1e-12)
     np.testing.assert_allclose(eps, D, atol=1e-12)
 
 
@@ -77,7 +80,7 @@ def test_flambda_step_descends_by_the_first_order_amount(sq):
     D = np.arange(nb, dtype=np.float64)          # ascending, unit gaps
     bound = 1e-5 * np.abs(G).max()
     C1, eps = orbopt.flambda_step(w.C, lam, D, bound)
-    U = w.C.T @ C1
+    U = w.C.T @ I.overlap(s) @ C1
     U = U * np.sign(np.diag(U))[None, :]         # eigenvector signs as near the identity
     E1, _ = orbopt.energy_lambda(s, B, H, enuc, w.C @ U, w.gamma, sub, rank)
     il = np.tril_indices(nb, -1)

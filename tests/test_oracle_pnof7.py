@@ -16,7 +16,8 @@ import numpy as np
 import pytest
 
 from oracle import brute, integrals as I, pnof7, rhf, ri
-from synthetic.systems import make_workload, pairing_columns
+from synthetic.systems import pairing_columns
+from tests.workloads import make_workload
 
 
 @pytest.fixture(scope="module")
@@ -187,7 +188,8 @@ def test_contracted_lagrangian_equals_the_per_orbital_form(name):
     """lambda from the RI transforms directly (no J^(q), K^(q)) equals lambda from
     the per-orbital AO matrices: two routes through the same algebra."""
     from oracle import integrals as I, pnof7, ri
-    from synthetic import make_workload, pairing_columns
+    from synthetic import pairing_columns
+    from tests.workloads import make_workload
     w = make_workload(name)
     s = w.system
     m = s.n_omega

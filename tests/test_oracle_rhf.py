@@ -17,7 +17,7 @@ import pytest
 from scipy.linalg import expm
 
 from oracle import integrals as I, rhf, ri
-from synthetic import make_workload
+from tests.workloads import make_workload
 from synthetic.systems import System
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")

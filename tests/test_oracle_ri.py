@@ -11,7 +11,8 @@ import numpy as np
 import pytest
 
 from oracle import brute, integrals as I, ri
-from synthetic.systems import System, make_workload, random_orthogonal
+from synthetic.systems import System, random_orthogonal
+from tests.workloads import make_workload
 
 
 def _two_atom():

@@ -2,7 +2,9 @@
 import numpy as np
 import pytest
 
-from synthetic import make_workload, pairing_columns
+from oracle import integrals
+from synthetic import orthonormal_orbitals, pairing_columns
+from tests.workloads import make_workload
 
 SHAPES = {
     "square4": (24, 80, 4, 2, 12),
@@ -21,7 +23,10 @@ def test_shapes(name):
     assert (s.nbf, s.naux, s.n_strong, s.n_weak_per, s.n_omega) == (nbf, naux, ni, ng, nom)
     assert s.n_electrons == 2 * s.n_strong
     assert w.C.shape == (nbf, nbf)
-    np.testing.assert_allclose(w.C.T @ w.C, np.eye(nbf), atol=1e-12)
+    # orthonormal functions: C^T S C = I in the overlap metric (not C^T C = I)
+    S = integrals.overlap(s)
+    np.testing.assert_allclose(w.C.T @ S @ w.C, np.eye(nbf), atol=1e-11)
+    np.testing.assert_allclose(w.Q.T @ w.Q, np.eye(nbf), atol=1e-12)
     assert w.gamma.shape == (ni * ng,)
     assert ((w.gamma >= 0.05) & (w.gamma <= 0.3)).all()
 
@@ -56,3 +61,15 @@ def test_without_basis_functions_trims_the_tail():
     assert t.n_omega == s.n_omega and t.atom_xyz is s.atom_xyz
     with pytest.raises(ValueError):
         without_basis_functions(s, s.nbf - s.n_omega + 1)
+
+
+def test_orthonormal_orbitals_is_the_inverse_square_root():
+    """S^-1/2 Q: (S^-1/2)^2 S = I and S^-1/2 symmetric, on a random SPD matrix."""
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((9, 9))
+    S = A @ A.T + 0.5 * np.eye(9)
+    X = orthonormal_orbitals(S, np.eye(9))
+    np.testing.assert_allclose(X, X.T, atol=1e-13)
+    np.testing.assert_allclose(X @ X @ S, np.eye(9), atol=1e-12)
+    with pytest.raises(ValueError):
+        orthonormal_orbitals(-S, np.eye(9))

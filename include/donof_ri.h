@@ -51,7 +51,9 @@ extern "C" {
 #define DONOF_RI_E_ARG (-1)            /* bad size, null pointer, bad mode          */
 #define DONOF_RI_E_OOM (-2)            /* device allocation failed                  */
 #define DONOF_RI_E_CUDA (-3)           /* CUDA runtime / launch error               */
-#define DONOF_RI_E_METRIC_NOT_PD (-4)  /* Cholesky pivot of G below 1e-14 max(G_kk)  */
+#define DONOF_RI_E_METRIC_NOT_PD (-4)  /* Cholesky pivot of G (or, for DONOF_RI_SLICE4,
+                                          of the overlap S) below 1e-14 of the largest
+                                          diagonal element                          */
 #define DONOF_RI_E_NONFINITE (-5)      /* NaN / Inf in an input                     */
 #define DONOF_RI_E_TIMEOUT (-6)        /* a bounded device-side wait gave up        */
 #define DONOF_RI_E_STATE (-7)          /* call order (e.g. jk_mo before a FULL transform) */
@@ -66,9 +68,16 @@ extern "C" {
                               power-of-two exponent and four balanced 8-bit digits;
                               13 BF16 tensor-core MMAs per product (digit pairs of
                               weight >= 2^-32 of the leading pair), summed exactly in
-                              FP32 within 256-wide K chunks and in int64 across
-                              chunks: FP64-class results (about 2^-31 of the row
-                              scale) from BF16 tensor cores                          */
+                              FP32 within 512-wide K chunks and across chunks in
+                              int64 or double-float: FP64-class results (about 2^-31
+                              of the row scale) from BF16 tensor cores.  Computes in
+                              the orbital basis orthonormalised by the Cholesky
+                              factor of the overlap (S = L L^T: orbitals L^T C,
+                              fitted tensor L^-1 B L^-T, set up at init), where the
+                              orbital coefficients of orthonormal orbitals are at
+                              most 1 and the fixed-point products lose no bits to
+                              cancellation; AO outputs (b_half, J^(q), K^(q)) are
+                              transformed back when they are copied out             */
 
 /* Transform modes. */
 #define DONOF_RI_HALF 0  /* half transform + diagonal (orbital step, Table 3)          */

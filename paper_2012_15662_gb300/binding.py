@@ -481,13 +481,6 @@ class Engine:
         return self.fetch(DONOF_RI_FETCH_OVERLAP)
 
 
-def engine_and_workload(name: str, precision: int = DONOF_RI_FP64, seed=None, stream=None):
-    """A context for a named synthetic workload and the workload, whose orbitals
-    C = S^-1/2 Q are built from the overlap matrix this context evaluated."""
-    from synthetic import make_workload, workload_system
-    eng = Engine(workload_system(name, seed), precision, stream=stream)
-    return eng, make_workload(name, eng.overlap(), seed=seed)
-
     def optimize_occupations(self, gamma0: np.ndarray, max_iter: int = 5000, gtol: float = 1e-8,
                              etol: float = 1e-14):
         """(gamma, E, grad, iterations, stop reason) from the device L-BFGS (max_iter 0: evaluate only)."""
@@ -515,3 +508,11 @@ def engine_and_workload(name: str, precision: int = DONOF_RI_FP64, seed=None, st
         g = np.empty(self.system.n_strong * self.system.n_weak_per)
         _check(load().donof_ri_gamma_guess(self.ctx, net.ptr, float(clip), _ptr(g)), "donof_ri_gamma_guess")
         return g
+
+
+def engine_and_workload(name: str, precision: int = DONOF_RI_FP64, seed=None, stream=None):
+    """A context for a named synthetic workload and the workload, whose orbitals
+    C = S^-1/2 Q are built from the overlap matrix this context evaluated."""
+    from synthetic import make_workload, workload_system
+    eng = Engine(workload_system(name, seed), precision, stream=stream)
+    return eng, make_workload(name, eng.overlap(), seed=seed)

@@ -325,6 +325,7 @@ int donof_ri_init_ex(const donof_ri_system* sys, int precision, void* stream, co
   if (precision == DONOF_RI_TF32X3) TRY(mixed_init(ctx));
   if (precision == DONOF_RI_SLICE4) TRY(s4_init(ctx));
   if (cudaStreamSynchronize(s) != cudaSuccess) TRY(DONOF_RI_E_CUDA);
+  TRY(consume_status(ctx));  // the overlap's factorisation of the SLICE4 working basis
   if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess ||

@@ -148,6 +148,9 @@ int launch_dgemm(donof_ri_ctx* ctx, const Gemm64& g);
 int setup_integrals(donof_ri_ctx* ctx);
 int setup_cholesky_and_fit(donof_ri_ctx* ctx);
 int fit_forward(donof_ri_ctx* ctx);
+// A = L L^T in place (row-major n x n, lower factor) and R <- L^-1 R (R n x ncol row-major)
+int cholesky_lower(donof_ri_ctx* ctx, double* A, int n, double* maxdiag, double rel_min);
+int forward_subst(donof_ri_ctx* ctx, const double* L, int n, double* R, long long ncol);
 void max_diag_public(donof_ri_ctx* ctx, const double* G, double* out);
 // modchol.cu: G = P L D L^T P^T with the Cheng-Higham correction, B from it
 int setup_modified_and_fit(donof_ri_ctx* ctx, double tol);

@@ -20,11 +20,14 @@
 // every partial sum of groups 0..2 is an integer of magnitude <= 2^24 and their
 // FP32 accumulation is exact; groups 3 and 4 may round once they pass 2^24, an
 // error below 2^-38 of the leading group's scale.  After every chunk the
-// epilogue folds the five sums into one int64 per output (v = sum_g G_g
-// 2^(32 - 8g); the value is 2^(ea + eb - 46) v), so the reduction over K is
-// exact in its leading 38 bits and independent of order; the other errors are
-// the 31-bit digit representation of the operands and the dropped pair
-// products (g >= 5).
+// epilogue combines the five sums: J_pq and the multi-chunk J^(q), K^(q) and full
+// transform fold them into one int64 per output (v = sum_g G_g 2^(32 - 8g); the
+// value is 2^(ea + eb - 46) v), so the reduction over K is exact in its leading
+// 38 bits and independent of order; single-chunk units convert them straight to
+// a double-float pair (groups_to_df); the half transform rounds each group term
+// to an integer at its output scale (half_fold) and adds the chunks' integers.
+// The other errors are the 31-bit digit representation of the operands and the
+// dropped pair products (g >= 5).
 // Outputs feeding another GEMM are re-digitised in integer arithmetic, with
 // bound-based exponents (b_half) or exact row maxima (d, J^(q), K^(q)).
 //
@@ -117,21 +120,6 @@ struct S4Params {
 // ---------------------------------------------------------------------------
 // integer / double-float helpers
 // ---------------------------------------------------------------------------
-// round(v * 2^s) as an int32, clamped to [-2^30, 2^30].
-__device__ __forceinline__ int round_shift(long long v, int s) {
-  long long x;
-  if (s >= 0) {
-    x = s >= 40 ? (v > 0 ? (1LL << 40) : (v < 0 ? -(1LL << 40) : 0)) : (v << s);
-  } else {
-    const int sh = -s > 62 ? 62 : -s;
-    x = (v + (1LL << (sh - 1))) >> sh;
-  }
-  const long long lim = 1LL << 30;
-  x = x > lim ? lim : x;
-  x = x < -lim ? -lim : x;
-  return (int)x;
-}
-
 // Four balanced digits of |X| < 2^30 as BF16 values.  U = X + 0x80808080 holds
 // digit + 128 in each byte (the top digit lies in [-64, 64]).  A byte b placed
 // under the exponent of 2^23 reads as the float 2^23 + b, and subtracting
@@ -522,7 +510,9 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_ge
     const int wg = ew / 4;      // epilogue warpgroup: column blocks wg, wg + NWG, ...
     const int row = q * 32 + lane;
     constexpr bool SUM_DF = (KIND == S_FULLSQ || KIND == S_FOCK);
-    constexpr int NACC = (KIND == S_FOCK) ? 1 : BN / NWG;  // FOCK units are single chunks: no running sums
+    // FOCK units are single chunks, and the half transform keeps its partial sums in its
+    // output: neither carries running sums
+    constexpr int NACC = (KIND == S_FOCK || s4_half(KIND)) ? 1 : BN / NWG;
     long long acc[NACC];
     float sh[SUM_DF ? BN / NWG : 1], sl[SUM_DF ? BN / NWG : 1];
 #pragma unroll
@@ -648,14 +638,26 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_ge
             if (CW == 16) tmem_wait16(gr[g]);
             else tmem_wait8(gr[g]);
           }
-          if (s4_half(KIND) && (ONE || nch == 1)) {
-            // Single-chunk half transform: one output integer at the finer of the two
-            // output scales (exponents e3, e6), Xf = sum_g rint(G_g 2^(sigma - 8g)) in
-            // int32 (see half_fold), without the int64 fold.  xf_to_digits_kernel
-            // derives both digit layouts from it.
+          if (s4_half(KIND)) {
+            // Half transform: one output integer at the finer of the two output scales
+            // (exponents e3, e6), X = sum_g rint(G_g 2^(sigma - 8g)) in int32 per chunk
+            // (see half_fold), without an int64 fold.  A unit of several K chunks adds
+            // each chunk's integer to the one the same thread stored for the previous
+            // chunk of this unit (a read of its own write, held in L2) and clamps the
+            // sum, so no running sums occupy registers or local memory; each chunk adds
+            // at most 2.5 units of rounding.  xf_to_digits_kernel derives both digit
+            // layouts from the final integer.
             if (!rvalid) continue;
             const int lrow = lane / 16, l16 = lane % 16;
             int* basef = p.x6 + (size_t)P * p.m * p.nbp + nu;
+            int prev[ONE ? 1 : CW];
+            if (!ONE && ch > 0) {
+#pragma unroll
+              for (int j = 0; j < CW; ++j) {
+                const int col = nt * BN + c * CW + j;
+                prev[j] = col < p.m ? basef[(size_t)col * p.nbp] : 0;
+              }
+            }
 #pragma unroll
             for (int j = 0; j < CW; ++j) {
               const int i = c * CW + j;
@@ -665,12 +667,18 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_ge
 #pragma unroll
                 for (int g = 0; g < S4_NG; ++g) H[g] = __uint_as_float(gr[g][j]) * exp2_int(-8 * g);
                 const int emin = min(es_3[lrow * BN + i], es_6[i * 16 + l16]);
-                basef[(size_t)col * p.nbp] = half_fold(H, ea + es_b[i] + 17 - emin);
+                int X = half_fold(H, ea + es_b[i] + 17 - emin);
+                if (!ONE && ch > 0) {
+                  long long t = (long long)prev[j] + X;
+                  t = t > (1LL << 30) ? (1LL << 30) : (t < -(1LL << 30) ? -(1LL << 30) : t);
+                  X = (int)t;
+                }
+                basef[(size_t)col * p.nbp] = X;
               }
             }
             continue;
           }
-          if (s4_half(KIND) || KIND == S_JMO) {
+          if (KIND == S_JMO) {
             // int64 fold: running sums over K chunks (J_pq's partials stay integers)
             long long v[CW];
 #pragma unroll
@@ -684,20 +692,6 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_ge
 #pragma unroll
               for (int j = 0; j < CW; ++j) acc[NACC == 1 ? 0 : cb * CW + j] = v[j];
               continue;
-            }
-            if (!rvalid) continue;
-            if (s4_half(KIND)) {
-              const int lrow = lane / 16, l16 = lane % 16;
-              int* basef = p.x6 + (size_t)P * p.m * p.nbp + nu;
-#pragma unroll
-              for (int j = 0; j < CW; ++j) {
-                const int i = c * CW + j;
-                const int col = nt * BN + i;
-                if (col < p.m) {
-                  const int emin = min(es_3[lrow * BN + i], es_6[i * 16 + l16]);
-                  basef[(size_t)col * p.nbp] = round_shift(v[j], ea + es_b[i] - 15 - emin);
-                }
-              }
             }
             continue;
           }
@@ -1416,9 +1410,18 @@ struct donof::S4Buffers {
   int target[donof::S_NKINDS];                        // CTA count the split kinds aim at
   int *eB1, *eB5, *eC, *e3, *e6, *ed, *eJK;          // row exponents
   float *rmaxB, *maxB, *absC, *absCt;
-  float2* Cdf;    // C rows p (every p < nbf) as double-float pairs
-  float2* Hdf;    // H as double-float pairs (fixed at init)
-  float2* Cdfp;   // C rows p (< N_O) as double-float pairs, the energy prep's own copy (its stream
+  // Working basis: the orbital basis orthonormalised by the Cholesky factor of the
+  // overlap, chi' = chi L^-T with S = L L^T.  Orbitals are C' = L^T C (C'^T C' = I),
+  // the fitted tensor B'^P = L^-1 B^P L^-T and H' = L^-1 H L^-T; every GEMM operand
+  // and the energy row work in it, and AO outputs are transformed back.
+  double* Ls;     // L [mu][nu] row-major, lower triangle (FP64)
+  float2* LsTdf;  // L^T [nu][mu] as double-float pairs
+  float2* Cin;    // C^T rows [p][mu] (every p < nbf) as double-float pairs
+  double* Cp;     // C'^T rows [p][mu'] (every p < nbf), FP64
+  float2* Cinp;   // the energy prep's own double-float C^T rows (p < N_O)
+  float2* Cdf;    // C' rows p (every p < nbf) as double-float pairs
+  float2* Hdf;    // H' as double-float pairs (fixed at init)
+  float2* Cdfp;   // C' rows p (< N_O) as double-float pairs, the energy prep's own copy (its stream
                   // may run ahead of the transform that writes Cdf)
   float2* dpart;  // diagonal partials [nu tile][m][nx] from the digit pass
   double* dmat;   // d [m][nx] FP64
@@ -1519,6 +1522,59 @@ static void s4_plan_jkao(S4Buffers* sb) {
   // the shared memory holds the deeper of the two pipelines' stages
   const int sj = sb->plan[S_JAO].stages, sk = sb->plan[S_KAO].stages;
   if (p.stages > (sj > sk ? sj : sk)) p.stages = sj > sk ? sj : sk;
+}
+
+// L L^T = S (FP64 Cholesky of the overlap) into sb->Ls, Li = L^-1, and the fitted
+// tensor and core Hamiltonian in the working basis: Bw^P = Li B^P Li^T (Tb: scratch
+// of the same size), Hw = Li H Li^T; L^T as double-float pairs into sb->LsTdf.
+__global__ void transpose_df_kernel(const double* X, int n, float2* out) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= (long long)n * n) return;
+  const int r = (int)(i / n), c = (int)(i % n);
+  out[i] = to_df(X[(size_t)c * n + r]);
+}
+
+__global__ void identity64_kernel(int n, double* X) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= (long long)n * n) return;
+  X[i] = (i / n == i % n) ? 1.0 : 0.0;
+}
+
+static int s4_working_basis(donof_ri_ctx* ctx, double* Li, double* Tb, double* Bw, double* Hw) {
+  S4Buffers* sb = ctx->s4;
+  const int nb = ctx->nbf, nx = ctx->naux;
+  const long long n2 = (long long)nb * nb;
+  cudaStream_t s = ctx->stream;
+  int rc;
+  DONOF_CUDA_TRY(cudaMemcpyAsync(sb->Ls, ctx->d_S, n2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  if ((rc = cholesky_lower(ctx, sb->Ls, nb, ctx->d_scratch_max, 1e-14))) return rc;
+  identity64_kernel<<<ceil_div_u(n2, 256), 256, 0, s>>>(nb, Li);
+  DONOF_LAUNCH_CHECK(ctx);
+  if ((rc = forward_subst(ctx, sb->Ls, nb, Li, nb))) return rc;  // Li = L^-1
+  transpose_df_kernel<<<ceil_div_u(n2, 256), 256, 0, s>>>(sb->Ls, nb, sb->LsTdf);
+  DONOF_LAUNCH_CHECK(ctx);
+  for (int which = 0; which < 2; ++which) {
+    // X <- Li X (one matrix per auxiliary function), then X Li^T
+    const double* X = which == 0 ? ctx->d_B : ctx->d_H;
+    double* T = Tb;  // free again for H once Bw is formed
+    double* out = which == 0 ? Bw : Hw;
+    const int batch = which == 0 ? nx : 1;
+    Gemm64 g{};
+    g.M = nb; g.N = nb; g.K = nb; g.batch = batch;
+    g.A = Li; g.sAb = 0; g.sAm = nb; g.sAk = 1;
+    g.B = X; g.sBb = n2; g.sBk = nb; g.sBn = 1;
+    g.C = T; g.sCb = n2; g.sCm = nb; g.sCn = 1;
+    g.alpha = 1.0; g.beta = 0.0;
+    if ((rc = launch_dgemm(ctx, g))) return rc;
+    Gemm64 h{};
+    h.M = nb; h.N = nb; h.K = nb; h.batch = batch;
+    h.A = T; h.sAb = n2; h.sAm = nb; h.sAk = 1;
+    h.B = Li; h.sBb = 0; h.sBk = 1; h.sBn = nb;  // element (k, n) of Li^T = Li[n][k]
+    h.C = out; h.sCb = n2; h.sCm = nb; h.sCn = 1;
+    h.alpha = 1.0; h.beta = 0.0;
+    if ((rc = launch_dgemm(ctx, h))) return rc;
+  }
+  return DONOF_RI_OK;
 }
 
 int s4_init(donof_ri_ctx* ctx) {
@@ -1645,6 +1701,11 @@ int s4_init(donof_ri_ctx* ctx) {
   ALLOC(sb->maxB, nbs * nbs * 4);
   ALLOC(sb->absC, ms * nbs * 4);
   ALLOC(sb->absCt, ms * nbs * 4);
+  ALLOC(sb->Ls, nbs * nbs * 8);
+  ALLOC(sb->LsTdf, nbs * nbs * 8);
+  ALLOC(sb->Cin, nbs * nbs * 8);
+  ALLOC(sb->Cp, nbs * nbs * 8);
+  ALLOC(sb->Cinp, ms * nbs * 8);
   ALLOC(sb->Cdf, nbs * nbs * 8);
   ALLOC(sb->Hdf, nbs * nbs * 8);
   ALLOC(sb->Cdfp, ms * nbs * 8);
@@ -1661,26 +1722,52 @@ int s4_init(donof_ri_ctx* ctx) {
   ALLOC(sb->partial_j, jbytes);
 #undef ALLOC
 
-  // one-time digitisation of B in both operand layouts, and its maxima for the bounds
+  // The working basis (see S4Buffers): L from the overlap, then B' = L^-1 B L^-T and
+  // H' = L^-1 H L^-T in FP64 (temporaries freed after the digitisation), L^T as
+  // double-float pairs for the per-iteration C' = L^T C.
   cudaStream_t s = ctx->stream;
-  to_df_kernel<<<ceil_div_u(nbs * nbs, 256), 256, 0, s>>>(ctx->d_H, nbs * nbs, sb->Hdf);
+  double *Li = nullptr, *Tb = nullptr, *Bw = nullptr, *Hw = nullptr;
+  int rc;
+  auto free_tmp = [&]() {
+    if (Li) cudaFree(Li);
+    if (Tb) cudaFree(Tb);
+    if (Bw) cudaFree(Bw);
+    if (Hw) cudaFree(Hw);
+  };
+  if (cudaMalloc((void**)&Li, nbs * nbs * 8) != cudaSuccess || cudaMalloc((void**)&Tb, nxs * nbs * nbs * 8) != cudaSuccess ||
+      cudaMalloc((void**)&Bw, nxs * nbs * nbs * 8) != cudaSuccess || cudaMalloc((void**)&Hw, nbs * nbs * 8) != cudaSuccess) {
+    cudaGetLastError();
+    free_tmp();
+    return DONOF_RI_E_OOM;
+  }
+  if ((rc = s4_working_basis(ctx, Li, Tb, Bw, Hw))) {
+    cudaStreamSynchronize(s);
+    free_tmp();
+    return rc;
+  }
+  // one-time digitisation of B' in both operand layouts, and its maxima for the bounds
+  to_df_kernel<<<ceil_div_u(nbs * nbs, 256), 256, 0, s>>>(Hw, nbs * nbs, sb->Hdf);
   if (cudaMemsetAsync(sb->ticket, 0, sizeof(unsigned int), s) != cudaSuccess) return DONOF_RI_E_CUDA;
   {
-    long long rows = nxs * nbs;  // rows (P, nu) over mu (B symmetric)
-    slice_f64_kernel<<<ceil_div_u(rows * 32, 256), 256, 0, s>>>(ctx->d_B, rows, nb, nb, 1, sb->B1, nbp, sb->eB1,
+    long long rows = nxs * nbs;  // rows (P, nu) over mu (B' symmetric)
+    slice_f64_kernel<<<ceil_div_u(rows * 32, 256), 256, 0, s>>>(Bw, rows, nb, nb, 1, sb->B1, nbp, sb->eB1,
                                                                  nullptr, nullptr, nullptr);
     DONOF_LAUNCH_CHECK(ctx);
     long long rows5 = nbs * nbs;  // rows (mu nu) over P
-    slice_f64_kernel<<<ceil_div_u(rows5 * 32, 256), 256, 0, s>>>(ctx->d_B, rows5, nx, 1, nbs * nbs, sb->B5, nxp,
+    slice_f64_kernel<<<ceil_div_u(rows5 * 32, 256), 256, 0, s>>>(Bw, rows5, nx, 1, nbs * nbs, sb->B5, nxp,
                                                                   sb->eB5, nullptr, nullptr, nullptr);
     DONOF_LAUNCH_CHECK(ctx);
-    bmax_rows_kernel<<<ceil_div_u(nxs * nbs, 256), 256, 0, s>>>(ctx->d_B, nx, nb, sb->rmaxB);
+    bmax_rows_kernel<<<ceil_div_u(nxs * nbs, 256), 256, 0, s>>>(Bw, nx, nb, sb->rmaxB);
     DONOF_LAUNCH_CHECK(ctx);
-    bmax_aux_kernel<<<ceil_div_u(nbs * nbs, 256), 256, 0, s>>>(ctx->d_B, nx, nb, sb->maxB);
+    bmax_aux_kernel<<<ceil_div_u(nbs * nbs, 256), 256, 0, s>>>(Bw, nx, nb, sb->maxB);
     DONOF_LAUNCH_CHECK(ctx);
   }
+  if (cudaStreamSynchronize(s) != cudaSuccess) {
+    free_tmp();
+    return DONOF_RI_E_CUDA;
+  }
+  free_tmp();
 
-  int rc;
   for (int k = 0; k < S_NKINDS; ++k) {
     S4Params& p = sb->plan[k];
     p.nb = nb; p.nx = nx; p.m = m; p.nbp = nbp; p.nxp = nxp; p.mp = mp;
@@ -1783,6 +1870,7 @@ void s4_free(donof_ri_ctx* ctx) {
   if (!sb) return;
   void* bufs[] = {sb->mir_jao, sb->mir_kao, sb->jao_tmap_full, sb->jao_tmap, sb->kao_tmap, sb->X6,    sb->B1,   sb->B5,   sb->Ct,   sb->L3,   sb->L6, sb->Dp,  sb->JKp,  sb->eB1,   sb->eB5,
                   sb->eC,    sb->e3,   sb->e6,   sb->ed,   sb->eJK, sb->rmaxB, sb->maxB, sb->absC, sb->absCt,
+                  sb->Ls,    sb->LsTdf, sb->Cin,   sb->Cp,   sb->Cinp,
                   sb->Cdf,   sb->Hdf,   sb->Cdfp,  sb->eterm, sb->ticket, sb->dpart, sb->dmat, sb->JKhi, sb->JKlo, sb->W,  sb->HCt, sb->Yt,   sb->partial, sb->partial_j};
   for (void* b : bufs)
     if (b) cudaFree(b);
@@ -1837,9 +1925,17 @@ int s4_transform(donof_ri_ctx* ctx, int mode) {
   int rc;
   {
     ProfScope ps(ctx, DONOF_RI_ROW_OTHER);
-    // C^T rows p over mu (C column-major = rows p contiguous)
-    // (and every row of C as double-float pairs, for lambda)
-    launch_pdl(slice_rows_kernel, dim3(nb), dim3(SLICE_ROWS_THREADS), 0, s, (const double*)ctx->d_C, m, nb,
+    // the orbitals in the working basis, C' = L^T C: rows of C'^T [p][mu'] =
+    // sum_mu C^T[p][mu] L[mu][mu'] (C column-major = rows p contiguous), in double-float
+    launch_pdl(to_df_kernel, dim3(ceil_div_u((long long)nb * nb, 256)), dim3(256), 0, s, (const double*)ctx->d_C,
+               (long long)nb * nb, sb->Cin);
+    DONOF_LAUNCH_CHECK(ctx);
+    launch_pdl(df_gemm_nt_kernel<double>, dim3((nb + DFG_TJ - 1) / DFG_TJ, (nb + DFG_TI - 1) / DFG_TI),
+               dim3(DFG_THREADS), 0, s, nb, nb, nb, (const float2*)sb->Cin, nb, (const float2*)sb->LsTdf, nb, sb->Cp,
+               nb);
+    DONOF_LAUNCH_CHECK(ctx);
+    // C'^T rows p over mu' (and every row of C' as double-float pairs, for lambda)
+    launch_pdl(slice_rows_kernel, dim3(nb), dim3(SLICE_ROWS_THREADS), 0, s, (const double*)sb->Cp, m, nb,
                (long long)nb, sb->Ct, sb->nbp, sb->eC, sb->absC, sb->absCt, sb->Cdf);
     DONOF_LAUNCH_CHECK(ctx);
     // the two bound passes are independent: e6 on the second stream
@@ -1968,10 +2064,13 @@ int s4_energy(donof_ri_ctx* ctx, int part) {
     launch_pdl(fock_weights_df_kernel, dim3(ceil_div_u(2LL * m * m, 256)), dim3(256), 0, s, (const double*)ctx->d_A,
                (const double*)ctx->d_Bc, m, sb->W);
     DONOF_LAUNCH_CHECK(ctx);
-    // (H C)^T [p][mu] as double-float pairs, from the prep's own double-float copy of C
-    // (this part may run on a second stream beside the transform)
+    // (H' C')^T [p][mu'] as double-float pairs, from the prep's own double-float copy of
+    // C' = L^T C (this part may run on a second stream beside the transform)
     launch_pdl(to_df_kernel, dim3(ceil_div_u((long long)m * nb, 256)), dim3(256), 0, s, (const double*)ctx->d_C,
-               (long long)m * nb, sb->Cdfp);
+               (long long)m * nb, sb->Cinp);
+    DONOF_LAUNCH_CHECK(ctx);
+    launch_pdl(df_gemm_nt_kernel<float2>, dim3((nb + DFG_TJ - 1) / DFG_TJ, (m + DFG_TI - 1) / DFG_TI), dim3(DFG_THREADS),
+               0, s, m, nb, nb, (const float2*)sb->Cinp, nb, (const float2*)sb->LsTdf, nb, sb->Cdfp, nb);
     DONOF_LAUNCH_CHECK(ctx);
     launch_pdl(df_gemm_nt_kernel<float2>, dim3((nb + DFG_TJ - 1) / DFG_TJ, (m + DFG_TI - 1) / DFG_TI), dim3(DFG_THREADS),
                0, s, m, nb, nb,
@@ -2229,16 +2328,35 @@ int s4_fetch(donof_ri_ctx* ctx, int what, double* dst, size_t count) {
       cudaGetLastError();
       return DONOF_RI_E_OOM;
     }
-    // rows (P, p) of the L3 digits over nu; consecutive P are mp rows apart
+    double* ao = nullptr;
+    if (cudaMalloc((void**)&ao, count * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(tmp);
+      return DONOF_RI_E_OOM;
+    }
+    // rows (P, p) of the L3 digits over nu'; consecutive P are mp rows apart
     for (int P = 0; P < nx && e == cudaSuccess; ++P) {
       unslice_kernel<<<ceil_div_u((long long)m * nb, 256), 256, 0, ctx->stream>>>(
           sb->L3 + (size_t)P * sb->mp * 4 * sb->nbp, sb->nbp, sb->e3 + (size_t)P * m, m, nb,
           tmp + (size_t)P * m * nb);
       e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dst, tmp, count * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    // back to the AO basis: b^P_{p nu} = sum_nu' b'^P_{p nu'} L_{nu nu'}
+    int rc = DONOF_RI_OK;
+    if (e == cudaSuccess) {
+      Gemm64 g{};
+      g.M = nx * m; g.N = nb; g.K = nb; g.batch = 1;
+      g.A = tmp; g.sAm = nb; g.sAk = 1;
+      g.B = sb->Ls; g.sBk = 1; g.sBn = nb;
+      g.C = ao; g.sCm = nb; g.sCn = 1;
+      g.alpha = 1.0; g.beta = 0.0;
+      rc = launch_dgemm(ctx, g);
+    }
+    if (e == cudaSuccess && !rc) e = cudaMemcpyAsync(dst, ao, count * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     cudaFree(tmp);
+    cudaFree(ao);
+    if (rc) return rc;
     return e == cudaSuccess ? DONOF_RI_OK : DONOF_RI_E_CUDA;
   }
   // d is kept as FP64 [p][P]; the fetch layout is [P][p]
@@ -2257,9 +2375,11 @@ int s4_copy_ao(donof_ri_ctx* ctx, double* Jao, double* Kao, bool jao_dev, bool k
   S4Buffers* sb = ctx->s4;
   const int nb = ctx->nbf, m = ctx->n_omega;
   const size_t n = (size_t)m * nb * nb;
-  double* tmp = nullptr;
-  if (cudaMalloc((void**)&tmp, n * sizeof(double)) != cudaSuccess) {
+  double *tmp = nullptr, *tmp2 = nullptr;
+  if (cudaMalloc((void**)&tmp, n * sizeof(double)) != cudaSuccess ||
+      cudaMalloc((void**)&tmp2, n * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
+    if (tmp) cudaFree(tmp);
     return DONOF_RI_E_OOM;
   }
   cudaError_t e = cudaSuccess;
@@ -2271,12 +2391,36 @@ int s4_copy_ao(donof_ri_ctx* ctx, double* Jao, double* Kao, bool jao_dev, bool k
     join_pair_kernel<<<ceil_div_u((long long)n, 256), 256, 0, ctx->stream>>>(sb->JKhi + off, sb->JKlo + off,
                                                                               (long long)m * nb, nb, sb->ldo, tmp);
     e = cudaGetLastError();
+    // back to the AO basis: X^(q) = L X'^(q) L^T for every orbital q
+    if (e == cudaSuccess) {
+      const long long n2 = (long long)nb * nb;
+      Gemm64 g{};
+      g.M = nb; g.N = nb; g.K = nb; g.batch = m;
+      g.A = sb->Ls; g.sAb = 0; g.sAm = nb; g.sAk = 1;
+      g.B = tmp; g.sBb = n2; g.sBk = nb; g.sBn = 1;
+      g.C = tmp2; g.sCb = n2; g.sCm = nb; g.sCn = 1;
+      g.alpha = 1.0; g.beta = 0.0;
+      int rc = launch_dgemm(ctx, g);
+      Gemm64 h{};
+      h.M = nb; h.N = nb; h.K = nb; h.batch = m;
+      h.A = tmp2; h.sAb = n2; h.sAm = nb; h.sAk = 1;
+      h.B = sb->Ls; h.sBb = 0; h.sBk = 1; h.sBn = nb;  // element (k, n) of L^T = L[n][k]
+      h.C = tmp; h.sCb = n2; h.sCm = nb; h.sCn = 1;
+      h.alpha = 1.0; h.beta = 0.0;
+      if (!rc) rc = launch_dgemm(ctx, h);
+      if (rc) {
+        cudaFree(tmp);
+        cudaFree(tmp2);
+        return rc;
+      }
+    }
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(dst, tmp, n * sizeof(double), dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                           ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   }
   cudaFree(tmp);
+  cudaFree(tmp2);
   return e == cudaSuccess ? DONOF_RI_OK : DONOF_RI_E_CUDA;
 }
 

@@ -304,31 +304,59 @@ __global__ void trsm_rows_kernel(int nx, const double* L, double* R, long long n
   }
 }
 
-int setup_cholesky_and_fit(donof_ri_ctx* ctx) {
-  const int nx = ctx->naux;
-  const long long nb2 = (long long)ctx->nbf * ctx->nbf;
-  double* G = ctx->d_G;
-  max_diag_kernel<<<1, 256, 0, ctx->stream>>>(nx, G, ctx->d_scratch_max);
+// A = L L^T in place for a symmetric positive definite n x n A (row-major; lower
+// factor, upper triangle zeroed).  maxdiag: one device double of scratch.  A pivot
+// below rel_min * max A_kk sets DEV_METRIC_NOT_PD in the context's status word.
+int cholesky_lower(donof_ri_ctx* ctx, double* A, int n, double* maxdiag, double rel_min) {
+  max_diag_kernel<<<1, 256, 0, ctx->stream>>>(n, A, maxdiag);
   DONOF_LAUNCH_CHECK(ctx);
-  for (int k0 = 0; k0 < nx; k0 += CH_NB) {
-    int nbk = nx - k0 < CH_NB ? nx - k0 : CH_NB;
-    potrf_block_kernel<<<1, 256, 0, ctx->stream>>>(nx, G, k0, nbk, ctx->d_scratch_max, 1e-14, ctx->d_status);
+  for (int k0 = 0; k0 < n; k0 += CH_NB) {
+    int nbk = n - k0 < CH_NB ? n - k0 : CH_NB;
+    potrf_block_kernel<<<1, 256, 0, ctx->stream>>>(n, A, k0, nbk, maxdiag, rel_min, ctx->d_status);
     DONOF_LAUNCH_CHECK(ctx);
-    int rows = nx - k0 - nbk;
+    int rows = n - k0 - nbk;
     if (rows <= 0) break;
-    trsm_panel_kernel<<<ceil_div_u(rows, 128), 128, 0, ctx->stream>>>(nx, G, k0, nbk);
+    trsm_panel_kernel<<<ceil_div_u(rows, 128), 128, 0, ctx->stream>>>(n, A, k0, nbk);
     DONOF_LAUNCH_CHECK(ctx);
     Gemm64 g{};
     g.M = rows; g.N = rows; g.K = nbk; g.batch = 1;
-    g.A = G + (long long)(k0 + nbk) * nx + k0; g.sAm = nx; g.sAk = 1;
-    g.B = G + (long long)(k0 + nbk) * nx + k0; g.sBk = 1; g.sBn = nx;
-    g.C = G + (long long)(k0 + nbk) * nx + (k0 + nbk); g.sCm = nx; g.sCn = 1;
+    g.A = A + (long long)(k0 + nbk) * n + k0; g.sAm = n; g.sAk = 1;
+    g.B = A + (long long)(k0 + nbk) * n + k0; g.sBk = 1; g.sBn = n;
+    g.C = A + (long long)(k0 + nbk) * n + (k0 + nbk); g.sCm = n; g.sCn = 1;
     g.alpha = -1.0; g.beta = 1.0;
     int rc = launch_dgemm(ctx, g);
     if (rc) return rc;
   }
-  zero_upper_kernel<<<ceil_div_u((long long)nx * nx, 256), 256, 0, ctx->stream>>>(nx, G);
+  zero_upper_kernel<<<ceil_div_u((long long)n * n, 256), 256, 0, ctx->stream>>>(n, A);
   DONOF_LAUNCH_CHECK(ctx);
+  return DONOF_RI_OK;
+}
+
+// R <- L^-1 R for a lower-triangular n x n L (row-major, zero upper triangle) and an
+// n x ncol row-major R: forward substitution over row blocks of R.
+int forward_subst(donof_ri_ctx* ctx, const double* L, int n, double* R, long long ncol) {
+  for (int i0 = 0; i0 < n; i0 += CH_NB) {
+    int nbk = n - i0 < CH_NB ? n - i0 : CH_NB;
+    if (i0 > 0) {
+      // N can exceed the grid limit in x only for ncol > 4e9; never for supported sizes.
+      Gemm64 g{};
+      g.M = nbk; g.N = (int)ncol; g.K = i0; g.batch = 1;
+      g.A = L + (long long)i0 * n; g.sAm = n; g.sAk = 1;
+      g.B = R; g.sBk = ncol; g.sBn = 1;
+      g.C = R + (long long)i0 * ncol; g.sCm = ncol; g.sCn = 1;
+      g.alpha = -1.0; g.beta = 1.0;
+      int rc = launch_dgemm(ctx, g);
+      if (rc) return rc;
+    }
+    trsm_rows_kernel<<<ceil_div_u(ncol, 128), 128, 0, ctx->stream>>>(n, L, R, ncol, i0, nbk);
+    DONOF_LAUNCH_CHECK(ctx);
+  }
+  return DONOF_RI_OK;
+}
+
+int setup_cholesky_and_fit(donof_ri_ctx* ctx) {
+  int rc = cholesky_lower(ctx, ctx->d_G, ctx->naux, ctx->d_scratch_max, 1e-14);
+  if (rc) return rc;
   return fit_forward(ctx);
 }
 
@@ -340,27 +368,7 @@ void max_diag_public(donof_ri_ctx* ctx, const double* G, double* out) {
 // B <- L^-1 B for the lower-triangular L in ctx->d_G (row-major, zero upper
 // triangle): forward substitution over row blocks of B.
 int fit_forward(donof_ri_ctx* ctx) {
-  const int nx = ctx->naux;
-  const long long nb2 = (long long)ctx->nbf * ctx->nbf;
-  const double* G = ctx->d_G;
-  double* R = ctx->d_B;
-  for (int i0 = 0; i0 < nx; i0 += CH_NB) {
-    int nbk = nx - i0 < CH_NB ? nx - i0 : CH_NB;
-    if (i0 > 0) {
-      // N can exceed the grid limit in x only for nb2 > 4e9; never for supported sizes.
-      Gemm64 g{};
-      g.M = nbk; g.N = (int)nb2; g.K = i0; g.batch = 1;
-      g.A = G + (long long)i0 * nx; g.sAm = nx; g.sAk = 1;
-      g.B = R; g.sBk = nb2; g.sBn = 1;
-      g.C = R + (long long)i0 * nb2; g.sCm = nb2; g.sCn = 1;
-      g.alpha = -1.0; g.beta = 1.0;
-      int rc = launch_dgemm(ctx, g);
-      if (rc) return rc;
-    }
-    trsm_rows_kernel<<<ceil_div_u(nb2, 128), 128, 0, ctx->stream>>>(nx, G, R, nb2, i0, nbk);
-    DONOF_LAUNCH_CHECK(ctx);
-  }
-  return DONOF_RI_OK;
+  return forward_subst(ctx, ctx->d_G, ctx->naux, ctx->d_B, (long long)ctx->nbf * ctx->nbf);
 }
 
 }  // namespace donof

@@ -51,7 +51,7 @@ def test_flambda_step_matches_oracle(name):
     np.testing.assert_allclose(diag, eps_o, atol=1e-9 * np.abs(eps_o).max())
     # eigenvectors column by column where the eigenvalue is separated (FP32 Jacobi,
     # then two FP64 first-order refinements)
-    overlap = np.abs(C_g.T @ C_o)
+    overlap = np.abs(C_g.T @ I.overlap(s) @ C_o)
     gaps = np.minimum(np.r_[np.inf, np.diff(eps_o)], np.r_[np.diff(eps_o), np.inf])
     sep = gaps > 1e-3 * np.abs(eps_o).max()
     assert sep.sum() >= nb // 2

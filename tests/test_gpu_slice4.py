@@ -6,10 +6,12 @@ against the FP64 oracle.  The arithmetic behind it: each operand row carries
 exactly (integers below 2^24 in FP32, then int64), and only products 2^-40 or
 more below the leading pair are dropped, so each GEMM result is good to about
 2^-31 of its row scale (observed J, K ~2e-9, dE ~1e-8 Eh).
-Sizes: square4, C6H12 (the benchmark workload), C10H20 and C16H32 element by
-element; C20H40 (nbf 720, naux 2520) on outputs the oracle computes one by one
-(b_half rows of the first auxiliary functions, from a partial forward
-substitution) and on properties that hold at any size.
+Sizes: square4, C6H12, C10H20 and C16H32 element by element; a C20H40 ring
+trimmed to nbf 523, naux 301 element by element (every half-transform and
+full-transform unit then spans two K chunks, the second one ragged, and every
+tile edge is ragged); C20H40 (nbf 720, naux 2520) on outputs the oracle
+computes one by one (b_half rows of the first auxiliary functions, from a
+partial forward substitution) and on properties that hold at any size.
 """
 import numpy as np
 import pytest
@@ -85,6 +87,36 @@ def test_bitwise_reproducible(case):
         out.append((J, K) + eng.energy_lagrangian(w.gamma))
     for a, b in zip(out[0], out[1]):
         np.testing.assert_array_equal(a, b)
+
+
+def test_two_chunk_odd_sizes():
+    """nbf 523 > 512 and naux 301: the half transform's and the full transform's K
+    (= nbf) spans two 512-wide chunks, the second of 11 elements."""
+    from paper_2012_15662_gb300 import binding as bd
+    from synthetic import (Workload, draw_gamma, orthonormal_orbitals, random_orthogonal, without_basis_functions,
+                           workload_system)
+    s = without_basis_functions(workload_system("c20h40"), 720 - 523, 2520 - 301)
+    assert (s.nbf, s.naux, s.n_omega) == (523, 301, 400)
+    rng = np.random.default_rng(523)
+    C = orthonormal_orbitals(I.overlap(s), random_orthogonal(s.nbf, rng))
+    w = Workload(name="c20h40-523", system=s, C=C, gamma=draw_gamma(s.n_strong, s.n_weak_per, rng))
+    ref = _oracle(w)
+    eng = bd.Engine(s, bd.DONOF_RI_SLICE4)
+    eng.transform(w.C, bd.DONOF_RI_FULL)
+    J, K = eng.jk_mo()
+    bh = eng.fetch(bd.DONOF_RI_FETCH_BHALF)
+    d = eng.fetch(bd.DONOF_RI_FETCH_DIAG)
+    Jao, Kao = eng.jk_ao()
+    E, lam = eng.energy_lagrangian(w.gamma)
+    eng.close()
+    assert np.abs(bh - ref["bh"]).max() <= 1e-8 * max(1.0, np.abs(ref["bh"]).max())
+    assert np.abs(d - ref["d"]).max() <= 1e-8 * max(1.0, np.abs(ref["d"]).max())
+    assert np.abs(J - ref["J"]).max() <= TOL_JK
+    assert np.abs(K - ref["K"]).max() <= TOL_JK
+    assert np.abs(Jao - ref["Jao"]).max() <= TOL_JK
+    assert np.abs(Kao - ref["Kao"]).max() <= TOL_JK
+    assert abs(E - ref["E"]) <= TOL_E, (E, ref["E"])
+    assert np.abs(lam - ref["lam"]).max() <= 1e-6
 
 
 def test_full_size_c20h40():

@@ -54,12 +54,26 @@ enum S4Kind {
   S_HALF = 0, S_FULLSQ = 1, S_JMO = 2, S_JAO = 3, S_KAO = 4, S_FOCK = 5, S_HALF1 = 6, S_JKAO = 7, S_NKINDS = 8
 };
 __host__ __device__ constexpr bool s4_half(int kind) { return kind == S_HALF || kind == S_HALF1; }
+
 static_assert(DONOF_RI_GEMM_FOCK - DONOF_RI_GEMM_HALF == S_FOCK, "GEMM profile rows follow the kind order");
 
 constexpr int S4_BM = 128;      // rows per tile
 constexpr int S4_BK = 32;       // BF16 elements per K block (one 64-byte swizzle row)
 constexpr int S4_KS = S4_BK / 16;  // MMA K steps per K block
 constexpr int S4_CHUNK_KB = 16; // K blocks per chunk (512 elements; groups 0..2 exact)
+// The kinds that contract over the orbital basis (K = nbf: the half and full
+// transforms and F^(p) C_p) take chunks of up to 23 blocks (736 elements), so that
+// a basis of up to 736 functions needs one epilogue drain per unit.  Past 512
+// elements group 2's FP32 sum may round once it exceeds 2^24, which needs most of
+// the chunk's top-digit products near their maximum; each rounding is at most one
+// unit of the group, and the 3 K/16 accumulations into it add at most
+// 3 K/16 2^(32-16) to the 2^(32 + 24.5)-scale sums: below 2^-30 of the largest
+// value the chunk can hold (the operands' 31-bit digits already cost 2^-31).
+constexpr int S4_CHUNK_KB_NB = 23;
+// K blocks per epilogue chunk of a kind
+__host__ __device__ constexpr int s4_chunk_kb(int kind) {
+  return (s4_half(kind) || kind == S_FULLSQ || kind == S_FOCK) ? S4_CHUNK_KB_NB : S4_CHUNK_KB;
+}
 constexpr int S4_PLANES = 4;
 constexpr int S4_NG = 5;        // digit-pair groups g = t + u = 0..4
 constexpr int S4_SHIFT = 46;    // value = 2^(ea + eb - 46) v
@@ -289,10 +303,11 @@ __device__ __forceinline__ void s4_unit(const S4Params& p, int b, int& batch, in
   else if (KIND == S_JAO || KIND == S_JKAO) { batch = 0; kb0 = 0; nkb = KBx; }
   else if (KIND == S_KAO) { batch = b; kb0 = 0; nkb = KBx; }
   else {
-    const int nc = (KBb + S4_CHUNK_KB - 1) / S4_CHUNK_KB;
+    constexpr int CKB = s4_chunk_kb(KIND);
+    const int nc = (KBb + CKB - 1) / CKB;
     batch = b / nc;
-    kb0 = (b % nc) * S4_CHUNK_KB;
-    nkb = min(S4_CHUNK_KB, KBb - kb0);
+    kb0 = (b % nc) * CKB;
+    nkb = min(CKB, KBb - kb0);
   }
 }
 
@@ -451,12 +466,13 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_ge
       for (int u = 0; u < nunits && ok; ++u) {
         int batch, kb0, nkb;
         s4_unit<KIND>(p, p.persist ? (tile0 + u * (int)gridDim.x) / p.ntiles : b0 + u, batch, kb0, nkb);
-        for (int ch = 0; ch * S4_CHUNK_KB < nkb && ok; ++ch) {
+        constexpr int CKB = s4_chunk_kb(KIND);
+        for (int ch = 0; ch * CKB < nkb && ok; ++ch) {
           const int set = cc % NSETS;
           if (!mbar_wait(&acce[set], (uint32_t)(((cc / NSETS) & 1) ^ 1), abort_flag, p.status)) { ok = false; break; }
           tc_fence_after();
           const uint32_t dbase = tmem_base + (uint32_t)(set * S4_NG * BN);
-          const int kbs = min(S4_CHUNK_KB, nkb - ch * S4_CHUNK_KB);
+          const int kbs = min(CKB, nkb - ch * CKB);
           for (int j = 0; j < kbs; ++j) {
             const int s = it % S;
             if (!mbar_wait(&full[s], (uint32_t)((it / S) & 1), abort_flag, p.status)) { ok = false; break; }
@@ -616,7 +632,7 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_ge
         ea = rvalid ? p.ea[mu] : 0;
         wrow = rvalid ? p.w[(size_t)batch * p.m + mu] : wrow;
       }
-      const int nch = (nkb + S4_CHUNK_KB - 1) / S4_CHUNK_KB;
+      const int nch = (nkb + s4_chunk_kb(KIND) - 1) / s4_chunk_kb(KIND);
       for (int ch = 0; ch < nch; ++ch) {
         const int set = cc % NSETS;
         if (!mbar_wait(&accf[set], (uint32_t)((cc / NSETS) & 1), abort_flag, p.status)) { ok = false; break; }
@@ -1540,6 +1556,21 @@ __global__ void identity64_kernel(int n, double* X) {
   X[i] = (i / n == i % n) ? 1.0 : 0.0;
 }
 
+// X^P <- (X^P + X^P^T) / 2 for each of `batch` n x n matrices: the two-sided products
+// below are symmetric only up to rounding, and the digit layouts take B' as symmetric.
+__global__ void symmetrize_kernel(double* X, int n, long long batch) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long n2 = (long long)n * n;
+  if (i >= batch * n2) return;
+  const long long b = i / n2;
+  const int r = (int)((i % n2) / n), c = (int)(i % n);
+  if (c <= r) return;
+  double* M = X + b * n2;
+  const double v = 0.5 * (M[(size_t)r * n + c] + M[(size_t)c * n + r]);
+  M[(size_t)r * n + c] = v;
+  M[(size_t)c * n + r] = v;
+}
+
 static int s4_working_basis(donof_ri_ctx* ctx, double* Li, double* Tb, double* Bw, double* Hw) {
   S4Buffers* sb = ctx->s4;
   const int nb = ctx->nbf, nx = ctx->naux;
@@ -1573,6 +1604,8 @@ static int s4_working_basis(donof_ri_ctx* ctx, double* Li, double* Tb, double* B
     h.C = out; h.sCb = n2; h.sCm = nb; h.sCn = 1;
     h.alpha = 1.0; h.beta = 0.0;
     if ((rc = launch_dgemm(ctx, h))) return rc;
+    symmetrize_kernel<<<ceil_div_u((long long)batch * n2, 256), 256, 0, s>>>(out, nb, batch);
+    DONOF_LAUNCH_CHECK(ctx);
   }
   return DONOF_RI_OK;
 }
@@ -1623,7 +1656,8 @@ int s4_init(donof_ri_ctx* ctx) {
     for (int nt = 0; nt < (nb + bn - 1) / bn; ++nt)
       if (nt * bn + bn - 1 >= mt * S4_BM) kao_tiles.push_back((mt << 16) | nt);
   s4_plan<S_KAO>(sb, 1, (int)kao_tiles.size(), m, S4Cfg<S_KAO>::CTAS * sms, S4Cfg<S_KAO>::CTAS * sms);
-  s4_plan<S_FOCK>(sb, (m + S4_BM - 1) / S4_BM, (nb + bn - 1) / bn, 2 * m * ((KBb + S4_CHUNK_KB - 1) / S4_CHUNK_KB), sms);
+  s4_plan<S_FOCK>(sb, (m + S4_BM - 1) / S4_BM, (nb + bn - 1) / bn,
+                  2 * m * ((KBb + s4_chunk_kb(S_FOCK) - 1) / s4_chunk_kb(S_FOCK)), sms);
   for (int k = 0; k < S_NKINDS; ++k) sb->max_stages[k] = sb->plan[k].stages;
   sb->target[S_FULLSQ] = S4Cfg<S_FULLSQ>::CTAS * sms;
   sb->target[S_JMO] = S4Cfg<S_JMO>::CTAS * sms;
@@ -1888,7 +1922,7 @@ static int launch_s4(donof_ri_ctx* ctx) {
   const bool one =
       KIND == S_FOCK ||
       ((KIND == S_HALF || KIND == S_FULLSQ || KIND == S_JAO || KIND == S_KAO || KIND == S_JKAO) &&
-       kext <= S4_CHUNK_KB * S4_BK);
+       kext <= s4_chunk_kb(KIND) * S4_BK);
   if constexpr (KIND == S_HALF) {
     const S4Params& p1 = sb->plan[S_HALF1];
     const int g1 = sb->grid[S_HALF1];

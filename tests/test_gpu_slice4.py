@@ -6,10 +6,10 @@ against the FP64 oracle.  The arithmetic behind it: each operand row carries
 exactly (integers below 2^24 in FP32, then int64), and only products 2^-40 or
 more below the leading pair are dropped, so each GEMM result is good to about
 2^-31 of its row scale (observed J, K ~2e-9, dE ~1e-8 Eh).
-Sizes: square4, C6H12, C10H20 and C16H32 element by element; a C20H40 ring
-trimmed to nbf 523, naux 301 element by element (every half-transform and
-full-transform unit then spans two K chunks, the second one ragged, and every
-tile edge is ragged); C20H40 (nbf 720, naux 2520) on outputs the oracle
+Sizes: square4, C6H12, C10H20 and C16H32 element by element; rings trimmed to
+nbf 523 and 761 with naux 301 element by element (at 761 the contractions over
+the orbital basis span two K chunks, the second one ragged; every tile edge is
+ragged); C20H40 (nbf 720, naux 2520) on outputs the oracle
 computes one by one (b_half rows of the first auxiliary functions, from a
 partial forward substitution) and on properties that hold at any size.
 """
@@ -89,17 +89,19 @@ def test_bitwise_reproducible(case):
         np.testing.assert_array_equal(a, b)
 
 
-def test_two_chunk_odd_sizes():
-    """nbf 523 > 512 and naux 301: the half transform's and the full transform's K
-    (= nbf) spans two 512-wide chunks, the second of 11 elements."""
+@pytest.mark.parametrize("n_c,nbf,naux", [(20, 523, 301), (24, 761, 301)])
+def test_large_basis_odd_sizes(n_c, nbf, naux):
+    """Odd sizes with a large orbital basis: nbf 523 (the contractions over the basis
+    in one K chunk, every tile edge ragged) and nbf 761 (the half and full transforms
+    and F^(p) C_p in two K chunks, the second of 25 elements), naux 301."""
     from paper_2012_15662_gb300 import binding as bd
-    from synthetic import (Workload, draw_gamma, orthonormal_orbitals, random_orthogonal, without_basis_functions,
-                           workload_system)
-    s = without_basis_functions(workload_system("c20h40"), 720 - 523, 2520 - 301)
-    assert (s.nbf, s.naux, s.n_omega) == (523, 301, 400)
-    rng = np.random.default_rng(523)
+    from synthetic import Workload, draw_gamma, make_system, orthonormal_orbitals, random_orthogonal, without_basis_functions
+    full = make_system("ring", n_c=n_c, seed=n_c, jitter=0.02)
+    s = without_basis_functions(full, full.nbf - nbf, full.naux - naux)
+    assert (s.nbf, s.naux) == (nbf, naux)
+    rng = np.random.default_rng(nbf)
     C = orthonormal_orbitals(I.overlap(s), random_orthogonal(s.nbf, rng))
-    w = Workload(name="c20h40-523", system=s, C=C, gamma=draw_gamma(s.n_strong, s.n_weak_per, rng))
+    w = Workload(name=f"c{n_c}-{nbf}", system=s, C=C, gamma=draw_gamma(s.n_strong, s.n_weak_per, rng))
     ref = _oracle(w)
     eng = bd.Engine(s, bd.DONOF_RI_SLICE4)
     eng.transform(w.C, bd.DONOF_RI_FULL)

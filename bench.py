@@ -61,19 +61,29 @@ def algorithmic_bytes(s):
             "split": 2 * m * nb * nb * (8 + 8) + 2 * m * nb * 4}
 
 
-def workload_desc(name):
-    from synthetic import workload_system
+def _system(name, trim_naux=0):
+    from synthetic import without_basis_functions, workload_system
     s = workload_system(name)
-    return s, (f"{name}: s-type ring, nbf={s.nbf}, naux={s.naux}, N_I={s.n_strong}, "
+    if 0 < trim_naux < s.naux:
+        s = without_basis_functions(s, 0, s.naux - trim_naux)
+    return s
+
+
+def workload_desc(name, trim_naux=0):
+    s = _system(name, trim_naux)
+    trimmed = f" (auxiliary set trimmed to its first {s.naux})" if 0 < trim_naux else ""
+    return s, (f"{name}{trimmed}: s-type ring, nbf={s.nbf}, naux={s.naux}, N_I={s.n_strong}, "
                f"N_g={s.n_weak_per}, N_Omega={s.n_omega}")
 
 
-def engine_workload(bd, name, precision, stream=None):
+def engine_workload(bd, name, precision, stream=None, trim_naux=0):
     """A context for the named workload and the workload itself, its orbitals
     C = S^-1/2 Q built from the overlap matrix the engine evaluated at init."""
-    from synthetic import make_workload, workload_system
-    eng = bd.Engine(workload_system(name), precision, stream=stream)
+    from synthetic import make_workload
+    s = _system(name, trim_naux)
+    eng = bd.Engine(s, precision, stream=stream)
     w = make_workload(name, eng.fetch(bd.DONOF_RI_FETCH_OVERLAP))
+    w.system = s
     return eng, w
 
 
@@ -301,6 +311,9 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default SLICE4 tile schedule")
     ap.add_argument("--fp64-steps", type=int, default=2,
                     help="iterations of the plain FP64 form on the same workload (mixed vs FP64 key; 0: skip)")
+    ap.add_argument("--trim-naux", type=int, default=0,
+                    help="keep only the first N auxiliary functions (a reduced case of the same orbital "
+                         "basis, for profiling captures; 0: the full set)")
     ap.add_argument("--extra-workloads", default="c6h12,c16h32",
                     help="comma-separated workloads also timed (CUDA-graph iterations) as extra keys")
     args = ap.parse_args()
@@ -313,7 +326,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return 0
-        _, desc = workload_desc(args.workload)
+        _, desc = workload_desc(args.workload, args.trim_naux)
         budget = max(2.0, min(20.0, 0.5 * (args.steps + args.warmup)))
         cb = cpu_baseline(args.workload, budget_s=budget)
         line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
@@ -333,10 +346,10 @@ def main():
         dist.init_process_group("nccl", rank=rank, world_size=world)
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    _, desc = workload_desc(args.workload)
+    _, desc = workload_desc(args.workload, args.trim_naux)
     prec = {"slice4": bd.DONOF_RI_SLICE4, "tf32x3": bd.DONOF_RI_TF32X3, "fp64": bd.DONOF_RI_FP64}[args.precision]
     stream = torch.cuda.Stream(device=dev)
-    eng, w = engine_workload(bd, args.workload, prec, stream=stream.cuda_stream)
+    eng, w = engine_workload(bd, args.workload, prec, stream=stream.cuda_stream, trim_naux=args.trim_naux)
     s = w.system
     nb, m = s.nbf, s.n_omega
     C_dev = torch.from_numpy(bd.Engine.colmajor(w.C)).to(dev)
@@ -455,9 +468,10 @@ def main():
         kind = GEMMS.index(dom)
         kernel = GEMM_KERNEL[args.precision].format(kind)
         if args.precision == "slice4":
-            # second template argument: every unit a single K chunk (K <= 512)
-            kext = s.naux if dom in ("jao", "kao") else s.nbf
-            one = dom == "fock" or (dom in ("half", "full_k", "jao", "kao") and kext <= 512)
+            # second template argument: every unit a single K chunk (the contractions over
+            # the orbital basis: K = nbf <= 736; over the auxiliary index: K = naux <= 512)
+            one = dom == "fock" or (dom in ("half", "full_k") and s.nbf <= 736) or (
+                dom in ("jao", "kao") and s.naux <= 512)
             kernel = f"s4_gemm_kernel<{kind}, {int(one)}>"
         traffic_key = "gemm_" + dom
     else:
@@ -530,10 +544,10 @@ def main():
     torch.cuda.empty_cache()
     if args.fp64_steps > 0 and prec != bd.DONOF_RI_FP64:
         line["mixed_vs_fp64"] = fp64_comparison(bd, torch, dev, args, w, res, value)
-    extra = [x for x in args.extra_workloads.split(",") if x and x != args.workload]
+    extra = [x for x in args.extra_workloads.split(",") if x and x not in (args.workload, "none")]
     if extra and world == 1:
         line["other_workloads"] = {x: time_workload(bd, torch, dev, x, prec) for x in extra}
-    if world == 1 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline and not args.trim_naux:
         line["cpu_baseline"] = cpu_baseline(args.workload)
     print(json.dumps(line))
     return 0
@@ -573,8 +587,7 @@ def fp64_comparison(bd, torch, dev, args, w, res, mixed_ms):
     deviation from it in E, J, K and lambda."""
     stream = torch.cuda.Stream(device=dev)
     t0 = time.perf_counter()
-    from synthetic import workload_system
-    eng = bd.Engine(workload_system(args.workload), bd.DONOF_RI_FP64, stream=stream.cuda_stream)
+    eng = bd.Engine(w.system, bd.DONOF_RI_FP64, stream=stream.cuda_stream)
     init_s = time.perf_counter() - t0
     ms, r64 = _graph_iterations(bd, torch, eng, w, stream, args.fp64_steps, 1)
     eng.close()

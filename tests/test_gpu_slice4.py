@@ -89,14 +89,15 @@ def test_bitwise_reproducible(case):
         np.testing.assert_array_equal(a, b)
 
 
-@pytest.mark.parametrize("n_c,nbf,naux", [(20, 523, 301), (24, 761, 301)])
-def test_large_basis_odd_sizes(n_c, nbf, naux):
+@pytest.mark.parametrize("n_c,nbf,naux,n_weak", [(20, 523, 301, 4), (24, 761, 301, 1)])
+def test_large_basis_odd_sizes(n_c, nbf, naux, n_weak):
     """Odd sizes with a large orbital basis: nbf 523 (the contractions over the basis
     in one K chunk, every tile edge ragged) and nbf 761 (the half and full transforms
-    and F^(p) C_p in two K chunks, the second of 25 elements), naux 301."""
+    and F^(p) C_p in two K chunks, the second of 25 elements; one weak orbital per
+    pair, N_Omega 192), naux 301."""
     from paper_2012_15662_gb300 import binding as bd
     from synthetic import Workload, draw_gamma, make_system, orthonormal_orbitals, random_orthogonal, without_basis_functions
-    full = make_system("ring", n_c=n_c, seed=n_c, jitter=0.02)
+    full = make_system("ring", n_c=n_c, seed=n_c, jitter=0.02, n_weak_per=n_weak)
     s = without_basis_functions(full, full.nbf - nbf, full.naux - naux)
     assert (s.nbf, s.naux) == (nbf, naux)
     rng = np.random.default_rng(nbf)

@@ -1886,7 +1886,10 @@ int s4_init(donof_ri_ctx* ctx) {
   }
   sb->plan[S_JKAO].stages = 0;
   s4_plan_jkao(sb);
-  sb->jk_merged = 1;
+  // J^(q) and K^(q) in one persistent launch while every unit is one K chunk (it
+  // saves a launch and its tail); beyond 512 auxiliary functions two launches are
+  // faster (C20H40: 14.4 against 15.7 ms).  s4_autotune measures both.
+  sb->jk_merged = nx <= S4_CHUNK_KB * S4_BK ? 1 : 0;
 #define OPTIN(KIND, ONE)                                                                                      \
   if (cudaFuncSetAttribute(s4_gemm_kernel<KIND, ONE>, cudaFuncAttributeMaxDynamicSharedMemorySize,           \
                            (int)sb->smem[KIND]) != cudaSuccess ||                                             \

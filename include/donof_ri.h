@@ -500,6 +500,30 @@ int donof_ri_on_features(donof_ri_ctx* ctx, float* X);
 int donof_ri_gamma_guess(donof_ri_ctx* ctx, donof_mlp* net, double clip, double* gamma);
 
 /*
+ * Closed-shell RI Hartree-Fock orbitals, the starting natural orbitals of the
+ * paper's calculations (Sec. 4, Computational Details: the guess NOs come from a
+ * Hartree-Fock calculation).  Roothaan-Hall iterations F C = S C eps in the
+ * overlap metric, F = H + J[D] - K[D]/2, D = 2 C_occ C_occ^T over the N_I lowest
+ * orbitals, J[D] and K[D] from the context's fitted tensor B (FP64, every
+ * precision), from the core-Hamiltonian guess with Pulay's DIIS over the last 8
+ * Fock matrices (error F D S - S D F).  The eigenproblem is solved on the device
+ * in the basis orthonormalised by the Cholesky factor of S.  Synchronous; device
+ * work buffers are allocated for the call and freed before it returns.
+ *   max_iter    iterations at most (>= 1)
+ *   tol         stop when max |F D S - S D F| <= tol (> 0)
+ *   C           [nbf][nbf] FP64 column-major (column p = orbital p), host or
+ *               device: the orbitals in increasing order of eps, C^T S C = I
+ *   eps         [nbf] orbital energies (host or device) or NULL
+ *   E           SCF energy (host) or NULL; iterations, commutator (host) or NULL
+ * Not converged after max_iter: the last iteration's orbitals and energy are
+ * returned, with commutator above tol.
+ * Errors: E_ARG, E_OOM, E_CUDA, E_UNSUPPORTED (nbf > 2048), E_NONFINITE,
+ *         E_METRIC_NOT_PD (the overlap is not positive definite).
+ */
+int donof_ri_rhf(donof_ri_ctx* ctx, int max_iter, double tol, double* C, double* eps, double* E, int* iterations,
+                 double* commutator);
+
+/*
  * J_pq = sum_P b^P_pp b^P_qq with no device allocation.
  * The paper has no counterpart: this entry point exists for callers that may
  * not allocate device memory (code running under an allocator or memory pool

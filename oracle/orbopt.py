@@ -90,3 +90,91 @@ def optimize(system, C0, gamma, subspace, weak_rank, max_iter=500, gtol=1e-6, ra
         else:
             radius *= 0.5
     return C, E, float(np.abs(lam - lam.T).max()), it
+
+
+# ---------------------------------------------------------------------------
+# The paper's outer / inner scheme to convergence (Sec. 2, Fig. 1: occupations for
+# fixed orbitals, then orbitals for fixed occupations, repeated), with the F^lambda
+# step for the orbitals.  Readings (the paper gives the step, not its controls):
+# the aufbau diagonal of the first step is the starting orbitals' energies (the
+# Hartree-Fock eigenvalues), later ones the previous step's eigenvalues, every gap
+# of the ascending diagonal raised to at least `gapmin` (orbitals degenerate in
+# energy but in different pairing subspaces would otherwise be mixed by 45
+# degrees); the damping bound starts at 0.1 max|lambda - lambda^T| of each inner
+# loop, grows by 1.5 (to at most 1) after an accepted step and halves after a
+# rejected one; an inner loop ends when max|lambda - lambda^T| <= gtol, when a step
+# lowers E by at most 1e-10 |E|, or after max_inner steps; the scheme has converged
+# when an outer iteration changes E by less than etol with max|lambda - lambda^T|
+# <= gtol.
+# ---------------------------------------------------------------------------
+def exact_rows(eri: np.ndarray, C: np.ndarray, n_om: int) -> dict:
+    """J, K, J^(q), K^(q) from four-index integrals (mu nu|l s) (the conventional route)."""
+    Cm = C[:, :n_om]
+    Jao = np.einsum("mnls,lq,sq->qmn", eri, Cm, Cm, optimize=True)
+    Kao = np.einsum("mlns,lq,sq->qmn", eri, Cm, Cm, optimize=True)
+    J = np.einsum("qmn,mp,np->pq", Jao, Cm, Cm, optimize=True)
+    K = np.einsum("qmn,mp,np->pq", Kao, Cm, Cm, optimize=True)
+    return dict(J=J, K=K, Jao=Jao, Kao=Kao)
+
+
+def _gap_floor(d: np.ndarray, gapmin: float) -> np.ndarray:
+    out = d.copy()
+    for k in range(1, out.size):
+        out[k] = max(out[k], out[k - 1] + gapmin)
+    return out
+
+
+def converge(system, C0, gamma0, diag0, subspace, weak_rank, B=None, eri=None, etol=1e-6, gtol=1e-4,
+             max_outer=60, max_inner=100, gapmin=0.01):
+    """Outer / inner iterations from (C0, gamma0) with the F^lambda step, on RI integrals
+    (B) or, when eri is given, on exact four-index integrals.  Returns dict(C, gamma,
+    diag, E, outer, inner_total, converged, history)."""
+    from . import onopt
+    m = system.n_omega
+    H = I.core_hamiltonian(system)
+    e_nuc = I.nuclear_repulsion(system)
+
+    def rows(C):
+        return exact_rows(eri, C, m) if eri is not None else ri.all_rows(B, C, m)
+
+    def energy_lam(C, g):
+        r = rows(C)
+        n = pnof7.occupations(g, system.n_strong, system.n_weak_per, subspace, weak_rank)
+        A, Bc = pnof7.coupling(n, subspace, weak_rank)
+        lam = pnof7.lagrangian(C, H, r["Jao"], r["Kao"], n, A, Bc)
+        Hd = np.einsum("mp,mn,np->p", C[:, :m], H, C[:, :m])
+        return pnof7.energy_from_lagrangian(lam, n, Hd, e_nuc), lam
+
+    C, g, diag = C0.copy(), np.array(gamma0, dtype=np.float64), np.array(diag0, dtype=np.float64)
+    hist, E_prev, total, converged = [], None, 0, False
+    for outer in range(1, max_outer + 1):
+        r = rows(C)
+        Hd = np.einsum("mp,mn,np->p", C[:, :m], H, C[:, :m])
+        g, E_on = onopt.optimize(g, system.n_strong, system.n_weak_per, subspace, weak_rank, Hd, r["J"], r["K"],
+                                 e_nuc, gtol=1e-8)[:2]
+        E, lam = energy_lam(C, g)
+        bound = 0.1 * max(np.abs(lam - lam.T).max(), 1e-12)
+        inner = 0
+        for inner in range(1, max_inner + 1):
+            if np.abs(lam - lam.T).max() <= gtol:
+                inner -= 1
+                break
+            Cn, eps = flambda_step(C, lam, _gap_floor(diag, gapmin), bound)
+            En, lamn = energy_lam(Cn, g)
+            if En < E:
+                dec = E - En
+                C, E, lam, diag = Cn, En, lamn, eps
+                bound = min(1.5 * bound, 1.0)
+                if dec <= 1e-10 * abs(E):
+                    break
+            else:
+                bound *= 0.5
+        total += inner
+        gm = float(np.abs(lam - lam.T).max())
+        hist.append(dict(outer=outer, E_occ=E_on, E=E, inner=inner, gmax=gm))
+        if E_prev is not None and abs(E - E_prev) < etol and gm <= gtol:
+            converged = True
+            break
+        E_prev = E
+    return dict(C=C, gamma=g, diag=diag, E=hist[-1]["E"], outer=len(hist), inner_total=total,
+                converged=converged, history=hist)

@@ -49,7 +49,7 @@ EXPORTS = [
     "donof_ri_strerror", "donof_ri_launch_count", "donof_ri_profile", "donof_ri_profile_read",
     "donof_ri_iteration", "donof_ri_jmo_noalloc", "donof_ri_optimize_occupations",
     "donof_ri_on_features", "donof_ri_gamma_guess", "donof_ri_rotate_orbitals", "donof_ri_autotune", "donof_ri_set_schedule", "donof_ri_exact_jk",
-    "donof_ri_energy_lagrangian_contracted", "donof_ri_flambda_step", "donof_ri_check_wait_timeout",
+    "donof_ri_energy_lagrangian_contracted", "donof_ri_flambda_step", "donof_ri_check_wait_timeout", "donof_ri_rhf",
     "donof_mlp_create", "donof_mlp_param_count", "donof_mlp_set_params", "donof_mlp_get_params",
     "donof_mlp_set_normalization", "donof_mlp_forward", "donof_mlp_loss_grad", "donof_mlp_train_step",
     "donof_mlp_destroy",
@@ -111,6 +111,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.donof_ri_launch_count.restype = ctypes.c_longlong
     lib.donof_ri_check_wait_timeout.argtypes = [vp, ctypes.c_longlong]
     lib.donof_ri_check_wait_timeout.restype = i
+    lib.donof_ri_rhf.argtypes = [vp, i, d, vp, vp, vp, vp, vp]
+    lib.donof_ri_rhf.restype = i
     lib.donof_ri_jmo_noalloc.argtypes = [vp, i, i, vp, vp]
     lib.donof_ri_jmo_noalloc.restype = i
     lib.donof_ri_iteration.argtypes = [vp, vp, vp, i, vp, vp, vp, vp, i]
@@ -475,6 +477,18 @@ class Engine:
 
     def launches(self) -> int:
         return donof_ri_launch_count(self.ctx)
+
+    def rhf(self, max_iter: int = 100, tol: float = 1e-9):
+        """Closed-shell RI-HF orbitals (donof_ri_rhf): (C [mu, p], eps, E, iterations, commutator)."""
+        nb = self.nbf
+        Ccm = np.empty(nb * nb)
+        eps = np.empty(nb)
+        E = ctypes.c_double()
+        it = ctypes.c_int()
+        com = ctypes.c_double()
+        _check(load().donof_ri_rhf(self.ctx, int(max_iter), float(tol), _ptr(Ccm), _ptr(eps), ctypes.byref(E),
+                                   ctypes.byref(it), ctypes.byref(com)), "donof_ri_rhf")
+        return Ccm.reshape(nb, nb).T.copy(), eps, E.value, it.value, com.value
 
     def overlap(self) -> np.ndarray:
         """The basis overlap matrix S the context evaluated at init."""

@@ -180,6 +180,8 @@ size_t flambda_scratch_doubles(int n);
 int flambda_step(donof_ri_ctx* ctx, const double* dprev, int first, double bound, double* scratch, double* gmax,
                  int* sweeps);
 int onopt_unfold(donof_ri_ctx* ctx, const float* d_Y, double clip, double* d_gamma);
+// flambda.cu: eigenvectors (row-major U, ascending eps) of a symmetric FP64 matrix, n <= FLAMBDA_MAX_NBF
+int eigh_sym(donof_ri_ctx* ctx, const double* F, int n, double* scratch, double* U, double* eps, int* sweeps);
 int mlp_forward_device(donof_mlp* n, const float* dX, int B, float** dY);
 int mlp_shape(const donof_mlp* n, int* F, int* O);
 int launch_occupations_coupling(donof_ri_ctx* ctx);

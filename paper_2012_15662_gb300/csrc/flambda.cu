@@ -29,9 +29,13 @@ constexpr int FL_MAXN = 160;
 // Sort key of an eigenvalue: NaN orders last, so that the ranks stay a permutation.
 __device__ __forceinline__ float fl_key(float x) { return x == x ? x : INFINITY; }
 
+// With Fsrc set, the matrix is Fsrc (FP64, row-major, symmetric) instead of F^lambda
+// (lam, dprev, first, bound and gmax are then unused): the general symmetric
+// eigensolver of eigh_sym.
 __global__ void __launch_bounds__(1024, 1) flambda_jacobi_kernel(int n, const double* lam, const double* dprev,
                                                                  int first, double bound, double* U, double* eps,
-                                                                 double* gmax, int* sweeps_out) {
+                                                                 double* gmax, int* sweeps_out,
+                                                                 const double* Fsrc) {
   extern __shared__ float fl_smem[];
   const int ld = n + 1;
   float* A = fl_smem;              // [n][n + 1]
@@ -50,7 +54,9 @@ __global__ void __launch_bounds__(1024, 1) flambda_jacobi_kernel(int n, const do
     const int q = e / n, p = e % n;
     float v;
     X[q * ld + p] = 0.f;
-    if (q == p) {
+    if (Fsrc) {
+      v = (float)Fsrc[e];
+    } else if (q == p) {
       v = (float)(first ? lam[(size_t)p * n + p] : dprev[p]);
     } else {
       const int hi = q > p ? q : p, lo = q > p ? p : q;
@@ -68,7 +74,7 @@ __global__ void __launch_bounds__(1024, 1) flambda_jacobi_kernel(int n, const do
   for (int o = 16; o > 0; o >>= 1) gm = fmax(gm, __shfl_xor_sync(0xffffffffu, gm, o));
   if (lane == 0) redd[wid] = gm;
   __syncthreads();
-  if (tid == 0 && gmax) {
+  if (tid == 0 && gmax && !Fsrc) {
     double m = 0.0;
     for (int w = 0; w < nt / 32; ++w) m = fmax(m, redd[w]);
     *gmax = m;
@@ -568,6 +574,100 @@ static int eig_refine(donof_ri_ctx* ctx, int n, const double* Fd, double* U, dou
   return DONOF_RI_OK;
 }
 
+// Two-sided block Jacobi on the FP64 symmetric matrix Fd (n > FL_MAXN), FP32 on global
+// memory, its buffers after the FP64 scratch; U (row-major, columns the eigenvectors in
+// increasing order of eigenvalue) and eps.  With lam, the gradient norm max|lambda -
+// lambda^T| goes to gm.  Returns the number of sweeps (or a negative status).
+static int fl_big_solve(donof_ri_ctx* ctx, int n, const double* Fd, const double* lam, double* scratch, double* U,
+                        double* eps, double* gm) {
+  const long long n2 = (long long)n * n;
+  const unsigned nblk = ceil_div_u(n2, 256);
+  const FlBig d = fl_big_dims(n);
+  char* base = (char*)(scratch + 6 * n2 + n + 2);
+  float* A = (float*)base;
+  float* X = A + (size_t)d.np * d.np;
+  float* Dg = X + (size_t)d.np * d.np;
+  unsigned int* conv = (unsigned int*)(Dg + (size_t)d.G * FLB2 * FLB2);
+  unsigned long long* gbits = (unsigned long long*)(conv + 2);
+  int* perm = (int*)(gbits + 1);
+  if (cudaFuncSetAttribute(fl_big_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)FL_UPDATE_SMEM) != cudaSuccess)
+    return DONOF_RI_E_CUDA;
+  const long long np2 = (long long)d.np * d.np;
+  DONOF_CUDA_TRY(cudaMemsetAsync(gbits, 0, sizeof(unsigned long long), ctx->stream));
+  if (lam) {
+    fl_big_gmax_kernel<<<nblk, 256, 0, ctx->stream>>>(n, lam, gbits);
+    DONOF_LAUNCH_CHECK(ctx);
+    DONOF_CUDA_TRY(cudaMemcpyAsync(gm, gbits, sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  fl_big_init_kernel<<<ceil_div_u(np2, 256), 256, 0, ctx->stream>>>(n, d.np, Fd, A, X);
+  DONOF_LAUNCH_CHECK(ctx);
+  int sweep = 0;
+  for (; sweep < 30; ++sweep) {
+    DONOF_CUDA_TRY(cudaMemsetAsync(conv, 0, 2 * sizeof(unsigned int), ctx->stream));
+    fl_big_conv_kernel<<<nblk, 256, 0, ctx->stream>>>(n, d.np, A, conv);
+    DONOF_LAUNCH_CHECK(ctx);
+    unsigned int hc[2] = {0u, 0u};
+    DONOF_CUDA_TRY(cudaMemcpyAsync(hc, conv, sizeof(hc), cudaMemcpyDeviceToHost, ctx->stream));
+    DONOF_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    float mo, mdia;
+    memcpy(&mo, &hc[0], sizeof(float));
+    memcpy(&mdia, &hc[1], sizeof(float));
+    if (!(mo > 1e-6f * fmaxf(mdia, 1e-30f))) break;
+    for (int r = 0; r < d.nbk - 1; ++r) {
+      fl_big_sub_kernel<<<d.G, 256, 0, ctx->stream>>>(d.np, d.nbk, r, A, conv, Dg);
+      DONOF_LAUNCH_CHECK(ctx);
+      fl_big_update_kernel<<<dim3(d.G, d.G), 256, FL_UPDATE_SMEM, ctx->stream>>>(d.np, d.nbk, r, A, X, Dg);
+      DONOF_LAUNCH_CHECK(ctx);
+    }
+  }
+  fl_big_rank_kernel<<<ceil_div_u(n, 256), 256, 0, ctx->stream>>>(n, d.np, A, perm);
+  DONOF_LAUNCH_CHECK(ctx);
+  fl_big_fill_kernel<<<nblk, 256, 0, ctx->stream>>>(n, d.np, A, X, perm, U, eps);
+  DONOF_LAUNCH_CHECK(ctx);
+  return sweep;
+}
+
+// Eigen-decomposition of a symmetric FP64 matrix F (n x n row-major, n <=
+// FLAMBDA_MAX_NBF): U (row-major; column k the eigenvector of the k-th smallest
+// eigenvalue eps[k]), by the F^lambda step's solver (FP32 Jacobi, then FP64
+// Newton-Schulz and two first-order refinements against F).  U and eps are device
+// buffers outside scratch (flambda_scratch_doubles(n) doubles).
+int eigh_sym(donof_ri_ctx* ctx, const double* F, int n, double* scratch, double* U_out, double* eps_out,
+             int* sweeps) {
+  const long long n2 = (long long)n * n;
+  double *U = scratch, *T = U + n2, *W = T + n2, *Z = W + n2, *Fd = Z + n2, *K = Fd + n2, *eps = K + n2,
+         *gm = eps + n;
+  int* sw = (int*)(gm + 1);
+  DONOF_CUDA_TRY(cudaMemcpyAsync(Fd, F, n2 * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+  int big_sweeps = -1;
+  if (n <= FL_MAXN) {
+    const size_t smem = 2 * (size_t)n * (n + 1) * sizeof(float);
+    if (cudaFuncSetAttribute(flambda_jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      return DONOF_RI_E_CUDA;
+    flambda_jacobi_kernel<<<1, 1024, smem, ctx->stream>>>(n, (const double*)nullptr, (const double*)nullptr, 0, 0.0,
+                                                          U, eps, (double*)nullptr, sw, (const double*)Fd);
+    DONOF_LAUNCH_CHECK(ctx);
+  } else {
+    big_sweeps = fl_big_solve(ctx, n, Fd, (const double*)nullptr, scratch, U, eps, gm);
+    if (big_sweeps < 0) return big_sweeps;
+  }
+  int rc;
+  if ((rc = eig_refine(ctx, n, Fd, U, T, W, Z, K, eps))) return rc;
+  DONOF_CUDA_TRY(cudaMemcpyAsync(U_out, U, n2 * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+  DONOF_CUDA_TRY(cudaMemcpyAsync(eps_out, eps, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+  if (sweeps) {
+    int hs = 0;
+    if (big_sweeps < 0) {
+      DONOF_CUDA_TRY(cudaMemcpyAsync(&hs, sw, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+      DONOF_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    }
+    *sweeps = big_sweeps >= 0 ? big_sweeps : hs;
+  }
+  return DONOF_RI_OK;
+}
+
 // One step on ctx->d_C (column-major = row-major C^T).  Scratch:
 // flambda_scratch_doubles(n) doubles.  The FP32 eigenvectors are orthonormalised
 // (Newton-Schulz) and refined twice in FP64 against the FP64 F^lambda by first-order
@@ -589,52 +689,12 @@ int flambda_step(donof_ri_ctx* ctx, const double* dprev, int first, double bound
     if (cudaFuncSetAttribute(flambda_jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
       return DONOF_RI_E_CUDA;
-    flambda_jacobi_kernel<<<1, 1024, smem, ctx->stream>>>(n, ctx->d_lambda, dprev, first, bound, U, eps, gm, sw);
+    flambda_jacobi_kernel<<<1, 1024, smem, ctx->stream>>>(n, ctx->d_lambda, dprev, first, bound, U, eps, gm, sw,
+                                                          (const double*)nullptr);
     DONOF_LAUNCH_CHECK(ctx);
   } else {
-    // block Jacobi; buffers after the FP64 scratch
-    const FlBig d = fl_big_dims(n);
-    char* base = (char*)(scratch + 6 * n2 + n + 2);
-    float* A = (float*)base;
-    float* X = A + (size_t)d.np * d.np;
-    float* Dg = X + (size_t)d.np * d.np;
-    unsigned int* conv = (unsigned int*)(Dg + (size_t)d.G * FLB2 * FLB2);
-    unsigned long long* gbits = (unsigned long long*)(conv + 2);
-    int* perm = (int*)(gbits + 1);
-    if (cudaFuncSetAttribute(fl_big_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)FL_UPDATE_SMEM) != cudaSuccess)
-      return DONOF_RI_E_CUDA;
-    const long long np2 = (long long)d.np * d.np;
-    DONOF_CUDA_TRY(cudaMemsetAsync(gbits, 0, sizeof(unsigned long long), ctx->stream));
-    fl_big_gmax_kernel<<<nblk, 256, 0, ctx->stream>>>(n, ctx->d_lambda, gbits);
-    DONOF_LAUNCH_CHECK(ctx);
-    DONOF_CUDA_TRY(cudaMemcpyAsync(gm, gbits, sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
-    fl_big_init_kernel<<<ceil_div_u(np2, 256), 256, 0, ctx->stream>>>(n, d.np, Fd, A, X);
-    DONOF_LAUNCH_CHECK(ctx);
-    int sweep = 0;
-    for (; sweep < 30; ++sweep) {
-      DONOF_CUDA_TRY(cudaMemsetAsync(conv, 0, 2 * sizeof(unsigned int), ctx->stream));
-      fl_big_conv_kernel<<<nblk, 256, 0, ctx->stream>>>(n, d.np, A, conv);
-      DONOF_LAUNCH_CHECK(ctx);
-      unsigned int hc[2] = {0u, 0u};
-      DONOF_CUDA_TRY(cudaMemcpyAsync(hc, conv, sizeof(hc), cudaMemcpyDeviceToHost, ctx->stream));
-      DONOF_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-      float mo, mdia;
-      memcpy(&mo, &hc[0], sizeof(float));
-      memcpy(&mdia, &hc[1], sizeof(float));
-      if (!(mo > 1e-6f * fmaxf(mdia, 1e-30f))) break;
-      for (int r = 0; r < d.nbk - 1; ++r) {
-        fl_big_sub_kernel<<<d.G, 256, 0, ctx->stream>>>(d.np, d.nbk, r, A, conv, Dg);
-        DONOF_LAUNCH_CHECK(ctx);
-        fl_big_update_kernel<<<dim3(d.G, d.G), 256, FL_UPDATE_SMEM, ctx->stream>>>(d.np, d.nbk, r, A, X, Dg);
-        DONOF_LAUNCH_CHECK(ctx);
-      }
-    }
-    fl_big_rank_kernel<<<ceil_div_u(n, 256), 256, 0, ctx->stream>>>(n, d.np, A, perm);
-    DONOF_LAUNCH_CHECK(ctx);
-    fl_big_fill_kernel<<<nblk, 256, 0, ctx->stream>>>(n, d.np, A, X, perm, U, eps);
-    DONOF_LAUNCH_CHECK(ctx);
-    big_sweeps = sweep;
+    big_sweeps = fl_big_solve(ctx, n, Fd, ctx->d_lambda, scratch, U, eps, gm);
+    if (big_sweeps < 0) return big_sweeps;
   }
   int rc;
   if ((rc = eig_refine(ctx, n, Fd, U, T, W, Z, K, eps))) return rc;

@@ -21,24 +21,37 @@ from . import binding as bd
 
 
 class _Inner:
-    """Device state of the inner iterations of one engine."""
+    """Device state of the inner iterations of one engine.  exact: the energy and
+    Lagrangian from exact four-centre J^(q), K^(q) (donof_ri_exact_jk, FP64 contexts)
+    instead of the RI transforms (the paper's RI -> exact restart)."""
 
-    def __init__(self, eng: "bd.Engine"):
+    def __init__(self, eng: "bd.Engine", exact: bool = False):
         import torch
         self.eng = eng
+        self.exact = exact
         nb = eng.nbf
         self.dev = torch.device("cuda")
         self.C = torch.empty(nb * nb, dtype=torch.float64, device=self.dev)
         self.C_try = torch.empty_like(self.C)
         self.E = np.zeros(1)
+        self.lam = np.empty(nb * nb)
 
-    def evaluate(self, C_dev, gamma):
-        """E at orbitals C_dev (also leaves lambda in the context for the next rotation)."""
+    def evaluate(self, C_dev, gamma, want_lambda=False):
+        """E at orbitals C_dev (also leaves lambda in the context for the next step)."""
         ctx = self.eng.ctx
-        bd.donof_ri_transform(ctx, C_dev, bd.DONOF_RI_HALF)
-        bd.donof_ri_jk_ao_batch(ctx)
-        bd.donof_ri_energy_lagrangian(ctx, gamma, self.E, None)
+        if self.exact:
+            bd.donof_ri_exact_jk(ctx, C_dev)
+        else:
+            bd.donof_ri_transform(ctx, C_dev, bd.DONOF_RI_HALF)
+            bd.donof_ri_jk_ao_batch(ctx)
+        bd.donof_ri_energy_lagrangian(ctx, gamma, self.E, self.lam if want_lambda else None)
         return float(self.E[0])
+
+    def gmax(self):
+        """max |lambda - lambda^T| of the last evaluate(want_lambda=True)."""
+        nb = self.eng.nbf
+        lam = self.lam.reshape(nb, nb)
+        return float(np.abs(lam - lam.T).max())
 
 
 def orbital_iterations(eng, C_colmajor, gamma, max_iter=100, gtol=1e-4, etol=1e-10, radius=0.05, r_max=0.3,
@@ -81,29 +94,43 @@ def orbital_iterations(eng, C_colmajor, gamma, max_iter=100, gtol=1e-4, etol=1e-
                 ms_per_iteration=1000.0 * dt / max(it, 1), radius=radius)
 
 
-def flambda_iterations(eng, C_colmajor, gamma, max_iter=100, gtol=1e-4, etol=1e-10, bound=0.1, bound_max=1.0):
+def _gap_floor(d, gapmin):
+    """The aufbau diagonal with every gap raised to at least gapmin (ascending)."""
+    out = np.array(d, dtype=np.float64, copy=True)
+    for k in range(1, out.size):
+        out[k] = max(out[k], out[k - 1] + gapmin)
+    return out
+
+
+def flambda_iterations(eng, C_colmajor, gamma, max_iter=100, gtol=1e-4, etol=1e-10, bound=0.1, bound_max=1.0,
+                       diag0=None, gapmin=0.0, relative_bound=False, state=None):
     """Inner iterations with the paper's step (donof_ri_flambda_step): F^lambda from the
-    Lagrangian, eigenvalues of the accepted step as the next diagonal (lambda_pp at the
-    first), off-diagonal elements damped to `bound`; a step that raises E is rejected
-    and halves the bound, an accepted one grows it by 1.5 (up to bound_max).
-    Returns dict(C, E, gmax, iterations, evaluations, energies, ms_per_iteration)."""
+    Lagrangian, eigenvalues of the accepted step as the next diagonal (diag0, else
+    lambda_pp, at the first), off-diagonal elements damped to `bound` (times the
+    max |lambda - lambda^T| at the start when relative_bound); a step that raises E is
+    rejected and halves the bound, an accepted one grows it by 1.5 (up to bound_max).
+    gapmin > 0 raises every gap of the ascending diagonal to at least gapmin, so that
+    degenerate orbitals of different pairing subspaces are not mixed by 45 degrees.
+    Returns dict(C, E, gmax, iterations, evaluations, energies, ms_per_iteration, diag)."""
     import torch
-    st = _Inner(eng)
+    st = state or _Inner(eng)
     nb = eng.nbf
     gamma = np.ascontiguousarray(gamma, dtype=np.float64)
     st.C.copy_(torch.as_tensor(np.ascontiguousarray(C_colmajor).reshape(-1)) if isinstance(C_colmajor, np.ndarray)
                else C_colmajor.reshape(-1))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    E = st.evaluate(st.C, gamma)
+    E = st.evaluate(st.C, gamma, want_lambda=relative_bound)
+    if relative_bound:
+        bound = bound * max(st.gmax(), 1e-12)
     energies = [E]
-    diag = np.zeros(nb)
-    have_diag = False
+    diag = np.zeros(nb) if diag0 is None else np.array(diag0, dtype=np.float64)
+    have_diag = diag0 is not None
     evals, gmax, it = 1, float("inf"), 0
     for it in range(1, max_iter + 1):
         trial = np.empty(nb)
         if have_diag:
-            trial[:] = diag
+            trial[:] = _gap_floor(diag, gapmin) if gapmin > 0 else diag
         gmax, _ = bd.donof_ri_flambda_step(eng.ctx, trial, not have_diag, bound, st.C_try)
         if gmax <= gtol:
             it -= 1
@@ -127,7 +154,48 @@ def flambda_iterations(eng, C_colmajor, gamma, max_iter=100, gtol=1e-4, etol=1e-
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     return dict(C=st.C.cpu().numpy().copy(), E=E, gmax=gmax, iterations=it, evaluations=evals, energies=energies,
-                ms_per_iteration=1000.0 * dt / max(it, 1))
+                ms_per_iteration=1000.0 * dt / max(it, 1), diag=diag.copy())
+
+
+def converge(eng, C0, gamma0, diag0, etol=1e-6, gtol=1e-4, max_outer=60, max_inner=100, gapmin=0.01, exact=False,
+             on_max_iter=20000):
+    """The paper's outer / inner scheme to convergence with the F^lambda step: per outer
+    iteration J, K of the current orbitals (one FULL transform, or exact four-centre
+    integrals when exact), the occupation optimisation, then F^lambda inner iterations
+    until max |lambda - lambda^T| <= gtol (at most max_inner).  Stops when an outer
+    iteration changes E by less than etol with max |lambda - lambda^T| <= gtol.
+    C0 [mu, p] numpy, gamma0, diag0 (the starting aufbau diagonal, e.g. the RHF orbital
+    energies).  Returns dict(C, gamma, E, outer, inner_total, converged, seconds,
+    ms_per_inner, history, diag)."""
+    import torch
+    C = bd.Engine.colmajor(C0)
+    gamma = np.array(gamma0, dtype=np.float64)
+    diag = np.array(diag0, dtype=np.float64)
+    st = _Inner(eng, exact=exact)
+    hist, E_prev, total_inner, converged = [], None, 0, False
+    t_inner = 0.0
+    t0 = time.perf_counter()
+    for o in range(1, max_outer + 1):
+        if exact:
+            bd.donof_ri_exact_jk(eng.ctx, C)
+        else:
+            bd.donof_ri_transform(eng.ctx, C, bd.DONOF_RI_FULL)
+        gamma, E_on, _, it_on, _ = eng.optimize_occupations(gamma, max_iter=on_max_iter, gtol=1e-8, etol=1e-14)
+        ti = time.perf_counter()
+        r = flambda_iterations(eng, C, gamma, max_iter=max_inner, gtol=gtol, etol=1e-10, bound=0.1, bound_max=1.0,
+                               diag0=diag, gapmin=gapmin, relative_bound=True, state=st)
+        t_inner += time.perf_counter() - ti
+        C, diag = r["C"], r["diag"]
+        total_inner += r["iterations"]
+        hist.append(dict(outer=o, E_occ=E_on, on_iterations=it_on, E=r["E"], gmax=r["gmax"], inner=r["iterations"]))
+        if E_prev is not None and abs(r["E"] - E_prev) < etol and r["gmax"] <= gtol:
+            converged = True
+            break
+        E_prev = r["E"]
+    torch.cuda.synchronize()
+    return dict(C=C.reshape(eng.nbf, eng.nbf).T.copy(), gamma=gamma, E=hist[-1]["E"], outer=len(hist),
+                inner_total=total_inner, converged=converged, seconds=time.perf_counter() - t0,
+                ms_per_inner=1000.0 * t_inner / max(total_inner, 1), history=hist, diag=diag)
 
 
 def solve(eng, C0, gamma0, max_outer=10, max_inner=50, etol=1e-6, gtol=1e-4, on_max_iter=20000):
@@ -156,42 +224,62 @@ def solve(eng, C0, gamma0, max_outer=10, max_inner=50, etol=1e-6, gtol=1e-4, on_
 
 
 def main():
-    """Compare the FP64 and SLICE4 engines and the learned occupation guess on one workload:
-    outer / inner iterations, energies, ms per inner iteration."""
+    """The paper's scheme to convergence from the RI-HF orbitals on one workload, with the
+    FP64 and SLICE4 engines (and the learned occupation guess when --learned > 0):
+    outer / inner iterations, energies, ms per inner iteration; with --restart, the
+    converged FP64 RI run restarted with exact four-centre integrals (nbf <= 256)."""
     import argparse
     import json
     from synthetic import standard_gamma
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="c6h12")
-    ap.add_argument("--outer", type=int, default=4)
-    ap.add_argument("--inner", type=int, default=25)
+    ap.add_argument("--outer", type=int, default=60)
+    ap.add_argument("--inner", type=int, default=100)
+    ap.add_argument("--etol", type=float, default=1e-6)
+    ap.add_argument("--gtol", type=float, default=1e-4)
+    ap.add_argument("--gapmin", type=float, default=0.01)
+    ap.add_argument("--forms", default="fp64,slice4")
     ap.add_argument("--learned", type=int, default=0, help="train the warm-start network on this many rings first")
+    ap.add_argument("--restart", action="store_true", help="restart the converged FP64 run with exact integrals")
     args = ap.parse_args()
     eng0, w = bd.engine_and_workload(args.workload, bd.DONOF_RI_FP64)
-    eng0.close()
+    t0 = time.perf_counter()
+    C0, eps0, E_hf, it_hf, com = eng0.rhf(max_iter=200, tol=1e-9)
+    t_hf = time.perf_counter() - t0
     s = w.system
     g0 = standard_gamma(s.n_strong, s.n_weak_per)
-    runs = [("fp64", bd.DONOF_RI_FP64, None), ("slice4", bd.DONOF_RI_SLICE4, None)]
-    net = None
+    runs = [(f, {"fp64": bd.DONOF_RI_FP64, "slice4": bd.DONOF_RI_SLICE4}[f], None) for f in args.forms.split(",")]
     if args.learned:
         from . import warmstart
-        X, Y = warmstart.training_set(args.learned)
+        X, Y = warmstart.training_set(args.learned, orbitals="rhf")
         net, _ = warmstart.train(X, Y)
         runs.append(("slice4+learned", bd.DONOF_RI_SLICE4, net))
-    out = []
+    out, conv64 = [], None
     for name, prec, nn in runs:
-        eng = bd.Engine(s, prec)
+        eng = eng0 if prec == bd.DONOF_RI_FP64 else bd.Engine(s, prec)
         start = g0
         if nn is not None:
-            eng.transform(w.C, bd.DONOF_RI_FULL)
+            eng.transform(C0, bd.DONOF_RI_FULL)
             start = eng.gamma_guess(nn)
-        t0 = time.perf_counter()
-        r = solve(eng, w.C, start, max_outer=args.outer, max_inner=args.inner)
-        dt = time.perf_counter() - t0
-        eng.close()
-        out.append(dict(form=name, E=r["E"], outer=r["outer"], inner_total=r["inner_total"], seconds=dt,
+        r = converge(eng, C0, start, eps0, etol=args.etol, gtol=args.gtol, max_outer=args.outer,
+                     max_inner=args.inner, gapmin=args.gapmin)
+        if prec == bd.DONOF_RI_FP64 and conv64 is None:
+            conv64 = r
+        else:
+            eng.close()
+        out.append(dict(form=name, E=r["E"], converged=r["converged"], outer=r["outer"],
+                        inner_total=r["inner_total"], seconds=r["seconds"], ms_per_inner=r["ms_per_inner"],
                         history=r["history"]))
-    print(json.dumps({"workload": args.workload, "runs": out}))
+    line = {"workload": args.workload, "rhf": {"E": E_hf, "iterations": it_hf, "commutator": com, "seconds": t_hf},
+            "runs": out}
+    if args.restart and conv64 is not None:
+        r = converge(eng0, conv64["C"], conv64["gamma"], conv64["diag"], etol=args.etol, gtol=args.gtol,
+                     max_outer=args.outer, max_inner=args.inner, gapmin=args.gapmin, exact=True)
+        line["restart_exact"] = dict(E=r["E"], converged=r["converged"], outer=r["outer"],
+                                     inner_total=r["inner_total"], seconds=r["seconds"],
+                                     ri_error=conv64["E"] - r["E"], history=r["history"])
+    eng0.close()
+    print(json.dumps(line))
 
 
 if __name__ == "__main__":

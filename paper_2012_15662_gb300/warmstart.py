@@ -38,14 +38,16 @@ def targets(gamma: np.ndarray, n_strong: int, n_weak_per: int) -> np.ndarray:
     return Y
 
 
-def sample(n_c, seed, precision=bd.DONOF_RI_SLICE4, max_iter=20000, etol=1e-13, jitter=0.05):
-    """(features, targets, iterations, energy) of one seeded ring from the standard guess."""
+def sample(n_c, seed, precision=bd.DONOF_RI_SLICE4, max_iter=20000, etol=1e-13, jitter=0.05, orbitals="random"):
+    """(features, targets, iterations, energy) of one seeded ring from the standard guess;
+    orbitals "random" (S^-1/2 Q) or "rhf" (the ring's RI-HF orbitals, donof_ri_rhf)."""
     from synthetic import make_system, ring_workload, standard_gamma
     eng = bd.Engine(make_system("ring", n_c=n_c, seed=seed, jitter=jitter), precision)
     try:
         workload = ring_workload(n_c, seed, eng.overlap(), jitter=jitter)
         s = workload.system
-        eng.transform(workload.C, bd.DONOF_RI_FULL)
+        C = workload.C if orbitals == "random" else eng.rhf(max_iter=200, tol=1e-8)[0]
+        eng.transform(C, bd.DONOF_RI_FULL)
         X = eng.on_features()
         g0 = standard_gamma(s.n_strong, s.n_weak_per)
         gam, E, grad, it, reason = eng.optimize_occupations(g0, max_iter=max_iter, gtol=1e-8, etol=etol)
@@ -54,13 +56,14 @@ def sample(n_c, seed, precision=bd.DONOF_RI_SLICE4, max_iter=20000, etol=1e-13, 
         eng.close()
 
 
-def training_set(n_systems: int, first_seed: int = 1000, n_c_range=(6, 12), precision=bd.DONOF_RI_SLICE4):
+def training_set(n_systems: int, first_seed: int = 1000, n_c_range=(6, 12), precision=bd.DONOF_RI_SLICE4,
+                 orbitals="random"):
     """Features and targets of n_systems seeded rings (C6..C12 in turn)."""
     lo, hi = n_c_range
     Xs, Ys = [], []
     for k in range(n_systems):
         n_c = lo + k % (hi - lo + 1)
-        X, Y, _, _ = sample(n_c, first_seed + k, precision)
+        X, Y, _, _ = sample(n_c, first_seed + k, precision, orbitals=orbitals)
         Xs.append(X)
         Ys.append(Y)
     return np.concatenate(Xs), np.concatenate(Ys)

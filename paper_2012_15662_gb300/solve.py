@@ -158,7 +158,7 @@ def flambda_iterations(eng, C_colmajor, gamma, max_iter=100, gtol=1e-4, etol=1e-
 
 
 def converge(eng, C0, gamma0, diag0, etol=1e-6, gtol=1e-4, max_outer=60, max_inner=100, gapmin=0.01, exact=False,
-             on_max_iter=20000):
+             on_max_iter=20000, time_limit=None, log=None):
     """The paper's outer / inner scheme to convergence with the F^lambda step: per outer
     iteration J, K of the current orbitals (one FULL transform, or exact four-centre
     integrals when exact), the occupation optimisation, then F^lambda inner iterations
@@ -166,7 +166,9 @@ def converge(eng, C0, gamma0, diag0, etol=1e-6, gtol=1e-4, max_outer=60, max_inn
     iteration changes E by less than etol with max |lambda - lambda^T| <= gtol.
     C0 [mu, p] numpy, gamma0, diag0 (the starting aufbau diagonal, e.g. the RHF orbital
     energies).  Returns dict(C, gamma, E, outer, inner_total, converged, seconds,
-    ms_per_inner, history, diag)."""
+    ms_per_inner, history, diag).  time_limit (seconds): stop after the outer iteration
+    that passes it (converged stays False); log: called with each outer iteration's
+    record."""
     import torch
     C = bd.Engine.colmajor(C0)
     gamma = np.array(gamma0, dtype=np.float64)
@@ -187,11 +189,16 @@ def converge(eng, C0, gamma0, diag0, etol=1e-6, gtol=1e-4, max_outer=60, max_inn
         t_inner += time.perf_counter() - ti
         C, diag = r["C"], r["diag"]
         total_inner += r["iterations"]
-        hist.append(dict(outer=o, E_occ=E_on, on_iterations=it_on, E=r["E"], gmax=r["gmax"], inner=r["iterations"]))
+        hist.append(dict(outer=o, E_occ=E_on, on_iterations=it_on, E=r["E"], gmax=r["gmax"], inner=r["iterations"],
+                         seconds=time.perf_counter() - t0))
+        if log is not None:
+            log(hist[-1])
         if E_prev is not None and abs(r["E"] - E_prev) < etol and r["gmax"] <= gtol:
             converged = True
             break
         E_prev = r["E"]
+        if time_limit is not None and time.perf_counter() - t0 > time_limit:
+            break
     torch.cuda.synchronize()
     return dict(C=C.reshape(eng.nbf, eng.nbf).T.copy(), gamma=gamma, E=hist[-1]["E"], outer=len(hist),
                 inner_total=total_inner, converged=converged, seconds=time.perf_counter() - t0,
@@ -241,7 +248,12 @@ def main():
     ap.add_argument("--forms", default="fp64,slice4")
     ap.add_argument("--learned", type=int, default=0, help="train the warm-start network on this many rings first")
     ap.add_argument("--restart", action="store_true", help="restart the converged FP64 run with exact integrals")
+    ap.add_argument("--time-limit", type=float, default=None, help="seconds per converge() run")
     args = ap.parse_args()
+    import sys
+
+    def log(rec):
+        print(json.dumps(rec), file=sys.stderr, flush=True)
     eng0, w = bd.engine_and_workload(args.workload, bd.DONOF_RI_FP64)
     t0 = time.perf_counter()
     C0, eps0, E_hf, it_hf, com = eng0.rhf(max_iter=200, tol=1e-9)
@@ -261,8 +273,9 @@ def main():
         if nn is not None:
             eng.transform(C0, bd.DONOF_RI_FULL)
             start = eng.gamma_guess(nn)
+        print(f"# {name}", file=sys.stderr, flush=True)
         r = converge(eng, C0, start, eps0, etol=args.etol, gtol=args.gtol, max_outer=args.outer,
-                     max_inner=args.inner, gapmin=args.gapmin)
+                     max_inner=args.inner, gapmin=args.gapmin, time_limit=args.time_limit, log=log)
         if prec == bd.DONOF_RI_FP64 and conv64 is None:
             conv64 = r
         else:
@@ -273,8 +286,10 @@ def main():
     line = {"workload": args.workload, "rhf": {"E": E_hf, "iterations": it_hf, "commutator": com, "seconds": t_hf},
             "runs": out}
     if args.restart and conv64 is not None:
+        print("# exact restart", file=sys.stderr, flush=True)
         r = converge(eng0, conv64["C"], conv64["gamma"], conv64["diag"], etol=args.etol, gtol=args.gtol,
-                     max_outer=args.outer, max_inner=args.inner, gapmin=args.gapmin, exact=True)
+                     max_outer=args.outer, max_inner=args.inner, gapmin=args.gapmin, exact=True,
+                     time_limit=args.time_limit, log=log)
         line["restart_exact"] = dict(E=r["E"], converged=r["converged"], outer=r["outer"],
                                      inner_total=r["inner_total"], seconds=r["seconds"],
                                      ri_error=conv64["E"] - r["E"], history=r["history"])

@@ -166,3 +166,35 @@ def test_full_size_c20h40():
     # energy from this path's own J, K (Eq. PNOF) equals the energy from lambda
     E2 = pnof7.energy(n, Hd, J, K, A, Bc, I.nuclear_repulsion(s))
     assert abs(E - E2) <= TOL_E
+
+
+def test_full_size_c20h40_against_oracle():
+    """C20H40, the benchmark's workload: J, K, E and lambda against the FP64 oracle (a
+    few minutes of host time: the three-centre integrals and the fit at full size)."""
+    from paper_2012_15662_gb300 import binding as bd
+    w = make_workload("c20h40")
+    s = w.system
+    eng = bd.Engine(s, bd.DONOF_RI_SLICE4)
+    eng.transform(w.C, bd.DONOF_RI_FULL)
+    J, K = eng.jk_mo()
+    eng.jk_ao(want=False)
+    E, lam = eng.energy_lagrangian(w.gamma)
+    eng.close()
+    B, L, G = ri.setup(s)
+    m = s.n_omega
+    bh = ri.half_transform(B, w.C, m)
+    del B, L, G
+    d = ri.diagonal(bh, w.C)
+    bf = ri.full_transform(bh, w.C)
+    Jo, Ko = ri.jk_mo(bf, d)
+    assert np.abs(J - Jo).max() <= TOL_JK
+    assert np.abs(K - Ko).max() <= TOL_JK
+    H = I.core_hamiltonian(s)
+    sub, rank = pairing_columns(s.n_strong, s.n_weak_per)
+    n = pnof7.occupations(w.gamma, s.n_strong, s.n_weak_per, sub, rank)
+    A, Bc = pnof7.coupling(n, sub, rank)
+    lamo = pnof7.lagrangian_contracted(w.C, H, bh, d, bf, n, A, Bc)
+    Hd = np.einsum("mp,mn,np->p", w.C[:, :m], H, w.C[:, :m])
+    Eo = pnof7.energy(n, Hd, Jo, Ko, A, Bc, I.nuclear_repulsion(s))
+    assert abs(E - Eo) <= TOL_E, (E, Eo)
+    assert np.abs(lam - lamo).max() <= 1e-6

@@ -453,6 +453,19 @@ int donof_ri_set_schedule(donof_ri_ctx* ctx, int kind, int stages, int option);
  */
 int donof_ri_rotate_orbitals(donof_ri_ctx* ctx, double radius, double* C, double* gmax);
 
+/*
+ * Rotate the context's orbitals by a given generator: C <- C expm(kappa), then one
+ * Newton-Schulz step in the overlap metric (C^T S C = I, the orbitals' constraint;
+ * Sec. 2, "Orbital Optimization with RI").  kappa [nbf][nbf] FP64 row-major
+ * antisymmetric (kappa_qp = -kappa_pq mixes orbital q into orbital p), host or
+ * device; the exponential by scaling and squaring with a degree-12 Taylor
+ * polynomial.  With the gradient dE/dkappa_qp = 4 (lambda_qp - lambda_pq) (q > p)
+ * of the last donof_ri_energy_lagrangian, this is the step of a quasi-Newton
+ * orbital optimisation.  C (optional) receives the rotated orbitals, column-major,
+ * host or device.  Invalidates the transforms.  Errors: E_ARG, E_NONFINITE, E_CUDA.
+ */
+int donof_ri_apply_rotation(donof_ri_ctx* ctx, const double* kappa, double* C);
+
 /* ------------------------------------------------------------------------
  * Learned warm start for the occupation optimisation.  The paper has no
  * learned part: this is the project's own addition.  A 3-layer MLP

@@ -49,7 +49,7 @@ EXPORTS = [
     "donof_ri_strerror", "donof_ri_launch_count", "donof_ri_profile", "donof_ri_profile_read",
     "donof_ri_iteration", "donof_ri_jmo_noalloc", "donof_ri_optimize_occupations",
     "donof_ri_on_features", "donof_ri_gamma_guess", "donof_ri_rotate_orbitals", "donof_ri_autotune", "donof_ri_set_schedule", "donof_ri_exact_jk",
-    "donof_ri_energy_lagrangian_contracted", "donof_ri_flambda_step", "donof_ri_check_wait_timeout", "donof_ri_rhf",
+    "donof_ri_energy_lagrangian_contracted", "donof_ri_flambda_step", "donof_ri_check_wait_timeout", "donof_ri_rhf", "donof_ri_apply_rotation",
     "donof_mlp_create", "donof_mlp_param_count", "donof_mlp_set_params", "donof_mlp_get_params",
     "donof_mlp_set_normalization", "donof_mlp_forward", "donof_mlp_loss_grad", "donof_mlp_train_step",
     "donof_mlp_destroy",
@@ -113,6 +113,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.donof_ri_check_wait_timeout.restype = i
     lib.donof_ri_rhf.argtypes = [vp, i, d, vp, vp, vp, vp, vp]
     lib.donof_ri_rhf.restype = i
+    lib.donof_ri_apply_rotation.argtypes = [vp, vp, vp]
+    lib.donof_ri_apply_rotation.restype = i
     lib.donof_ri_jmo_noalloc.argtypes = [vp, i, i, vp, vp]
     lib.donof_ri_jmo_noalloc.restype = i
     lib.donof_ri_iteration.argtypes = [vp, vp, vp, i, vp, vp, vp, vp, i]
@@ -285,6 +287,11 @@ def donof_ri_rotate_orbitals_dev(ctx, radius: float, C_out, gmax_out: np.ndarray
     """One rotation step; C_out a device tensor (column-major nbf*nbf) or None, gmax_out a 1-element float64 array."""
     _check(load().donof_ri_rotate_orbitals(ctx, float(radius), _ptr(C_out), gmax_out.ctypes.data),
            "donof_ri_rotate_orbitals")
+
+
+def donof_ri_apply_rotation(ctx, kappa, C_out=None):
+    """C <- C expm(kappa) (kappa row-major antisymmetric, numpy or device tensor); C_out optional."""
+    _check(load().donof_ri_apply_rotation(ctx, _ptr(kappa), _ptr(C_out)), "donof_ri_apply_rotation")
 
 
 def donof_ri_autotune(ctx, reps: int = 5):

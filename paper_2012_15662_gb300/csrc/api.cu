@@ -559,6 +559,24 @@ int donof_ri_rotate_orbitals(donof_ri_ctx* ctx, double radius, double* C, double
   return host ? consume_status(ctx) : DONOF_RI_OK;
 }
 
+int donof_ri_apply_rotation(donof_ri_ctx* ctx, const double* kappa, double* C) {
+  if (!ctx || !kappa) return DONOF_RI_E_ARG;
+  const size_t nb2 = (size_t)ctx->nbf * ctx->nbf;
+  int rc;
+  if (!ctx->d_rot && (rc = dalloc(&ctx->d_rot, 4 * nb2 + 2))) return rc;
+  {
+    ProfScope ps(ctx, DONOF_RI_ROW_OTHER);
+    DONOF_CUDA_TRY(cudaMemcpyAsync(ctx->d_rot, kappa, nb2 * sizeof(double),
+                                   is_device_ptr(kappa) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                   ctx->stream));
+    if ((rc = apply_rotation(ctx, ctx->d_rot))) return rc;
+  }
+  ctx->have_half = ctx->have_full = ctx->have_ao = ctx->have_lambda = 0;
+  bool host = false;
+  if ((rc = copy_out(ctx, C, ctx->d_C, nb2, &host))) return rc;
+  return host ? consume_status(ctx) : DONOF_RI_OK;
+}
+
 // One iteration with the energy row's prologue (occupations, couplings, Fock
 // weights and H C, which need only C and gamma) forked onto the side stream, so
 // that it runs concurrently with the transforms; joined before F^(p) C_p.  The

@@ -170,6 +170,8 @@ int onopt_launch(donof_ri_ctx* ctx, double* d_gamma, double* d_E, double* d_grad
                  int max_iter, double gtol, double etol);
 int onopt_features(donof_ri_ctx* ctx, float* d_X);
 int rotate_orbitals(donof_ri_ctx* ctx, double radius, double* scratch, double* gnorm);
+// rotate.cu: ctx->d_C <- d_C expm(kappa), kappa row-major in the first nbf^2 doubles of scratch
+int apply_rotation(donof_ri_ctx* ctx, double* scratch);
 int s4_autotune(donof_ri_ctx* ctx, int reps, int* report, int* tried);
 int s4_set_schedule(donof_ri_ctx* ctx, int kind, int stages, int option);
 // exact.cu: exact four-centre J^(q), K^(q), J, K into an FP64 context's buffers

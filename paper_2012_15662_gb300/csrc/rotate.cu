@@ -78,26 +78,36 @@ static int gemm_rr(donof_ri_ctx* ctx, int n, const double* A, bool At, const dou
   return launch_dgemm(ctx, g);
 }
 
-// Rotates ctx->d_C in place; gnorm[0] = max|G| (host).  Scratch: 4 n^2 + 2 doubles.
-int rotate_orbitals(donof_ri_ctx* ctx, double radius, double* scratch, double* gnorm) {
+// 1-norm of a row-major n x n matrix (max over columns of the column sums of |X|) into out[0].
+__global__ void rot_norm1_kernel(const double* X, int n, double* out) {
+  __shared__ double red[256];
+  double m = 0.0;
+  for (int c = threadIdx.x; c < n; c += 256) {
+    double col = 0.0;
+    for (int r = 0; r < n; ++r) col += fabs(X[(size_t)r * n + c]);
+    m = fmax(m, col);
+  }
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = red[0];
+}
+
+// X <- a X (row-major n x n)
+__global__ void rot_scale_kernel(int n, double a, double* X) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < (long long)n * n) X[i] *= a;
+}
+
+// C <- C expm(2^s X) for X = K (row-major, already scaled so that ||X||_1 <= 1/4),
+// then one Newton-Schulz step in the overlap metric.  K, U, T, W: n x n scratch.
+static int apply_scaled_rotation(donof_ri_ctx* ctx, int s, double* K, double* U, double* T, double* W) {
   const int n = ctx->nbf;
   const long long n2 = (long long)n * n;
-  double *K = scratch, *U = scratch + n2, *T = scratch + 2 * n2, *W = scratch + 3 * n2, *nrm = scratch + 4 * n2;
-  rot_norms_kernel<<<1, 256, 0, ctx->stream>>>(ctx->d_lambda, n, nrm);
-  DONOF_LAUNCH_CHECK(ctx);
-  double norms[2];
-  DONOF_CUDA_TRY(cudaMemcpyAsync(norms, nrm, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-  DONOF_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-  *gnorm = norms[0];
-  if (!(norms[0] > 0.0) || !(radius > 0.0)) return DONOF_RI_OK;
-  // ||kappa||_1 = radius * ||G||_1 / max|G|; scale by 2^-s so that ||X||_1 <= 1/4
-  const double k1 = radius * norms[1] / norms[0];
-  int s = 0;
-  while (k1 / ldexp(1.0, s) > 0.25 && s < 60) ++s;
-  const double scale = -radius / norms[0] / ldexp(1.0, s);
   const unsigned int nblk = ceil_div_u(n2, 256);
-  rot_kappa_kernel<<<nblk, 256, 0, ctx->stream>>>(ctx->d_lambda, n, scale, K);
-  DONOF_LAUNCH_CHECK(ctx);
   // Horner: U = I + X (I + X/2 (I + ... (I + X/12)))
   rot_axpy_identity_kernel<<<nblk, 256, 0, ctx->stream>>>(n, 1.0, 1.0 / 12.0, K, U);
   DONOF_LAUNCH_CHECK(ctx);
@@ -135,6 +145,50 @@ int rotate_orbitals(donof_ri_ctx* ctx, double radius, double* scratch, double* g
   DONOF_LAUNCH_CHECK(ctx);
   if ((rc = gemm_rr(ctx, n, U, false, T, ctx->d_C, 1.0, 0.0))) return rc;
   return DONOF_RI_OK;
+}
+
+// Rotates ctx->d_C in place; gnorm[0] = max|G| (host).  Scratch: 4 n^2 + 2 doubles.
+int rotate_orbitals(donof_ri_ctx* ctx, double radius, double* scratch, double* gnorm) {
+  const int n = ctx->nbf;
+  const long long n2 = (long long)n * n;
+  double *K = scratch, *U = scratch + n2, *T = scratch + 2 * n2, *W = scratch + 3 * n2, *nrm = scratch + 4 * n2;
+  rot_norms_kernel<<<1, 256, 0, ctx->stream>>>(ctx->d_lambda, n, nrm);
+  DONOF_LAUNCH_CHECK(ctx);
+  double norms[2];
+  DONOF_CUDA_TRY(cudaMemcpyAsync(norms, nrm, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  DONOF_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  *gnorm = norms[0];
+  if (!(norms[0] > 0.0) || !(radius > 0.0)) return DONOF_RI_OK;
+  // ||kappa||_1 = radius * ||G||_1 / max|G|; scale by 2^-s so that ||X||_1 <= 1/4
+  const double k1 = radius * norms[1] / norms[0];
+  int s = 0;
+  while (k1 / ldexp(1.0, s) > 0.25 && s < 60) ++s;
+  const double scale = -radius / norms[0] / ldexp(1.0, s);
+  const unsigned int nblk = ceil_div_u(n2, 256);
+  rot_kappa_kernel<<<nblk, 256, 0, ctx->stream>>>(ctx->d_lambda, n, scale, K);
+  DONOF_LAUNCH_CHECK(ctx);
+  return apply_scaled_rotation(ctx, s, K, U, T, W);
+}
+
+// Rotates ctx->d_C in place by expm(kappa), kappa a device copy (row-major n x n).
+// Scratch: 4 n^2 + 2 doubles (kappa may already sit in its first n^2).
+int apply_rotation(donof_ri_ctx* ctx, double* scratch) {
+  const int n = ctx->nbf;
+  const long long n2 = (long long)n * n;
+  double *K = scratch, *U = scratch + n2, *T = scratch + 2 * n2, *W = scratch + 3 * n2, *nrm = scratch + 4 * n2;
+  rot_norm1_kernel<<<1, 256, 0, ctx->stream>>>(K, n, nrm);
+  DONOF_LAUNCH_CHECK(ctx);
+  double k1 = 0.0;
+  DONOF_CUDA_TRY(cudaMemcpyAsync(&k1, nrm, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  DONOF_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  if (!isfinite(k1)) return DONOF_RI_E_NONFINITE;
+  int s = 0;
+  while (k1 / ldexp(1.0, s) > 0.25 && s < 60) ++s;
+  if (s > 0) {
+    rot_scale_kernel<<<ceil_div_u(n2, 256), 256, 0, ctx->stream>>>(n, ldexp(1.0, -s), K);
+    DONOF_LAUNCH_CHECK(ctx);
+  }
+  return apply_scaled_rotation(ctx, s, K, U, T, W);
 }
 
 }  // namespace donof

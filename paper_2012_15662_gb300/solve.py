@@ -157,8 +157,102 @@ def flambda_iterations(eng, C_colmajor, gamma, max_iter=100, gtol=1e-4, etol=1e-
                 ms_per_iteration=1000.0 * dt / max(it, 1), diag=diag.copy())
 
 
+def lbfgs_iterations(eng, C_colmajor, gamma, eps, max_iter=200, gtol=1e-4, memory=10, max_step=0.5,
+                     hmin=0.05, state=None):
+    """Quasi-Newton inner iterations (an addition beside the paper's F^lambda step): L-BFGS
+    on the rotation generator, C <- C expm(kappa) (donof_ri_apply_rotation), with the
+    gradient dE/dkappa_qp = 4 (lambda_qp - lambda_pq) (q > p) from the engine's
+    Lagrangian, the initial inverse Hessian diag 1 / (4 max(|eps_q - eps_p|, hmin))
+    from orbital energies eps (the HF ones), pairs transported as they are (no
+    parallel transport), a step capped at max_step radians and an Armijo
+    backtracking line search on E.  Stops when max |lambda - lambda^T| <= gtol.
+    Returns dict(C, E, gmax, iterations, evaluations, ms_per_iteration)."""
+    import torch
+    st = state or _Inner(eng)
+    nb = eng.nbf
+    gamma = np.ascontiguousarray(gamma, dtype=np.float64)
+    C_cur = np.ascontiguousarray(C_colmajor, dtype=np.float64).reshape(-1).copy()
+    il = np.tril_indices(nb, -1)
+    eps = np.asarray(eps, dtype=np.float64)
+    h0 = 1.0 / (4.0 * np.maximum(np.abs(eps[il[0]] - eps[il[1]]), hmin))
+
+    def evaluate(Ccm):
+        st.C.copy_(torch.as_tensor(Ccm))
+        E = st.evaluate(st.C, gamma, want_lambda=True)
+        lam = st.lam.reshape(nb, nb).T  # lambda[q][p] (the ABI returns it column-major)
+        G = lam - lam.T
+        return E, 4.0 * G[il], float(np.abs(G).max())
+
+    def kappa_of(x):
+        K = np.zeros((nb, nb))
+        K[il] = x
+        return K - K.T
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    E, g, gmax = evaluate(C_cur)
+    S, Y = [], []
+    evals, it = 1, 0
+    Ctry = np.empty(nb * nb)
+    for it in range(1, max_iter + 1):
+        if gmax <= gtol:
+            it -= 1
+            break
+        # two-loop recursion
+        q = g.copy()
+        alphas = []
+        for s_, y_ in reversed(list(zip(S, Y))):
+            rho = 1.0 / float(y_ @ s_)
+            a = rho * float(s_ @ q)
+            alphas.append((a, rho, s_, y_))
+            q -= a * y_
+        if S:
+            gam = float(S[-1] @ Y[-1]) / float(Y[-1] @ (h0 * Y[-1]))
+            r = gam * h0 * q
+        else:
+            r = h0 * q
+        for a, rho, s_, y_ in reversed(alphas):
+            b = rho * float(y_ @ r)
+            r += (a - b) * s_
+        d = -r
+        slope = float(g @ d)
+        if not slope < 0.0:  # not a descent direction: restart from the preconditioned gradient
+            S, Y = [], []
+            d = -h0 * g
+            slope = float(g @ d)
+        dmax = float(np.abs(d).max())
+        alpha = min(1.0, max_step / dmax) if dmax > 0 else 1.0
+        accepted = False
+        for _ in range(12):
+            bd.donof_ri_apply_rotation(eng.ctx, kappa_of(alpha * d), Ctry)
+            # apply_rotation rotated the context's own orbitals: start each trial from C_cur
+            En, gn, gmn = evaluate(Ctry)
+            evals += 1
+            if En <= E + 1e-4 * alpha * slope:
+                accepted = True
+                break
+            alpha *= 0.5
+            st.C.copy_(torch.as_tensor(C_cur))
+            bd.donof_ri_transform(eng.ctx, st.C, bd.DONOF_RI_HALF)  # back to the accepted orbitals
+        if not accepted:
+            evaluate(C_cur)  # leave the context at the accepted orbitals
+            break
+        sk, yk = alpha * d, gn - g
+        if float(sk @ yk) > 1e-12 * float(yk @ yk):
+            S.append(sk)
+            Y.append(yk)
+            if len(S) > memory:
+                S.pop(0)
+                Y.pop(0)
+        C_cur, E, g, gmax = Ctry.copy(), En, gn, gmn
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return dict(C=C_cur.copy(), E=E, gmax=gmax, iterations=it, evaluations=evals,
+                ms_per_iteration=1000.0 * dt / max(it, 1))
+
+
 def converge(eng, C0, gamma0, diag0, etol=1e-6, gtol=1e-4, max_outer=60, max_inner=100, gapmin=0.01, exact=False,
-             on_max_iter=20000, time_limit=None, log=None):
+             on_max_iter=20000, time_limit=None, log=None, inner="flambda"):
     """The paper's outer / inner scheme to convergence with the F^lambda step: per outer
     iteration J, K of the current orbitals (one FULL transform, or exact four-centre
     integrals when exact), the occupation optimisation, then F^lambda inner iterations
@@ -168,7 +262,8 @@ def converge(eng, C0, gamma0, diag0, etol=1e-6, gtol=1e-4, max_outer=60, max_inn
     energies).  Returns dict(C, gamma, E, outer, inner_total, converged, seconds,
     ms_per_inner, history, diag).  time_limit (seconds): stop after the outer iteration
     that passes it (converged stays False); log: called with each outer iteration's
-    record."""
+    record.  inner: "flambda" (the paper's step) or "lbfgs" (lbfgs_iterations, with
+    diag0 as its orbital energies)."""
     import torch
     C = bd.Engine.colmajor(C0)
     gamma = np.array(gamma0, dtype=np.float64)
@@ -184,10 +279,14 @@ def converge(eng, C0, gamma0, diag0, etol=1e-6, gtol=1e-4, max_outer=60, max_inn
             bd.donof_ri_transform(eng.ctx, C, bd.DONOF_RI_FULL)
         gamma, E_on, _, it_on, _ = eng.optimize_occupations(gamma, max_iter=on_max_iter, gtol=1e-8, etol=1e-14)
         ti = time.perf_counter()
-        r = flambda_iterations(eng, C, gamma, max_iter=max_inner, gtol=gtol, etol=1e-10, bound=0.1, bound_max=1.0,
-                               diag0=diag, gapmin=gapmin, relative_bound=True, state=st)
+        if inner == "lbfgs":
+            r = lbfgs_iterations(eng, C, gamma, diag0, max_iter=max_inner, gtol=gtol, state=st)
+        else:
+            r = flambda_iterations(eng, C, gamma, max_iter=max_inner, gtol=gtol, etol=1e-10, bound=0.1,
+                                   bound_max=1.0, diag0=diag, gapmin=gapmin, relative_bound=True, state=st)
+            diag = r["diag"]
         t_inner += time.perf_counter() - ti
-        C, diag = r["C"], r["diag"]
+        C = r["C"]
         total_inner += r["iterations"]
         hist.append(dict(outer=o, E_occ=E_on, on_iterations=it_on, E=r["E"], gmax=r["gmax"], inner=r["iterations"],
                          seconds=time.perf_counter() - t0))
@@ -246,6 +345,7 @@ def main():
     ap.add_argument("--gtol", type=float, default=1e-4)
     ap.add_argument("--gapmin", type=float, default=0.01)
     ap.add_argument("--forms", default="fp64,slice4")
+    ap.add_argument("--inner-step", default="flambda", choices=["flambda", "lbfgs"])
     ap.add_argument("--learned", type=int, default=0, help="train the warm-start network on this many rings first")
     ap.add_argument("--restart", action="store_true", help="restart the converged FP64 run with exact integrals")
     ap.add_argument("--time-limit", type=float, default=None, help="seconds per converge() run")
@@ -256,7 +356,7 @@ def main():
         print(json.dumps(rec), file=sys.stderr, flush=True)
     eng0, w = bd.engine_and_workload(args.workload, bd.DONOF_RI_FP64)
     t0 = time.perf_counter()
-    C0, eps0, E_hf, it_hf, com = eng0.rhf(max_iter=200, tol=1e-9)
+    C0, eps0, E_hf, it_hf, com = eng0.rhf(max_iter=200, tol=1e-8)
     t_hf = time.perf_counter() - t0
     s = w.system
     g0 = standard_gamma(s.n_strong, s.n_weak_per)
@@ -275,7 +375,8 @@ def main():
             start = eng.gamma_guess(nn)
         print(f"# {name}", file=sys.stderr, flush=True)
         r = converge(eng, C0, start, eps0, etol=args.etol, gtol=args.gtol, max_outer=args.outer,
-                     max_inner=args.inner, gapmin=args.gapmin, time_limit=args.time_limit, log=log)
+                     max_inner=args.inner, gapmin=args.gapmin, time_limit=args.time_limit, log=log,
+                     inner=args.inner_step)
         if prec == bd.DONOF_RI_FP64 and conv64 is None:
             conv64 = r
         else:
@@ -283,13 +384,13 @@ def main():
         out.append(dict(form=name, E=r["E"], converged=r["converged"], outer=r["outer"],
                         inner_total=r["inner_total"], seconds=r["seconds"], ms_per_inner=r["ms_per_inner"],
                         history=r["history"]))
-    line = {"workload": args.workload, "rhf": {"E": E_hf, "iterations": it_hf, "commutator": com, "seconds": t_hf},
+    line = {"workload": args.workload, "inner_step": args.inner_step, "rhf": {"E": E_hf, "iterations": it_hf, "commutator": com, "seconds": t_hf},
             "runs": out}
     if args.restart and conv64 is not None:
         print("# exact restart", file=sys.stderr, flush=True)
         r = converge(eng0, conv64["C"], conv64["gamma"], conv64["diag"], etol=args.etol, gtol=args.gtol,
                      max_outer=args.outer, max_inner=args.inner, gapmin=args.gapmin, exact=True,
-                     time_limit=args.time_limit, log=log)
+                     time_limit=args.time_limit, log=log, inner=args.inner_step)
         line["restart_exact"] = dict(E=r["E"], converged=r["converged"], outer=r["outer"],
                                      inner_total=r["inner_total"], seconds=r["seconds"],
                                      ri_error=conv64["E"] - r["E"], history=r["history"])

@@ -71,3 +71,42 @@ def test_digit_plane_form_converges_to_the_same_energy(oracle_runs):
     assert abs(r["E"] - ro["E"]) <= PATH_TOL, (r["E"], ro["E"])
     Eo, _ = orbopt.energy_lambda(s, B, I.core_hamiltonian(s), I.nuclear_repulsion(s), r["C"], r["gamma"], sub, rank)
     assert abs(Eo - r["E"]) <= 1e-6
+
+
+def test_quasi_newton_inner_step_converges(oracle_runs):
+    """The quasi-Newton orbital step (solve.lbfgs_iterations: L-BFGS on the rotation
+    generator through donof_ri_apply_rotation) converges the same scheme in fewer inner
+    iterations, to a stationary point at least as low as the F^lambda run's, whose
+    energy the oracle confirms."""
+    from paper_2012_15662_gb300 import binding as bd, solve
+    w, B, sub, rank, ro, xo = oracle_runs
+    s = w.system
+    eng = bd.Engine(s, bd.DONOF_RI_FP64)
+    C0, eps0, E_hf, it, com = eng.rhf(max_iter=100, tol=1e-9)
+    r = solve.converge(eng, C0, standard_gamma(s.n_strong, s.n_weak_per), eps0, inner="lbfgs", max_inner=300)
+    eng.close()
+    assert r["converged"], r["history"][-3:]
+    assert r["inner_total"] < ro["inner_total"]
+    assert r["E"] <= ro["E"] + PATH_TOL
+    Eo, lam = orbopt.energy_lambda(s, B, I.core_hamiltonian(s), I.nuclear_repulsion(s), r["C"], r["gamma"], sub, rank)
+    assert abs(Eo - r["E"]) <= 1e-9 * max(1.0, abs(Eo))
+    assert np.abs(lam - lam.T).max() <= 1.01e-4
+
+
+def test_apply_rotation_matches_expm():
+    """donof_ri_apply_rotation against scipy's expm: C expm(kappa), C^T S C = I."""
+    from scipy.linalg import expm
+    from paper_2012_15662_gb300 import binding as bd
+    w = make_workload("c6h12")
+    s = w.system
+    rng = np.random.default_rng(11)
+    X = rng.standard_normal((s.nbf, s.nbf)) * 0.3
+    kappa = np.ascontiguousarray(X - X.T)
+    eng = bd.Engine(s, bd.DONOF_RI_FP64)
+    eng.transform(w.C, bd.DONOF_RI_HALF)          # the context's orbitals
+    Ccm = np.empty(s.nbf * s.nbf)
+    bd.donof_ri_apply_rotation(eng.ctx, kappa, Ccm)
+    eng.close()
+    C1 = Ccm.reshape(s.nbf, s.nbf).T
+    np.testing.assert_allclose(C1, w.C @ expm(kappa), atol=1e-10)
+    np.testing.assert_allclose(C1.T @ I.overlap(s) @ C1, np.eye(s.nbf), atol=1e-12)

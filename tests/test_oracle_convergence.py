@@ -57,3 +57,15 @@ def test_exact_restart_takes_at_most_two_outer_iterations(runs):
     E_start = pnof7.energy(n, Hd, ex["J"], ex["K"], A, Bc, I.nuclear_repulsion(s))
     assert x["E"] <= E_start + 1e-12
     assert 0.0 < r["E"] - x["E"] < 0.05
+
+
+def test_exact_rows_equal_the_conventional_algorithm(runs):
+    """orbopt.exact_rows (einsum route) against brute.conventional_jk (Table 1 with the
+    projectors P^q, a loop per orbital) on the exact four-index integrals."""
+    from oracle import brute
+    s, hf, r, x, eri, sub, rank = runs
+    m = s.n_omega
+    a = orbopt.exact_rows(eri, r["C"], m)
+    J, K, Jao, Kao = brute.conventional_jk(eri, r["C"], m)
+    for got, want in ((a["J"], J), (a["K"], K), (a["Jao"], Jao), (a["Kao"], Kao)):
+        np.testing.assert_allclose(got, want, atol=1e-12)

@@ -32,8 +32,9 @@ import numpy as np
 
 ANGSTROM_TO_BOHR = 1.0 / 0.529177210903
 
-# Nuclear charges of the elements used by the rings.
-_Z = {"C": 6.0, "H": 1.0, "X": 2.0}
+# Nuclear charges of the elements used by the rings ("Gh": a ghost centre, which
+# carries auxiliary functions only).
+_Z = {"C": 6.0, "H": 1.0, "X": 2.0, "Gh": 0.0}
 
 
 def even_tempered(alpha0: float, ratio: float, n: int) -> np.ndarray:
@@ -128,7 +129,31 @@ _TABLES = {
                            aux={"C": (0.3, 2.0, 49), "H": (0.3, 2.2, 28)}),
     "ring_c20": BasisTable(basis={"C": (0.12, 2.0, 16), "H": (0.12, 1.9, 10)},
                            aux={"C": (0.3, 2.0, 56), "H": (0.3, 2.2, 35)}),
+    # The small rings' basis with an auxiliary set that fits the basis products: an
+    # s-type function on an atom cannot represent the product of two functions on
+    # different atoms (a Gaussian centred between them), so besides the atoms'
+    # own functions (0.2 upward, ratio 2, covering the products of the basis's
+    # exponents) ghost centres at 1/4, 1/2 and 3/4 of the way between every two
+    # atoms closer than 5 bohr carry five functions each (0.4 upward, ratio 2).
+    "ring_fit": BasisTable(basis={"C": (0.12, 2.5, 12), "H": (0.12, 3.0, 6), "Gh": (1.0, 1.0, 0)},
+                           aux={"C": (0.2, 2.0, 16), "H": (0.2, 2.0, 12), "Gh": (0.4, 2.0, 5)}),
 }
+
+# Ghost centres of the "ring_fit" auxiliary set.
+_GHOST_CUTOFF_BOHR = 5.0
+_GHOST_FRACTIONS = (0.25, 0.5, 0.75)
+
+
+def _ghost_centres(xyz: np.ndarray, cutoff: float = _GHOST_CUTOFF_BOHR,
+                   fractions=_GHOST_FRACTIONS) -> np.ndarray:
+    """Points (1 - f) A + f B for every pair of atoms A, B closer than `cutoff`
+    (bohr) and every f in `fractions`."""
+    out = []
+    for i in range(len(xyz)):
+        for j in range(i + 1, len(xyz)):
+            if np.linalg.norm(xyz[i] - xyz[j]) < cutoff:
+                out.extend((1.0 - f) * xyz[i] + f * xyz[j] for f in fractions)
+    return np.asarray(out, dtype=np.float64).reshape(-1, 3)
 
 
 def _assemble(name: str, xyz: np.ndarray, elem: list[str], table: BasisTable,
@@ -164,21 +189,31 @@ def make_system(kind: str, n_c: int = 0, seed: int = 0, jitter: float = 0.02,
     auxiliary functions per atom, N_I = 4, N_g = 2.
     kind = "ring": CnH2n ring with n_c carbons, seeded jitter (A), N_I equal to
     half the electron count, N_g weak orbitals per strong one.
+    kind = "ring_fit": the same ring (n_c <= 12) with the small rings' basis and
+    an auxiliary set that includes ghost centres between the atoms (the
+    "ring_fit" table), for studies that need a small fitting error.
     """
     if kind == "square":
         xyz, elem = _square_geometry(1.5)
         return _assemble("square4", xyz, elem, _TABLES["square"], 4, 2)
-    if kind != "ring":
+    if kind not in ("ring", "ring_fit"):
         raise ValueError(f"unknown system kind {kind!r}")
     rng = np.random.default_rng(seed)
     xyz, elem = _ring_geometry(n_c, jitter, rng)
+    n_elec = 6 * n_c + 2 * n_c
+    if kind == "ring_fit":
+        if n_c > 12:
+            raise ValueError("the fitted-auxiliary rings use the small rings' basis (n_c <= 12)")
+        ghosts = _ghost_centres(xyz)
+        xyz = np.concatenate([xyz, ghosts])
+        elem = elem + ["Gh"] * len(ghosts)
+        return _assemble(f"c{n_c}h{2 * n_c}fit", xyz, elem, _TABLES["ring_fit"], n_elec // 2, n_weak_per)
     if n_c <= 12:
         table = _TABLES["ring_small"]
     elif n_c <= 16:
         table = _TABLES["ring_c16"]
     else:
         table = _TABLES["ring_c20"]
-    n_elec = 6 * n_c + 2 * n_c
     return _assemble(f"c{n_c}h{2 * n_c}", xyz, elem, table, n_elec // 2, n_weak_per)
 
 
@@ -242,6 +277,9 @@ WORKLOADS = {
     "c16h32": dict(kind="ring", n_c=16, seed=4),
     # C20H40 ring, nbf=720, naux=2520, N_Omega=400
     "c20h40": dict(kind="ring", n_c=20, seed=5),
+    # the C6H12 ring above with 180 ghost centres in its auxiliary set,
+    # nbf=144, naux=1140, N_Omega=120
+    "c6h12fit": dict(kind="ring_fit", n_c=6, seed=2),
 }
 
 

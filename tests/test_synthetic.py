@@ -73,3 +73,23 @@ def test_orthonormal_orbitals_is_the_inverse_square_root():
     np.testing.assert_allclose(X @ X @ S, np.eye(9), atol=1e-12)
     with pytest.raises(ValueError):
         orthonormal_orbitals(-S, np.eye(9))
+
+
+def test_ring_fit_ghost_centres():
+    """c6h12fit: the c6h12 ring plus ghost centres (no charge, no basis function,
+    five auxiliary functions each) at 1/4, 1/2, 3/4 between atoms closer than 5 bohr,
+    all distinct from each other and from the atoms."""
+    from synthetic.systems import make_system, workload_system
+    s = workload_system("c6h12fit")
+    r = workload_system("c6h12")
+    na = r.n_atoms
+    assert (s.nbf, s.naux, s.n_omega) == (144, 1140, 120)
+    np.testing.assert_array_equal(s.atom_xyz[:na], r.atom_xyz)
+    assert (s.atom_charge[na:] == 0.0).all() and s.n_electrons == r.n_electrons
+    assert s.bf_atom.max() < na
+    ghosts = np.arange(na, s.n_atoms)
+    assert (np.bincount(s.aux_atom, minlength=s.n_atoms)[ghosts] == 5).all()
+    d = np.linalg.norm(s.atom_xyz[:, None] - s.atom_xyz[None], axis=-1) + 1e9 * np.eye(s.n_atoms)
+    assert d.min() > 0.4
+    with pytest.raises(ValueError):
+        make_system("ring_fit", n_c=16)

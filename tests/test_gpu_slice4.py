@@ -198,3 +198,25 @@ def test_full_size_c20h40_against_oracle():
     Eo = pnof7.energy(n, Hd, Jo, Ko, A, Bc, I.nuclear_repulsion(s))
     assert abs(E - Eo) <= TOL_E, (E, Eo)
     assert np.abs(lam - lamo).max() <= 1e-6
+
+
+def test_ghost_centre_auxiliary_set():
+    """C6H12 with the ghost-centre auxiliary set (N_aux 1140, Coulomb metric condition
+    number ~9e11 against ~1e7 for the on-atom sets): SLICE4 and the FP64 form against
+    the oracle at the same tolerances."""
+    from paper_2012_15662_gb300 import binding as bd
+    w = make_workload("c6h12fit")
+    ref = _oracle(w)
+    for prec in (bd.DONOF_RI_SLICE4, bd.DONOF_RI_FP64):
+        eng = bd.Engine(w.system, prec)
+        eng.transform(w.C, bd.DONOF_RI_FULL)
+        J, K = eng.jk_mo()
+        Jao, Kao = eng.jk_ao()
+        E, lam = eng.energy_lagrangian(w.gamma)
+        eng.close()
+        err = dict(J=np.abs(J - ref["J"]).max(), K=np.abs(K - ref["K"]).max(),
+                   Jao=np.abs(Jao - ref["Jao"]).max(), Kao=np.abs(Kao - ref["Kao"]).max(),
+                   E=abs(E - ref["E"]), lam=np.abs(lam - ref["lam"]).max())
+        print(prec, err)
+        assert max(err["J"], err["K"], err["Jao"], err["Kao"]) <= TOL_JK, (prec, err)
+        assert err["E"] <= TOL_E and err["lam"] <= 1e-6, (prec, err)

@@ -472,6 +472,13 @@ class Engine:
         donof_ri_energy_lagrangian(self.ctx, np.ascontiguousarray(gamma, dtype=np.float64), E, lam_cm)
         return float(E[0]), lam_cm.reshape(self.nbf, self.nbf).T.copy()
 
+    def energy_lagrangian_contracted(self, gamma: np.ndarray):
+        """E and lambda with F^(p) C_p straight from the transforms (no J^(q), K^(q))."""
+        E = np.zeros(1)
+        lam_cm = np.empty(self.nbf * self.nbf)
+        donof_ri_energy_lagrangian_contracted(self.ctx, np.ascontiguousarray(gamma, dtype=np.float64), E, lam_cm)
+        return float(E[0]), lam_cm.reshape(self.nbf, self.nbf).T.copy()
+
     def fetch(self, what: int) -> np.ndarray:
         nb, nx, m = self.nbf, self.naux, self.n_omega
         shapes = {

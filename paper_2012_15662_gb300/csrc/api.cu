@@ -497,6 +497,13 @@ int donof_ri_autotune(donof_ri_ctx* ctx, int reps, int* report, int* tried) {
 
 int donof_ri_energy_lagrangian_contracted(donof_ri_ctx* ctx, const double* gamma, double* E, double* lambda) {
   if (!ctx || !gamma) return DONOF_RI_E_ARG;
+  if (ctx->precision == DONOF_RI_SLICE4) {
+    if (!ctx->have_half) return DONOF_RI_E_STATE;
+    int rc = gamma_input(ctx, gamma);
+    if (rc) return rc;
+    if ((rc = s4_energy_contracted(ctx))) return rc;
+    return energy_outputs(ctx, E, lambda);
+  }
   if (ctx->precision != DONOF_RI_FP64) return DONOF_RI_E_UNSUPPORTED;
   if (!ctx->have_full) return DONOF_RI_E_STATE;
   const size_t nb = ctx->nbf, nx = ctx->naux, m = ctx->n_omega;

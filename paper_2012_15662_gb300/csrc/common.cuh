@@ -202,6 +202,7 @@ void s4_free(donof_ri_ctx* ctx);
 int s4_transform(donof_ri_ctx* ctx, int mode);
 int s4_jk_ao(donof_ri_ctx* ctx);
 int s4_energy(donof_ri_ctx* ctx, int part);
+int s4_energy_contracted(donof_ri_ctx* ctx);
 int s4_fetch(donof_ri_ctx* ctx, int what, double* dst, size_t count);
 int s4_copy_ao(donof_ri_ctx* ctx, double* Jao, double* Kao, bool jao_dev, bool kao_dev);
 

@@ -50,8 +50,13 @@ namespace donof {
 // between it and the two-CTA S_HALF.
 // S_JKAO: J^(q) and K^(q) of one orbital iteration in one persistent launch (the
 // J^(q) tiles, then the K^(q) (tile, orbital) units).
+// S_CTR: the contracted Lagrangian's F^(p) C_p without J^(q), K^(q): one GEMM over
+// K = (q, P), sum_q sum_P X^P_qp b^P_{q mu}, as one unit per orbital q (rows p of the
+// X digits, columns mu of the b_half digits in the K^(q) layout, both over P) whose
+// chunks are converted to double-float and summed across the CTA's orbitals.
 enum S4Kind {
-  S_HALF = 0, S_FULLSQ = 1, S_JMO = 2, S_JAO = 3, S_KAO = 4, S_FOCK = 5, S_HALF1 = 6, S_JKAO = 7, S_NKINDS = 8
+  S_HALF = 0, S_FULLSQ = 1, S_JMO = 2, S_JAO = 3, S_KAO = 4, S_FOCK = 5, S_HALF1 = 6, S_JKAO = 7, S_CTR = 8,
+  S_NKINDS = 9
 };
 __host__ __device__ constexpr bool s4_half(int kind) { return kind == S_HALF || kind == S_HALF1; }
 
@@ -129,6 +134,7 @@ struct S4Params {
   const int* ea2;
   const int* eb2;
   int ntiles2, u_split;
+  double* bfull;    // FULLSQ: when set, b^P_qp is also stored, [P][q][p] (FP64)
 };
 
 // ---------------------------------------------------------------------------
@@ -301,7 +307,7 @@ __device__ __forceinline__ void s4_unit(const S4Params& p, int b, int& batch, in
   else if (KIND == S_FULLSQ) { batch = b; kb0 = 0; nkb = KBb; }
   else if (KIND == S_JMO) { batch = 0; kb0 = b * S4_CHUNK_KB; nkb = min(S4_CHUNK_KB, KBx - kb0); }
   else if (KIND == S_JAO || KIND == S_JKAO) { batch = 0; kb0 = 0; nkb = KBx; }
-  else if (KIND == S_KAO) { batch = b; kb0 = 0; nkb = KBx; }
+  else if (KIND == S_KAO || KIND == S_CTR) { batch = b; kb0 = 0; nkb = KBx; }
   else {
     constexpr int CKB = s4_chunk_kb(KIND);
     const int nc = (KBb + CKB - 1) / CKB;
@@ -358,7 +364,7 @@ __device__ __forceinline__ void s4_loads(const S4Params& p, uint8_t* st, uint64_
     } else if (KIND == S_JKAO) {  // K^(q) unit of the merged launch
       tma_load_4d(da, &p.a2, bar, k0, t, mt * S4_BM, batch);
       tma_load_4d(db, &p.b2, bar, k0, t, n0, batch);
-    } else {  // S_KAO
+    } else {  // S_KAO, S_CTR
       tma_load_4d(da, &p.a, bar, k0, t, mt * S4_BM, batch);
       tma_load_4d(db, &p.b, bar, k0, t, n0, batch);
     }
@@ -525,10 +531,10 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_ge
     const int q = warp & 3;     // TMEM lane quarter this warp may access
     const int wg = ew / 4;      // epilogue warpgroup: column blocks wg, wg + NWG, ...
     const int row = q * 32 + lane;
-    constexpr bool SUM_DF = (KIND == S_FULLSQ || KIND == S_FOCK);
-    // FOCK units are single chunks, and the half transform keeps its partial sums in its
-    // output: neither carries running sums
-    constexpr int NACC = (KIND == S_FOCK || s4_half(KIND)) ? 1 : BN / NWG;
+    constexpr bool SUM_DF = (KIND == S_FULLSQ || KIND == S_FOCK || KIND == S_CTR);
+    // FOCK units are single chunks, CTR converts every chunk on its own, and the half
+    // transform keeps its partial sums in its output: none carries int64 running sums
+    constexpr int NACC = (KIND == S_FOCK || KIND == S_CTR || s4_half(KIND)) ? 1 : BN / NWG;
     long long acc[NACC];
     float sh[SUM_DF ? BN / NWG : 1], sl[SUM_DF ? BN / NWG : 1];
 #pragma unroll
@@ -562,7 +568,7 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_ge
           const int i = lane + 32 * k, col = nt * BN + i;
           rb[k] = 0;
           if (i < BN) {
-            if (KIND == S_KAO || KIND == S_FOCK || (KIND == S_JKAO && kao))
+            if (KIND == S_KAO || KIND == S_FOCK || KIND == S_CTR || (KIND == S_JKAO && kao))
               rb[k] = col < p.nb ? eB[(size_t)batch * p.nb + col] : 0;
             else rb[k] = col < p.m ? eB[col] : 0;
           }
@@ -623,6 +629,11 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_ge
         mu = mt * S4_BM + row;
         rvalid = mu < p.nb;
         ea = rvalid ? eA[(size_t)batch * p.nb + mu] : 0;
+      } else if (KIND == S_CTR) {
+        // the row is orbital p of the X digits of orbital q = batch
+        mu = mt * S4_BM + row;
+        rvalid = mu < p.m;
+        ea = rvalid ? p.ea[(size_t)batch * p.m + mu] : 0;
       }
       // FOCK: the row is orbital p (C^T digits), the unit's weight W[batch][p] is per row
       float2 wrow = make_float2(0.f, 0.f);
@@ -713,9 +724,11 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_ge
           }
           // The value of every output of the block as a double-float pair (h, l).  A
           // single-chunk unit converts its five group sums directly (groups_to_df); a
-          // multi-chunk one keeps exact int64 running sums until its last chunk.
+          // multi-chunk one keeps exact int64 running sums until its last chunk.  CTR
+          // converts every chunk and adds it to the CTA's running double-float sums
+          // (the exponents are the same for the chunks of a unit, not across units).
           float hv[CW], lv[CW];
-          if (ONE) {
+          if (ONE || KIND == S_CTR) {
 #pragma unroll
             for (int j = 0; j < CW; ++j) {
               const uint32_t G[S4_NG] = {gr[0][j], gr[1][j], gr[2][j], gr[3][j], gr[4][j]};
@@ -749,6 +762,7 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_ge
                 const float ph = xh * xh;
                 const float pl = fmaf(xh, xh, -ph) + 2.f * xh * xl;
                 df_add(sh[SUM_DF ? cb * CW + j : 0], sl[SUM_DF ? cb * CW + j : 0], ph, pl);
+                if (p.bfull) p.bfull[((size_t)batch * p.m + mu) * p.m + nt * BN + i] = (double)xh + (double)xl;
               }
             }
           } else if (KIND == S_FOCK) {
@@ -762,6 +776,11 @@ __global__ void __launch_bounds__(S4Cfg<KIND>::THREADS, S4Cfg<KIND>::CTAS) s4_ge
                 const float pl = fmaf(xh, wv.x, -ph) + (xh * wv.y + xl * wv.x);
                 df_add(sh[SUM_DF ? cb * CW + j : 0], sl[SUM_DF ? cb * CW + j : 0], ph, pl);
               }
+            }
+          } else if (KIND == S_CTR) {
+#pragma unroll
+            for (int j = 0; j < CW; ++j) {
+              if (nt * BN + c * CW + j < p.nb) df_add(sh[SUM_DF ? cb * CW + j : 0], sl[SUM_DF ? cb * CW + j : 0], hv[j], lv[j]);
             }
           } else if (KIND == S_JAO || (KIND == S_JKAO && !kao)) {
 #pragma unroll
@@ -1070,6 +1089,72 @@ __global__ void __launch_bounds__(256) reduce_df_kernel(const float2* partial, i
     outdf[i] = make_float2(th, tl);
   } else {
     out[i] = (double)th + (double)tl;
+  }
+}
+
+// The contracted Lagrangian's first operand,
+//   X^P_qp = [q = p] w_pP - B_pq b^P_qp,  w_pP = sum_r A_pr b^P_rr,
+// as digit rows (q, p) over P with the row's exact exponent: X digits
+// [q][p][4][nxp], eX[q][p].  b^P_qp from bf [P][q][p] (FP64), w [p][P], B [p][q].
+// Block (32, 8) per orbital q and 32 consecutive p: one pass for the row maxima,
+// a second that rounds each value to its integer, turns a 32 x 32 (P, p) block
+// around in shared memory and writes each digit row's 32 consecutive P at once.
+__global__ void __launch_bounds__(256) ctr_digits_kernel(const double* __restrict__ bf, const double* __restrict__ Bc,
+                                                         const double* __restrict__ w, int m, int nx, int nxp,
+                                                         __nv_bfloat16* __restrict__ Xd, int* __restrict__ eX) {
+  pdl_entry();
+  __shared__ double red[8][32];
+  __shared__ int tile[32][33];
+  __shared__ int es[32];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int q = blockIdx.y, p0 = blockIdx.x * 32, p = p0 + tx;
+  const bool pv = p < m;
+  const double bqp = pv ? Bc[(size_t)p * m + q] : 0.0;
+  const bool diag = pv && p == q;
+  double mx = 0.0;
+  if (pv) {
+    for (int P = ty; P < nx; P += 8) {
+      double x = -bqp * bf[((size_t)P * m + q) * m + p];
+      if (diag) x += w[(size_t)p * nx + P];
+      mx = fmax(mx, fabs(x));
+    }
+  }
+  red[ty][tx] = mx;
+  __syncthreads();
+  if (ty == 0) {
+#pragma unroll
+    for (int y = 1; y < 8; ++y) mx = fmax(mx, red[y][tx]);
+    const int e = expo_of(mx);
+    es[tx] = e;
+    if (pv) eX[(size_t)q * m + p] = e;
+  }
+  __syncthreads();
+  const int e = es[tx];
+  for (int P0 = 0; P0 < nx; P0 += 32) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int P = P0 + ty + 8 * k;
+      int X = 0;
+      if (pv && P < nx) {
+        double x = -bqp * bf[((size_t)P * m + q) * m + p];
+        if (diag) x += w[(size_t)p * nx + P];
+        X = __double2int_rn(scale_pow2(x, 31 - e));
+      }
+      tile[ty + 8 * k][tx] = X;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int pr = ty + 8 * k, P = P0 + tx;
+      if (p0 + pr < m && P < nx) {
+        __nv_bfloat16 d[4];
+        digits_bf16(tile[tx][pr], d);
+        __nv_bfloat16* o = Xd + ((size_t)q * m + p0 + pr) * 4 * nxp + P;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) o[(size_t)t * nxp] = d[t];
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -1445,6 +1530,11 @@ struct donof::S4Buffers {
   float2* W;
   float2* HCt;  // (H C)^T [p][mu], double-float
   float2* Yt;   // Y^T [p][mu] = (F^(p) C_p)^T, double-float
+  // contracted Lagrangian (allocated on its first call)
+  double* bf;          // b^P_qp [P][q][p]
+  double* wP;          // w [p][P]
+  __nv_bfloat16* Xd;   // X digits [q][p][4][nxp]
+  int* eX;             // their row exponents [q][p]
   double* eterm;          // the energy's per-orbital terms
   unsigned int* ticket;   // energy_terms_kernel's completion counter (zero between launches)
   void* partial;
@@ -1658,6 +1748,7 @@ int s4_init(donof_ri_ctx* ctx) {
   s4_plan<S_KAO>(sb, 1, (int)kao_tiles.size(), m, S4Cfg<S_KAO>::CTAS * sms, S4Cfg<S_KAO>::CTAS * sms);
   s4_plan<S_FOCK>(sb, (m + S4_BM - 1) / S4_BM, (nb + bn - 1) / bn,
                   2 * m * ((KBb + s4_chunk_kb(S_FOCK) - 1) / s4_chunk_kb(S_FOCK)), sms);
+  s4_plan<S_CTR>(sb, (m + S4_BM - 1) / S4_BM, (nb + bn - 1) / bn, m, sms);
   for (int k = 0; k < S_NKINDS; ++k) sb->max_stages[k] = sb->plan[k].stages;
   sb->target[S_FULLSQ] = S4Cfg<S_FULLSQ>::CTAS * sms;
   sb->target[S_JMO] = S4Cfg<S_JMO>::CTAS * sms;
@@ -1666,6 +1757,8 @@ int s4_init(donof_ri_ctx* ctx) {
   size_t pbytes = 2 * (size_t)sb->plan[S_FULLSQ].nsplit * m * m * sizeof(float2);
   const size_t jbytes = 2 * (size_t)sb->plan[S_JMO].nsplit * m * m * sizeof(long long);
   size_t t = 2 * (size_t)sb->plan[S_FOCK].nsplit * nb * m * sizeof(float2);
+  if (t > pbytes) pbytes = t;
+  t = (size_t)sb->plan[S_CTR].nsplit * nb * m * sizeof(float2);
   if (t > pbytes) pbytes = t;
 
 #define ALLOC(ptr, bytes)                                             \
@@ -1897,7 +1990,7 @@ int s4_init(donof_ri_ctx* ctx) {
                            (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)                               \
     return DONOF_RI_E_CUDA;
   OPTIN(S_HALF, 0) OPTIN(S_HALF, 1) OPTIN(S_HALF1, 0) OPTIN(S_HALF1, 1) OPTIN(S_FULLSQ, 0) OPTIN(S_FULLSQ, 1) OPTIN(S_JMO, 0) OPTIN(S_JAO, 0) OPTIN(S_JAO, 1)
-  OPTIN(S_KAO, 0) OPTIN(S_KAO, 1) OPTIN(S_FOCK, 1) OPTIN(S_JKAO, 0) OPTIN(S_JKAO, 1)
+  OPTIN(S_KAO, 0) OPTIN(S_KAO, 1) OPTIN(S_FOCK, 1) OPTIN(S_JKAO, 0) OPTIN(S_JKAO, 1) OPTIN(S_CTR, 0)
 #undef OPTIN
   return DONOF_RI_OK;
 }
@@ -1908,7 +2001,8 @@ void s4_free(donof_ri_ctx* ctx) {
   void* bufs[] = {sb->mir_jao, sb->mir_kao, sb->jao_tmap_full, sb->jao_tmap, sb->kao_tmap, sb->X6,    sb->B1,   sb->B5,   sb->Ct,   sb->L3,   sb->L6, sb->Dp,  sb->JKp,  sb->eB1,   sb->eB5,
                   sb->eC,    sb->e3,   sb->e6,   sb->ed,   sb->eJK, sb->rmaxB, sb->maxB, sb->absC, sb->absCt,
                   sb->Ls,    sb->LsTdf, sb->Cin,   sb->Cp,   sb->Cinp,
-                  sb->Cdf,   sb->Hdf,   sb->Cdfp,  sb->eterm, sb->ticket, sb->dpart, sb->dmat, sb->JKhi, sb->JKlo, sb->W,  sb->HCt, sb->Yt,   sb->partial, sb->partial_j};
+                  sb->Cdf,   sb->Hdf,   sb->Cdfp,  sb->eterm, sb->ticket, sb->dpart, sb->dmat, sb->JKhi, sb->JKlo, sb->W,  sb->HCt, sb->Yt,   sb->partial, sb->partial_j,
+                  sb->bf,    sb->wP,    sb->Xd,    sb->eX};
   for (void* b : bufs)
     if (b) cudaFree(b);
   free(sb);
@@ -1919,7 +2013,9 @@ template <int KIND>
 static int launch_s4(donof_ri_ctx* ctx) {
   S4Buffers* sb = ctx->s4;
   if (sb->grid[KIND] <= 0) return DONOF_RI_OK;
-  ProfScope ps(ctx, KIND == S_JKAO ? DONOF_RI_GEMM_JAO : DONOF_RI_GEMM_HALF + KIND);
+  ProfScope ps(ctx, KIND == S_JKAO  ? DONOF_RI_GEMM_JAO
+                    : KIND == S_CTR ? DONOF_RI_GEMM_FOCK
+                                    : DONOF_RI_GEMM_HALF + KIND);
   // single-chunk epilogue where every unit's K fits one chunk (F^(p) C_p: always)
   const int kext = (KIND == S_JAO || KIND == S_KAO || KIND == S_JKAO) ? ctx->naux : ctx->nbf;
   const bool one =
@@ -2121,6 +2217,83 @@ int s4_energy(donof_ri_ctx* ctx, int part) {
              p.nsplit, m, nb, (double*)nullptr, sb->Yt, (const double*)ctx->d_n, (const float2*)sb->HCt);
   DONOF_LAUNCH_CHECK(ctx);
   // lambda[p][q] = Y^T_p . C_q for every q < nbf
+  launch_pdl(df_gemm_nt_kernel<double>, dim3((nb + DFG_TJ - 1) / DFG_TJ, (m + DFG_TI - 1) / DFG_TI), dim3(DFG_THREADS),
+             0, s, m, nb, nb,
+             (const float2*)sb->Yt, nb, (const float2*)sb->Cdf, nb, ctx->d_lambda, nb);
+  DONOF_LAUNCH_CHECK(ctx);
+  launch_pdl(energy_terms_kernel, dim3(m), dim3(32), 0, s, nb, m, (const float2*)sb->Cdf, (const float2*)sb->HCt,
+             (const double*)ctx->d_n, (const double*)ctx->d_lambda, (const double*)ctx->d_enuc, sb->eterm, sb->ticket,
+             ctx->d_E);
+  DONOF_LAUNCH_CHECK(ctx);
+  return DONOF_RI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Contracted Lagrangian on the digit path.  With w_pP = sum_q A_pq b^P_qq and
+// X^P_qp = [q = p] w_pP - B_pq b^P_qp,
+//   F^(p) C_p = n_p H C_p + sum_q sum_P X^P_qp b^P_{q .}
+// (J^(q) C_p = sum_P b^P_qq b^P_{p .}, K^(q) C_p = sum_P b^P_{q .} b^P_qp), one
+// digit-plane GEMM of N_b N_Omega^2 N_aux products (S_CTR) in place of J^(q),
+// K^(q) and the Fock sum.  b^P_qp comes from the full transform's GEMM run once more
+// with its store switched on, w from an FP64 GEMM, X's digits from
+// ctr_digits_kernel; Y, lambda and E then as in s4_energy.
+// ---------------------------------------------------------------------------
+static int s4_ctr_setup(donof_ri_ctx* ctx) {
+  S4Buffers* sb = ctx->s4;
+  const long long nb = ctx->nbf, nx = ctx->naux, m = ctx->n_omega, nxp = sb->nxp;
+  if (cudaMalloc((void**)&sb->bf, (size_t)(nx * m * m * 8)) != cudaSuccess ||
+      cudaMalloc((void**)&sb->wP, (size_t)(m * nx * 8)) != cudaSuccess ||
+      cudaMalloc((void**)&sb->Xd, (size_t)(m * m * 4 * nxp * 2)) != cudaSuccess ||
+      cudaMalloc((void**)&sb->eX, (size_t)(m * m * 4)) != cudaSuccess) {
+    cudaGetLastError();
+    return DONOF_RI_E_OOM;
+  }
+  // A = X digits [m][m][4][nxp] rows p (per q) over P; B = L6 [m][nb][4][nxp] rows mu (per q) over P
+  S4Params& p = sb->plan[S_CTR];
+  const int bn = S4Cfg<S_CTR>::BN;
+  long long dA[4] = {nx, 4, m, m}, sA[3] = {nxp, 4 * nxp, m * 4 * nxp};
+  int bA[4] = {S4_BK, 1, S4_BM, 1};
+  long long dB[4] = {nx, 4, nb, m}, sB[3] = {nxp, 4 * nxp, nb * 4 * nxp};
+  int bB[4] = {S4_BK, 1, bn, 1};
+  int rc;
+  if ((rc = s4_map(sb, &p.a, sb->Xd, 4, dA, sA, bA))) return rc;
+  if ((rc = s4_map(sb, &p.b, sb->L6, 4, dB, sB, bB))) return rc;
+  p.ea = sb->eX; p.eb = sb->e6;
+  p.prow = (int)m; p.pcol = (int)nb;
+  return DONOF_RI_OK;
+}
+
+int s4_energy_contracted(donof_ri_ctx* ctx) {
+  S4Buffers* sb = ctx->s4;
+  const int nb = ctx->nbf, nx = ctx->naux, m = ctx->n_omega;
+  cudaStream_t s = ctx->stream;
+  int rc;
+  if (!sb->Xd && (rc = s4_ctr_setup(ctx))) return rc;
+  // occupations, couplings A and B, (H' C')^T
+  if ((rc = s4_energy(ctx, ENERGY_PREP))) return rc;
+  ProfScope ps(ctx, DONOF_RI_ROW_ENERGY);
+  {
+    S4Params& pf = sb->plan[S_FULLSQ];
+    pf.bfull = sb->bf;
+    rc = launch_s4<S_FULLSQ>(ctx);
+    pf.bfull = nullptr;
+    if (rc) return rc;
+  }
+  Gemm64 g{};  // w[p][P] = sum_q A_pq d[q][P]
+  g.M = m; g.N = nx; g.K = m; g.batch = 1;
+  g.A = ctx->d_A; g.sAm = m; g.sAk = 1;
+  g.B = sb->dmat; g.sBk = nx; g.sBn = 1;
+  g.C = sb->wP; g.sCm = nx; g.sCn = 1;
+  g.alpha = 1.0; g.beta = 0.0;
+  if ((rc = launch_dgemm(ctx, g))) return rc;
+  launch_pdl(ctr_digits_kernel, dim3((m + 31) / 32, m), dim3(32, 8), 0, s, (const double*)sb->bf,
+             (const double*)ctx->d_Bc, (const double*)sb->wP, m, nx, sb->nxp, sb->Xd, sb->eX);
+  DONOF_LAUNCH_CHECK(ctx);
+  if ((rc = launch_s4<S_CTR>(ctx))) return rc;
+  const S4Params& p = sb->plan[S_CTR];
+  launch_pdl(reduce_df_kernel, dim3(ceil_div_u((long long)nb * m, 32)), dim3(32, 8), 0, s, (const float2*)p.partial,
+             p.nsplit, m, nb, (double*)nullptr, sb->Yt, (const double*)ctx->d_n, (const float2*)sb->HCt);
+  DONOF_LAUNCH_CHECK(ctx);
   launch_pdl(df_gemm_nt_kernel<double>, dim3((nb + DFG_TJ - 1) / DFG_TJ, (m + DFG_TI - 1) / DFG_TI), dim3(DFG_THREADS),
              0, s, m, nb, nb,
              (const float2*)sb->Yt, nb, (const float2*)sb->Cdf, nb, ctx->d_lambda, nb);

@@ -268,11 +268,21 @@ int donof_ri_flambda_step(donof_ri_ctx* ctx, double* diag, int first, double bou
  * with w_pP = sum_q A_pq b^P_qq (one batched DGEMM over P of N_b x N_Omega x
  * N_Omega, N_b N_aux N_Omega^2 multiply-adds in place of 2 N_b^2 N_aux N_Omega for
  * J^(q), K^(q) and the Fock sum).  lambda and E as in donof_ri_energy_lagrangian,
- * which gives the same values.  Needs the full transform b^P_qp: call after a
- * FULL donof_ri_transform (no donof_ri_jk_ao_batch needed).  FP64 contexts; its
- * scratch (N_aux N_Omega (1 + N_Omega + N_b) doubles) is allocated on first use.
- * Errors: E_ARG, E_OOM, E_STATE (no FULL transform since the orbitals changed),
- * E_UNSUPPORTED (precision other than DONOF_RI_FP64).
+ * which gives the same values (no donof_ri_jk_ao_batch needed).
+ * FP64 contexts: needs the full transform b^P_qp (call after a FULL
+ * donof_ri_transform); scratch of N_aux N_Omega (1 + N_Omega + N_b) doubles,
+ * allocated on first use.
+ * DONOF_RI_SLICE4 contexts: needs a HALF or FULL transform; the call runs the full
+ * transform's digit-plane GEMM once more with b^P_qp stored (FP64), forms
+ * X^P_qp = [q = p] w_pP - B_pq b^P_qp as digit rows (q, p) over P, and contracts
+ * sum_q sum_P X^P_qp b^P_{q .} in one digit-plane GEMM over K = (q, P) (exact
+ * sums per K chunk, double-float across chunks and orbitals); scratch of
+ * N_aux N_Omega (N_Omega + 1) doubles, 8 N_Omega^2 N_aux bytes of digits and
+ * N_Omega^2 exponents, allocated on first use.  lambda and E within the digit
+ * path's tolerances of the per-orbital form.
+ * Errors: E_ARG, E_OOM, E_STATE (no FULL transform (FP64) or no transform
+ * (SLICE4) since the orbitals changed), E_UNSUPPORTED (DONOF_RI_TF32X3),
+ * E_TIMEOUT (SLICE4: a bounded device wait ran out).
  */
 int donof_ri_energy_lagrangian_contracted(donof_ri_ctx* ctx, const double* gamma, double* E, double* lambda);
 

@@ -2241,25 +2241,42 @@ int s4_energy(donof_ri_ctx* ctx, int part) {
 static int s4_ctr_setup(donof_ri_ctx* ctx) {
   S4Buffers* sb = ctx->s4;
   const long long nb = ctx->nbf, nx = ctx->naux, m = ctx->n_omega, nxp = sb->nxp;
-  if (cudaMalloc((void**)&sb->bf, (size_t)(nx * m * m * 8)) != cudaSuccess ||
-      cudaMalloc((void**)&sb->wP, (size_t)(m * nx * 8)) != cudaSuccess ||
-      cudaMalloc((void**)&sb->Xd, (size_t)(m * m * 4 * nxp * 2)) != cudaSuccess ||
-      cudaMalloc((void**)&sb->eX, (size_t)(m * m * 4)) != cudaSuccess) {
+  // every buffer and both tensor maps first, then the context's pointers: a failed
+  // set-up leaves nothing behind and the next call starts again
+  double *bf = nullptr, *wP = nullptr;
+  __nv_bfloat16* Xd = nullptr;
+  int* eX = nullptr;
+  auto release = [&]() {
+    cudaFree(bf);
+    cudaFree(wP);
+    cudaFree(Xd);
+    cudaFree(eX);
+  };
+  if (cudaMalloc((void**)&bf, (size_t)(nx * m * m * 8)) != cudaSuccess ||
+      cudaMalloc((void**)&wP, (size_t)(m * nx * 8)) != cudaSuccess ||
+      cudaMalloc((void**)&Xd, (size_t)(m * m * 4 * nxp * 2)) != cudaSuccess ||
+      cudaMalloc((void**)&eX, (size_t)(m * m * 4)) != cudaSuccess) {
     cudaGetLastError();
+    release();
     return DONOF_RI_E_OOM;
   }
   // A = X digits [m][m][4][nxp] rows p (per q) over P; B = L6 [m][nb][4][nxp] rows mu (per q) over P
-  S4Params& p = sb->plan[S_CTR];
   const int bn = S4Cfg<S_CTR>::BN;
   long long dA[4] = {nx, 4, m, m}, sA[3] = {nxp, 4 * nxp, m * 4 * nxp};
   int bA[4] = {S4_BK, 1, S4_BM, 1};
   long long dB[4] = {nx, 4, nb, m}, sB[3] = {nxp, 4 * nxp, nb * 4 * nxp};
   int bB[4] = {S4_BK, 1, bn, 1};
+  CUtensorMap ma, mb;
   int rc;
-  if ((rc = s4_map(sb, &p.a, sb->Xd, 4, dA, sA, bA))) return rc;
-  if ((rc = s4_map(sb, &p.b, sb->L6, 4, dB, sB, bB))) return rc;
-  p.ea = sb->eX; p.eb = sb->e6;
+  if ((rc = s4_map(sb, &ma, Xd, 4, dA, sA, bA)) || (rc = s4_map(sb, &mb, sb->L6, 4, dB, sB, bB))) {
+    release();
+    return rc;
+  }
+  S4Params& p = sb->plan[S_CTR];
+  p.a = ma; p.b = mb;
+  p.ea = eX; p.eb = sb->e6;
   p.prow = (int)m; p.pcol = (int)nb;
+  sb->bf = bf; sb->wP = wP; sb->Xd = Xd; sb->eX = eX;
   return DONOF_RI_OK;
 }
 
@@ -2466,7 +2483,6 @@ int s4_set_schedule(donof_ri_ctx* ctx, int kind, int stages, int option) {
 static int s4_tune_jk_merge(donof_ri_ctx* ctx, int reps, cudaEvent_t a, cudaEvent_t b, void* flush, size_t fbytes,
                             int* tried) {
   S4Buffers* sb = ctx->s4;
-  const int nb = ctx->nbf, m = ctx->n_omega;
   float t[2] = {0.f, 0.f};
   int rc;
   for (int merged = 0; merged < 2; ++merged) {

@@ -343,7 +343,11 @@ def main():
     """The paper's scheme to convergence from the RI-HF orbitals on one workload, with the
     FP64 and SLICE4 engines (and the learned occupation guess when --learned > 0):
     outer / inner iterations, energies, ms per inner iteration; with --restart, the
-    converged FP64 RI run restarted with exact four-centre integrals (nbf <= 256)."""
+    converged FP64 RI run restarted with exact four-centre integrals (nbf <= 256).
+    --checkpoint PATH writes the converged FP64 RI state (and, after --restart, the
+    exact one to PATH_exact) as PATH.json + PATH.bin; --resume PATH starts from such a
+    state instead of the RI-HF guess (with --forms "" and --restart: the exact restart
+    straight from the file)."""
     import argparse
     import json
     from synthetic import standard_gamma
@@ -359,18 +363,29 @@ def main():
     ap.add_argument("--learned", type=int, default=0, help="train the warm-start network on this many rings first")
     ap.add_argument("--restart", action="store_true", help="restart the converged FP64 run with exact integrals")
     ap.add_argument("--time-limit", type=float, default=None, help="seconds per converge() run")
+    ap.add_argument("--checkpoint", default=None, help="write the converged FP64 states to PATH.json / PATH.bin")
+    ap.add_argument("--resume", default=None, help="start from a state written by --checkpoint")
     args = ap.parse_args()
     import sys
 
     def log(rec):
         print(json.dumps(rec), file=sys.stderr, flush=True)
+    from .checkpoint import load_state, save_state
     eng0, w = bd.engine_and_workload(args.workload, bd.DONOF_RI_FP64)
-    t0 = time.perf_counter()
-    C0, eps0, E_hf, it_hf, com = eng0.rhf(max_iter=200, tol=1e-8)
-    t_hf = time.perf_counter() - t0
     s = w.system
-    g0 = standard_gamma(s.n_strong, s.n_weak_per)
-    runs = [(f, {"fp64": bd.DONOF_RI_FP64, "slice4": bd.DONOF_RI_SLICE4}[f], None) for f in args.forms.split(",")]
+    state = None
+    if args.resume:
+        state = load_state(args.resume, workload=args.workload, nbf=s.nbf)
+        C0, eps0, g0 = state["C"], state["diag"], state["gamma"]
+        start_rec = {"resumed_from": args.resume, "E": state["E"], "outer": state["outer"], "form": state["form"]}
+    else:
+        t0 = time.perf_counter()
+        C0, eps0, E_hf, it_hf, com = eng0.rhf(max_iter=200, tol=1e-8)
+        t_hf = time.perf_counter() - t0
+        g0 = standard_gamma(s.n_strong, s.n_weak_per)
+        start_rec = {"E": E_hf, "iterations": it_hf, "commutator": com, "seconds": t_hf}
+    runs = [(f, {"fp64": bd.DONOF_RI_FP64, "slice4": bd.DONOF_RI_SLICE4}[f], None)
+            for f in args.forms.split(",") if f]
     if args.learned:
         from . import warmstart
         X, Y = warmstart.training_set(args.learned, orbitals="rhf")
@@ -394,8 +409,13 @@ def main():
         out.append(dict(form=name, E=r["E"], converged=r["converged"], outer=r["outer"],
                         inner_total=r["inner_total"], seconds=r["seconds"], ms_per_inner=r["ms_per_inner"],
                         history=r["history"]))
-    line = {"workload": args.workload, "inner_step": args.inner_step, "rhf": {"E": E_hf, "iterations": it_hf, "commutator": com, "seconds": t_hf},
-            "runs": out}
+    line = {"workload": args.workload, "inner_step": args.inner_step,
+            ("start" if state is not None else "rhf"): start_rec, "runs": out}
+    if args.checkpoint and conv64 is not None:
+        save_state(args.checkpoint, args.workload, conv64["C"], conv64["gamma"], conv64["diag"], conv64["E"],
+                   conv64["outer"], conv64["converged"], "fp64")
+    if conv64 is None and state is not None:
+        conv64 = dict(C=C0, gamma=g0, diag=eps0, E=state["E"])  # the restart starts from the file
     if args.restart and conv64 is not None:
         print("# exact restart", file=sys.stderr, flush=True)
         r = converge(eng0, conv64["C"], conv64["gamma"], conv64["diag"], etol=args.etol, gtol=args.gtol,
@@ -404,6 +424,9 @@ def main():
         line["restart_exact"] = dict(E=r["E"], converged=r["converged"], outer=r["outer"],
                                      inner_total=r["inner_total"], seconds=r["seconds"],
                                      ri_error=conv64["E"] - r["E"], history=r["history"])
+        if args.checkpoint:
+            save_state(args.checkpoint + "_exact", args.workload, r["C"], r["gamma"], r["diag"], r["E"], r["outer"],
+                       r["converged"], "fp64-exact")
     eng0.close()
     print(json.dumps(line))
 
